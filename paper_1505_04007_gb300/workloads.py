@@ -1,0 +1,233 @@
+"""Seeded synthetic inputs for the PIC/FDTD-Drude time step.
+
+This module builds the inputs that both the CUDA library and the FP64 CPU
+oracle consume: grid sizes, time step, the per-cell material map with its
+Drude table, the electron bunch (positions and momenta), the probe points and
+the DFT frequency grid.  It holds none of the method's arithmetic (no field
+update, push, deposit or transform); it only draws and lays out inputs.
+
+The workloads stand in for the paper's setup (Sec. III: an electron bunch
+moving parallel to a silver film, Drude parameters per cell, absorbing
+boundaries, an E-field probe above the film whose spectrum shows the surface
+plasmon modes).  The paper gives no grid, time step or particle count, so the
+sizes below are the three single-instance workloads the project benchmarks:
+
+* ``c1`` 128x32x48 cells, dx=2 nm, 1000 steps, 20 nm film, 4096 electrons
+  at 30 keV, one probe (FP64 parity size).
+* ``c2`` 384x128x128 cells, dx=2 nm, 8000 steps, 40 nm film, 1e5 electrons
+  at 50 keV, a line of 64 probes (paper-scale run, the timed workload).
+* ``c3`` 768x256x256 cells, dx=1 nm, 12000 steps, 10 nm film, 1e6 electrons
+  at 30 keV, one probe (streaming-limit size).
+
+Positions come from ``numpy.random.default_rng(seed)`` (PCG64) with a fixed
+rejection order, so every consumer sees identical arrays.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# CODATA 2018 constants, passed verbatim to both implementations.
+C0 = 299792458.0
+EPS0 = 8.8541878128e-12
+MU0 = 1.25663706212e-6
+QE = 1.602176634e-19
+ME = 9.1093837015e-31
+MEC2_KEV = 510.99895
+
+# Boundary codes per face (x-lo, x-hi, y-lo, y-hi, z-lo, z-hi).
+BC_CPML, BC_PEC, BC_PERIODIC = 0, 1, 2
+
+# Silver Drude parameters used by the workloads (rad/s, 1/s).
+AG_WP = 1.37e16
+AG_GAMMA = 3.2e13
+
+# The particle margin: non-periodic axes keep electrons this many cells away
+# from the outer faces (the freeze rule uses the same number).
+MARGIN_CELLS = 2
+
+
+@dataclasses.dataclass
+class Workload:
+    """Everything one simulation instance needs, in SI units.
+
+    ``material`` is uint8 [nz][ny][nx] (x fastest); ``table`` is float64
+    [n_materials][3] holding (wp [rad/s], gamma [1/s], eps_inf) per id.
+    ``xyz`` and ``u`` are float64 [n][3] (metres and gamma*v in m/s).
+    """
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    dx: float
+    dy: float
+    dz: float
+    dt: float
+    nsteps: int
+    bc: tuple = (BC_CPML,) * 6
+    cpml_cells: int = 8
+    cpml_order: float = 3.0
+    cpml_sigma_fac: float = 0.8
+    cpml_kappa_max: float = 1.0
+    cpml_alpha_max: float = 0.0
+    material: np.ndarray = None
+    table: np.ndarray = None
+    xyz: np.ndarray = None
+    u: np.ndarray = None
+    q_macro: float = 0.0
+    m_macro: float = 0.0
+    probes: np.ndarray = None
+    comp_mask: int = 0b111
+    freqs: np.ndarray = None
+    info: dict = dataclasses.field(default_factory=dict)
+
+    @property
+    def ncells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def nparticles(self) -> int:
+        return 0 if self.xyz is None else int(self.xyz.shape[0])
+
+
+def yee_dt(dx: float, dy: float, dz: float, courant: float = 0.5) -> float:
+    """dt = courant * dx / (c*sqrt(3)) for a cubic grid (general form
+    courant / (c*sqrt(1/dx^2+1/dy^2+1/dz^2)))."""
+    return courant / (C0 * math.sqrt(1.0 / dx**2 + 1.0 / dy**2 + 1.0 / dz**2))
+
+
+def electron_momentum(kinetic_kev: float) -> float:
+    """gamma*v [m/s] of an electron of the given kinetic energy."""
+    g = 1.0 + kinetic_kev / MEC2_KEV
+    beta = math.sqrt(1.0 - 1.0 / (g * g))
+    return g * beta * C0
+
+
+def slab_material(nx: int, ny: int, nz: int, k0: int, k1: int) -> np.ndarray:
+    """uint8 map with id 1 in cell planes k0..k1-1 (a film spanning x and y)."""
+    m = np.zeros((nz, ny, nx), dtype=np.uint8)
+    m[k0:k1] = 1
+    return m
+
+
+def drude_table(wp: float = AG_WP, gamma: float = AG_GAMMA, eps_inf: float = 1.0) -> np.ndarray:
+    return np.array([[0.0, 0.0, 1.0], [wp, gamma, eps_inf]], dtype=np.float64)
+
+
+def allowed(w: Workload, pts: np.ndarray) -> np.ndarray:
+    """Mask of positions an electron may occupy: inside the margin on every
+    non-periodic axis and not in a cell whose material has wp > 0."""
+    n = (w.nx, w.ny, w.nz)
+    d = (w.dx, w.dy, w.dz)
+    ok = np.ones(pts.shape[0], dtype=bool)
+    cells = []
+    for a in range(3):
+        xi = pts[:, a] / d[a]
+        periodic = w.bc[2 * a] == BC_PERIODIC
+        if periodic:
+            xi = np.mod(xi, n[a])
+        else:
+            ok &= (xi >= MARGIN_CELLS) & (xi < n[a] - MARGIN_CELLS)
+        cells.append(np.clip(np.floor(xi).astype(np.int64), 0, n[a] - 1))
+    metal = w.table[w.material[cells[2], cells[1], cells[0]], 0] > 0.0
+    return ok & ~metal
+
+
+def gaussian_bunch(w: Workload, n: int, centre, sigma, seed: int = 1505) -> np.ndarray:
+    """n positions drawn from an isotropic Gaussian, rejected points redrawn
+    in batches (fixed order: draw, keep allowed, repeat) until n are kept."""
+    rng = np.random.default_rng(seed)
+    centre = np.asarray(centre, dtype=np.float64)
+    out = np.empty((0, 3))
+    drawn = 0
+    while out.shape[0] < n:
+        need = n - out.shape[0]
+        pts = centre + sigma * rng.standard_normal((need, 3))
+        drawn += need
+        out = np.concatenate([out, pts[allowed(w, pts)]], axis=0)
+    w.info["bunch_drawn"] = drawn
+    w.info["bunch_rejected_fraction"] = 1.0 - n / drawn
+    return out[:n]
+
+
+def freq_grid(f0: float = 0.5e15, f1: float = 2.5e15, df: float = 1.0e12) -> np.ndarray:
+    nf = int(round((f1 - f0) / df)) + 1
+    return f0 + df * np.arange(nf, dtype=np.float64)
+
+
+def _bunch_workload(name, nx, ny, nz, dx, nsteps, film_k0, film_k1, npart, charge, kev,
+                    centre, sigma, probes, seed=1505, nfreq_step=1.0e12):
+    w = Workload(name=name, nx=nx, ny=ny, nz=nz, dx=dx, dy=dx, dz=dx,
+                 dt=yee_dt(dx, dx, dx), nsteps=nsteps)
+    w.cpml_alpha_max = 0.05 * EPS0 * AG_WP
+    w.material = slab_material(nx, ny, nz, film_k0, film_k1)
+    w.table = drude_table()
+    w.q_macro = -charge / npart
+    w.m_macro = ME * (charge / npart) / QE
+    if npart:
+        w.xyz = gaussian_bunch(w, npart, centre, sigma, seed=seed)
+        w.u = np.zeros_like(w.xyz)
+        w.u[:, 0] = electron_momentum(kev)
+    w.probes = np.asarray(probes, dtype=np.float64).reshape(-1, 3)
+    w.freqs = freq_grid(df=nfreq_step)
+    w.info.update(film_cells=(film_k0, film_k1), kev=kev, charge=charge)
+    return w
+
+
+def c1(seed: int = 1505, nsteps: int = 1000) -> Workload:
+    """128x32x48, dx=2 nm, 20 nm film at cell planes 8..17, 4096 electrons,
+    sigma 5 nm, 1 fC, 30 keV along +x, centred 10 nm above the film top at
+    x=20 nm; one probe 5 nm above the top, 3/4 of the way along the interior."""
+    dx = 2e-9
+    nx, ny, nz = 128, 32, 48
+    top = 18 * dx
+    L = 8
+    probe = [(L + 0.75 * (nx - 2 * L)) * dx, 0.5 * ny * dx, top + 5e-9]
+    return _bunch_workload("c1", nx, ny, nz, dx, nsteps, 8, 18, 4096, 1e-15, 30.0,
+                           (20e-9, 0.5 * ny * dx, top + 10e-9), 5e-9, [probe], seed)
+
+
+def c2(seed: int = 1505, nsteps: int = 8000, nparticles: int = 100000) -> Workload:
+    """384x128x128, dx=2 nm, 40 nm film at cell planes 8..27, 1e5 electrons,
+    sigma 8 nm, 1 fC, 50 keV, 15 nm above the top, x centre 44 nm; a line of
+    64 probes 5 nm above the top along x."""
+    dx = 2e-9
+    nx, ny, nz = 384, 128, 128
+    top = 28 * dx
+    L = 8
+    lo, length = L * dx, (nx - 2 * L) * dx
+    probes = [[lo + (p + 0.5) * length / 64, 0.5 * ny * dx, top + 5e-9] for p in range(64)]
+    return _bunch_workload("c2", nx, ny, nz, dx, nsteps, 8, 28, nparticles, 1e-15, 50.0,
+                           (44e-9, 0.5 * ny * dx, top + 15e-9), 8e-9, probes, seed)
+
+
+def c3(seed: int = 1505, nsteps: int = 12000, nparticles: int = 1000000) -> Workload:
+    """768x256x256, dx=1 nm, 10 nm film at cell planes 8..17, 1e6 electrons,
+    sigma 5 nm, 2 fC, 30 keV, 5 nm above the top, x centre 25 nm; one probe."""
+    dx = 1e-9
+    nx, ny, nz = 768, 256, 256
+    top = 18 * dx
+    L = 8
+    probe = [(L + 0.75 * (nx - 2 * L)) * dx, 0.5 * ny * dx, top + 5e-9]
+    return _bunch_workload("c3", nx, ny, nz, dx, nsteps, 8, 18, nparticles, 2e-15, 30.0,
+                           (25e-9, 0.5 * ny * dx, top + 5e-9), 5e-9, [probe], seed)
+
+
+def scaled(w: Workload, nx: int, ny: int, nz: int, nparticles: int, nsteps: int,
+           seed: int = 1505) -> Workload:
+    """A smaller instance with the same film planes, bunch recipe and probe
+    rule as ``w`` (used for parity cases the oracle finishes in seconds)."""
+    k0, k1 = w.info["film_cells"]
+    dx = w.dx
+    top = k1 * dx
+    L = w.cpml_cells
+    gap = (w.info.get("gap", None) or (10e-9 if w.name == "c1" else 5e-9))
+    probe = [(L + 0.75 * (nx - 2 * L)) * dx, 0.5 * ny * dx, top + 5e-9]
+    return _bunch_workload(w.name + "_scaled", nx, ny, nz, dx, nsteps, k0, k1, nparticles,
+                           w.info["charge"], w.info["kev"],
+                           ((L + 4) * dx, 0.5 * ny * dx, top + gap), 5e-9, [probe], seed)
+
+
+WORKLOADS = {"c1": c1, "c2": c2, "c3": c3}

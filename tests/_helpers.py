@@ -1,0 +1,115 @@
+"""Small synthetic cases and textbook diagnostics shared by the tests.
+
+The diagnostics here are written from their definitions (cloud-in-cell charge
+at grid nodes, the node divergence of edge fields, the discrete field energy)
+and are independent of both the oracle and the CUDA library.
+"""
+import numpy as np
+
+from paper_1505_04007_gb300 import workloads as W
+
+
+def box_workload(nx, ny, nz, dx=2e-9, bc=(W.BC_PEC,) * 6, material=None, table=None,
+                 courant=0.5, name="box", dy=None, dz=None):
+    dy = dx if dy is None else dy
+    dz = dx if dz is None else dz
+    w = W.Workload(name=name, nx=nx, ny=ny, nz=nz, dx=dx, dy=dy, dz=dz,
+                   dt=W.yee_dt(dx, dy, dz, courant), nsteps=0, bc=tuple(bc))
+    w.material = np.zeros((nz, ny, nx), np.uint8) if material is None else material.astype(np.uint8)
+    w.table = W.drude_table() if table is None else np.asarray(table, np.float64)
+    w.cpml_alpha_max = 0.05 * W.EPS0 * W.AG_WP
+    return w
+
+
+def periodic_axes(w):
+    return [w.bc[2 * a] == W.BC_PERIODIC for a in range(3)]
+
+
+def cic_charge(w, xyz, q):
+    """Charge density at nodes [nz][ny][nx] from linear node shapes."""
+    rho = np.zeros((w.nz, w.ny, w.nx))
+    d = np.array([w.dx, w.dy, w.dz])
+    n = np.array([w.nx, w.ny, w.nz])
+    per = periodic_axes(w)
+    V = w.dx * w.dy * w.dz
+    for p in range(xyz.shape[0]):
+        xi = xyz[p] / d
+        b = np.floor(xi).astype(int)
+        f = xi - b
+        for dk in (0, 1):
+            for dj in (0, 1):
+                for di in (0, 1):
+                    idx = [b[0] + di, b[1] + dj, b[2] + dk]
+                    ok = True
+                    for a in range(3):
+                        if per[a]:
+                            idx[a] %= n[a]
+                        elif not (0 <= idx[a] < n[a]):
+                            ok = False
+                    if not ok:
+                        continue
+                    wgt = (f[0] if di else 1 - f[0]) * (f[1] if dj else 1 - f[1]) * (f[2] if dk else 1 - f[2])
+                    rho[idx[2], idx[1], idx[0]] += q * wgt / V
+    return rho
+
+
+def node_divergence(w, fx, fy, fz):
+    """div at node (i,j,k) of edge fields: (Fx(i+1/2)-Fx(i-1/2))/dx + ...;
+    arrays [nz][ny][nx], x edge i+1/2 stored at index i.  On non-periodic
+    axes the value below index 0 is taken as zero (result at index 0 is only
+    meaningful on periodic axes)."""
+    per = periodic_axes(w)
+
+    def back(a, axis):
+        if per[axis]:
+            return np.roll(a, 1, axis=2 - axis)
+        b = np.zeros_like(a)
+        sl = [slice(None)] * 3
+        sl2 = [slice(None)] * 3
+        sl[2 - axis] = slice(1, None)
+        sl2[2 - axis] = slice(0, -1)
+        b[tuple(sl)] = a[tuple(sl2)]
+        return b
+
+    return (fx - back(fx, 0)) / w.dx + (fy - back(fy, 1)) / w.dy + (fz - back(fz, 2)) / w.dz
+
+
+def interior_node_mask(w, margin=1):
+    """Nodes at least ``margin`` cells (plus the CPML slab) away from every
+    non-periodic face."""
+    m = np.ones((w.nz, w.ny, w.nx), bool)
+    per = periodic_axes(w)
+    n = (w.nx, w.ny, w.nz)
+    for a in range(3):
+        if per[a]:
+            continue
+        lo = margin + (w.cpml_cells if W.BC_CPML in (w.bc[2 * a], w.bc[2 * a + 1]) else 0)
+        idx = np.arange(n[a])
+        keep = (idx >= lo) & (idx < n[a] - lo)
+        shape = [1, 1, 1]
+        shape[2 - a] = n[a]
+        m &= keep.reshape(shape)
+    return m
+
+
+def edge_wp2(w, comp, values=None):
+    """Mean of wp^2 (or of a per-material ``values`` table) over the four
+    cells sharing each edge of component comp (clamped at non-periodic faces,
+    wrapped on periodic ones)."""
+    wp2 = ((w.table[:, 0] ** 2) if values is None else np.asarray(values))[w.material]
+    per = periodic_axes(w)
+    a1, a2 = (comp + 1) % 3, (comp + 2) % 3
+
+    def shift_back(a, axis):
+        if per[axis]:
+            return np.roll(a, 1, axis=2 - axis)
+        out = a.copy()
+        sl = [slice(None)] * 3
+        sl2 = [slice(None)] * 3
+        sl[2 - axis] = slice(1, None)
+        sl2[2 - axis] = slice(0, -1)
+        out[tuple(sl)] = a[tuple(sl2)]
+        return out
+
+    s1 = shift_back(wp2, a1)
+    return 0.25 * (wp2 + s1 + shift_back(wp2, a2) + shift_back(s1, a2))
