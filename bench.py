@@ -1,0 +1,315 @@
+"""Benchmark of the PIC/FDTD-Drude time step (one JSON line on rank 0).
+
+A "step" is one full time step of the hot path: H update (+CPML), electron
+push + Esirkepov deposit, Drude-ADE + Ampere E update (+CPML), probe sampling
+and (every 64 steps) the probe-DFT flush.  Workload (default): 384x128x128
+cells, dx = 2 nm, 40 nm silver film, 1e5 electrons at 50 keV, 64 probes x
+2001 frequencies, FP32 state with FP64 DFT accumulators.
+
+Metric: cell-updates per second (Gcell-upd/s) over the whole job; with
+--gpus N (torchrun) every rank steps its own independent instance (weak
+scaling, no data-path collective).
+
+--impl reference times the FP64 CPU oracle (the deliberately plain reference
+implementation) on the host cores over a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+FALLBACK_HBM_GBS = 6800.0
+KERNELS_PER_STEP = 4          # update_H, push_deposit, update_E, step_tail
+DFT_KERNELS_PER_FLUSH = 2     # phasor table, accumulate
+DFT_BLOCK = 64
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4096)
+    ap.add_argument("--warmup", type=int, default=128)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["c1", "c2", "c3"], default="c2")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=20.0,
+                    help="target CPU seconds of the oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    v = d[k]
+                    if isinstance(v, dict):
+                        v = v.get("value", v.get("gbs"))
+                    return float(v), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def algorithmic_bytes(w, real_bytes):
+    """Bytes each field kernel must move per launch at minimum (one read of
+    every input it needs, one write of every output), counted from the
+    workload geometry.  See the design doc for the per-cell figures."""
+    N = w.ncells
+    L = w.cpml_cells
+    n = (w.nx, w.ny, w.nz)
+    # cells inside k CPML slabs (psi read+write of 2 components per slab axis)
+    inside = []
+    for a in range(3):
+        has = 0 in (w.bc[2 * a], w.bc[2 * a + 1])
+        m = np.zeros(n[a], bool)
+        if has:
+            m[:L] = True
+            m[n[a] - L:] = True
+        inside.append(m)
+    slab_cells = 0
+    for a in range(3):
+        other = N // n[a]
+        slab_cells += int(inside[a].sum()) * other
+    psi = slab_cells * 2 * 2 * real_bytes  # 2 components, read + write
+    # metal edges (any of the four cells around the edge has wp > 0): J_p read + write
+    wp = w.table[:, 0][w.material] > 0
+    metal_edges = 0
+    for c in range(3):
+        m = wp.copy()
+        for ax in ((c + 1) % 3, (c + 2) % 3):
+            m = m | np.roll(m, 1, axis=2 - ax)
+        metal_edges += int(m.sum())
+    h_bytes = N * 9 * real_bytes + psi
+    e_bytes = N * (9 * real_bytes + 3) + psi + metal_edges * 2 * real_bytes
+    return {"update_H": h_bytes, "update_E": e_bytes, "metal_edges": metal_edges, "slab_cells": slab_cells}
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        self.out = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r.split(",") for r in out.strip().splitlines() if r.strip()]
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        import hashlib
+        src = os.path.join(ROOT, "paper_1505_04007_gb300", "csrc", d["source"])
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        k = d["kernels"].get(kernel)
+        if k is None or d.get("source_sha") != sha:
+            return None
+        return float(k["dram_bytes_per_launch_full"])
+    except Exception:
+        return None
+
+
+def cpu_reference(w, target_s, warm=1):
+    """Time the FP64 oracle on the host cores over a bounded number of full
+    steps of the workload; returns (Gcell-upd/s, steps, threads, seconds)."""
+    from oracle import oracle as O
+    threads = O.set_threads(len(os.sched_getaffinity(0)))
+    o = O.from_workload(w)
+    o.step(warm)
+    t0 = time.perf_counter()
+    o.step(1)
+    one = time.perf_counter() - t0
+    nsteps = max(1, int(target_s / max(one, 1e-3)) - 1)
+    t0 = time.perf_counter()
+    o.step(nsteps)
+    dt = time.perf_counter() - t0
+    o.close()
+    return w.ncells * nsteps / dt / 1e9, nsteps, threads, dt
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    from paper_1505_04007_gb300 import workloads as W
+    mk = W.WORKLOADS[args.workload]
+    w = mk()
+    desc = (f"{args.workload}: {w.nx}x{w.ny}x{w.nz} cells dx={w.dx*1e9:g}nm, film planes {w.info['film_cells']}, "
+            f"{w.nparticles} e- at {w.info['kev']:g} keV, {len(w.probes)} probes x {len(w.freqs)} freqs, CPML 8")
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        v, nst, thr, secs = cpu_reference(w, args.ref_seconds)
+        line = {"impl": "reference", "metric": "Gcell-upd/s", "value": v, "unit": "Gcell-upd/s",
+                "n_gpus": args.gpus, "steps": nst, "warmup": 1, "ms_per_step": secs / nst * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": desc, "parallelism": "none (host cores)"},
+                "cpu_baseline": {"value": v, "unit": "Gcell-upd/s", "cores": thr, "kind": "oracle",
+                                 "sample": f"{nst} full time steps of the workload (of the {args.steps} requested), "
+                                           f"FP64 oracle, OpenMP over cells, particles serial"},
+                "e2e": {"value": v, "unit": "Gcell-upd/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    from paper_1505_04007_gb300 import pic
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    prec = pic.PIC_FP32 if args.precision == "fp32" else pic.PIC_FP64
+    real = 4 if prec == pic.PIC_FP32 else 8
+    stream = torch.cuda.Stream()
+    sim = pic.Simulation(w, prec, stream=stream)
+    sim.step(args.warmup)
+    sim.sync()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ------------------------------------------------ timed region (device)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    sim.sync()
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    cells_total = w.ncells * args.steps * world
+    value = cells_total / (ms / 1e3) / 1e9
+    launches = KERNELS_PER_STEP * args.steps + DFT_KERNELS_PER_FLUSH * (args.steps // DFT_BLOCK)
+
+    # ------------------------------ per-kernel durations (CUDA events, live)
+    prof = sim.profile(min(args.steps, 1024))
+    ab = algorithmic_bytes(w, real)
+    peak, peak_kind = measured_peak()
+    dom = "update_E" if prof["update_E"] >= prof["update_H"] else "update_H"
+    achieved = ab[dom] / (prof[dom] * 1e-6) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": f"{peak_kind} copy bandwidth",
+            "traffic": traffic_for(dom), "algorithmic_bytes_per_launch": ab[dom],
+            "kernel_us": {k: round(v, 3) for k, v in prof.items()}}
+    sim.close()
+
+    # -------------------------------------------- end-to-end through the API
+    e2e = None
+    if not args.no_e2e:
+        barrier()
+        t0 = time.perf_counter()
+        s2 = pic.Simulation(w, prec, stream=stream)
+        s2.step(args.steps)
+        spec = s2.probe_read()
+        t1 = time.perf_counter()
+        s2.close()
+        secs = t1 - t0
+        if dist is not None:
+            t = torch.tensor([secs], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            secs = float(t.item())
+        h2d = w.ncells + w.nparticles * 3 * 2 * 8 + len(w.probes) * 24 + len(w.freqs) * 8
+        d2h = spec.size * 16
+        e2e = {"value": cells_total / secs / 1e9, "unit": "Gcell-upd/s",
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "includes": "pic_create (material tables, upload) + particles + probes + steps + spectrum read"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, nst, thr, secs = cpu_reference(w, args.ref_seconds)
+        cpu = {"value": v, "unit": "Gcell-upd/s", "cores": thr, "kind": "oracle",
+               "sample": f"{nst} full time steps of the same workload, FP64, {secs:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": "Gcell-upd/s", "value": value, "unit": "Gcell-upd/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if prec == pic.PIC_FP32 else "f64", "data": "synthetic",
+                "config": {"workload": desc, "global_batch": world, "parallelism": f"replicas x{world}",
+                           "l2": "state larger than the 129 MB L2 (no flush)",
+                           "particle_pushes_per_s": w.nparticles * args.steps * world / (ms / 1e3)},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * pic.h -- C ABI of libpic: the 3D particle-in-cell time step on a Yee FDTD
+ * grid with Drude metals, after "Numerical study of three-dimensional PIC for
+ * the surface plasmon excitation based on Drude model" (Liu, Zhao, Wang, Liu).
+ *
+ * One time step n -> n+1 (Sec. II; the particle-field coupling is the usual
+ * Yee PIC one, Sec. II last paragraph):
+ *   1. H^{n+1/2} = H^{n-1/2} - dt/mu0 curl E^n                    (vacuum Yee)
+ *      with convolutional-PML (CPML) terms in the absorbing face slabs;
+ *   2. electrons: staggered trilinear gather of E^n and
+ *      B^n = mu0 (H^{n-1/2} + H^{n+1/2})/2, relativistic Boris push,
+ *      x^{n+1} = x^n + dt u/gamma (u = gamma v);
+ *   3. charge-conserving (Esirkepov) free current J_f^{n+1/2};
+ *   4. Drude polarisation current, Eq. 6 (E read at level n):
+ *        J^{n+1/2} = (2-g dt)/(2+g dt) J^{n-1/2} + 2 dt eps0 wp^2/(2+g dt) E^n
+ *      then Eq. 8: E^{n+1} = E^n + dt/(eps0 eps_inf)[curl H^{n+1/2} - J^{n+1/2} - J_f^{n+1/2}];
+ *   5. probe DFT: F[p][c][f] += E_c^{n+1}(x_p) exp(+i 2 pi f (n+1) dt) dt.
+ *
+ * Conventions for every call:
+ *  - SI units.  Arrays of the grid are [nz][ny][nx] with x fastest.
+ *  - Yee staggering: Ex (i+1/2,j,k)  Ey (i,j+1/2,k)  Ez (i,j,k+1/2)
+ *                    Hx (i,j+1/2,k+1/2)  Hy (i+1/2,j,k+1/2)  Hz (i+1/2,j+1/2,k)
+ *    On a non-periodic axis the outer faces are node 0 and node n; tangential
+ *    E on them is held at zero.
+ *  - Every call returns PIC_OK (0) or a negative PIC_ERR_* code; the message
+ *    of the last failure on the calling thread is pic_last_error().
+ *  - Host arrays passed in are copied before the call returns; the caller
+ *    keeps ownership.  Output host arrays are written before return.
+ *  - Device work runs on the handle's stream (pic_config.stream or
+ *    pic_set_stream).  pic_step is asynchronous; calls that return data to the
+ *    host synchronise that stream and report device-side errors.
+ *  - A handle is not thread-safe: one thread at a time per handle.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_OK 0
+#define PIC_ERR_ARG -1         /* invalid argument or out-of-range input */
+#define PIC_ERR_CFL -2         /* dt violates the Yee + Drude stability bound */
+#define PIC_ERR_OOM -3         /* device allocation or workspace too small */
+#define PIC_ERR_CUDA -4        /* a CUDA runtime call failed */
+#define PIC_ERR_NONFINITE -5   /* a NaN/Inf was detected in the state */
+#define PIC_ERR_STATE -6       /* call not valid in the handle's current state */
+#define PIC_ERR_UNSUPPORTED -7 /* configuration outside what the library implements */
+#define PIC_ERR_DEVICE -8      /* a kernel reported an internal error */
+
+enum { PIC_FP32 = 0, PIC_FP64 = 1 };
+enum { PIC_BC_CPML = 0, PIC_BC_PEC = 1, PIC_BC_PERIODIC = 2 };
+enum {
+    PIC_EX = 0, PIC_EY, PIC_EZ,
+    PIC_HX, PIC_HY, PIC_HZ,
+    PIC_JPX, PIC_JPY, PIC_JPZ, /* Drude polarisation current (Eq. 6) */
+    PIC_JFX, PIC_JFY, PIC_JFZ  /* free (particle + source) current of the last step */
+};
+
+/* Drude parameters of one material id (Eq. 1): plasma frequency wp [rad/s],
+ * collision rate gamma [1/s], high-frequency permittivity eps_inf (1 in the
+ * paper).  wp = 0 is a plain dielectric (vacuum when eps_inf = 1). */
+typedef struct {
+    double wp;
+    double gamma;
+    double eps_inf;
+} pic_material;
+
+typedef struct {
+    int64_t nx, ny, nz;           /* cells per axis, each >= 1 */
+    double dx, dy, dz;            /* cell size [m] */
+    double dt;                    /* time step [s] */
+    double eps0, mu0;             /* vacuum constants [F/m], [H/m] */
+    int32_t precision;            /* PIC_FP32 (fields, J, particles in float) or PIC_FP64 */
+    int32_t bc[6];                /* x-lo, x-hi, y-lo, y-hi, z-lo, z-hi: PIC_BC_*; periodic must pair */
+    int32_t cpml_cells;           /* absorbing slab thickness L in cells */
+    double cpml_order;            /* grading exponent m */
+    double cpml_sigma_fac;        /* sigma_max = fac (m+1)/(eta0 d) */
+    double cpml_kappa_max;        /* kappa at the outer face (1 = no stretching) */
+    double cpml_alpha_max;        /* CFS shift at the inner face [S/m] */
+    const uint8_t *material_id;   /* host [nz][ny][nx] ids into materials[] */
+    const pic_material *materials;
+    int32_t n_materials;          /* 1..256 */
+    int64_t max_particles;        /* capacity reserved at create */
+    int32_t max_probes;           /* capacity for pic_probe_dft */
+    int32_t max_freqs;
+    void *workspace;              /* optional caller-owned device memory (NULL: library allocates) */
+    size_t workspace_bytes;       /* size of workspace, >= pic_workspace_size() */
+    void *stream;                 /* cudaStream_t for all device work (NULL: a stream the library creates) */
+    uint64_t flags;               /* reserved, must be 0 */
+} pic_config;
+
+typedef struct {
+    int64_t step;          /* completed time steps */
+    int64_t n_particles;   /* particles added */
+    int64_t n_frozen;      /* particles stopped by the boundary/metal rule */
+    int32_t device_error;  /* bit set reported by kernels (0 = none) */
+    int32_t n_edge_classes;
+} pic_stats;
+
+typedef struct pic_handle pic_handle;
+
+/* Message for the last failing call on this thread ("" if none).  The
+ * string stays valid until the thread's next library call. */
+const char *pic_last_error(void);
+
+/* Device bytes pic_create needs for cfg (grid state, particles and probe
+ * capacity).  Nothing is allocated.  Errors: PIC_ERR_ARG on an invalid cfg. */
+int pic_workspace_size(const pic_config *cfg, size_t *bytes);
+
+/* Build a simulation: validates sizes and the stability bound
+ * c^2 dt^2 sum(1/d^2) + wp_max^2 dt^2/4 < 1, derives the per-edge Drude
+ * coefficients of Eq. 6 and the Ampere factor of Eq. 8 from the material map
+ * (wp^2 on an edge is the mean over the four cells sharing it, gamma its
+ * wp^2-weighted mean, eps_inf the plain mean), builds the CPML profiles, and
+ * zeroes E, H, J.  Device memory comes from cfg->workspace if given (the
+ * caller keeps it alive until pic_destroy), else from cudaMalloc.
+ * *out receives an opaque handle owned by the library until pic_destroy.
+ * Errors: PIC_ERR_ARG, PIC_ERR_CFL, PIC_ERR_OOM, PIC_ERR_UNSUPPORTED (more
+ * than 256 distinct edge materials), PIC_ERR_CUDA. */
+int pic_create(const pic_config *cfg, pic_handle **out);
+
+/* Release the handle and any memory the library allocated.  Waits for the
+ * handle's stream.  NULL is accepted. */
+int pic_destroy(pic_handle *h);
+
+/* Use another cudaStream_t for subsequent device work (NULL: a stream the
+ * library creates and owns).  Waits for the old stream; drops captured step
+ * graphs.  The legacy default stream cannot be captured into graphs, so pass
+ * a created stream, not 0, when sharing one. */
+int pic_set_stream(pic_handle *h, void *stream);
+
+/* Append n macro-electrons: xyz [n][3] positions [m], u [n][3] gamma*v [m/s],
+ * charge q_macro [C] (negative for electrons) and mass m_macro [kg] of each
+ * (all particles of a handle share q and m).  Every position must lie at
+ * least two cells inside each non-periodic face and outside cells with
+ * wp > 0; otherwise nothing is added, *n_rejected (if non-NULL) receives the
+ * count of offending particles and PIC_ERR_ARG is returned.  Positions on
+ * periodic axes are wrapped.  Exceeding max_particles is PIC_ERR_OOM. */
+int pic_add_particles(pic_handle *h, int64_t n, const double *xyz, const double *u,
+                      double q_macro, double m_macro, int64_t *n_rejected);
+
+/* Read particles back in the order they were added: xyz [n][3] (m),
+ * u [n][3] (m/s), status [n] (0 live, 1 frozen).  Any pointer may be NULL.
+ * Synchronises. */
+int pic_get_particles(pic_handle *h, double *xyz, double *u, uint8_t *status);
+
+/* 1: electrons deposit current (default).  0: they are test particles that
+ * feel the fields but do not drive them. */
+int pic_set_deposit(pic_handle *h, int on);
+
+/* Prescribed current density added to J_f on the edges of component comp
+ * (0..2) with indices box = {i0,i1,j0,j1,k0,k1} (half-open) at every step:
+ * amp * exp(-s^2) * sin(2 pi f0 (t-t0)) for f0 > 0, amp * (-2 s) exp(-s^2)
+ * for f0 == 0, s = (t-t0)/tau, evaluated at t = (n+1/2) dt.  At most 16. */
+int pic_add_source(pic_handle *h, int comp, const int64_t *box, double amp, double t0,
+                   double tau, double f0);
+
+/* Configure the probe DFT (Sec. IV, the spectrum of the field above the
+ * film): np points xyz [np][3] (m), components comp_mask (bit c = E_c),
+ * nf frequencies freq_hz [nf].  Zeroes the accumulators.  Points must lie at
+ * least one cell inside each non-periodic face.  Capacity: max_probes,
+ * max_freqs. */
+int pic_probe_dft(pic_handle *h, int np, const double *xyz, uint32_t comp_mask, int nf,
+                  const double *freq_hz);
+
+/* Advance nsteps time steps (asynchronous on the handle's stream; whole
+ * groups of steps are replayed from a captured CUDA graph). */
+int pic_step(pic_handle *h, int64_t nsteps);
+
+/* Wait for the handle's stream; report a kernel-side error as PIC_ERR_DEVICE. */
+int pic_sync(pic_handle *h);
+
+/* Copy the probe spectra to out [np][3][nf][2] (re, im; components not in
+ * the mask are zero).  Synchronises. */
+int pic_probe_read(pic_handle *h, double *out);
+
+/* Copy grid array `which` (PIC_EX..PIC_JFZ) to out [nz][ny][nx] as double.
+ * Synchronises. */
+int pic_get_field(pic_handle *h, int which, double *out);
+
+/* Overwrite E or H component `which` (PIC_EX..PIC_HZ) from in [nz][ny][nx]
+ * (rounded to the state precision).  Used for initial conditions and
+ * restarts.  Synchronises. */
+int pic_set_field(pic_handle *h, int which, const double *in);
+
+/* Counters and the device error word.  Synchronises. */
+int pic_get_stats(pic_handle *h, pic_stats *out);
+
+/* Time the given number of steps on the handle's stream with CUDA events and
+ * return the average duration of each kernel kind in microseconds:
+ * out[0] H update, out[1] push+deposit, out[2] E update, out[3] step tail
+ * (probe sampling), out[4] probe DFT flush per step, out[5] whole step.
+ * Runs real steps (the simulation advances).  Synchronises. */
+int pic_profile_steps(pic_handle *h, int64_t nsteps, double *out_us);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIC_H */

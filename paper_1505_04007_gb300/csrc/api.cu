@@ -1,0 +1,900 @@
+// api.cu -- host runtime behind the C ABI of include/pic.h.
+//
+// A handle owns one simulation instance on one device: a single arena of
+// device memory (caller workspace or one cudaMalloc), the per-edge material
+// classes and CPML profiles built on the host at create time, the particle
+// and probe buffers, and a captured CUDA graph that replays DFT_BLOCK steps
+// plus one probe-DFT flush.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/pic.h"
+#include "pic_internal.cuh"
+
+using namespace pic;
+
+static thread_local std::string g_err;
+
+static int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+static int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                          \
+    do {                                                                                        \
+        cudaError_t _e = (expr);                                                                \
+        if (_e != cudaSuccess) return fail(PIC_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(_e)); \
+    } while (0)
+
+// ------------------------------------------------------------------ arena --
+struct Arena {
+    char *base = nullptr;  // nullptr: sizing pass
+    size_t used = 0;
+    template <typename P>
+    P *take(size_t count) {
+        used = (used + 255) & ~size_t(255);
+        P *p = base ? reinterpret_cast<P *>(base + used) : nullptr;
+        used += count * sizeof(P);
+        return p;
+    }
+};
+
+static bool is_periodic(const pic_config *c, int a) { return c->bc[2 * a] == PIC_BC_PERIODIC; }
+static bool has_cpml(const pic_config *c, int a) {
+    return c->bc[2 * a] == PIC_BC_CPML || c->bc[2 * a + 1] == PIC_BC_CPML;
+}
+
+static int validate(const pic_config *c) {
+    if (!c) return fail(PIC_ERR_ARG, "config is NULL");
+    if (c->flags != 0) return fail(PIC_ERR_ARG, "flags must be 0");
+    if (c->precision != PIC_FP32 && c->precision != PIC_FP64) return fail(PIC_ERR_ARG, "unknown precision");
+    const int64_t n[3] = {c->nx, c->ny, c->nz};
+    const double d[3] = {c->dx, c->dy, c->dz};
+    for (int a = 0; a < 3; a++) {
+        if (n[a] < 1 || n[a] > (1 << 20)) return fail(PIC_ERR_ARG, "axis %d: %lld cells out of range", a, (long long)n[a]);
+        if (!(d[a] > 0.0) || !std::isfinite(d[a])) return fail(PIC_ERR_ARG, "axis %d: bad cell size", a);
+        int lo = c->bc[2 * a], hi = c->bc[2 * a + 1];
+        if (lo < 0 || lo > 2 || hi < 0 || hi > 2) return fail(PIC_ERR_ARG, "axis %d: unknown boundary code", a);
+        if ((lo == PIC_BC_PERIODIC) != (hi == PIC_BC_PERIODIC))
+            return fail(PIC_ERR_ARG, "axis %d: periodic boundaries must be paired", a);
+        if (has_cpml(c, a) && n[a] < 2 * (int64_t)c->cpml_cells + 4)
+            return fail(PIC_ERR_ARG, "axis %d: %lld cells cannot hold two %d-cell CPML slabs", a, (long long)n[a],
+                        c->cpml_cells);
+    }
+    if (c->ny > 4 * 65535LL || c->nz > 2 * 65535LL) return fail(PIC_ERR_UNSUPPORTED, "grid too tall for the launch shape");
+    if (c->cpml_cells < 1 && (has_cpml(c, 0) || has_cpml(c, 1) || has_cpml(c, 2)))
+        return fail(PIC_ERR_ARG, "cpml_cells must be >= 1");
+    if (!(c->dt > 0.0) || !(c->eps0 > 0.0) || !(c->mu0 > 0.0)) return fail(PIC_ERR_ARG, "dt, eps0, mu0 must be > 0");
+    if (c->n_materials < 1 || c->n_materials > 256 || !c->materials || !c->material_id)
+        return fail(PIC_ERR_ARG, "need 1..256 materials and a material map");
+    double wpmax = 0.0;
+    for (int m = 0; m < c->n_materials; m++) {
+        const pic_material &mt = c->materials[m];
+        if (!(mt.wp >= 0.0) || !(mt.gamma >= 0.0) || !(mt.eps_inf > 0.0))
+            return fail(PIC_ERR_ARG, "material %d: need wp >= 0, gamma >= 0, eps_inf > 0", m);
+        wpmax = std::max(wpmax, mt.wp);
+    }
+    const double c2 = 1.0 / (c->eps0 * c->mu0);
+    const double s = 1.0 / (d[0] * d[0]) + 1.0 / (d[1] * d[1]) + 1.0 / (d[2] * d[2]);
+    if (!(c2 * c->dt * c->dt * s + 0.25 * wpmax * wpmax * c->dt * c->dt < 1.0))
+        return fail(PIC_ERR_CFL, "dt=%g violates c^2 dt^2 sum(1/d^2) + wp^2 dt^2/4 < 1", c->dt);
+    if (c->max_particles < 0 || c->max_probes < 0 || c->max_freqs < 0) return fail(PIC_ERR_ARG, "negative capacity");
+    if (c->max_probes > 20000) return fail(PIC_ERR_UNSUPPORTED, "max_probes above 20000");
+    return PIC_OK;
+}
+
+// ---------------------------------------------------------------- the sim --
+struct SimBase {
+    virtual ~SimBase() {}
+};
+
+template <typename T>
+struct Sim : SimBase {
+    pic_config cfg{};
+    int n[3];
+    double d[3];
+    long long N = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void *arena = nullptr;
+    bool own_arena = false;
+    size_t arena_bytes = 0;
+
+    Grid<T> g{};
+    Fields<T> f{};
+    Particles<T> p{};
+    PushParams<T> pp{};
+    Probes<T> pr{};
+    uint8_t *d_mat = nullptr, *d_mat_metal = nullptr;
+    uint8_t *d_ecls[3] = {nullptr, nullptr, nullptr};
+    uint8_t *d_cls_metal = nullptr;
+    T *d_cls[3] = {nullptr, nullptr, nullptr};
+    T *d_prof[18];
+    int *d_flag = nullptr;
+    long long *d_step = nullptr;
+    int *d_err = nullptr;
+    double *d_probe_xyz = nullptr, *d_freq = nullptr, *d_samples = nullptr, *d_F = nullptr, *d_phasor = nullptr;
+    size_t n_tiles = 0;
+    int n_classes = 0;
+
+    std::vector<Source> sources;
+    long long step_host = 0;
+    int buffered = 0;
+    bool bold_stale = false;
+    bool have_q = false;
+    double q = 0, m = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+
+    // all device buffers, in one pass; base == nullptr only measures
+    void plan(Arena &a) {
+        const size_t Ts = (size_t)N;
+        for (int c = 0; c < 3; c++) {
+            f.E[c] = a.take<T>(Ts);
+            f.H[c] = a.take<T>(Ts);
+            f.Jp[c] = a.take<T>(Ts);
+            f.Jf[c] = a.take<T>(Ts);
+        }
+        for (int ax = 0; ax < 3; ax++) {
+            size_t slab = 0;
+            if (g.cpml[ax]) slab = (size_t)(N / n[ax]) * 2 * cfg.cpml_cells;
+            for (int s = 0; s < 2; s++) {
+                f.psiH[ax][s] = slab ? a.take<T>(slab) : nullptr;
+                f.psiE[ax][s] = slab ? a.take<T>(slab) : nullptr;
+            }
+        }
+        for (int ax = 0; ax < 3; ax++)
+            for (int q6 = 0; q6 < 6; q6++) d_prof[ax * 6 + q6] = a.take<T>(n[ax]);
+        d_mat = a.take<uint8_t>(Ts);
+        d_mat_metal = a.take<uint8_t>(256);
+        for (int c = 0; c < 3; c++) d_ecls[c] = a.take<uint8_t>(Ts);
+        for (int q3 = 0; q3 < 3; q3++) d_cls[q3] = a.take<T>(256);
+        d_cls_metal = a.take<uint8_t>(256);
+        d_flag = a.take<int>(n_tiles);
+        d_step = a.take<long long>(1);
+        d_err = a.take<int>(1);
+        const size_t mp = (size_t)cfg.max_particles;
+        for (int c = 0; c < 3; c++) {
+            p.cell[c] = a.take<int>(mp);
+            p.off[c] = a.take<T>(mp);
+            p.u[c] = a.take<T>(mp);
+            p.bold[c] = a.take<T>(mp);
+        }
+        p.status = a.take<uint8_t>(mp);
+        p.id = a.take<long long>(mp);
+        const size_t npb = (size_t)cfg.max_probes, nfb = (size_t)cfg.max_freqs;
+        d_probe_xyz = a.take<double>(3 * npb);
+        d_freq = a.take<double>(nfb);
+        d_samples = a.take<double>((size_t)DFT_BLOCK * npb * 3);
+        d_F = a.take<double>(npb * 3 * nfb * 2);
+        d_phasor = a.take<double>((size_t)DFT_BLOCK * nfb * 2);
+    }
+
+    void init_geometry(const pic_config *c) {
+        cfg = *c;
+        cfg.material_id = nullptr;
+        cfg.materials = nullptr;
+        n[0] = (int)c->nx; n[1] = (int)c->ny; n[2] = (int)c->nz;
+        d[0] = c->dx; d[1] = c->dy; d[2] = c->dz;
+        N = (long long)n[0] * n[1] * n[2];
+        for (int a = 0; a < 3; a++) {
+            g.n[a] = n[a];
+            g.per[a] = is_periodic(c, a);
+            g.cpml[a] = has_cpml(c, a);
+            g.r[a] = (T)(1.0 / d[a]);
+            g.nt[a] = (n[a] + (a == 0 ? TILE_X : a == 1 ? TILE_Y : TILE_Z) - 1) /
+                      (a == 0 ? TILE_X : a == 1 ? TILE_Y : TILE_Z);
+        }
+        g.L = c->cpml_cells;
+        g.cH = (T)(c->dt / c->mu0);
+        g.ncell = N;
+        n_tiles = (size_t)g.nt[0] * g.nt[1] * g.nt[2];
+    }
+
+    // CPML grading at position pos (cell units) along axis a.
+    void profile(int a, double pos, double &b, double &aa, double &ik) const {
+        const double L = cfg.cpml_cells;
+        double rho = 0.0;
+        if (g.cpml[a]) {
+            if (cfg.bc[2 * a] == PIC_BC_CPML && pos < L) rho = L - pos;
+            if (cfg.bc[2 * a + 1] == PIC_BC_CPML && pos > n[a] - L) rho = std::max(rho, pos - (n[a] - L));
+        }
+        if (rho <= 0.0) { b = 1.0; aa = 0.0; ik = 1.0; return; }
+        const double eta0 = std::sqrt(cfg.mu0 / cfg.eps0);
+        const double x = rho / L, xm = std::pow(x, cfg.cpml_order);
+        const double sigma = cfg.cpml_sigma_fac * (cfg.cpml_order + 1.0) / (eta0 * d[a]) * xm;
+        const double kappa = 1.0 + (cfg.cpml_kappa_max - 1.0) * xm;
+        const double alpha = cfg.cpml_alpha_max * (1.0 - x);
+        b = std::exp(-(sigma / kappa + alpha) * cfg.dt / cfg.eps0);
+        const double den = sigma * kappa + kappa * kappa * alpha;
+        aa = (sigma > 0.0 && den > 0.0) ? sigma * (b - 1.0) / den : 0.0;
+        ik = 1.0 / kappa;
+    }
+
+    int build_tables(const pic_config *c, std::vector<uint8_t> ecls[3], std::vector<T> cls[3],
+                     std::vector<uint8_t> &cls_metal) {
+        // distinct multisets of the four cell ids around an edge -> class
+        std::unordered_map<uint32_t, int> classes;
+        const uint8_t *mat = c->material_id;
+        auto wrapc = [&](int a, int x) {
+            if (x < 0) return g.per[a] ? x + n[a] : 0;
+            if (x >= n[a]) return g.per[a] ? x - n[a] : n[a] - 1;
+            return x;
+        };
+        for (int q3 = 0; q3 < 3; q3++) cls[q3].assign(256, (T)0);
+        cls_metal.assign(256, 0);
+        for (int comp = 0; comp < 3; comp++) {
+            ecls[comp].resize((size_t)N);
+            const int a1 = (comp + 1) % 3, a2 = (comp + 2) % 3;
+            uint32_t last_key = 0xffffffffu;
+            int last_cls = -1;
+            for (int k = 0; k < n[2]; k++)
+                for (int j = 0; j < n[1]; j++)
+                    for (int i = 0; i < n[0]; i++) {
+                        int ids[4], t = 0;
+                        for (int s1 = -1; s1 <= 0; s1++)
+                            for (int s2 = -1; s2 <= 0; s2++) {
+                                int p3[3] = {i, j, k};
+                                p3[a1] = wrapc(a1, p3[a1] + s1);
+                                p3[a2] = wrapc(a2, p3[a2] + s2);
+                                ids[t++] = mat[((size_t)p3[2] * n[1] + p3[1]) * n[0] + p3[0]];
+                            }
+                        std::sort(ids, ids + 4);
+                        const uint32_t key = (uint32_t)ids[0] | (uint32_t)ids[1] << 8 | (uint32_t)ids[2] << 16 |
+                                             (uint32_t)ids[3] << 24;
+                        int cl;
+                        if (key == last_key) {
+                            cl = last_cls;
+                        } else {
+                            auto it = classes.find(key);
+                            if (it == classes.end()) {
+                                if ((int)classes.size() >= 256)
+                                    return fail(PIC_ERR_UNSUPPORTED, "more than 256 distinct edge materials");
+                                cl = (int)classes.size();
+                                classes[key] = cl;
+                                double sw = 0, swg = 0, se = 0;
+                                for (int q4 = 0; q4 < 4; q4++) {
+                                    const pic_material &mt = c->materials[ids[q4]];
+                                    sw += mt.wp * mt.wp;
+                                    swg += mt.wp * mt.wp * mt.gamma;
+                                    se += mt.eps_inf;
+                                }
+                                const double wp2 = sw / 4.0, gam = sw > 0 ? swg / sw : 0.0, einf = se / 4.0;
+                                const double dt = c->dt;
+                                cls[0][cl] = (T)((2.0 - gam * dt) / (2.0 + gam * dt));
+                                cls[1][cl] = (T)(2.0 * dt * c->eps0 * wp2 / (2.0 + gam * dt));
+                                cls[2][cl] = (T)(dt / (c->eps0 * einf));
+                                cls_metal[cl] = wp2 > 0.0;
+                            } else {
+                                cl = it->second;
+                            }
+                            last_key = key;
+                            last_cls = cl;
+                        }
+                        ecls[comp][((size_t)k * n[1] + j) * n[0] + i] = (uint8_t)cl;
+                    }
+        }
+        n_classes = (int)classes.size();
+        return PIC_OK;
+    }
+
+    int create(const pic_config *c) {
+        init_geometry(c);
+        for (size_t e = 0; e < (size_t)N; e++)
+            if (c->material_id[e] >= c->n_materials)
+                return fail(PIC_ERR_ARG, "material id %d at cell %zu out of range", c->material_id[e], e);
+        std::vector<uint8_t> ecls[3], cls_metal;
+        std::vector<T> cls[3];
+        int rc = build_tables(c, ecls, cls, cls_metal);
+        if (rc) return rc;
+
+        Arena sizing;
+        plan(sizing);
+        arena_bytes = sizing.used;
+        if (c->workspace) {
+            if (c->workspace_bytes < arena_bytes)
+                return fail(PIC_ERR_OOM, "workspace of %zu bytes is below the %zu needed", c->workspace_bytes,
+                            arena_bytes);
+            if (((uintptr_t)c->workspace) & 255) return fail(PIC_ERR_ARG, "workspace must be 256-byte aligned");
+            arena = c->workspace;
+        } else {
+            cudaError_t e = cudaMalloc(&arena, arena_bytes);
+            if (e != cudaSuccess) {
+                arena = nullptr;
+                return fail(PIC_ERR_OOM, "cudaMalloc(%zu): %s", arena_bytes, cudaGetErrorString(e));
+            }
+            own_arena = true;
+        }
+        Arena real;
+        real.base = (char *)arena;
+        plan(real);
+
+        if (c->stream) {
+            stream = (cudaStream_t)c->stream;
+        } else {
+            CUDA_TRY(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+            own_stream = true;
+        }
+        CUDA_TRY(cudaMemsetAsync(arena, 0, arena_bytes, stream));
+
+        // material map and per-material metal flag (particle absorption)
+        std::vector<uint8_t> metal(256, 0);
+        for (int m2 = 0; m2 < c->n_materials; m2++) metal[m2] = c->materials[m2].wp > 0.0;
+        CUDA_TRY(cudaMemcpyAsync(d_mat, c->material_id, (size_t)N, cudaMemcpyHostToDevice, stream));
+        CUDA_TRY(cudaMemcpyAsync(d_mat_metal, metal.data(), 256, cudaMemcpyHostToDevice, stream));
+        for (int comp = 0; comp < 3; comp++)
+            CUDA_TRY(cudaMemcpyAsync(d_ecls[comp], ecls[comp].data(), (size_t)N, cudaMemcpyHostToDevice, stream));
+        for (int q3 = 0; q3 < 3; q3++)
+            CUDA_TRY(cudaMemcpyAsync(d_cls[q3], cls[q3].data(), 256 * sizeof(T), cudaMemcpyHostToDevice, stream));
+        CUDA_TRY(cudaMemcpyAsync(d_cls_metal, cls_metal.data(), 256, cudaMemcpyHostToDevice, stream));
+        // CPML profiles: per axis bE aE ikE bH aH ikH
+        for (int a = 0; a < 3; a++) {
+            std::vector<T> pf[6];
+            for (auto &v : pf) v.resize(n[a]);
+            for (int x = 0; x < n[a]; x++) {
+                double b, aa, ik;
+                profile(a, (double)x, b, aa, ik);
+                pf[0][x] = (T)b; pf[1][x] = (T)aa; pf[2][x] = (T)ik;
+                profile(a, x + 0.5, b, aa, ik);
+                pf[3][x] = (T)b; pf[4][x] = (T)aa; pf[5][x] = (T)ik;
+            }
+            for (int q6 = 0; q6 < 6; q6++)
+                CUDA_TRY(cudaMemcpyAsync(d_prof[a * 6 + q6], pf[q6].data(), n[a] * sizeof(T), cudaMemcpyHostToDevice,
+                                         stream));
+        }
+        CUDA_TRY(cudaStreamSynchronize(stream));  // host staging vectors die at return
+
+        for (int a = 0; a < 3; a++) {
+            f.bE[a] = d_prof[a * 6 + 0]; f.aE[a] = d_prof[a * 6 + 1]; f.ikE[a] = d_prof[a * 6 + 2];
+            f.bH[a] = d_prof[a * 6 + 3]; f.aH[a] = d_prof[a * 6 + 4]; f.ikH[a] = d_prof[a * 6 + 5];
+            f.ecls[a] = d_ecls[a];
+        }
+        f.cls_kJ = d_cls[0]; f.cls_bJ = d_cls[1]; f.cls_cE = d_cls[2];
+        f.cls_metal = d_cls_metal;
+        f.jf_flag = d_flag;
+        f.step = d_step;
+        p.n = 0;
+        pp.mat = d_mat;
+        pp.mat_metal = d_mat_metal;
+        pp.deposit = 1;
+        pp.err = d_err;
+        pp.mu0 = (T)c->mu0;
+        pp.inv_c2 = (T)(c->eps0 * c->mu0);
+        for (int a = 0; a < 3; a++) pp.dtd[a] = (T)(c->dt / d[a]);
+        pr.np = 0; pr.nf = 0; pr.mask = 0;
+        pr.xyz_cells = d_probe_xyz; pr.freq = d_freq; pr.samples = d_samples; pr.F = d_F; pr.phasor = d_phasor;
+        pr.dt = c->dt;
+        return PIC_OK;
+    }
+
+    ~Sim() override {
+        if (stream) cudaStreamSynchronize(stream);
+        drop_graph();
+        if (own_arena && arena) cudaFree(arena);
+        if (own_stream && stream) cudaStreamDestroy(stream);
+    }
+
+    void drop_graph() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
+        gexec = nullptr;
+        graph = nullptr;
+    }
+
+    // ---------------------------------------------------------- stepping --
+    void launch_step() {
+        launch_update_H<T>(g, f, stream);
+        launch_push_deposit<T>(g, f, p, pp, stream);
+        launch_sources<T>(g, f, sources.data(), (int)sources.size(), cfg.dt, stream);
+        launch_update_E<T>(g, f, stream);
+        launch_step_tail<T>(g, f, pr, d_step, stream);
+    }
+
+    int ensure_graph() {
+        if (gexec) return PIC_OK;
+        CUDA_TRY(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+        for (int s = 0; s < DFT_BLOCK; s++) launch_step();
+        launch_dft_flush<T>(pr, d_step, DFT_BLOCK, stream);
+        cudaError_t e = cudaStreamEndCapture(stream, &graph);
+        if (e != cudaSuccess) { graph = nullptr; return fail(PIC_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e)); }
+        e = cudaGraphInstantiate(&gexec, graph, 0);
+        if (e != cudaSuccess) { gexec = nullptr; return fail(PIC_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e)); }
+        return PIC_OK;
+    }
+
+    int refresh_bold() {
+        if (bold_stale) {
+            launch_gather_bold<T>(g, f, p, stream);
+            CUDA_TRY(cudaGetLastError());
+            bold_stale = false;
+        }
+        return PIC_OK;
+    }
+
+    int step(long long nsteps) {
+        if (nsteps < 0) return fail(PIC_ERR_ARG, "negative step count");
+        int rc = refresh_bold();
+        if (rc) return rc;
+        while (nsteps > 0) {
+            if (buffered == 0 && nsteps >= DFT_BLOCK) {
+                rc = ensure_graph();
+                if (rc) return rc;
+                CUDA_TRY(cudaGraphLaunch(gexec, stream));
+                nsteps -= DFT_BLOCK;
+                step_host += DFT_BLOCK;
+                continue;
+            }
+            launch_step();
+            CUDA_TRY(cudaGetLastError());
+            buffered++;
+            step_host++;
+            nsteps--;
+            if (buffered == DFT_BLOCK) {
+                launch_dft_flush<T>(pr, d_step, DFT_BLOCK, stream);
+                buffered = 0;
+            }
+        }
+        CUDA_TRY(cudaGetLastError());
+        return PIC_OK;
+    }
+
+    int flush_probes() {
+        if (buffered > 0) {
+            launch_dft_flush<T>(pr, d_step, buffered, stream);
+            CUDA_TRY(cudaGetLastError());
+            buffered = 0;
+        }
+        return PIC_OK;
+    }
+
+    int sync() {
+        CUDA_TRY(cudaStreamSynchronize(stream));
+        int err = 0;
+        CUDA_TRY(cudaMemcpy(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (err) return fail(PIC_ERR_DEVICE, "kernel error bits 0x%x", err);
+        return PIC_OK;
+    }
+
+    int profile_steps(long long nsteps, double *out) {
+        int rc = refresh_bold();
+        if (rc) return rc;
+        for (int q6 = 0; q6 < 6; q6++) out[q6] = 0.0;
+        if (nsteps <= 0) return PIC_OK;
+        const int B = DFT_BLOCK;
+        std::vector<cudaEvent_t> ev((size_t)B * 6);
+        for (auto &e : ev) CUDA_TRY(cudaEventCreate(&e));
+        long long done = 0;
+        double acc[6] = {0, 0, 0, 0, 0, 0};
+        while (done < nsteps) {
+            const int cnt = (int)std::min<long long>(B, nsteps - done);
+            for (int s = 0; s < cnt; s++) {
+                cudaEvent_t *e = &ev[(size_t)s * 6];
+                cudaEventRecord(e[0], stream);
+                launch_update_H<T>(g, f, stream);
+                cudaEventRecord(e[1], stream);
+                launch_push_deposit<T>(g, f, p, pp, stream);
+                launch_sources<T>(g, f, sources.data(), (int)sources.size(), cfg.dt, stream);
+                cudaEventRecord(e[2], stream);
+                launch_update_E<T>(g, f, stream);
+                cudaEventRecord(e[3], stream);
+                launch_step_tail<T>(g, f, pr, d_step, stream);
+                cudaEventRecord(e[4], stream);
+                buffered++;
+                step_host++;
+                if (buffered == DFT_BLOCK) {
+                    launch_dft_flush<T>(pr, d_step, DFT_BLOCK, stream);
+                    buffered = 0;
+                }
+                cudaEventRecord(e[5], stream);
+            }
+            CUDA_TRY(cudaGetLastError());
+            CUDA_TRY(cudaEventSynchronize(ev[(size_t)(cnt - 1) * 6 + 5]));
+            for (int s = 0; s < cnt; s++) {
+                cudaEvent_t *e = &ev[(size_t)s * 6];
+                float ms;
+                for (int q5 = 0; q5 < 5; q5++) {
+                    cudaEventElapsedTime(&ms, e[q5], e[q5 + 1]);
+                    acc[q5] += ms;
+                }
+                cudaEventElapsedTime(&ms, e[0], e[5]);
+                acc[5] += ms;
+            }
+            done += cnt;
+        }
+        for (auto &e : ev) cudaEventDestroy(e);
+        for (int q6 = 0; q6 < 6; q6++) out[q6] = acc[q6] * 1000.0 / (double)nsteps;
+        return sync();
+    }
+};
+
+struct pic_handle {
+    int precision;
+    SimBase *sim;
+};
+
+template <typename T>
+static Sim<T> *S(pic_handle *h) {
+    return static_cast<Sim<T> *>(h->sim);
+}
+
+#define DISPATCH(h, call)                                                       \
+    ((h)->precision == PIC_FP64 ? S<double>(h)->call : S<float>(h)->call)
+
+// ---------------------------------------------------------- entry points --
+template <typename T>
+static int add_particles_t(Sim<T> *s, int64_t n, const double *xyz, const double *u, double q, double m,
+                           int64_t *n_rejected) {
+    if (n_rejected) *n_rejected = 0;
+    if (n < 0 || (n > 0 && (!xyz || !u))) return fail(PIC_ERR_ARG, "bad particle arrays");
+    if (!(m > 0.0) || !std::isfinite(q)) return fail(PIC_ERR_ARG, "need m_macro > 0 and finite q_macro");
+    if (s->have_q && (q != s->q || m != s->m)) return fail(PIC_ERR_ARG, "all particles must share q_macro and m_macro");
+    if (s->p.n + n > s->cfg.max_particles)
+        return fail(PIC_ERR_OOM, "%lld particles exceed max_particles=%lld", (long long)(s->p.n + n),
+                    (long long)s->cfg.max_particles);
+    std::vector<int> cell[3];
+    std::vector<T> off[3], uu[3];
+    for (int a = 0; a < 3; a++) { cell[a].resize(n); off[a].resize(n); uu[a].resize(n); }
+    std::vector<uint8_t> mat((size_t)s->N);
+    int64_t bad = 0;
+    // the material map lives on the device; copy it once for the check
+    if (n > 0) {
+        CUDA_TRY(cudaMemcpyAsync(mat.data(), s->d_mat, (size_t)s->N, cudaMemcpyDeviceToHost, s->stream));
+        CUDA_TRY(cudaStreamSynchronize(s->stream));
+    }
+    std::vector<uint8_t> metal(256);
+    CUDA_TRY(cudaMemcpy(metal.data(), s->d_mat_metal, 256, cudaMemcpyDeviceToHost));
+    for (int64_t q2 = 0; q2 < n; q2++) {
+        bool ok = true;
+        int c3[3];
+        for (int a = 0; a < 3; a++) {
+            double xi = xyz[3 * q2 + a] / s->d[a];
+            if (!std::isfinite(xi) || !std::isfinite(u[3 * q2 + a])) { ok = false; xi = 0; }
+            if (s->g.per[a]) xi -= std::floor(xi / s->n[a]) * s->n[a];
+            double fl = std::floor(xi);
+            int ci = (int)fl;
+            double o = xi - fl;
+            if (s->g.per[a] && ci >= s->n[a]) { ci -= s->n[a]; }
+            if (!s->g.per[a] && (xi < 2.0 || xi >= s->n[a] - 2.0)) ok = false;
+            ci = std::min(std::max(ci, 0), s->n[a] - 1);
+            c3[a] = ci;
+            cell[a][q2] = ci;
+            T ot = (T)o;
+            if (ot >= T(1)) ot = std::nextafter(T(1), T(0));
+            off[a][q2] = ot;
+            uu[a][q2] = (T)u[3 * q2 + a];
+        }
+        if (ok && metal[mat[((size_t)c3[2] * s->n[1] + c3[1]) * s->n[0] + c3[0]]]) ok = false;
+        if (!ok) bad++;
+    }
+    if (n_rejected) *n_rejected = bad;
+    if (bad) return fail(PIC_ERR_ARG, "%lld particles outside the allowed region", (long long)bad);
+    const long long base = s->p.n;
+    std::vector<long long> ids(n);
+    for (int64_t q2 = 0; q2 < n; q2++) ids[q2] = base + q2;
+    for (int a = 0; a < 3; a++) {
+        CUDA_TRY(cudaMemcpyAsync(s->p.cell[a] + base, cell[a].data(), n * sizeof(int), cudaMemcpyHostToDevice, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(s->p.off[a] + base, off[a].data(), n * sizeof(T), cudaMemcpyHostToDevice, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(s->p.u[a] + base, uu[a].data(), n * sizeof(T), cudaMemcpyHostToDevice, s->stream));
+    }
+    CUDA_TRY(cudaMemcpyAsync(s->p.id + base, ids.data(), n * sizeof(long long), cudaMemcpyHostToDevice, s->stream));
+    CUDA_TRY(cudaMemsetAsync(s->p.status + base, 0, (size_t)n, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    s->p.n = base + n;
+    s->have_q = true;
+    s->q = q;
+    s->m = m;
+    s->pp.qmdt2 = (T)(q * s->cfg.dt / (2.0 * m));
+    for (int c = 0; c < 3; c++) {
+        const int a1 = (c + 1) % 3, a2 = (c + 2) % 3;
+        s->pp.jscale[c] = (T)(-q / (s->cfg.dt * s->d[a1] * s->d[a2]));
+    }
+    s->bold_stale = true;
+    s->drop_graph();
+    return PIC_OK;
+}
+
+template <typename T>
+static int get_particles_t(Sim<T> *s, double *xyz, double *u, uint8_t *status) {
+    int rc = s->sync();
+    if (rc) return rc;
+    const long long n = s->p.n;
+    std::vector<int> cell[3];
+    std::vector<T> off[3], uu[3];
+    std::vector<uint8_t> st(n);
+    std::vector<long long> id(n);
+    for (int a = 0; a < 3; a++) {
+        cell[a].resize(n); off[a].resize(n); uu[a].resize(n);
+        CUDA_TRY(cudaMemcpy(cell[a].data(), s->p.cell[a], n * sizeof(int), cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy(off[a].data(), s->p.off[a], n * sizeof(T), cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy(uu[a].data(), s->p.u[a], n * sizeof(T), cudaMemcpyDeviceToHost));
+    }
+    CUDA_TRY(cudaMemcpy(st.data(), s->p.status, n, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(id.data(), s->p.id, n * sizeof(long long), cudaMemcpyDeviceToHost));
+    for (long long q2 = 0; q2 < n; q2++) {
+        const long long o = id[q2];
+        if (o < 0 || o >= n) return fail(PIC_ERR_DEVICE, "corrupt particle id");
+        for (int a = 0; a < 3; a++) {
+            if (xyz) xyz[3 * o + a] = ((double)cell[a][q2] + (double)off[a][q2]) * s->d[a];
+            if (u) u[3 * o + a] = (double)uu[a][q2];
+        }
+        if (status) status[o] = st[q2];
+    }
+    return PIC_OK;
+}
+
+template <typename T>
+static int probe_dft_t(Sim<T> *s, int np, const double *xyz, uint32_t mask, int nf, const double *freq) {
+    if (np < 0 || nf < 0 || (mask & ~7u)) return fail(PIC_ERR_ARG, "bad probe arguments");
+    if (np > s->cfg.max_probes || nf > s->cfg.max_freqs)
+        return fail(PIC_ERR_OOM, "probe capacity is %d x %d", s->cfg.max_probes, s->cfg.max_freqs);
+    if ((np > 0 && !xyz) || (nf > 0 && !freq)) return fail(PIC_ERR_ARG, "NULL probe arrays");
+    std::vector<double> cells((size_t)np * 3);
+    for (int q2 = 0; q2 < np; q2++)
+        for (int a = 0; a < 3; a++) {
+            double xi = xyz[3 * q2 + a] / s->d[a];
+            if (!std::isfinite(xi)) return fail(PIC_ERR_ARG, "non-finite probe position");
+            if (!s->g.per[a] && (xi < 1.0 || xi >= s->n[a] - 1.0))
+                return fail(PIC_ERR_ARG, "probe %d lies within one cell of a face", q2);
+            cells[3 * q2 + a] = xi;
+        }
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (np) CUDA_TRY(cudaMemcpy(s->d_probe_xyz, cells.data(), cells.size() * sizeof(double), cudaMemcpyHostToDevice));
+    if (nf) CUDA_TRY(cudaMemcpy(s->d_freq, freq, nf * sizeof(double), cudaMemcpyHostToDevice));
+    if (np && nf) CUDA_TRY(cudaMemset(s->d_F, 0, (size_t)np * 3 * nf * 2 * sizeof(double)));
+    s->pr.np = np;
+    s->pr.nf = nf;
+    s->pr.mask = mask;
+    s->buffered = 0;
+    s->drop_graph();
+    return PIC_OK;
+}
+
+template <typename T>
+static int probe_read_t(Sim<T> *s, double *out) {
+    if (s->pr.np == 0 || s->pr.nf == 0) return fail(PIC_ERR_STATE, "no probes configured");
+    int rc = s->flush_probes();
+    if (rc) return rc;
+    rc = s->sync();
+    if (rc) return rc;
+    CUDA_TRY(cudaMemcpy(out, s->d_F, (size_t)s->pr.np * 3 * s->pr.nf * 2 * sizeof(double), cudaMemcpyDeviceToHost));
+    return PIC_OK;
+}
+
+template <typename T>
+static T *field_of(Sim<T> *s, int which) {
+    const int c = which % 3;
+    switch (which / 3) {
+    case 0: return s->f.E[c];
+    case 1: return s->f.H[c];
+    case 2: return s->f.Jp[c];
+    default: return s->f.Jf[c];
+    }
+}
+
+template <typename T>
+static int get_field_t(Sim<T> *s, int which, double *out) {
+    if (which < 0 || which > 11 || !out) return fail(PIC_ERR_ARG, "bad field id");
+    int rc = s->sync();
+    if (rc) return rc;
+    std::vector<T> tmp((size_t)s->N);
+    CUDA_TRY(cudaMemcpy(tmp.data(), field_of(s, which), (size_t)s->N * sizeof(T), cudaMemcpyDeviceToHost));
+    for (size_t e = 0; e < (size_t)s->N; e++) out[e] = (double)tmp[e];
+    return PIC_OK;
+}
+
+template <typename T>
+static int set_field_t(Sim<T> *s, int which, const double *in) {
+    if (which < 0 || which > 5 || !in) return fail(PIC_ERR_ARG, "only E and H components can be set");
+    int rc = s->sync();
+    if (rc) return rc;
+    std::vector<T> tmp((size_t)s->N);
+    for (size_t e = 0; e < (size_t)s->N; e++) tmp[e] = (T)in[e];
+    CUDA_TRY(cudaMemcpy(field_of(s, which), tmp.data(), (size_t)s->N * sizeof(T), cudaMemcpyHostToDevice));
+    if (which >= PIC_HX) s->bold_stale = true;
+    return PIC_OK;
+}
+
+template <typename T>
+static int stats_t(Sim<T> *s, pic_stats *out) {
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return fail(PIC_ERR_CUDA, "%s", cudaGetErrorString(e));
+    int err = 0;
+    CUDA_TRY(cudaMemcpy(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    std::vector<uint8_t> st((size_t)s->p.n);
+    if (s->p.n) CUDA_TRY(cudaMemcpy(st.data(), s->p.status, (size_t)s->p.n, cudaMemcpyDeviceToHost));
+    long long fr = 0;
+    for (auto v : st) fr += v != 0;
+    out->step = s->step_host;
+    out->n_particles = s->p.n;
+    out->n_frozen = fr;
+    out->device_error = err;
+    out->n_edge_classes = s->n_classes;
+    return PIC_OK;
+}
+
+extern "C" {
+
+const char *pic_last_error(void) { return g_err.c_str(); }
+
+int pic_workspace_size(const pic_config *cfg, size_t *bytes) {
+    g_err.clear();
+    int rc = validate(cfg);
+    if (rc) return rc;
+    if (!bytes) return fail(PIC_ERR_ARG, "bytes is NULL");
+    Arena a;
+    if (cfg->precision == PIC_FP64) {
+        Sim<double> s;
+        s.init_geometry(cfg);
+        s.plan(a);
+    } else {
+        Sim<float> s;
+        s.init_geometry(cfg);
+        s.plan(a);
+    }
+    *bytes = a.used;
+    return PIC_OK;
+}
+
+int pic_create(const pic_config *cfg, pic_handle **out) {
+    g_err.clear();
+    if (!out) return fail(PIC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int rc = validate(cfg);
+    if (rc) return rc;
+    pic_handle *h = new pic_handle;
+    h->precision = cfg->precision;
+    if (cfg->precision == PIC_FP64) {
+        auto *s = new Sim<double>;
+        h->sim = s;
+        rc = s->create(cfg);
+    } else {
+        auto *s = new Sim<float>;
+        h->sim = s;
+        rc = s->create(cfg);
+    }
+    if (rc) {
+        std::string msg = g_err;
+        delete h->sim;
+        delete h;
+        g_err = msg;
+        return rc;
+    }
+    *out = h;
+    return PIC_OK;
+}
+
+int pic_destroy(pic_handle *h) {
+    g_err.clear();
+    if (!h) return PIC_OK;
+    delete h->sim;
+    delete h;
+    return PIC_OK;
+}
+
+int pic_set_stream(pic_handle *h, void *stream) {
+    g_err.clear();
+    if (!h) return fail(PIC_ERR_ARG, "NULL handle");
+    auto apply = [&](auto *s) -> int {
+        CUDA_TRY(cudaStreamSynchronize(s->stream));
+        s->drop_graph();
+        if (s->own_stream) { cudaStreamDestroy(s->stream); s->own_stream = false; }
+        if (stream) {
+            s->stream = (cudaStream_t)stream;
+        } else {
+            CUDA_TRY(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+            s->own_stream = true;
+        }
+        return PIC_OK;
+    };
+    return h->precision == PIC_FP64 ? apply(S<double>(h)) : apply(S<float>(h));
+}
+
+int pic_add_particles(pic_handle *h, int64_t n, const double *xyz, const double *u, double q_macro,
+                      double m_macro, int64_t *n_rejected) {
+    g_err.clear();
+    if (!h) return fail(PIC_ERR_ARG, "NULL handle");
+    return h->precision == PIC_FP64 ? add_particles_t(S<double>(h), n, xyz, u, q_macro, m_macro, n_rejected)
+                                    : add_particles_t(S<float>(h), n, xyz, u, q_macro, m_macro, n_rejected);
+}
+
+int pic_get_particles(pic_handle *h, double *xyz, double *u, uint8_t *status) {
+    g_err.clear();
+    if (!h) return fail(PIC_ERR_ARG, "NULL handle");
+    return h->precision == PIC_FP64 ? get_particles_t(S<double>(h), xyz, u, status)
+                                    : get_particles_t(S<float>(h), xyz, u, status);
+}
+
+int pic_set_deposit(pic_handle *h, int on) {
+    g_err.clear();
+    if (!h) return fail(PIC_ERR_ARG, "NULL handle");
+    if (h->precision == PIC_FP64) { S<double>(h)->pp.deposit = on != 0; S<double>(h)->drop_graph(); }
+    else { S<float>(h)->pp.deposit = on != 0; S<float>(h)->drop_graph(); }
+    return PIC_OK;
+}
+
+int pic_add_source(pic_handle *h, int comp, const int64_t *box, double amp, double t0, double tau, double f0) {
+    g_err.clear();
+    if (!h || !box) return fail(PIC_ERR_ARG, "NULL argument");
+    if (comp < 0 || comp > 2 || !(tau > 0.0) || f0 < 0.0) return fail(PIC_ERR_ARG, "bad source parameters");
+    auto apply = [&](auto *s) -> int {
+        if ((int)s->sources.size() >= MAX_SOURCES) return fail(PIC_ERR_ARG, "at most %d sources", MAX_SOURCES);
+        Source src{};
+        src.comp = comp;
+        for (int a = 0; a < 3; a++) {
+            if (box[2 * a] < 0 || box[2 * a + 1] > s->n[a] || box[2 * a] >= box[2 * a + 1])
+                return fail(PIC_ERR_ARG, "source box outside the grid on axis %d", a);
+            src.box[2 * a] = (int)box[2 * a];
+            src.box[2 * a + 1] = (int)box[2 * a + 1];
+        }
+        src.amp = amp; src.t0 = t0; src.tau = tau; src.f0 = f0;
+        s->sources.push_back(src);
+        s->drop_graph();
+        return PIC_OK;
+    };
+    return h->precision == PIC_FP64 ? apply(S<double>(h)) : apply(S<float>(h));
+}
+
+int pic_probe_dft(pic_handle *h, int np, const double *xyz, uint32_t comp_mask, int nf, const double *freq_hz) {
+    g_err.clear();
+    if (!h) return fail(PIC_ERR_ARG, "NULL handle");
+    return h->precision == PIC_FP64 ? probe_dft_t(S<double>(h), np, xyz, comp_mask, nf, freq_hz)
+                                    : probe_dft_t(S<float>(h), np, xyz, comp_mask, nf, freq_hz);
+}
+
+int pic_step(pic_handle *h, int64_t nsteps) {
+    g_err.clear();
+    if (!h) return fail(PIC_ERR_ARG, "NULL handle");
+    return DISPATCH(h, step(nsteps));
+}
+
+int pic_sync(pic_handle *h) {
+    g_err.clear();
+    if (!h) return fail(PIC_ERR_ARG, "NULL handle");
+    return DISPATCH(h, sync());
+}
+
+int pic_probe_read(pic_handle *h, double *out) {
+    g_err.clear();
+    if (!h || !out) return fail(PIC_ERR_ARG, "NULL argument");
+    return h->precision == PIC_FP64 ? probe_read_t(S<double>(h), out) : probe_read_t(S<float>(h), out);
+}
+
+int pic_get_field(pic_handle *h, int which, double *out) {
+    g_err.clear();
+    if (!h) return fail(PIC_ERR_ARG, "NULL handle");
+    return h->precision == PIC_FP64 ? get_field_t(S<double>(h), which, out) : get_field_t(S<float>(h), which, out);
+}
+
+int pic_set_field(pic_handle *h, int which, const double *in) {
+    g_err.clear();
+    if (!h) return fail(PIC_ERR_ARG, "NULL handle");
+    return h->precision == PIC_FP64 ? set_field_t(S<double>(h), which, in) : set_field_t(S<float>(h), which, in);
+}
+
+int pic_get_stats(pic_handle *h, pic_stats *out) {
+    g_err.clear();
+    if (!h || !out) return fail(PIC_ERR_ARG, "NULL argument");
+    return h->precision == PIC_FP64 ? stats_t(S<double>(h), out) : stats_t(S<float>(h), out);
+}
+
+int pic_profile_steps(pic_handle *h, int64_t nsteps, double *out_us) {
+    g_err.clear();
+    if (!h || !out_us) return fail(PIC_ERR_ARG, "NULL argument");
+    return DISPATCH(h, profile_steps(nsteps, out_us));
+}
+
+}  // extern "C"

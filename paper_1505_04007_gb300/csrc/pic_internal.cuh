@@ -1,0 +1,112 @@
+// pic_internal.cuh -- device-side data views and kernel launchers shared by
+// the translation units of libpic.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pic {
+
+// Tiles that carry the "free current was deposited here this step" flag.
+constexpr int TILE_X = 32, TILE_Y = 4, TILE_Z = 4;
+// Probe samples buffered on the device between DFT flushes (one graph).
+constexpr int DFT_BLOCK = 64;
+constexpr int MAX_SOURCES = 16;
+
+// Device error bits.
+enum : int {
+    DEVERR_JUMP = 1,       // a particle moved more than one cell in a step
+    DEVERR_NONFINITE = 2,  // non-finite momentum in the pusher
+};
+
+// Grid geometry and scalar coefficients, passed by value to every kernel.
+template <typename T>
+struct Grid {
+    int n[3];        // nx, ny, nz
+    int per[3];      // axis is periodic
+    int cpml[3];     // axis has absorbing slabs (psi storage exists)
+    int L;           // slab thickness in cells
+    T r[3];          // 1/dx, 1/dy, 1/dz
+    T cH;            // dt/mu0
+    int nt[3];       // flag tiles per axis
+    long long ncell;
+};
+
+// The two field components that carry a derivative along axis a.
+__host__ __device__ inline int psi_comp(int a, int s) { return (a + 1 + s) % 3; }
+
+template <typename T>
+struct Fields {
+    T *E[3], *H[3], *Jp[3], *Jf[3];
+    // psi[a][s]: derivative along axis a of the (a+1+s)%3 component's curl
+    // term; compact storage over the 2L slab cells of axis a.
+    T *psiH[3][2], *psiE[3][2];
+    const T *bE[3], *aE[3], *ikE[3];  // CPML profile at integer positions
+    const T *bH[3], *aH[3], *ikH[3];  // CPML profile at half-integer positions
+    const uint8_t *ecls[3];           // edge class per E component
+    const T *cls_kJ, *cls_bJ, *cls_cE; // per-class Eq. 6 / Eq. 8 factors
+    const uint8_t *cls_metal;         // per-class: wp^2 > 0
+    int *jf_flag;                     // per tile: step+1 when J_f was written
+    const long long *step;            // device step counter n
+};
+
+template <typename T>
+struct Particles {
+    int *cell[3];      // integer cell of the position
+    T *off[3];         // offset within the cell, [0,1)
+    T *u[3];           // gamma*v [m/s]
+    T *bold[3];        // H^{n-1/2} gathered at x^n (carried from the last push)
+    uint8_t *status;   // 0 live, 1 frozen
+    long long *id;     // input order
+    long long n;
+};
+
+template <typename T>
+struct PushParams {
+    T qmdt2;        // q dt / (2 m)
+    T inv_c2;       // 1/c^2
+    T dtd[3];       // dt / d_a
+    T mu0;
+    T jscale[3];    // -q / (dt d_a1 d_a2) for the J_a deposit
+    const uint8_t *mat;       // cell material id
+    const uint8_t *mat_metal; // per material id: wp > 0
+    int deposit;
+    int *err;
+};
+
+template <typename T>
+struct Probes {
+    int np, nf;
+    unsigned mask;
+    const double *xyz_cells;  // [np][3] positions in cell units
+    const double *freq;       // [nf]
+    double *samples;          // [DFT_BLOCK][np][3]
+    double *F;                // [np][3][nf][2]
+    double *phasor;           // [DFT_BLOCK][nf][2]
+    double dt;
+};
+
+struct Source {
+    int comp;
+    int box[6];
+    double amp, t0, tau, f0;
+};
+
+// ---------------------------------------------------------------- launchers
+template <typename T> void launch_update_H(const Grid<T> &g, const Fields<T> &f, cudaStream_t s);
+template <typename T> void launch_update_E(const Grid<T> &g, const Fields<T> &f, cudaStream_t s);
+template <typename T>
+void launch_push_deposit(const Grid<T> &g, const Fields<T> &f, const Particles<T> &p,
+                         const PushParams<T> &pp, cudaStream_t s);
+template <typename T>
+void launch_gather_bold(const Grid<T> &g, const Fields<T> &f, const Particles<T> &p, cudaStream_t s);
+template <typename T>
+void launch_sources(const Grid<T> &g, const Fields<T> &f, const Source *src, int nsrc, double dt,
+                    cudaStream_t s);
+template <typename T>
+void launch_step_tail(const Grid<T> &g, const Fields<T> &f, const Probes<T> &pr, long long *step,
+                      cudaStream_t s);
+template <typename T>
+void launch_dft_flush(const Probes<T> &pr, const long long *step, int count, cudaStream_t s);
+
+}  // namespace pic

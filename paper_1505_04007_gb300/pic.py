@@ -1,0 +1,313 @@
+"""Python binding of libpic (include/pic.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method; all of the time step runs in the CUDA kernels of
+libpic.  The library must be built for the GPU (``build.build()``); if it is
+missing or cannot be loaded, loading raises instead of falling back to
+anything else.
+
+``Simulation`` is a convenience wrapper that builds a ``pic_config`` from a
+``workloads.Workload``, takes its device memory from PyTorch (one uint8
+tensor handed to the library as its workspace) and runs on a PyTorch stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+PIC_OK = 0
+PIC_FP32, PIC_FP64 = 0, 1
+PIC_EX, PIC_EY, PIC_EZ, PIC_HX, PIC_HY, PIC_HZ, PIC_JPX, PIC_JPY, PIC_JPZ, PIC_JFX, PIC_JFY, PIC_JFZ = range(12)
+
+ERRORS = {-1: "PIC_ERR_ARG", -2: "PIC_ERR_CFL", -3: "PIC_ERR_OOM", -4: "PIC_ERR_CUDA", -5: "PIC_ERR_NONFINITE",
+          -6: "PIC_ERR_STATE", -7: "PIC_ERR_UNSUPPORTED", -8: "PIC_ERR_DEVICE"}
+
+# Names the header declares; tests check the library exports each of them.
+EXPORTS = ("pic_last_error", "pic_workspace_size", "pic_create", "pic_destroy", "pic_set_stream",
+           "pic_add_particles", "pic_get_particles", "pic_set_deposit", "pic_add_source", "pic_probe_dft",
+           "pic_step", "pic_sync", "pic_probe_read", "pic_get_field", "pic_set_field", "pic_get_stats",
+           "pic_profile_steps")
+
+
+class pic_material(C.Structure):
+    _fields_ = [("wp", C.c_double), ("gamma", C.c_double), ("eps_inf", C.c_double)]
+
+
+class pic_config(C.Structure):
+    _fields_ = [("nx", C.c_int64), ("ny", C.c_int64), ("nz", C.c_int64),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double), ("dt", C.c_double),
+                ("eps0", C.c_double), ("mu0", C.c_double),
+                ("precision", C.c_int32), ("bc", C.c_int32 * 6),
+                ("cpml_cells", C.c_int32), ("cpml_order", C.c_double), ("cpml_sigma_fac", C.c_double),
+                ("cpml_kappa_max", C.c_double), ("cpml_alpha_max", C.c_double),
+                ("material_id", C.POINTER(C.c_uint8)), ("materials", C.POINTER(pic_material)),
+                ("n_materials", C.c_int32), ("max_particles", C.c_int64), ("max_probes", C.c_int32),
+                ("max_freqs", C.c_int32), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t),
+                ("stream", C.c_void_p), ("flags", C.c_uint64)]
+
+
+class pic_stats(C.Structure):
+    _fields_ = [("step", C.c_int64), ("n_particles", C.c_int64), ("n_frozen", C.c_int64),
+                ("device_error", C.c_int32), ("n_edge_classes", C.c_int32)]
+
+
+class PicError(RuntimeError):
+    def __init__(self, code, where):
+        msg = _lib.pic_last_error().decode() if _lib is not None else ""
+        super().__init__(f"{where}: {ERRORS.get(code, code)} {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libpic (building it first if sources are newer).  Raises if the
+    library cannot be built or loaded: there is no other implementation."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpic not found at {path}")
+    L = C.CDLL(path)
+    h = C.c_void_p
+    dp = C.POINTER(C.c_double)
+    L.pic_last_error.restype = C.c_char_p
+    L.pic_workspace_size.argtypes = [C.POINTER(pic_config), C.POINTER(C.c_size_t)]
+    L.pic_create.argtypes = [C.POINTER(pic_config), C.POINTER(h)]
+    L.pic_destroy.argtypes = [h]
+    L.pic_set_stream.argtypes = [h, C.c_void_p]
+    L.pic_add_particles.argtypes = [h, C.c_int64, dp, dp, C.c_double, C.c_double, C.POINTER(C.c_int64)]
+    L.pic_get_particles.argtypes = [h, dp, dp, C.POINTER(C.c_uint8)]
+    L.pic_set_deposit.argtypes = [h, C.c_int]
+    L.pic_add_source.argtypes = [h, C.c_int, C.POINTER(C.c_int64), C.c_double, C.c_double, C.c_double, C.c_double]
+    L.pic_probe_dft.argtypes = [h, C.c_int, dp, C.c_uint32, C.c_int, dp]
+    L.pic_step.argtypes = [h, C.c_int64]
+    L.pic_sync.argtypes = [h]
+    L.pic_probe_read.argtypes = [h, dp]
+    L.pic_get_field.argtypes = [h, C.c_int, dp]
+    L.pic_set_field.argtypes = [h, C.c_int, dp]
+    L.pic_get_stats.argtypes = [h, C.POINTER(pic_stats)]
+    L.pic_profile_steps.argtypes = [h, C.c_int64, dp]
+    _lib = L
+    return L
+
+
+def _check(rc, where):
+    if rc != PIC_OK:
+        raise PicError(rc, where)
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+# --------------------------------------------------------------- C names --
+def pic_last_error() -> str:
+    return load().pic_last_error().decode()
+
+
+def pic_workspace_size(cfg: pic_config) -> int:
+    n = C.c_size_t(0)
+    _check(load().pic_workspace_size(C.byref(cfg), C.byref(n)), "pic_workspace_size")
+    return n.value
+
+
+def pic_create(cfg: pic_config) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(load().pic_create(C.byref(cfg), C.byref(h)), "pic_create")
+    return h
+
+
+def pic_destroy(h) -> None:
+    _check(load().pic_destroy(h), "pic_destroy")
+
+
+def pic_set_stream(h, stream: int | None) -> None:
+    _check(load().pic_set_stream(h, C.c_void_p(stream or None)), "pic_set_stream")
+
+
+def pic_add_particles(h, xyz: np.ndarray, u: np.ndarray, q_macro: float, m_macro: float) -> None:
+    x = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    v = np.ascontiguousarray(u, dtype=np.float64).reshape(-1, 3)
+    bad = C.c_int64(0)
+    _check(load().pic_add_particles(h, x.shape[0], _dp(x), _dp(v), q_macro, m_macro, C.byref(bad)),
+           "pic_add_particles")
+
+
+def pic_get_particles(h, n: int):
+    x = np.empty((n, 3)); u = np.empty((n, 3)); s = np.empty(n, dtype=np.uint8)
+    _check(load().pic_get_particles(h, _dp(x), _dp(u), s.ctypes.data_as(C.POINTER(C.c_uint8))),
+           "pic_get_particles")
+    return x, u, s
+
+
+def pic_set_deposit(h, on: bool) -> None:
+    _check(load().pic_set_deposit(h, int(bool(on))), "pic_set_deposit")
+
+
+def pic_add_source(h, comp, box, amp, t0, tau, f0=0.0) -> None:
+    b = (C.c_int64 * 6)(*[int(v) for v in box])
+    _check(load().pic_add_source(h, int(comp), b, amp, t0, tau, f0), "pic_add_source")
+
+
+def pic_probe_dft(h, xyz, comp_mask, freqs) -> None:
+    p = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    f = np.ascontiguousarray(freqs, dtype=np.float64)
+    _check(load().pic_probe_dft(h, p.shape[0], _dp(p), int(comp_mask), f.size, _dp(f)), "pic_probe_dft")
+
+
+def pic_step(h, nsteps: int) -> None:
+    _check(load().pic_step(h, int(nsteps)), "pic_step")
+
+
+def pic_sync(h) -> None:
+    _check(load().pic_sync(h), "pic_sync")
+
+
+def pic_probe_read(h, nprobe: int, nfreq: int) -> np.ndarray:
+    out = np.empty(nprobe * 3 * nfreq * 2)
+    _check(load().pic_probe_read(h, _dp(out)), "pic_probe_read")
+    z = out.reshape(nprobe, 3, nfreq, 2)
+    return z[..., 0] + 1j * z[..., 1]
+
+
+def pic_get_field(h, which: int, shape) -> np.ndarray:
+    out = np.empty(int(np.prod(shape)))
+    _check(load().pic_get_field(h, int(which), _dp(out)), "pic_get_field")
+    return out.reshape(shape)
+
+
+def pic_set_field(h, which: int, arr) -> None:
+    a = np.ascontiguousarray(arr, dtype=np.float64).reshape(-1)
+    _check(load().pic_set_field(h, int(which), _dp(a)), "pic_set_field")
+
+
+def pic_get_stats(h) -> pic_stats:
+    s = pic_stats()
+    _check(load().pic_get_stats(h, C.byref(s)), "pic_get_stats")
+    return s
+
+
+def pic_profile_steps(h, nsteps: int) -> dict:
+    out = np.zeros(6)
+    _check(load().pic_profile_steps(h, int(nsteps), _dp(out)), "pic_profile_steps")
+    keys = ("update_H", "push_deposit", "update_E", "step_tail", "dft_flush", "step")
+    return dict(zip(keys, out.tolist()))
+
+
+# ------------------------------------------------------------ convenience --
+def make_config(w, precision=PIC_FP32, max_particles=None, max_probes=None, max_freqs=None,
+                eps0=None, mu0=None) -> tuple[pic_config, tuple]:
+    """pic_config for a Workload; returns (cfg, keepalive) where keepalive
+    holds the host arrays the config points to."""
+    from . import workloads as W
+    mat = np.ascontiguousarray(w.material, dtype=np.uint8)
+    tab = (pic_material * len(w.table))(*[pic_material(*map(float, r)) for r in w.table])
+    cfg = pic_config()
+    cfg.nx, cfg.ny, cfg.nz = w.nx, w.ny, w.nz
+    cfg.dx, cfg.dy, cfg.dz, cfg.dt = w.dx, w.dy, w.dz, w.dt
+    cfg.eps0 = W.EPS0 if eps0 is None else eps0
+    cfg.mu0 = W.MU0 if mu0 is None else mu0
+    cfg.precision = precision
+    cfg.bc = (C.c_int32 * 6)(*w.bc)
+    cfg.cpml_cells = w.cpml_cells
+    cfg.cpml_order = w.cpml_order
+    cfg.cpml_sigma_fac = w.cpml_sigma_fac
+    cfg.cpml_kappa_max = w.cpml_kappa_max
+    cfg.cpml_alpha_max = w.cpml_alpha_max
+    cfg.material_id = mat.ctypes.data_as(C.POINTER(C.c_uint8))
+    cfg.materials = tab
+    cfg.n_materials = len(w.table)
+    cfg.max_particles = w.nparticles if max_particles is None else max_particles
+    nprobe = 0 if w.probes is None else len(w.probes)
+    nfreq = 0 if w.freqs is None else len(w.freqs)
+    cfg.max_probes = nprobe if max_probes is None else max_probes
+    cfg.max_freqs = nfreq if max_freqs is None else max_freqs
+    cfg.flags = 0
+    return cfg, (mat, tab)
+
+
+class Simulation:
+    """One libpic handle for a Workload, with PyTorch-owned device memory."""
+
+    def __init__(self, w, precision=PIC_FP32, particles=True, probes=True, torch_memory=True,
+                 stream=None, **cap):
+        import torch
+        self.w = w
+        self.shape = (w.nz, w.ny, w.nx)
+        cfg, self._keep = make_config(w, precision, **cap)
+        self._ws = None
+        if torch_memory:
+            nbytes = pic_workspace_size(cfg)
+            self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+            base = self._ws.data_ptr()
+            aligned = (base + 255) & ~255
+            cfg.workspace = C.c_void_p(aligned)
+            cfg.workspace_bytes = nbytes
+        if stream is None:
+            self._stream = torch.cuda.Stream()
+        else:
+            self._stream = stream
+        cfg.stream = C.c_void_p(self._stream.cuda_stream)
+        self.h = pic_create(cfg)
+        self.n = 0
+        self.nprobe = 0
+        self.nfreq = 0
+        if particles and w.nparticles:
+            self.add_particles(w.xyz, w.u, w.q_macro, w.m_macro)
+        if probes and w.probes is not None and w.freqs is not None:
+            self.probe_dft(w.probes, w.freqs, w.comp_mask)
+
+    @property
+    def stream(self):
+        return self._stream
+
+    def add_particles(self, xyz, u, q, m):
+        pic_add_particles(self.h, xyz, u, q, m)
+        self.n += len(xyz)
+
+    def probe_dft(self, xyz, freqs, mask=0b111):
+        pic_probe_dft(self.h, xyz, mask, freqs)
+        self.nprobe, self.nfreq = len(np.asarray(xyz).reshape(-1, 3)), len(freqs)
+
+    def step(self, n=1):
+        pic_step(self.h, n)
+
+    def sync(self):
+        pic_sync(self.h)
+
+    def field(self, which):
+        return pic_get_field(self.h, which, self.shape)
+
+    def set_field(self, which, arr):
+        pic_set_field(self.h, which, arr)
+
+    def particles(self):
+        return pic_get_particles(self.h, self.n)
+
+    def probe_read(self):
+        return pic_probe_read(self.h, self.nprobe, self.nfreq)
+
+    def stats(self):
+        return pic_get_stats(self.h)
+
+    def profile(self, nsteps):
+        return pic_profile_steps(self.h, nsteps)
+
+    def close(self):
+        if getattr(self, "h", None):
+            pic_destroy(self.h)
+            self.h = None
+            self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,81 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every
+entry point include/pic.h declares, and rejects invalid configurations on the
+host before touching the device."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1505_04007_gb300 import pic as P
+from paper_1505_04007_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "pic.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char \*)\s*(pic_\w+)\s*\(", src, re.M)))
+
+
+def test_header_matches_binding_list():
+    assert declared_functions() == sorted(P.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    L = P.load()
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_struct_layout_matches_header():
+    # offsets of the trailing fields pin the ctypes mirror to the C layout
+    assert C.sizeof(P.pic_material) == 24
+    assert P.pic_config.flags.offset == C.sizeof(P.pic_config) - 8
+    assert C.sizeof(P.pic_stats) == 32
+
+
+def _cfg(**kw):
+    w = W.c1(nsteps=0)
+    for k, v in kw.items():
+        setattr(w, k, v)
+    cfg, keep = P.make_config(w, P.PIC_FP32)
+    return cfg, keep, w
+
+
+def test_workspace_size_is_host_only_and_scales():
+    cfg, keep, w = _cfg()
+    n32 = P.pic_workspace_size(cfg)
+    cfg.precision = P.PIC_FP64
+    n64 = P.pic_workspace_size(cfg)
+    # 12 state arrays per cell in the state precision plus 4 bytes of tables
+    assert n32 >= w.ncells * (12 * 4 + 4)
+    assert n64 > n32
+
+
+@pytest.mark.parametrize("mutate,code", [
+    (lambda c: setattr(c, "dt", c.dt * 2.5), -2),                        # CFL
+    (lambda c: c.bc.__setitem__(0, W.BC_PERIODIC), -1),                   # unpaired periodic
+    (lambda c: setattr(c, "cpml_cells", 40), -1),                         # slabs do not fit
+    (lambda c: setattr(c, "precision", 7), -1),
+    (lambda c: setattr(c, "flags", 1), -1),
+    (lambda c: setattr(c, "n_materials", 0), -1),
+])
+def test_create_rejects_invalid_config_on_host(mutate, code):
+    cfg, keep, _ = _cfg()
+    mutate(cfg)
+    h = C.c_void_p()
+    rc = P.load().pic_create(C.byref(cfg), C.byref(h))
+    assert rc == code
+    assert not h.value
+    assert P.pic_last_error() != ""
+
+
+def test_cfl_bound_includes_drude_term():
+    # a plasma frequency high enough to break wp^2 dt^2/4 < 1 - c^2 dt^2 sum(1/d^2)
+    cfg, keep, w = _cfg()
+    tab = (P.pic_material * 2)(P.pic_material(0, 0, 1), P.pic_material(1.8 / cfg.dt, 0, 1))
+    cfg.materials = tab
+    h = C.c_void_p()
+    assert P.load().pic_create(C.byref(cfg), C.byref(h)) == -2
