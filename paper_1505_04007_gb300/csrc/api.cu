@@ -172,6 +172,7 @@ struct Sim : SimBase {
             p.cell[c] = a.take<int>(mp);
             p.off[c] = a.take<T>(mp);
             p.u[c] = a.take<T>(mp);
+            p.ulo[c] = a.take<T>(mp);
             p.bold[c] = a.take<T>(mp);
         }
         p.status = a.take<uint8_t>(mp);
@@ -205,7 +206,7 @@ struct Sim : SimBase {
         n_tiles = (size_t)g.nt[0] * g.nt[1] * g.nt[2];
     }
 
-    // CPML grading at position pos (cell units) along axis a.
+    // CPML grading at position pos (cell units) along axis a: b-1, a, 1/kappa.
     void profile(int a, double pos, double &b, double &aa, double &ik) const {
         const double L = cfg.cpml_cells;
         double rho = 0.0;
@@ -213,15 +214,15 @@ struct Sim : SimBase {
             if (cfg.bc[2 * a] == PIC_BC_CPML && pos < L) rho = L - pos;
             if (cfg.bc[2 * a + 1] == PIC_BC_CPML && pos > n[a] - L) rho = std::max(rho, pos - (n[a] - L));
         }
-        if (rho <= 0.0) { b = 1.0; aa = 0.0; ik = 1.0; return; }
+        if (rho <= 0.0) { b = 0.0; aa = 0.0; ik = 1.0; return; }
         const double eta0 = std::sqrt(cfg.mu0 / cfg.eps0);
         const double x = rho / L, xm = std::pow(x, cfg.cpml_order);
         const double sigma = cfg.cpml_sigma_fac * (cfg.cpml_order + 1.0) / (eta0 * d[a]) * xm;
         const double kappa = 1.0 + (cfg.cpml_kappa_max - 1.0) * xm;
         const double alpha = cfg.cpml_alpha_max * (1.0 - x);
-        b = std::exp(-(sigma / kappa + alpha) * cfg.dt / cfg.eps0);
+        b = std::expm1(-(sigma / kappa + alpha) * cfg.dt / cfg.eps0);  // b - 1
         const double den = sigma * kappa + kappa * kappa * alpha;
-        aa = (sigma > 0.0 && den > 0.0) ? sigma * (b - 1.0) / den : 0.0;
+        aa = (sigma > 0.0 && den > 0.0) ? sigma * b / den : 0.0;
         ik = 1.0 / kappa;
     }
 
@@ -275,7 +276,7 @@ struct Sim : SimBase {
                                 }
                                 const double wp2 = sw / 4.0, gam = sw > 0 ? swg / sw : 0.0, einf = se / 4.0;
                                 const double dt = c->dt;
-                                cls[0][cl] = (T)((2.0 - gam * dt) / (2.0 + gam * dt));
+                                cls[0][cl] = (T)(-2.0 * gam * dt / (2.0 + gam * dt));  // kJ - 1
                                 cls[1][cl] = (T)(2.0 * dt * c->eps0 * wp2 / (2.0 + gam * dt));
                                 cls[2][cl] = (T)(dt / (c->eps0 * einf));
                                 cls_metal[cl] = wp2 > 0.0;
@@ -341,7 +342,7 @@ struct Sim : SimBase {
         for (int q3 = 0; q3 < 3; q3++)
             CUDA_TRY(cudaMemcpyAsync(d_cls[q3], cls[q3].data(), 256 * sizeof(T), cudaMemcpyHostToDevice, stream));
         CUDA_TRY(cudaMemcpyAsync(d_cls_metal, cls_metal.data(), 256, cudaMemcpyHostToDevice, stream));
-        // CPML profiles: per axis bE aE ikE bH aH ikH
+        // CPML profiles: per axis (b-1, a, 1/kappa) at E positions, then at H positions
         for (int a = 0; a < 3; a++) {
             std::vector<T> pf[6];
             for (auto &v : pf) v.resize(n[a]);
@@ -363,7 +364,7 @@ struct Sim : SimBase {
             f.bH[a] = d_prof[a * 6 + 3]; f.aH[a] = d_prof[a * 6 + 4]; f.ikH[a] = d_prof[a * 6 + 5];
             f.ecls[a] = d_ecls[a];
         }
-        f.cls_kJ = d_cls[0]; f.cls_bJ = d_cls[1]; f.cls_cE = d_cls[2];
+        f.cls_kJm1 = d_cls[0]; f.cls_bJ = d_cls[1]; f.cls_cE = d_cls[2];
         f.cls_metal = d_cls_metal;
         f.jf_flag = d_flag;
         f.step = d_step;
@@ -546,8 +547,8 @@ static int add_particles_t(Sim<T> *s, int64_t n, const double *xyz, const double
         return fail(PIC_ERR_OOM, "%lld particles exceed max_particles=%lld", (long long)(s->p.n + n),
                     (long long)s->cfg.max_particles);
     std::vector<int> cell[3];
-    std::vector<T> off[3], uu[3];
-    for (int a = 0; a < 3; a++) { cell[a].resize(n); off[a].resize(n); uu[a].resize(n); }
+    std::vector<T> off[3], uu[3], ulo[3];
+    for (int a = 0; a < 3; a++) { cell[a].resize(n); off[a].resize(n); uu[a].resize(n); ulo[a].resize(n); }
     std::vector<uint8_t> mat((size_t)s->N);
     int64_t bad = 0;
     // the material map lives on the device; copy it once for the check
@@ -576,6 +577,7 @@ static int add_particles_t(Sim<T> *s, int64_t n, const double *xyz, const double
             if (ot >= T(1)) ot = std::nextafter(T(1), T(0));
             off[a][q2] = ot;
             uu[a][q2] = (T)u[3 * q2 + a];
+            ulo[a][q2] = (T)(u[3 * q2 + a] - (double)uu[a][q2]);
         }
         if (ok && metal[mat[((size_t)c3[2] * s->n[1] + c3[1]) * s->n[0] + c3[0]]]) ok = false;
         if (!ok) bad++;
@@ -589,6 +591,7 @@ static int add_particles_t(Sim<T> *s, int64_t n, const double *xyz, const double
         CUDA_TRY(cudaMemcpyAsync(s->p.cell[a] + base, cell[a].data(), n * sizeof(int), cudaMemcpyHostToDevice, s->stream));
         CUDA_TRY(cudaMemcpyAsync(s->p.off[a] + base, off[a].data(), n * sizeof(T), cudaMemcpyHostToDevice, s->stream));
         CUDA_TRY(cudaMemcpyAsync(s->p.u[a] + base, uu[a].data(), n * sizeof(T), cudaMemcpyHostToDevice, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(s->p.ulo[a] + base, ulo[a].data(), n * sizeof(T), cudaMemcpyHostToDevice, s->stream));
     }
     CUDA_TRY(cudaMemcpyAsync(s->p.id + base, ids.data(), n * sizeof(long long), cudaMemcpyHostToDevice, s->stream));
     CUDA_TRY(cudaMemsetAsync(s->p.status + base, 0, (size_t)n, s->stream));
@@ -613,11 +616,12 @@ static int get_particles_t(Sim<T> *s, double *xyz, double *u, uint8_t *status) {
     if (rc) return rc;
     const long long n = s->p.n;
     std::vector<int> cell[3];
-    std::vector<T> off[3], uu[3];
+    std::vector<T> off[3], uu[3], ul[3];
     std::vector<uint8_t> st(n);
     std::vector<long long> id(n);
     for (int a = 0; a < 3; a++) {
-        cell[a].resize(n); off[a].resize(n); uu[a].resize(n);
+        cell[a].resize(n); off[a].resize(n); uu[a].resize(n); ul[a].resize(n);
+        CUDA_TRY(cudaMemcpy(ul[a].data(), s->p.ulo[a], n * sizeof(T), cudaMemcpyDeviceToHost));
         CUDA_TRY(cudaMemcpy(cell[a].data(), s->p.cell[a], n * sizeof(int), cudaMemcpyDeviceToHost));
         CUDA_TRY(cudaMemcpy(off[a].data(), s->p.off[a], n * sizeof(T), cudaMemcpyDeviceToHost));
         CUDA_TRY(cudaMemcpy(uu[a].data(), s->p.u[a], n * sizeof(T), cudaMemcpyDeviceToHost));
@@ -629,7 +633,7 @@ static int get_particles_t(Sim<T> *s, double *xyz, double *u, uint8_t *status) {
         if (o < 0 || o >= n) return fail(PIC_ERR_DEVICE, "corrupt particle id");
         for (int a = 0; a < 3; a++) {
             if (xyz) xyz[3 * o + a] = ((double)cell[a][q2] + (double)off[a][q2]) * s->d[a];
-            if (u) u[3 * o + a] = (double)uu[a][q2];
+            if (u) u[3 * o + a] = (double)uu[a][q2] + (double)ul[a][q2];
         }
         if (status) status[o] = st[q2];
     }

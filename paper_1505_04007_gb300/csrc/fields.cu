@@ -69,22 +69,22 @@ __global__ void __launch_bounds__(256) k_update_H(Grid<T> g, Fields<T> f) {
         const T b = f.bH[0][i], a = f.aH[0][i];
         kx = f.ikH[0][i];
         const long long q = psi_at(g, 0, s0, i, j, k);
-        pxy = b * f.psiH[0][0][q] + a * dEz_dx; f.psiH[0][0][q] = pxy;  // Hy's d/dx
-        pxz = b * f.psiH[0][1][q] + a * dEy_dx; f.psiH[0][1][q] = pxz;  // Hz's d/dx
+        pxy = f.psiH[0][0][q] + (b * f.psiH[0][0][q] + a * dEz_dx); f.psiH[0][0][q] = pxy;  // Hy's d/dx
+        pxz = f.psiH[0][1][q] + (b * f.psiH[0][1][q] + a * dEy_dx); f.psiH[0][1][q] = pxz;  // Hz's d/dx
     }
     if (s1 >= 0) {
         const T b = f.bH[1][j], a = f.aH[1][j];
         ky = f.ikH[1][j];
         const long long q = psi_at(g, 1, s1, i, j, k);
-        pyz = b * f.psiH[1][0][q] + a * dEx_dy; f.psiH[1][0][q] = pyz;  // Hz's d/dy
-        pyx = b * f.psiH[1][1][q] + a * dEz_dy; f.psiH[1][1][q] = pyx;  // Hx's d/dy
+        pyz = f.psiH[1][0][q] + (b * f.psiH[1][0][q] + a * dEx_dy); f.psiH[1][0][q] = pyz;  // Hz's d/dy
+        pyx = f.psiH[1][1][q] + (b * f.psiH[1][1][q] + a * dEz_dy); f.psiH[1][1][q] = pyx;  // Hx's d/dy
     }
     if (s2 >= 0) {
         const T b = f.bH[2][k], a = f.aH[2][k];
         kz = f.ikH[2][k];
         const long long q = psi_at(g, 2, s2, i, j, k);
-        pzx = b * f.psiH[2][0][q] + a * dEy_dz; f.psiH[2][0][q] = pzx;  // Hx's d/dz
-        pzy = b * f.psiH[2][1][q] + a * dEx_dz; f.psiH[2][1][q] = pzy;  // Hy's d/dz
+        pzx = f.psiH[2][0][q] + (b * f.psiH[2][0][q] + a * dEy_dz); f.psiH[2][0][q] = pzx;  // Hx's d/dz
+        pzy = f.psiH[2][1][q] + (b * f.psiH[2][1][q] + a * dEx_dz); f.psiH[2][1][q] = pzy;  // Hy's d/dz
     }
     const T cx = ky * dEz_dy + pyx - kz * dEy_dz - pzx;
     const T cy = kz * dEx_dz + pzy - kx * dEz_dx - pxy;
@@ -101,7 +101,11 @@ __device__ __forceinline__ void ampere(const Fields<T> &f, int c, long long e, T
     T E = f.E[c][e];
     T jp = T(0);
     if (f.cls_metal[cls]) {
-        jp = f.cls_kJ[cls] * f.Jp[c][e] + f.cls_bJ[cls] * E;
+        // Eq. 6 written as an increment, J += (kJ-1) J + bJ E: the decay factor
+        // kJ = (2-g dt)/(2+g dt) sits within g dt of 1, so kJ-1 (precomputed in
+        // FP64) keeps the collision rate exact in FP32 where kJ itself would not.
+        const T j0 = f.Jp[c][e];
+        jp = j0 + (f.cls_kJm1[cls] * j0 + f.cls_bJ[cls] * E);
         f.Jp[c][e] = jp;
     }
     f.E[c][e] = E + f.cls_cE[cls] * (curl - jp - jf);
@@ -145,12 +149,12 @@ __global__ void __launch_bounds__(256) k_update_E(Grid<T> g, Fields<T> f) {
         if (s1 >= 0) {
             ky = f.ikE[1][j];
             const long long q = psi_at(g, 1, s1, i, j, k);
-            py = f.bE[1][j] * f.psiE[1][1][q] + f.aE[1][j] * dHz_dy; f.psiE[1][1][q] = py;
+            py = f.psiE[1][1][q] + (f.bE[1][j] * f.psiE[1][1][q] + f.aE[1][j] * dHz_dy); f.psiE[1][1][q] = py;
         }
         if (s2 >= 0) {
             kz = f.ikE[2][k];
             const long long q = psi_at(g, 2, s2, i, j, k);
-            pz = f.bE[2][k] * f.psiE[2][0][q] + f.aE[2][k] * dHy_dz; f.psiE[2][0][q] = pz;
+            pz = f.psiE[2][0][q] + (f.bE[2][k] * f.psiE[2][0][q] + f.aE[2][k] * dHy_dz); f.psiE[2][0][q] = pz;
         }
         ampere(f, 0, e, ky * dHz_dy + py - kz * dHy_dz - pz, jf[0]);
     }
@@ -161,12 +165,12 @@ __global__ void __launch_bounds__(256) k_update_E(Grid<T> g, Fields<T> f) {
         if (s2 >= 0) {
             kz = f.ikE[2][k];
             const long long q = psi_at(g, 2, s2, i, j, k);
-            pz = f.bE[2][k] * f.psiE[2][1][q] + f.aE[2][k] * dHx_dz; f.psiE[2][1][q] = pz;
+            pz = f.psiE[2][1][q] + (f.bE[2][k] * f.psiE[2][1][q] + f.aE[2][k] * dHx_dz); f.psiE[2][1][q] = pz;
         }
         if (s0 >= 0) {
             kx = f.ikE[0][i];
             const long long q = psi_at(g, 0, s0, i, j, k);
-            px = f.bE[0][i] * f.psiE[0][0][q] + f.aE[0][i] * dHz_dx; f.psiE[0][0][q] = px;
+            px = f.psiE[0][0][q] + (f.bE[0][i] * f.psiE[0][0][q] + f.aE[0][i] * dHz_dx); f.psiE[0][0][q] = px;
         }
         ampere(f, 1, e, kz * dHx_dz + pz - kx * dHz_dx - px, jf[1]);
     }
@@ -177,12 +181,12 @@ __global__ void __launch_bounds__(256) k_update_E(Grid<T> g, Fields<T> f) {
         if (s0 >= 0) {
             kx = f.ikE[0][i];
             const long long q = psi_at(g, 0, s0, i, j, k);
-            px = f.bE[0][i] * f.psiE[0][1][q] + f.aE[0][i] * dHy_dx; f.psiE[0][1][q] = px;
+            px = f.psiE[0][1][q] + (f.bE[0][i] * f.psiE[0][1][q] + f.aE[0][i] * dHy_dx); f.psiE[0][1][q] = px;
         }
         if (s1 >= 0) {
             ky = f.ikE[1][j];
             const long long q = psi_at(g, 1, s1, i, j, k);
-            py = f.bE[1][j] * f.psiE[1][0][q] + f.aE[1][j] * dHx_dy; f.psiE[1][0][q] = py;
+            py = f.psiE[1][0][q] + (f.bE[1][j] * f.psiE[1][0][q] + f.aE[1][j] * dHx_dy); f.psiE[1][0][q] = py;
         }
         ampere(f, 2, e, kx * dHy_dx + px - ky * dHx_dy - py, jf[2]);
     }

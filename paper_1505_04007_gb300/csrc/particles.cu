@@ -8,7 +8,11 @@
 //   (linear node shapes, 4-node window per axis), and finally
 //   bold <- H^{n+1/2}(x^{n+1}) for the next step.
 // Positions are kept as (integer cell, offset in [0,1)) so FP32 offsets keep
-// full relative precision however large the grid.
+// full relative precision however large the grid.  The momentum is a
+// compensated pair (u + ulo): the Boris step is applied as one increment
+// du = 2 h E + u' x s (u' = u- + u- x t), which is computed to full relative
+// precision, and folded in with an error-free TwoSum, so per-step momentum
+// changes that are ~1e-4 of |u| are not truncated by the FP32 mantissa.
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -76,9 +80,11 @@ __global__ void __launch_bounds__(128) k_push_deposit(Grid<T> g, Fields<T> f, Pa
     const long long step = *f.step;
 
     int c0[3];
-    T o0[3], u[3], E[3], B[3];
+    T o0[3], u[3], ul[3], E[3], B[3];
 #pragma unroll
-    for (int a = 0; a < 3; a++) { c0[a] = p.cell[a][q]; o0[a] = p.off[a][q]; u[a] = p.u[a][q]; }
+    for (int a = 0; a < 3; a++) {
+        c0[a] = p.cell[a][q]; o0[a] = p.off[a][q]; u[a] = p.u[a][q]; ul[a] = p.ulo[a][q];
+    }
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         E[a] = gather(f.E[a], g, c0, o0, STAG_E[a]);
@@ -86,10 +92,10 @@ __global__ void __launch_bounds__(128) k_push_deposit(Grid<T> g, Fields<T> f, Pa
         B[a] = pp.mu0 * T(0.5) * (p.bold[a][q] + hnew);
     }
 
-    // relativistic Boris rotation
-    T um[3], t[3], s[3], up[3];
+    // relativistic Boris rotation, as an increment of u
+    T um[3], t[3], s[3], up[3], du[3];
 #pragma unroll
-    for (int a = 0; a < 3; a++) um[a] = u[a] + pp.qmdt2 * E[a];
+    for (int a = 0; a < 3; a++) um[a] = (u[a] + ul[a]) + pp.qmdt2 * E[a];
     const T gm = sqrt(T(1) + (um[0] * um[0] + um[1] * um[1] + um[2] * um[2]) * pp.inv_c2);
     const T h = pp.qmdt2 / gm;
 #pragma unroll
@@ -101,10 +107,20 @@ __global__ void __launch_bounds__(128) k_push_deposit(Grid<T> g, Fields<T> f, Pa
     up[0] = um[0] + (um[1] * t[2] - um[2] * t[1]);
     up[1] = um[1] + (um[2] * t[0] - um[0] * t[2]);
     up[2] = um[2] + (um[0] * t[1] - um[1] * t[0]);
-    T un[3];
-    un[0] = um[0] + (up[1] * s[2] - up[2] * s[1]) + pp.qmdt2 * E[0];
-    un[1] = um[1] + (up[2] * s[0] - up[0] * s[2]) + pp.qmdt2 * E[1];
-    un[2] = um[2] + (up[0] * s[1] - up[1] * s[0]) + pp.qmdt2 * E[2];
+    du[0] = T(2) * pp.qmdt2 * E[0] + (up[1] * s[2] - up[2] * s[1]);
+    du[1] = T(2) * pp.qmdt2 * E[1] + (up[2] * s[0] - up[0] * s[2]);
+    du[2] = T(2) * pp.qmdt2 * E[2] + (up[0] * s[1] - up[1] * s[0]);
+    T un[3], unl[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        // TwoSum(u, du): exact sum as s + err, then renormalise with the trailing part
+        const T sm = u[a] + du[a];
+        const T bv = sm - u[a];
+        const T err = (u[a] - (sm - bv)) + (du[a] - bv);
+        const T lo = ul[a] + err;
+        un[a] = sm + lo;
+        unl[a] = lo - (un[a] - sm);
+    }
     const T gn = sqrt(T(1) + (un[0] * un[0] + un[1] * un[1] + un[2] * un[2]) * pp.inv_c2);
     if (!isfinite(gn)) { atomicOr(pp.err, DEVERR_NONFINITE); p.status[q] = 1; return; }
     const T ig = T(1) / gn;
@@ -115,7 +131,7 @@ __global__ void __launch_bounds__(128) k_push_deposit(Grid<T> g, Fields<T> f, Pa
     bool frozen = false;
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        T x = o0[a] + un[a] * pp.dtd[a] * ig;
+        T x = o0[a] + (un[a] + unl[a]) * pp.dtd[a] * ig;
         T fl = floor(x);
         int sh = (int)fl;
         x -= fl;
@@ -186,6 +202,7 @@ __global__ void __launch_bounds__(128) k_push_deposit(Grid<T> g, Fields<T> f, Pa
         p.cell[a][q] = c1w[a];
         p.off[a][q] = o1[a];
         p.u[a][q] = un[a];
+        p.ulo[a][q] = unl[a];
     }
 #pragma unroll
     for (int a = 0; a < 3; a++) p.bold[a][q] = gather(f.H[a], g, c1w, o1, STAG_H[a]);

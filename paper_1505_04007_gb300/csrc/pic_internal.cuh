@@ -41,10 +41,12 @@ struct Fields {
     // psi[a][s]: derivative along axis a of the (a+1+s)%3 component's curl
     // term; compact storage over the 2L slab cells of axis a.
     T *psiH[3][2], *psiE[3][2];
-    const T *bE[3], *aE[3], *ikE[3];  // CPML profile at integer positions
-    const T *bH[3], *aH[3], *ikH[3];  // CPML profile at half-integer positions
+    // CPML profiles: b-1, a and 1/kappa at integer (E) and half-integer (H)
+    // positions; psi is advanced as psi += (b-1) psi + a dF.
+    const T *bE[3], *aE[3], *ikE[3];
+    const T *bH[3], *aH[3], *ikH[3];
     const uint8_t *ecls[3];           // edge class per E component
-    const T *cls_kJ, *cls_bJ, *cls_cE; // per-class Eq. 6 / Eq. 8 factors
+    const T *cls_kJm1, *cls_bJ, *cls_cE; // per-class Eq. 6 (kJ-1, bJ) and Eq. 8 factors
     const uint8_t *cls_metal;         // per-class: wp^2 > 0
     int *jf_flag;                     // per tile: step+1 when J_f was written
     const long long *step;            // device step counter n
@@ -54,7 +56,8 @@ template <typename T>
 struct Particles {
     int *cell[3];      // integer cell of the position
     T *off[3];         // offset within the cell, [0,1)
-    T *u[3];           // gamma*v [m/s]
+    T *u[3];           // gamma*v [m/s], leading part
+    T *ulo[3];         // trailing part: gamma*v = u + ulo (compensated sum)
     T *bold[3];        // H^{n-1/2} gathered at x^n (carried from the last push)
     uint8_t *status;   // 0 live, 1 frozen
     long long *id;     // input order

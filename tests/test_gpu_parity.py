@@ -243,5 +243,7 @@ def test_library_allocated_memory_path(P):
     b = P.Simulation(w, P.PIC_FP64, torch_memory=True)
     a.step(80)
     b.step(80)
-    for c in range(6):
-        assert np.array_equal(a.field(c), b.field(c)) or np.allclose(a.field(c), b.field(c), rtol=1e-12, atol=0)
+    fa = [a.field(c) for c in range(6)]
+    fb = [b.field(c) for c in range(6)]
+    # atomics may sum in a different order: compare to rounding, not bitwise
+    assert rel_l2(fa[:3], fb[:3]) <= 1e-13 and rel_l2(fa[3:], fb[3:]) <= 1e-13
