@@ -197,6 +197,31 @@ int pic_get_stats(pic_handle *h, pic_stats *out);
  * Runs real steps (the simulation advances).  Synchronises. */
 int pic_profile_steps(pic_handle *h, int64_t nsteps, double *out_us);
 
+/* Probe-DFT fold that allocates no device memory.  The paper has no
+ * counterpart; this is a service for callers that cannot call cudaMalloc:
+ * code whose device memory is owned entirely by another allocator (a
+ * framework's caching pool, a fixed arena budgeted at start-up) and
+ * latency-critical loops where cudaMalloc/cudaFree would synchronise the
+ * device.  It does what pic_probe_read's flush does for a handle, on
+ * caller-provided device arrays:
+ *   F[p][c][f] += dt * sum_s samples[s][p][c] * exp(+i 2 pi freq_hz[f] (first_step+s+1) dt)
+ * for s < count and the components c set in comp_mask (FP64 throughout).
+ * samples: device [count][np][3] (sample s is E at step first_step+s+1);
+ * freq_hz: device [nf]; F: device [np][3][nf][2] (re, im), accumulated into.
+ * The caller owns all three arrays.  The phase table lives in a fixed 2 MiB
+ * __device__ array inside the library (held on every GPU that loads the
+ * library until the process exits); nf above 2048 is rejected with
+ * PIC_ERR_ARG.  The first call on each device looks up that array's device
+ * address with the device current; make that first call before any stream
+ * capture.  Every call on a device shares the array, so calls whose work
+ * overlaps on the GPU (different streams, or threads) race on it; serialise
+ * them on one stream.  Asynchronous on `stream` (NULL: the legacy default
+ * stream); launch errors are returned, kernel faults surface at the next
+ * synchronisation. */
+int pic_dft_fold_static(const double *samples, int64_t count, int np, uint32_t comp_mask,
+                        const double *freq_hz, int nf, int64_t first_step, double dt, double *F,
+                        void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -95,6 +95,9 @@ struct Source {
     double amp, t0, tau, f0;
 };
 
+// Record the message returned by pic_last_error() on this thread; returns code.
+int set_last_error(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+
 // ---------------------------------------------------------------- launchers
 template <typename T> void launch_update_H(const Grid<T> &g, const Fields<T> &f, cudaStream_t s);
 template <typename T> void launch_update_E(const Grid<T> &g, const Fields<T> &f, cudaStream_t s);

@@ -30,7 +30,7 @@ ERRORS = {-1: "PIC_ERR_ARG", -2: "PIC_ERR_CFL", -3: "PIC_ERR_OOM", -4: "PIC_ERR_
 EXPORTS = ("pic_last_error", "pic_workspace_size", "pic_create", "pic_destroy", "pic_set_stream",
            "pic_add_particles", "pic_get_particles", "pic_set_deposit", "pic_add_source", "pic_probe_dft",
            "pic_step", "pic_sync", "pic_probe_read", "pic_get_field", "pic_set_field", "pic_get_stats",
-           "pic_profile_steps")
+           "pic_profile_steps", "pic_dft_fold_static")
 
 
 class pic_material(C.Structure):
@@ -94,6 +94,8 @@ def load(path: str | None = None):
     L.pic_set_field.argtypes = [h, C.c_int, dp]
     L.pic_get_stats.argtypes = [h, C.POINTER(pic_stats)]
     L.pic_profile_steps.argtypes = [h, C.c_int64, dp]
+    L.pic_dft_fold_static.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_uint32, C.c_void_p, C.c_int,
+                                      C.c_int64, C.c_double, C.c_void_p, C.c_void_p]
     _lib = L
     return L
 
@@ -199,6 +201,15 @@ def pic_profile_steps(h, nsteps: int) -> dict:
     _check(load().pic_profile_steps(h, int(nsteps), _dp(out)), "pic_profile_steps")
     keys = ("update_H", "push_deposit", "update_E", "step_tail", "dft_flush", "step")
     return dict(zip(keys, out.tolist()))
+
+
+def pic_dft_fold_static(samples_ptr: int, count: int, np_: int, comp_mask: int, freq_ptr: int, nf: int,
+                        first_step: int, dt: float, F_ptr: int, stream: int | None = None) -> None:
+    """Allocation-free probe-DFT fold on caller device arrays (raw device
+    addresses, e.g. ``tensor.data_ptr()``); see include/pic.h."""
+    _check(load().pic_dft_fold_static(C.c_void_p(samples_ptr), int(count), int(np_), int(comp_mask),
+                                      C.c_void_p(freq_ptr), int(nf), int(first_step), float(dt),
+                                      C.c_void_p(F_ptr), C.c_void_p(stream or None)), "pic_dft_fold_static")
 
 
 # ------------------------------------------------------------ convenience --
