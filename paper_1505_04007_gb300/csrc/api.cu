@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <unordered_map>
 #include <vector>
 
@@ -129,11 +130,16 @@ struct Sim : SimBase {
     Grid<T> g{};
     Fields<T> f{};
     Particles<T> p{};
+    Particles<T> psort{};  // scratch arrays the sort scatters into
+    SortBuffers sb{};
+    int since_sort = SORT_EVERY;
     PushParams<T> pp{};
     Probes<T> pr{};
     uint8_t *d_mat = nullptr, *d_mat_metal = nullptr;
     uint8_t *d_ecls[3] = {nullptr, nullptr, nullptr};
     uint8_t *d_cls_metal = nullptr;
+    FieldPlan fplan{};
+    bool use_plan = false;
     T *d_cls[3] = {nullptr, nullptr, nullptr};
     T *d_prof[18];
     int *d_flag = nullptr;
@@ -189,6 +195,18 @@ struct Sim : SimBase {
         }
         p.status = a.take<uint8_t>(mp);
         p.id = a.take<long long>(mp);
+        for (int c = 0; c < 3; c++) {
+            psort.cell[c] = a.take<int>(mp);
+            psort.off[c] = a.take<T>(mp);
+            psort.u[c] = a.take<T>(mp);
+            psort.ulo[c] = a.take<T>(mp);
+            psort.bold[c] = a.take<T>(mp);
+        }
+        psort.status = a.take<uint8_t>(mp);
+        psort.id = a.take<long long>(mp);
+        sb.key = a.take<int>(mp);
+        sb.count = a.take<int>((size_t)sb.nbricks + 1);
+        sb.part = a.take<int>(((size_t)sb.nbricks + 1 + SCAN_TILE - 1) / SCAN_TILE);
         const size_t npb = (size_t)cfg.max_probes, nfb = (size_t)cfg.max_freqs;
         d_probe_xyz = a.take<double>(3 * npb);
         d_freq = a.take<double>(nfb);
@@ -216,6 +234,8 @@ struct Sim : SimBase {
         g.cH = (T)(c->dt / c->mu0);
         g.ncell = N;
         n_tiles = (size_t)g.nt[0] * g.nt[1] * g.nt[2];
+        for (int a = 0; a < 3; a++) sb.nb[a] = (n[a] + SORT_BRICK - 1) / SORT_BRICK;
+        sb.nbricks = sb.nb[0] * sb.nb[1] * sb.nb[2];
     }
 
     // CPML grading at position pos (cell units) along axis a: b-1, a, 1/kappa.
@@ -354,6 +374,29 @@ struct Sim : SimBase {
         for (int q3 = 0; q3 < 3; q3++)
             CUDA_TRY(cudaMemcpyAsync(d_cls[q3], cls[q3].data(), 256 * sizeof(T), cudaMemcpyHostToDevice, stream));
         CUDA_TRY(cudaMemcpyAsync(d_cls_metal, cls_metal.data(), 256, cudaMemcpyHostToDevice, stream));
+        // FP32 with whole four-cell groups per row: cut the grid for the
+        // four-cells-per-thread kernels (planes of one non-metal material
+        // take the kernel without per-edge material reads)
+        if constexpr (std::is_same<T, float>::value) {
+          if (n[0] % 4 == 0) {
+            std::vector<uint8_t> plane_cls(n[2], 255);
+            for (int k = 0; k < n[2]; k++) {
+                int first = -1;
+                bool mixed = false;
+                for (int comp = 0; comp < 3 && !mixed; comp++) {
+                    const uint8_t *row = ecls[comp].data() + (size_t)k * n[1] * n[0];
+                    for (size_t q = 0; q < (size_t)n[1] * n[0]; q++) {
+                        if (first < 0) first = row[q];
+                        else if (row[q] != first) { mixed = true; break; }
+                    }
+                }
+                if (!mixed && first >= 0 && !cls_metal[first]) plane_cls[k] = (uint8_t)first;
+            }
+            std::vector<float> cE(256);
+            for (int q = 0; q < 256; q++) cE[q] = (float)cls[2][q];
+            use_plan = make_field_plan(g, plane_cls.data(), cE.data(), fplan);
+          }
+        }
         // CPML profiles: per axis (b-1, a, 1/kappa) at E positions, then at H positions
         for (int a = 0; a < 3; a++) {
             std::vector<T> pf[6];
@@ -409,18 +452,22 @@ struct Sim : SimBase {
     }
 
     // ---------------------------------------------------------- stepping --
-    void launch_step() {
-        launch_update_H<T>(g, f, stream);
+    void launch_step(bool sort) {
+        if (sort) {
+            psort.n = p.n;
+            launch_sort<T>(p, psort, sb, stream);
+        }
+        launch_update_H<T>(g, f, use_plan ? &fplan : nullptr, stream);
         launch_push_deposit<T>(g, f, p, pp, stream);
         launch_sources<T>(g, f, sources.data(), (int)sources.size(), cfg.dt, stream);
-        launch_update_E<T>(g, f, stream);
+        launch_update_E<T>(g, f, use_plan ? &fplan : nullptr, stream);
         launch_step_tail<T>(g, f, pr, d_step, stream);
     }
 
     int ensure_graph() {
         if (gexec) return PIC_OK;
         CUDA_TRY(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
-        for (int s = 0; s < DFT_BLOCK; s++) launch_step();
+        for (int s = 0; s < DFT_BLOCK; s++) launch_step(s % SORT_EVERY == 0);
         launch_dft_flush<T>(pr, d_step, DFT_BLOCK, stream);
         cudaError_t e = cudaStreamEndCapture(stream, &graph);
         if (e != cudaSuccess) { graph = nullptr; return fail(PIC_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e)); }
@@ -449,9 +496,12 @@ struct Sim : SimBase {
                 CUDA_TRY(cudaGraphLaunch(gexec, stream));
                 nsteps -= DFT_BLOCK;
                 step_host += DFT_BLOCK;
+                since_sort = DFT_BLOCK - (DFT_BLOCK - 1) / SORT_EVERY * SORT_EVERY;  // steps since its last sort
                 continue;
             }
-            launch_step();
+            const bool sort = since_sort >= SORT_EVERY;
+            launch_step(sort);
+            since_sort = sort ? 1 : since_sort + 1;
             CUDA_TRY(cudaGetLastError());
             buffered++;
             step_host++;
@@ -496,13 +546,19 @@ struct Sim : SimBase {
             const int cnt = (int)std::min<long long>(B, nsteps - done);
             for (int s = 0; s < cnt; s++) {
                 cudaEvent_t *e = &ev[(size_t)s * 6];
+                const bool sort = since_sort >= SORT_EVERY;
+                if (sort) {
+                    psort.n = p.n;
+                    launch_sort<T>(p, psort, sb, stream);
+                }
+                since_sort = sort ? 1 : since_sort + 1;
                 cudaEventRecord(e[0], stream);
-                launch_update_H<T>(g, f, stream);
+                launch_update_H<T>(g, f, use_plan ? &fplan : nullptr, stream);
                 cudaEventRecord(e[1], stream);
                 launch_push_deposit<T>(g, f, p, pp, stream);
                 launch_sources<T>(g, f, sources.data(), (int)sources.size(), cfg.dt, stream);
                 cudaEventRecord(e[2], stream);
-                launch_update_E<T>(g, f, stream);
+                launch_update_E<T>(g, f, use_plan ? &fplan : nullptr, stream);
                 cudaEventRecord(e[3], stream);
                 launch_step_tail<T>(g, f, pr, d_step, stream);
                 cudaEventRecord(e[4], stream);

@@ -197,20 +197,39 @@ static dim3 field_grid(const int n[3], dim3 blk) {
 }
 
 template <typename T>
-void launch_update_H(const Grid<T> &g, const Fields<T> &f, cudaStream_t s) {
+void launch_update_H(const Grid<T> &g, const Fields<T> &f, const FieldPlan *, cudaStream_t s) {
     dim3 blk(32, 4, 2);
     k_update_H<T><<<field_grid(g.n, blk), blk, 0, s>>>(g, f);
 }
 
 template <typename T>
-void launch_update_E(const Grid<T> &g, const Fields<T> &f, cudaStream_t s) {
+void launch_update_E(const Grid<T> &g, const Fields<T> &f, const FieldPlan *, cudaStream_t s) {
     dim3 blk(32, 4, 2);
     k_update_E<T><<<field_grid(g.n, blk), blk, 0, s>>>(g, f);
 }
 
-template void launch_update_H<float>(const Grid<float> &, const Fields<float> &, cudaStream_t);
-template void launch_update_H<double>(const Grid<double> &, const Fields<double> &, cudaStream_t);
-template void launch_update_E<float>(const Grid<float> &, const Fields<float> &, cudaStream_t);
-template void launch_update_E<double>(const Grid<double> &, const Fields<double> &, cudaStream_t);
+// FP32 with a plan (nx a multiple of 4): the four-cells-per-thread kernels of fields_v4.cu.
+template <>
+void launch_update_H<float>(const Grid<float> &g, const Fields<float> &f, const FieldPlan *plan, cudaStream_t s) {
+    dim3 blk(32, 4, 2);
+    if (plan) {
+        launch_v4_H(g, f, *plan, s);
+    } else {
+        k_update_H<float><<<field_grid(g.n, blk), blk, 0, s>>>(g, f);
+    }
+}
+
+template <>
+void launch_update_E<float>(const Grid<float> &g, const Fields<float> &f, const FieldPlan *plan, cudaStream_t s) {
+    dim3 blk(32, 4, 2);
+    if (plan) {
+        launch_v4_E(g, f, *plan, s);
+    } else {
+        k_update_E<float><<<field_grid(g.n, blk), blk, 0, s>>>(g, f);
+    }
+}
+
+template void launch_update_H<double>(const Grid<double> &, const Fields<double> &, const FieldPlan *, cudaStream_t);
+template void launch_update_E<double>(const Grid<double> &, const Fields<double> &, const FieldPlan *, cudaStream_t);
 
 }  // namespace pic

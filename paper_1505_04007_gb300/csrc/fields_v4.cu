@@ -1,0 +1,417 @@
+// fields_v4.cu -- FP32 field updates with four consecutive x cells per thread.
+//
+// Every centre, row and plane access is one 16-byte load, which keeps enough
+// bytes in flight to stream the grid near the HBM copy rate.  The grid is cut
+// (make_field_plan) into an interior box without absorbing layers and face
+// boxes over the CPML slabs, and both are cut again by z-runs into planes of
+// one uniform non-metal material and planes holding metal or mixed
+// materials.  Each piece gets a kernel compiled for exactly what it needs, so
+// the bulk of the grid runs code with no CPML or material branches at all.
+// The pieces write disjoint cells, so the split adds no traffic.  Per cell
+// the arithmetic is that of the scalar kernels in fields.cu (same curl,
+// increment forms, held tangential edges).
+//
+// Requires nx % 4 == 0 and, with CPML along x, cpml_cells % 4 == 0, so a
+// four-cell group is either wholly inside an x slab or wholly outside.
+#include "pic_internal.cuh"
+
+namespace pic {
+
+namespace {
+
+struct F4 {
+    float v[4];
+};
+__device__ __forceinline__ F4 ld4(const float *p) {
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    return F4{{q.x, q.y, q.z, q.w}};
+}
+__device__ __forceinline__ void st4(float *p, const F4 &a) {
+    *reinterpret_cast<float4 *>(p) = make_float4(a.v[0], a.v[1], a.v[2], a.v[3]);
+}
+__device__ __forceinline__ F4 zero4() { return F4{{0.f, 0.f, 0.f, 0.f}}; }
+__device__ __forceinline__ F4 fill4(float x) { return F4{{x, x, x, x}}; }
+
+__device__ __forceinline__ int slab(const Grid<float> &g, int a, int x) {
+    if (!g.cpml[a]) return -1;
+    if (x < g.L) return x;
+    if (x >= g.n[a] - g.L) return x - (g.n[a] - 2 * g.L);
+    return -1;
+}
+__device__ __forceinline__ long long psi_idx(const Grid<float> &g, int a, int s, int i, int j, int k) {
+    const long long L2 = 2 * g.L;
+    if (a == 0) return ((long long)k * g.n[1] + j) * L2 + s;
+    if (a == 1) return ((long long)k * L2 + s) * g.n[0] + i;
+    return ((long long)s * g.n[1] + j) * g.n[0] + i;
+}
+
+// CPML state of one four-cell group for one derivative axis: the profile
+// (b-1, a, 1/kappa) per cell and where its two psi components live.
+struct Slab4 {
+    bool on;
+    F4 b, a, ik;
+    long long q;
+};
+
+__device__ __forceinline__ Slab4 slab4(const Grid<float> &g, const float *const *bp, const float *const *ap,
+                                       const float *const *kp, int axis, int i0, int j, int k) {
+    Slab4 s;
+    const int x = axis == 0 ? i0 : (axis == 1 ? j : k);
+    const int sp = slab(g, axis, x);
+    s.on = sp >= 0;
+    s.q = 0;
+    s.b = zero4();
+    s.a = zero4();
+    s.ik = fill4(1.f);
+    if (s.on) {
+        s.q = psi_idx(g, axis, sp, i0, j, k);
+        if (axis == 0) {
+            s.b = ld4(bp[0] + i0);
+            s.a = ld4(ap[0] + i0);
+            s.ik = ld4(kp[0] + i0);
+        } else {
+            s.b = fill4(bp[axis][x]);
+            s.a = fill4(ap[axis][x]);
+            s.ik = fill4(kp[axis][x]);
+        }
+    }
+    return s;
+}
+
+// psi += (b-1) psi + a dF for the four cells; returns the new psi.
+__device__ __forceinline__ F4 advance(const Slab4 &s, float *psi, const float d[4], bool store) {
+    F4 p = ld4(psi + s.q);
+#pragma unroll
+    for (int m = 0; m < 4; m++) p.v[m] = p.v[m] + (s.b.v[m] * p.v[m] + s.a.v[m] * d[m]);
+    if (store) st4(psi + s.q, p);
+    return p;
+}
+
+// H^{n+1/2} for cells i0..i0+3 of row (j, k).
+template <bool CPML>
+__device__ __forceinline__ void h4(const Grid<float> &g, const Fields<float> &f, int i0, int j, int k,
+                                   long long step) {
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const long long sy = nx, sz = (long long)nx * ny;
+    const long long e = k * sz + j * sy + i0;
+
+    // clear the free current the previous step deposited in this tile
+    const long long t = ((long long)(k / TILE_Z) * g.nt[1] + j / TILE_Y) * g.nt[0] + i0 / TILE_X;
+    if (step > 0 && f.jf_flag[t] == (int)step) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) st4(f.Jf[c] + e, zero4());
+    }
+
+    const bool hjp = (j + 1 < ny) || g.per[1];
+    const bool hkp = (k + 1 < nz) || g.per[2];
+    const bool hip = (i0 + 4 < nx) || g.per[0];
+    const long long ojp = (j + 1 < ny) ? sy : -(long long)(ny - 1) * sy;
+    const long long okp = (k + 1 < nz) ? sz : -(long long)(nz - 1) * sz;
+    const long long oip = (i0 + 4 < nx) ? 4 : -(long long)(nx - 4);
+
+    const F4 ex = ld4(f.E[0] + e), ey = ld4(f.E[1] + e), ez = ld4(f.E[2] + e);
+    const F4 ez_jp = hjp ? ld4(f.E[2] + e + ojp) : zero4();
+    const F4 ex_jp = hjp ? ld4(f.E[0] + e + ojp) : zero4();
+    const F4 ey_kp = hkp ? ld4(f.E[1] + e + okp) : zero4();
+    const F4 ex_kp = hkp ? ld4(f.E[0] + e + okp) : zero4();
+    const float ez_ip = hip ? f.E[2][e + oip] : 0.f;
+    const float ey_ip = hip ? f.E[1][e + oip] : 0.f;
+    F4 hx = ld4(f.H[0] + e), hy = ld4(f.H[1] + e), hz = ld4(f.H[2] + e);
+
+    const float rx = g.r[0], ry = g.r[1], rz = g.r[2];
+    float dEz_dy[4], dEy_dz[4], dEx_dz[4], dEz_dx[4], dEy_dx[4], dEx_dy[4];
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+        const float ezn = m < 3 ? ez.v[m + 1] : ez_ip;
+        const float eyn = m < 3 ? ey.v[m + 1] : ey_ip;
+        dEz_dy[m] = (ez_jp.v[m] - ez.v[m]) * ry;
+        dEy_dz[m] = (ey_kp.v[m] - ey.v[m]) * rz;
+        dEx_dz[m] = (ex_kp.v[m] - ex.v[m]) * rz;
+        dEz_dx[m] = (ezn - ez.v[m]) * rx;
+        dEy_dx[m] = (eyn - ey.v[m]) * rx;
+        dEx_dy[m] = (ex_jp.v[m] - ex.v[m]) * ry;
+    }
+    if (!CPML) {
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            hx.v[m] -= g.cH * (dEz_dy[m] - dEy_dz[m]);
+            hy.v[m] -= g.cH * (dEx_dz[m] - dEz_dx[m]);
+            hz.v[m] -= g.cH * (dEy_dx[m] - dEx_dy[m]);
+        }
+    } else {
+        const Slab4 sx = slab4(g, f.bH, f.aH, f.ikH, 0, i0, j, k);
+        const Slab4 syl = slab4(g, f.bH, f.aH, f.ikH, 1, i0, j, k);
+        const Slab4 szl = slab4(g, f.bH, f.aH, f.ikH, 2, i0, j, k);
+        F4 pxy = zero4(), pxz = zero4(), pyz = zero4(), pyx = zero4(), pzx = zero4(), pzy = zero4();
+        if (sx.on) {
+            pxy = advance(sx, f.psiH[0][0], dEz_dx, true);   // Hy's d/dx
+            pxz = advance(sx, f.psiH[0][1], dEy_dx, true);   // Hz's d/dx
+        }
+        if (syl.on) {
+            pyz = advance(syl, f.psiH[1][0], dEx_dy, true);  // Hz's d/dy
+            pyx = advance(syl, f.psiH[1][1], dEz_dy, true);  // Hx's d/dy
+        }
+        if (szl.on) {
+            pzx = advance(szl, f.psiH[2][0], dEy_dz, true);  // Hx's d/dz
+            pzy = advance(szl, f.psiH[2][1], dEx_dz, true);  // Hy's d/dz
+        }
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            const float kx = sx.ik.v[m], ky = syl.ik.v[m], kz = szl.ik.v[m];
+            hx.v[m] -= g.cH * (ky * dEz_dy[m] + pyx.v[m] - kz * dEy_dz[m] - pzx.v[m]);
+            hy.v[m] -= g.cH * (kz * dEx_dz[m] + pzy.v[m] - kx * dEz_dx[m] - pxy.v[m]);
+            hz.v[m] -= g.cH * (kx * dEy_dx[m] + pxz.v[m] - ky * dEx_dy[m] - pyz.v[m]);
+        }
+    }
+    st4(f.H[0] + e, hx);
+    st4(f.H[1] + e, hy);
+    st4(f.H[2] + e, hz);
+}
+
+// Eq. 6 (increment form) on a metal edge, then Eq. 8.
+__device__ __forceinline__ float ampere1(const Fields<float> &f, int comp, int cls, long long em, float E, float curl,
+                                         float jf) {
+    float jp = 0.f;
+    if (f.cls_metal[cls]) {
+        const float j0 = f.Jp[comp][em];
+        jp = j0 + (f.cls_kJm1[cls] * j0 + f.cls_bJ[cls] * E);
+        f.Jp[comp][em] = jp;
+    }
+    return E + f.cls_cE[cls] * (curl - jp - jf);
+}
+
+// E^{n+1} (with the Drude current of Eq. 6) for cells i0..i0+3 of row (j, k).
+// MAT: per-edge material classes (else every edge has the Ampere factor cEu
+// of one non-metal material and carries no polarisation current).
+template <bool CPML, bool MAT>
+__device__ __forceinline__ void e4(const Grid<float> &g, const Fields<float> &f, int i0, int j, int k,
+                                   long long step, float cEu) {
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const long long sy = nx, sz = (long long)nx * ny;
+    const long long e = k * sz + j * sy + i0;
+
+    const bool fx0 = !g.per[0] && i0 == 0;  // only cell m = 0 can sit on the x face
+    const bool fy = !g.per[1] && j == 0, fz = !g.per[2] && k == 0;
+    const long long ojm = j > 0 ? sy : (g.per[1] ? -(long long)(ny - 1) * sy : 0);
+    const long long okm = k > 0 ? sz : (g.per[2] ? -(long long)(nz - 1) * sz : 0);
+    const long long oim = i0 > 0 ? 1 : (g.per[0] ? -(long long)(nx - 1) : 0);
+
+    const long long t = ((long long)(k / TILE_Z) * g.nt[1] + j / TILE_Y) * g.nt[0] + i0 / TILE_X;
+    const bool jf_here = f.jf_flag[t] == (int)(step + 1);
+    const F4 jfx = jf_here ? ld4(f.Jf[0] + e) : zero4();
+    const F4 jfy = jf_here ? ld4(f.Jf[1] + e) : zero4();
+    const F4 jfz = jf_here ? ld4(f.Jf[2] + e) : zero4();
+
+    const F4 hx = ld4(f.H[0] + e), hy = ld4(f.H[1] + e), hz = ld4(f.H[2] + e);
+    const F4 hz_jm = ld4(f.H[2] + e - ojm), hx_jm = ld4(f.H[0] + e - ojm);
+    const F4 hy_km = ld4(f.H[1] + e - okm), hx_km = ld4(f.H[0] + e - okm);
+    const float hz_im = f.H[2][e - oim], hy_im = f.H[1][e - oim];
+    F4 ex = ld4(f.E[0] + e), ey = ld4(f.E[1] + e), ez = ld4(f.E[2] + e);
+    uchar4 cl0 = make_uchar4(0, 0, 0, 0), cl1 = cl0, cl2 = cl0;
+    if (MAT) {
+        cl0 = *reinterpret_cast<const uchar4 *>(f.ecls[0] + e);
+        cl1 = *reinterpret_cast<const uchar4 *>(f.ecls[1] + e);
+        cl2 = *reinterpret_cast<const uchar4 *>(f.ecls[2] + e);
+    }
+    const int cls[3][4] = {{cl0.x, cl0.y, cl0.z, cl0.w}, {cl1.x, cl1.y, cl1.z, cl1.w}, {cl2.x, cl2.y, cl2.z, cl2.w}};
+
+    const float rx = g.r[0], ry = g.r[1], rz = g.r[2];
+    float dHz_dy[4], dHy_dz[4], dHx_dz[4], dHz_dx[4], dHy_dx[4], dHx_dy[4];
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+        const float hzm = m > 0 ? hz.v[m - 1] : hz_im;
+        const float hym = m > 0 ? hy.v[m - 1] : hy_im;
+        dHz_dy[m] = (hz.v[m] - hz_jm.v[m]) * ry;
+        dHy_dz[m] = (hy.v[m] - hy_km.v[m]) * rz;
+        dHx_dz[m] = (hx.v[m] - hx_km.v[m]) * rz;
+        dHz_dx[m] = (hz.v[m] - hzm) * rx;
+        dHy_dx[m] = (hy.v[m] - hym) * rx;
+        dHx_dy[m] = (hx.v[m] - hx_jm.v[m]) * ry;
+    }
+    // psi and 1/kappa terms; held edges (E stays zero) leave their psi untouched
+    F4 pxy = zero4(), pxz = zero4(), pyx = zero4(), pyz = zero4(), pzx = zero4(), pzy = zero4();
+    F4 kx = fill4(1.f), ky = fill4(1.f), kz = fill4(1.f);
+    if (CPML) {
+        const Slab4 sx = slab4(g, f.bE, f.aE, f.ikE, 0, i0, j, k);
+        const Slab4 syl = slab4(g, f.bE, f.aE, f.ikE, 1, i0, j, k);
+        const Slab4 szl = slab4(g, f.bE, f.aE, f.ikE, 2, i0, j, k);
+        kx = sx.ik;
+        ky = syl.ik;
+        kz = szl.ik;
+        if (sx.on) {
+            // Ey's and Ez's d/dx: cell 0 is held when it sits on the x face
+            const F4 o0 = ld4(f.psiE[0][0] + sx.q), o1 = ld4(f.psiE[0][1] + sx.q);
+            pxy = advance(sx, f.psiE[0][0], dHz_dx, false);
+            pxz = advance(sx, f.psiE[0][1], dHy_dx, false);
+            if (fx0) {
+                pxy.v[0] = o0.v[0];
+                pxz.v[0] = o1.v[0];
+            }
+            if (!fz) st4(f.psiE[0][0] + sx.q, pxy);
+            if (!fy) st4(f.psiE[0][1] + sx.q, pxz);
+        }
+        if (syl.on) {
+            pyx = advance(syl, f.psiE[1][1], dHz_dy, !(fy || fz));  // Ex's d/dy
+            const F4 o0 = ld4(f.psiE[1][0] + syl.q);
+            pyz = advance(syl, f.psiE[1][0], dHx_dy, false);        // Ez's d/dy
+            if (fx0) pyz.v[0] = o0.v[0];
+            if (!fy) st4(f.psiE[1][0] + syl.q, pyz);
+        }
+        if (szl.on) {
+            pzx = advance(szl, f.psiE[2][0], dHy_dz, !(fy || fz));  // Ex's d/dz
+            const F4 o1 = ld4(f.psiE[2][1] + szl.q);
+            pzy = advance(szl, f.psiE[2][1], dHx_dz, false);        // Ey's d/dz
+            if (fx0) pzy.v[0] = o1.v[0];
+            if (!fz) st4(f.psiE[2][1] + szl.q, pzy);
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+        const bool fx = fx0 && m == 0;
+        const bool doX = !(fy || fz), doY = !(fx || fz), doZ = !(fx || fy);
+        const long long em = e + m;
+        const float cx = ky.v[m] * dHz_dy[m] + pyx.v[m] - kz.v[m] * dHy_dz[m] - pzx.v[m];
+        const float cy = kz.v[m] * dHx_dz[m] + pzy.v[m] - kx.v[m] * dHz_dx[m] - pxy.v[m];
+        const float cz = kx.v[m] * dHy_dx[m] + pxz.v[m] - ky.v[m] * dHx_dy[m] - pyz.v[m];
+        if (MAT) {
+            if (doX) ex.v[m] = ampere1(f, 0, cls[0][m], em, ex.v[m], cx, jfx.v[m]);
+            if (doY) ey.v[m] = ampere1(f, 1, cls[1][m], em, ey.v[m], cy, jfy.v[m]);
+            if (doZ) ez.v[m] = ampere1(f, 2, cls[2][m], em, ez.v[m], cz, jfz.v[m]);
+        } else {
+            if (doX) ex.v[m] += cEu * (cx - jfx.v[m]);
+            if (doY) ey.v[m] += cEu * (cy - jfy.v[m]);
+            if (doZ) ez.v[m] += cEu * (cz - jfz.v[m]);
+        }
+    }
+    st4(f.E[0] + e, ex);
+    st4(f.E[1] + e, ey);
+    st4(f.E[2] + e, ez);
+}
+
+// Thread -> cell group inside a box; false when past its end.
+__device__ __forceinline__ bool box_cell(const Box &b, long long q, int &i0, int &j, int &k) {
+    const int wx = (b.hi[0] - b.lo[0]) / 4, wy = b.hi[1] - b.lo[1], wz = b.hi[2] - b.lo[2];
+    if (q >= (long long)wx * wy * wz) return false;
+    i0 = b.lo[0] + 4 * (int)(q % wx);
+    j = b.lo[1] + (int)((q / wx) % wy);
+    k = b.lo[2] + (int)(q / ((long long)wx * wy));
+    return true;
+}
+
+#define BOX_CELL(bl)                                                                                   \
+    int i0, j, k;                                                                                      \
+    const Box &b = (bl).b[blockIdx.y];                                                                 \
+    if (!box_cell(b, blockIdx.x * (long long)blockDim.x + threadIdx.x, i0, j, k)) return;
+
+__global__ void __launch_bounds__(256) k_H4_bulk(Grid<float> g, Fields<float> f, BoxList bl) {
+    BOX_CELL(bl);
+    h4<false>(g, f, i0, j, k, *f.step);
+}
+__global__ void __launch_bounds__(256) k_H4_cpml(Grid<float> g, Fields<float> f, BoxList bl) {
+    BOX_CELL(bl);
+    h4<true>(g, f, i0, j, k, *f.step);
+}
+// one non-metal material, no absorbing layer
+__global__ void __launch_bounds__(256) k_E4_vac(Grid<float> g, Fields<float> f, BoxList bl) {
+    BOX_CELL(bl);
+    e4<false, false>(g, f, i0, j, k, *f.step, b.cE);
+}
+// metal or several materials, no absorbing layer
+__global__ void __launch_bounds__(256) k_E4_mat(Grid<float> g, Fields<float> f, BoxList bl) {
+    BOX_CELL(bl);
+    e4<false, true>(g, f, i0, j, k, *f.step, 0.f);
+}
+// one non-metal material inside the absorbing slabs
+__global__ void __launch_bounds__(256) k_E4_cpml_vac(Grid<float> g, Fields<float> f, BoxList bl) {
+    BOX_CELL(bl);
+    e4<true, false>(g, f, i0, j, k, *f.step, b.cE);
+}
+// metal or several materials inside the absorbing slabs
+__global__ void __launch_bounds__(256) k_E4_cpml_mat(Grid<float> g, Fields<float> f, BoxList bl) {
+    BOX_CELL(bl);
+    e4<true, true>(g, f, i0, j, k, *f.step, 0.f);
+}
+
+long long groups(const Box &b) {
+    return (long long)((b.hi[0] - b.lo[0]) / 4) * (b.hi[1] - b.lo[1]) * (b.hi[2] - b.lo[2]);
+}
+
+long long most_groups(const BoxList &bl) {
+    long long m = 0;
+    for (int q = 0; q < bl.n; q++) m = groups(bl.b[q]) > m ? groups(bl.b[q]) : m;
+    return m;
+}
+
+template <typename K>
+void launch_list(K kernel, const Grid<float> &g, const Fields<float> &f, const BoxList &bl, cudaStream_t s) {
+    const int blk = 256;
+    const long long most = most_groups(bl);
+    if (bl.n > 0 && most > 0) kernel<<<dim3((unsigned)((most + blk - 1) / blk), bl.n), blk, 0, s>>>(g, f, bl);
+}
+
+bool add_box(BoxList &bl, int x0, int x1, int y0, int y1, int z0, int z1, float cE) {
+    if (!(x1 > x0 && y1 > y0 && z1 > z0)) return true;
+    if (bl.n >= MAX_BOXES) return false;
+    bl.b[bl.n++] = Box{{x0, y0, z0}, {x1, y1, z1}, cE};
+    return true;
+}
+
+// Cut a box by z-runs of plane class into the vacuum list (one non-metal
+// class per run) and the material list.
+bool split_by_planes(const int lo[3], const int hi[3], const uint8_t *plane_cls, const float *cls_cE, BoxList &vac,
+                     BoxList &mat) {
+    int k = lo[2];
+    while (k < hi[2]) {
+        int k1 = k + 1;
+        while (k1 < hi[2] && plane_cls[k1] == plane_cls[k]) k1++;
+        const bool uniform = plane_cls[k] != 255;
+        if (!add_box(uniform ? vac : mat, lo[0], hi[0], lo[1], hi[1], k, k1, uniform ? cls_cE[plane_cls[k]] : 0.f))
+            return false;
+        k = k1;
+    }
+    return true;
+}
+
+}  // namespace
+
+bool make_field_plan(const Grid<float> &g, const uint8_t *plane_cls, const float *cls_cE, FieldPlan &p) {
+    p = FieldPlan{};
+    if (g.n[0] % 4 != 0 || (g.cpml[0] && g.L % 4 != 0)) return false;
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; a++) {
+        lo[a] = g.cpml[a] ? g.L : 0;
+        hi[a] = g.cpml[a] ? g.n[a] - g.L : g.n[a];
+    }
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    // interior box and the face boxes around it (a partition of the grid)
+    add_box(p.bulk, lo[0], hi[0], lo[1], hi[1], lo[2], hi[2], 0.f);
+    const int faces[6][6] = {{0, nx, 0, ny, 0, lo[2]},
+                             {0, nx, 0, ny, hi[2], nz},
+                             {0, nx, 0, lo[1], lo[2], hi[2]},
+                             {0, nx, hi[1], ny, lo[2], hi[2]},
+                             {0, lo[0], lo[1], hi[1], lo[2], hi[2]},
+                             {hi[0], nx, lo[1], hi[1], lo[2], hi[2]}};
+    for (auto &fb : faces) add_box(p.faces, fb[0], fb[1], fb[2], fb[3], fb[4], fb[5], 0.f);
+    // E: the same partition, cut by plane material
+    if (!split_by_planes(lo, hi, plane_cls, cls_cE, p.vac, p.mat)) return false;
+    for (auto &fb : faces) {
+        const int flo[3] = {fb[0], fb[2], fb[4]}, fhi[3] = {fb[1], fb[3], fb[5]};
+        if (flo[0] >= fhi[0] || flo[1] >= fhi[1] || flo[2] >= fhi[2]) continue;
+        if (!split_by_planes(flo, fhi, plane_cls, cls_cE, p.fvac, p.fmat)) return false;
+    }
+    return true;
+}
+
+void launch_v4_H(const Grid<float> &g, const Fields<float> &f, const FieldPlan &plan, cudaStream_t s) {
+    launch_list(k_H4_bulk, g, f, plan.bulk, s);
+    launch_list(k_H4_cpml, g, f, plan.faces, s);
+}
+
+void launch_v4_E(const Grid<float> &g, const Fields<float> &f, const FieldPlan &plan, cudaStream_t s) {
+    launch_list(k_E4_vac, g, f, plan.vac, s);
+    launch_list(k_E4_mat, g, f, plan.mat, s);
+    launch_list(k_E4_cpml_vac, g, f, plan.fvac, s);
+    launch_list(k_E4_cpml_mat, g, f, plan.fmat, s);
+}
+
+}  // namespace pic

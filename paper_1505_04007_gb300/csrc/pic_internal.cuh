@@ -12,6 +12,10 @@ constexpr int TILE_X = 32, TILE_Y = 4, TILE_Z = 4;
 // Probe samples buffered on the device between DFT flushes (one graph).
 constexpr int DFT_BLOCK = 64;
 constexpr int MAX_SOURCES = 16;
+// Electrons are re-sorted by 4x4x4-cell brick every SORT_EVERY steps.
+constexpr int SORT_BRICK = 4;
+constexpr int SORT_EVERY = 16;
+constexpr int SCAN_TILE = 4096;  // entries per block of the prefix scan
 
 // Device error bits.
 enum : int {
@@ -89,6 +93,16 @@ struct Probes {
     double dt;
 };
 
+// Counting-sort state: brick key per electron, per-brick counts (then
+// offsets, then cursors) and the per-block partial sums of the scan.
+struct SortBuffers {
+    int nb[3];       // bricks per axis
+    int nbricks;     // nb[0]*nb[1]*nb[2]; frozen electrons use key nbricks
+    int *key;        // [max_particles]
+    int *count;      // [nbricks + 1]
+    int *part;       // [ceil((nbricks + 1) / SCAN_TILE)]
+};
+
 struct Source {
     int comp;
     int box[6];
@@ -98,12 +112,45 @@ struct Source {
 // Record the message returned by pic_last_error() on this thread; returns code.
 int set_last_error(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
 
+// ------------------------------------------------------------- field plan
+// Boxes of cells for the FP32 four-cells-per-thread kernels (x bounds are
+// multiples of 4).  cE is the Ampere factor of a box whose edges all share
+// one non-metal material (used by the vacuum kernel only).
+struct Box {
+    int lo[3], hi[3];
+    float cE;
+};
+constexpr int MAX_BOXES = 16;
+struct BoxList {
+    int n;
+    Box b[MAX_BOXES];
+};
+// How the grid is cut for the FP32 field kernels: the interior box (no CPML
+// slab) and the face boxes over the slabs (H), and the same partition cut by
+// z-runs into planes of one uniform non-metal material (vac) and planes with
+// metal or mixed materials (mat), inside and over the slabs (E).
+struct FieldPlan {
+    BoxList bulk, faces, vac, mat, fvac, fmat;
+};
+// FP32 four-cells-per-thread field kernels (nx % 4 == 0), fields_v4.cu
+void launch_v4_H(const Grid<float> &g, const Fields<float> &f, const FieldPlan &plan, cudaStream_t s);
+void launch_v4_E(const Grid<float> &g, const Fields<float> &f, const FieldPlan &plan, cudaStream_t s);
+// plane_cls[k]: the class all edges of plane k share if it is non-metal, else
+// 255.  Returns false when the grid does not suit these kernels.
+bool make_field_plan(const Grid<float> &g, const uint8_t *plane_cls, const float *cls_cE, FieldPlan &p);
+
 // ---------------------------------------------------------------- launchers
-template <typename T> void launch_update_H(const Grid<T> &g, const Fields<T> &f, cudaStream_t s);
-template <typename T> void launch_update_E(const Grid<T> &g, const Fields<T> &f, cudaStream_t s);
+// Field updates; with a plan (FP32) the four-cells-per-thread kernels run,
+// otherwise the one-cell-per-thread kernels of fields.cu.
+template <typename T>
+void launch_update_H(const Grid<T> &g, const Fields<T> &f, const FieldPlan *plan, cudaStream_t s);
+template <typename T>
+void launch_update_E(const Grid<T> &g, const Fields<T> &f, const FieldPlan *plan, cudaStream_t s);
 template <typename T>
 void launch_push_deposit(const Grid<T> &g, const Fields<T> &f, const Particles<T> &p,
                          const PushParams<T> &pp, cudaStream_t s);
+template <typename T>
+void launch_sort(const Particles<T> &p, const Particles<T> &scratch, const SortBuffers &sb, cudaStream_t s);
 template <typename T>
 void launch_gather_bold(const Grid<T> &g, const Fields<T> &f, const Particles<T> &p, cudaStream_t s);
 template <typename T>

@@ -91,7 +91,7 @@ int scratch_for_current_device(double **out) {
 extern "C" int pic_dft_fold_static(const double *samples, int64_t count, int np, uint32_t comp_mask,
                                    const double *freq_hz, int nf, int64_t first_step, double dt, double *F,
                                    void *stream) {
-    pic::set_last_error(PIC_OK, "");
+    pic::set_last_error(PIC_OK, "%s", "");
     if (count < 0 || np < 0 || nf < 0 || (comp_mask & ~7u) || !(dt > 0.0))
         return pic::set_last_error(PIC_ERR_ARG, "bad arguments to pic_dft_fold_static");
     if (nf > STATIC_MAX_FREQS)

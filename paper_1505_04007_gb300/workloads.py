@@ -164,8 +164,8 @@ def _bunch_workload(name, nx, ny, nz, dx, nsteps, film_k0, film_k1, npart, charg
     w.cpml_alpha_max = 0.05 * EPS0 * AG_WP
     w.material = slab_material(nx, ny, nz, film_k0, film_k1)
     w.table = drude_table()
-    w.q_macro = -charge / npart
-    w.m_macro = ME * (charge / npart) / QE
+    w.q_macro = -charge / max(npart, 1)
+    w.m_macro = ME * (charge / max(npart, 1)) / QE
     if npart:
         w.xyz = gaussian_bunch(w, npart, centre, sigma, seed=seed)
         w.u = np.zeros_like(w.xyz)

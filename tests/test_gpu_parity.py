@@ -96,10 +96,24 @@ def test_fields_periodic_and_pec_fp64(P):
     compare_fields(o, s, 1e-10)
 
 
-def test_fields_with_source_fp32(P):
-    w = film_box(40, 24, 30)
-    srcs = [(2, (20, 21, 12, 13, 16, 17), 1e18, 30 * w.dt, 8 * w.dt, 0.0)]
+# nx % 4 == 0 takes the four-cells-per-thread FP32 kernels, 37 the scalar ones
+@pytest.mark.parametrize("shape", [(40, 24, 30), (37, 21, 29)])
+def test_fields_with_source_fp32(P, shape):
+    w = film_box(*shape)
+    srcs = [(2, (20, 21, 12, 13, 16, 17), 1e18, 30 * w.dt, 8 * w.dt, 0.0),
+            (1, (14, 18, 3, 15, 14, 15), 4e17, 36 * w.dt, 9 * w.dt, 1.2e15)]
     o, s = run_pair(P, w, 150, P.PIC_FP32, particles=False, probes=False, sources=srcs)
+    compare_fields(o, s, 2e-5)
+
+
+@pytest.mark.parametrize("bc", [
+    (W.BC_PEC, W.BC_CPML, W.BC_PERIODIC, W.BC_PERIODIC, W.BC_CPML, W.BC_PEC),
+    (W.BC_PERIODIC, W.BC_PERIODIC, W.BC_CPML, W.BC_PEC, W.BC_PEC, W.BC_CPML)])
+def test_fields_mixed_boundaries_fp32(P, bc):
+    w = film_box(36, 20, 28, bc=bc)
+    srcs = [(1, (10, 12, 5, 15, 16, 17), 1e18, 30 * w.dt, 8 * w.dt, 0.0),
+            (2, (3, 6, 9, 11, 15, 16), 6e17, 40 * w.dt, 8 * w.dt, 1.4e15)]
+    o, s = run_pair(P, w, 140, P.PIC_FP32, particles=False, probes=False, sources=srcs)
     compare_fields(o, s, 2e-5)
 
 
