@@ -146,6 +146,8 @@ struct Sim : SimBase {
     long long *d_step = nullptr;
     int *d_err = nullptr;
     double *d_probe_xyz = nullptr, *d_freq = nullptr, *d_samples = nullptr, *d_F = nullptr, *d_phasor = nullptr;
+    long long *d_st_idx = nullptr;
+    T *d_st_w = nullptr;
     size_t n_tiles = 0;
     int n_classes = 0;
 
@@ -209,6 +211,8 @@ struct Sim : SimBase {
         sb.part = a.take<int>(((size_t)sb.nbricks + 1 + SCAN_TILE - 1) / SCAN_TILE);
         const size_t npb = (size_t)cfg.max_probes, nfb = (size_t)cfg.max_freqs;
         d_probe_xyz = a.take<double>(3 * npb);
+        d_st_idx = a.take<long long>(24 * npb);
+        d_st_w = a.take<T>(24 * npb);
         d_freq = a.take<double>(nfb);
         d_samples = a.take<double>((size_t)DFT_BLOCK * npb * 3);
         d_F = a.take<double>(npb * 3 * nfb * 2);
@@ -432,7 +436,7 @@ struct Sim : SimBase {
         pp.inv_c2 = (T)(c->eps0 * c->mu0);
         for (int a = 0; a < 3; a++) pp.dtd[a] = (T)(c->dt / d[a]);
         pr.np = 0; pr.nf = 0; pr.mask = 0;
-        pr.xyz_cells = d_probe_xyz; pr.freq = d_freq; pr.samples = d_samples; pr.F = d_F; pr.phasor = d_phasor;
+        pr.xyz_cells = d_probe_xyz; pr.st_idx = d_st_idx; pr.st_w = d_st_w; pr.freq = d_freq; pr.samples = d_samples; pr.F = d_F; pr.phasor = d_phasor;
         pr.dt = c->dt;
         return PIC_OK;
     }
@@ -723,8 +727,34 @@ static int probe_dft_t(Sim<T> *s, int np, const double *xyz, uint32_t mask, int 
                 return fail(PIC_ERR_ARG, "probe %d lies within one cell of a face", q2);
             cells[3 * q2 + a] = xi;
         }
+    // interpolation stencil of every (probe, component): 8 corners of the
+    // component's staggered lattice, index and trilinear weight
+    std::vector<long long> st_idx((size_t)np * 24);
+    std::vector<T> st_w((size_t)np * 24);
+    for (int q2 = 0; q2 < np; q2++)
+        for (int c = 0; c < 3; c++)
+            for (int corner = 0; corner < 8; corner++) {
+                long long idx = 0, stride = 1;
+                double wt = 1.0;
+                for (int a = 0; a < 3; a++) {
+                    const double sa = cells[3 * q2 + a] - (a == c ? 0.5 : 0.0);
+                    const double fl = std::floor(sa);
+                    const int bit = (corner >> a) & 1;
+                    int ib = (int)fl + bit;
+                    const int na = s->n[a];
+                    if (s->g.per[a]) ib = ((ib % na) + na) % na;
+                    else ib = std::min(std::max(ib, 0), na - 1);
+                    wt *= bit ? (sa - fl) : 1.0 - (sa - fl);
+                    idx += (long long)ib * stride;
+                    stride *= na;
+                }
+                st_idx[(size_t)q2 * 24 + c * 8 + corner] = idx;
+                st_w[(size_t)q2 * 24 + c * 8 + corner] = (T)wt;
+            }
     CUDA_TRY(cudaStreamSynchronize(s->stream));
     if (np) CUDA_TRY(cudaMemcpy(s->d_probe_xyz, cells.data(), cells.size() * sizeof(double), cudaMemcpyHostToDevice));
+    if (np) CUDA_TRY(cudaMemcpy(s->d_st_idx, st_idx.data(), st_idx.size() * sizeof(long long), cudaMemcpyHostToDevice));
+    if (np) CUDA_TRY(cudaMemcpy(s->d_st_w, st_w.data(), st_w.size() * sizeof(T), cudaMemcpyHostToDevice));
     if (nf) CUDA_TRY(cudaMemcpy(s->d_freq, freq, nf * sizeof(double), cudaMemcpyHostToDevice));
     if (np && nf) CUDA_TRY(cudaMemset(s->d_F, 0, (size_t)np * 3 * nf * 2 * sizeof(double)));
     s->pr.np = np;

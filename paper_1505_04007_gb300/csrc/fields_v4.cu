@@ -288,20 +288,26 @@ __device__ __forceinline__ void e4(const Grid<float> &g, const Fields<float> &f,
     st4(f.E[2] + e, ez);
 }
 
-// Thread -> cell group inside a box; false when past its end.
-__device__ __forceinline__ bool box_cell(const Box &b, long long q, int &i0, int &j, int &k) {
-    const int wx = (b.hi[0] - b.lo[0]) / 4, wy = b.hi[1] - b.lo[1], wz = b.hi[2] - b.lo[2];
-    if (q >= (long long)wx * wy * wz) return false;
-    i0 = b.lo[0] + 4 * (int)(q % wx);
-    j = b.lo[1] + (int)((q / wx) % wy);
-    k = b.lo[2] + (int)(q / ((long long)wx * wy));
+// Thread -> cell group: the groups of all boxes of a list are numbered one
+// after the other, so every block has work whatever the box sizes.
+__device__ __forceinline__ bool list_cell(const BoxList &bl, long long q, int &bi, int &i0, int &j, int &k) {
+    if (q >= bl.first[bl.n]) return false;
+    bi = 0;
+    while (q >= bl.first[bi + 1]) bi++;
+    const Box &b = bl.b[bi];
+    const long long r = q - bl.first[bi];
+    const int wx = (b.hi[0] - b.lo[0]) / 4, wy = b.hi[1] - b.lo[1];
+    i0 = b.lo[0] + 4 * (int)(r % wx);
+    j = b.lo[1] + (int)((r / wx) % wy);
+    k = b.lo[2] + (int)(r / ((long long)wx * wy));
     return true;
 }
 
 #define BOX_CELL(bl)                                                                                   \
-    int i0, j, k;                                                                                      \
-    const Box &b = (bl).b[blockIdx.y];                                                                 \
-    if (!box_cell(b, blockIdx.x * (long long)blockDim.x + threadIdx.x, i0, j, k)) return;
+    int bi, i0, j, k;                                                                                  \
+    if (!list_cell((bl), blockIdx.x * (long long)blockDim.x + threadIdx.x, bi, i0, j, k)) return;      \
+    const Box &b = (bl).b[bi];                                                                         \
+    (void)b;
 
 __global__ void __launch_bounds__(256) k_H4_bulk(Grid<float> g, Fields<float> f, BoxList bl) {
     BOX_CELL(bl);
@@ -336,23 +342,19 @@ long long groups(const Box &b) {
     return (long long)((b.hi[0] - b.lo[0]) / 4) * (b.hi[1] - b.lo[1]) * (b.hi[2] - b.lo[2]);
 }
 
-long long most_groups(const BoxList &bl) {
-    long long m = 0;
-    for (int q = 0; q < bl.n; q++) m = groups(bl.b[q]) > m ? groups(bl.b[q]) : m;
-    return m;
-}
-
 template <typename K>
 void launch_list(K kernel, const Grid<float> &g, const Fields<float> &f, const BoxList &bl, cudaStream_t s) {
     const int blk = 256;
-    const long long most = most_groups(bl);
-    if (bl.n > 0 && most > 0) kernel<<<dim3((unsigned)((most + blk - 1) / blk), bl.n), blk, 0, s>>>(g, f, bl);
+    const long long total = bl.first[bl.n];
+    if (total > 0) kernel<<<(unsigned)((total + blk - 1) / blk), blk, 0, s>>>(g, f, bl);
 }
 
 bool add_box(BoxList &bl, int x0, int x1, int y0, int y1, int z0, int z1, float cE) {
     if (!(x1 > x0 && y1 > y0 && z1 > z0)) return true;
     if (bl.n >= MAX_BOXES) return false;
-    bl.b[bl.n++] = Box{{x0, y0, z0}, {x1, y1, z1}, cE};
+    bl.b[bl.n] = Box{{x0, y0, z0}, {x1, y1, z1}, cE};
+    bl.first[bl.n + 1] = bl.first[bl.n] + groups(bl.b[bl.n]);
+    bl.n++;
     return true;
 }
 

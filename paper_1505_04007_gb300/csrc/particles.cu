@@ -296,6 +296,21 @@ __global__ void k_gather_bold(Grid<T> g, Fields<T> f, Particles<T> p) {
 }
 
 // ------------------------------------------------------------ brick sort --
+// Lanes of a warp that share a key make one atomic between them: the leader
+// adds the group size and each lane gets its own slot from the old value.
+// After the first sort most of a warp sits in one brick, so the counters of
+// dense bricks see a few atomics instead of one per electron.
+__device__ __forceinline__ int warp_grouped_add(int *ctr, int key) {
+    const unsigned active = __activemask();
+    const unsigned group = __match_any_sync(active, key);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(group) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&ctr[key], __popc(group));
+    base = __shfl_sync(group, base, leader);
+    return base + __popc(group & ((1u << lane) - 1));
+}
+
 // key = brick of the electron's cell (frozen electrons after all bricks)
 template <typename T>
 __global__ void k_sort_hist(Particles<T> p, SortBuffers sb) {
@@ -307,7 +322,7 @@ __global__ void k_sort_hist(Particles<T> p, SortBuffers sb) {
         key = (bz * sb.nb[1] + by) * sb.nb[0] + bx;
     }
     sb.key[q] = key;
-    atomicAdd(&sb.count[key], 1);
+    warp_grouped_add(sb.count, key);
 }
 
 // Exclusive scan of count[0..n) in place, SCAN_TILE entries per block (four
@@ -377,7 +392,7 @@ template <typename T>
 __global__ void k_sort_scatter(Particles<T> p, Particles<T> dst, SortBuffers sb) {
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (q >= p.n) return;
-    const int slot = atomicAdd(&sb.count[sb.key[q]], 1);
+    const int slot = warp_grouped_add(sb.count, sb.key[q]);
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         dst.cell[a][slot] = p.cell[a][q];

@@ -86,6 +86,8 @@ struct Probes {
     int np, nf;
     unsigned mask;
     const double *xyz_cells;  // [np][3] positions in cell units
+    const long long *st_idx;  // [np][3][8] grid index of each interpolation corner
+    const T *st_w;            // [np][3][8] trilinear weight of each corner
     const double *freq;       // [nf]
     double *samples;          // [DFT_BLOCK][np][3]
     double *F;                // [np][3][nf][2]
@@ -124,6 +126,7 @@ constexpr int MAX_BOXES = 16;
 struct BoxList {
     int n;
     Box b[MAX_BOXES];
+    long long first[MAX_BOXES + 1];  // prefix sums of four-cell groups per box
 };
 // How the grid is cut for the FP32 field kernels: the interior box (no CPML
 // slab) and the face boxes over the slabs (H), and the same partition cut by

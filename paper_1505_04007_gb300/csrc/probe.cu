@@ -6,10 +6,9 @@
 // DFT_BLOCK slots.  Every DFT_BLOCK steps (and before any read) the ring is
 // folded into the FP64 accumulators:
 //     F[p][c][f] += dt * sum_s E_c(x_p, t_s) exp(+i 2 pi f t_s),  t_s = (n_s+1) dt.
-// The phase of each (slot, frequency) pair is computed once per flush with an
-// FP64 sincos of the exact time; for the FP32 state the per-block partial sum
-// runs in float (the samples carry FP32 rounding already) and the running
-// accumulators stay FP64.
+// The phases of a flush are built in FP64 from the exact time of its first
+// step; for the FP32 state the per-block partial sum runs in float (the
+// samples carry FP32 rounding already) and the running accumulators stay FP64.
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -56,54 +55,24 @@ void launch_sources(const Grid<T> &g, const Fields<T> &f, const Source *src, int
     k_sources<T><<<dim3((unsigned)nblk, (unsigned)nsrc), blk, 0, s>>>(g, f, sl, dt);
 }
 
-// E component c interpolated at a position given in cell units (double).
+// One block: each warp interpolates whole probes (24 lanes = 3 components x
+// 8 corners of the precomputed stencil, summed by shuffles), then thread 0
+// advances the step counter once every sample of step n is written.
 template <typename T>
-__device__ T probe_value(const Grid<T> &g, const T *F, const double *xi, int c) {
-    int i0[3], i1[3];
-    T w[3];
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        const double s = xi[a] - (a == c ? 0.5 : 0.0);
-        const double b = floor(s);
-        int ib = (int)b;
-        w[a] = (T)(s - b);
-        int jb = ib + 1;
-        const int n = g.n[a];
-        if (g.per[a]) {
-            ib = ((ib % n) + n) % n;
-            jb = ((jb % n) + n) % n;
-        } else {
-            ib = ib < 0 ? 0 : (ib >= n ? n - 1 : ib);
-            jb = jb < 0 ? 0 : (jb >= n ? n - 1 : jb);
-        }
-        i0[a] = ib;
-        i1[a] = jb;
-    }
-    T v = T(0);
-#pragma unroll
-    for (int dk = 0; dk < 2; dk++)
-#pragma unroll
-        for (int dj = 0; dj < 2; dj++)
-#pragma unroll
-            for (int di = 0; di < 2; di++) {
-                const long long e = ((long long)(dk ? i1[2] : i0[2]) * g.n[1] + (dj ? i1[1] : i0[1])) * g.n[0] +
-                                    (di ? i1[0] : i0[0]);
-                const T wt = (di ? w[0] : T(1) - w[0]) * (dj ? w[1] : T(1) - w[1]) * (dk ? w[2] : T(1) - w[2]);
-                v += wt * F[e];
-            }
-    return v;
-}
-
-// Single block: sample the probes for step n, then advance the step counter.
-template <typename T>
-__global__ void k_step_tail(Grid<T> g, Fields<T> f, Probes<T> pr, long long *step) {
+__global__ void __launch_bounds__(1024) k_step_tail(Grid<T> g, Fields<T> f, Probes<T> pr, long long *step) {
     const long long n = *step;
     const int slot = (int)(n % DFT_BLOCK);
-    for (int q = threadIdx.x; q < pr.np * 3; q += blockDim.x) {
-        const int p = q / 3, c = q % 3;
-        double v = 0.0;
-        if (pr.mask & (1u << c)) v = (double)probe_value(g, f.E[c], pr.xyz_cells + 3 * p, c);
-        pr.samples[((long long)slot * pr.np + p) * 3 + c] = v;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int c = lane >> 3;
+    for (int p = warp; p < pr.np; p += nwarps) {
+        T v = T(0);
+        if (c < 3 && (pr.mask & (1u << c))) {
+            const long long q = (long long)p * 24 + lane;
+            v = pr.st_w[q] * f.E[c][pr.st_idx[q]];
+        }
+#pragma unroll
+        for (int off = 4; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off, 8);
+        if ((lane & 7) == 0 && c < 3) pr.samples[((long long)slot * pr.np + p) * 3 + c] = (double)v;
     }
     __syncthreads();
     if (threadIdx.x == 0) *step = n + 1;
@@ -111,56 +80,87 @@ __global__ void k_step_tail(Grid<T> g, Fields<T> f, Probes<T> pr, long long *ste
 
 template <typename T>
 void launch_step_tail(const Grid<T> &g, const Fields<T> &f, const Probes<T> &pr, long long *step, cudaStream_t s) {
-    int blk = pr.np * 3;
-    blk = blk < 32 ? 32 : (blk > 512 ? 512 : ((blk + 31) / 32) * 32);
+    int blk = 32 * pr.np;
+    blk = blk < 32 ? 32 : (blk > 1024 ? 1024 : blk);
     k_step_tail<T><<<1, blk, 0, s>>>(g, f, pr, step);
 }
 
-// Phase table: phasor[s][f] for the count most recent steps.
+// Phase table phasor[s][f] = exp(+i 2 pi f (n_s+1) dt) for the count most
+// recent steps.  A thread covers PHASE_RUN consecutive steps of one
+// frequency: one FP64 sincos for its first step and one for the per-step
+// rotation, then a complex product per step (error below 1e-15 per run).
+constexpr int PHASE_RUN = 8;
+
 __global__ void k_dft_phasor(const double *freq, int nf, double *phasor, const long long *step, int count, double dt) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = blockIdx.y;
-    if (f >= nf) return;
-    const long long n = *step - count + s;  // the step that produced this sample
-    const double t = (double)(n + 1) * dt;
-    double sn, cs;
-    sincos(2.0 * 3.141592653589793 * freq[f] * t, &sn, &cs);
-    phasor[((long long)s * nf + f) * 2] = cs;
-    phasor[((long long)s * nf + f) * 2 + 1] = sn;
+    const int s0 = blockIdx.y * PHASE_RUN;
+    if (f >= nf || s0 >= count) return;
+    const long long n0 = *step - count;  // the step that produced slot s = 0
+    const double w = 2.0 * 3.141592653589793 * freq[f];
+    double zr, zi, rr, ri;
+    sincos(w * ((double)(n0 + s0 + 1) * dt), &zi, &zr);
+    sincos(w * dt, &ri, &rr);
+    const int s1 = s0 + PHASE_RUN < count ? s0 + PHASE_RUN : count;
+    for (int s = s0; s < s1; s++) {
+        phasor[((long long)s * nf + f) * 2] = zr;
+        phasor[((long long)s * nf + f) * 2 + 1] = zi;
+        const double tr = zr * rr - zi * ri;
+        zi = zr * ri + zi * rr;
+        zr = tr;
+    }
 }
 
-// One thread per (probe, component, frequency): fold the buffered samples.
+// Fold the buffered samples into the FP64 accumulators.  A thread owns one
+// frequency and DFT_ROWS (probe, component) rows of a block; the block's
+// samples sit in shared memory, so each phase is read once per thread.
+constexpr int DFT_ROWS = 16;
+
 template <typename A>
-__global__ void k_dft_accumulate(const double *samples, const double *phasor, double *F,
-                                 int np, int nf, unsigned mask, const long long *step, int count, double dt) {
+__global__ void __launch_bounds__(128) k_dft_accumulate(const double *samples, const double *phasor, double *F, int np,
+                                                        int nf, unsigned mask, const long long *step, int count,
+                                                        double dt) {
+    __shared__ A s_smp[DFT_BLOCK][DFT_ROWS];
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
-    const int pc = blockIdx.y;
-    const int p = pc / 3, c = pc % 3;
-    if (f >= nf || !(mask & (1u << c))) return;
+    const int row0 = blockIdx.y * DFT_ROWS;
+    const int nrows = np * 3;
     const long long n0 = *step - count;
-    A re = A(0), im = A(0);
-    for (int s = 0; s < count; s++) {
+    for (int q = threadIdx.x; q < count * DFT_ROWS; q += blockDim.x) {
+        const int s = q / DFT_ROWS, r = q % DFT_ROWS;
         const int slot = (int)((n0 + s) % DFT_BLOCK);
-        const A v = (A)samples[((long long)slot * np + p) * 3 + c];
+        s_smp[s][r] = (row0 + r < nrows) ? (A)samples[(long long)slot * nrows + row0 + r] : A(0);
+    }
+    __syncthreads();
+    if (f >= nf) return;
+    A re[DFT_ROWS], im[DFT_ROWS];
+#pragma unroll
+    for (int r = 0; r < DFT_ROWS; r++) re[r] = im[r] = A(0);
+    for (int s = 0; s < count; s++) {
         const A cr = (A)phasor[((long long)s * nf + f) * 2];
         const A ci = (A)phasor[((long long)s * nf + f) * 2 + 1];
-        re += v * cr;
-        im += v * ci;
+#pragma unroll
+        for (int r = 0; r < DFT_ROWS; r++) {
+            re[r] += s_smp[s][r] * cr;
+            im[r] += s_smp[s][r] * ci;
+        }
     }
-    double *out = F + (((long long)p * 3 + c) * nf + f) * 2;
-    out[0] += (double)re * dt;
-    out[1] += (double)im * dt;
+#pragma unroll
+    for (int r = 0; r < DFT_ROWS; r++) {
+        const int row = row0 + r;
+        if (row >= nrows || !(mask & (1u << (row % 3)))) continue;
+        double *out = F + ((long long)row * nf + f) * 2;
+        out[0] += (double)re[r] * dt;
+        out[1] += (double)im[r] * dt;
+    }
 }
 
 template <typename T>
 void launch_dft_flush(const Probes<T> &pr, const long long *step, int count, cudaStream_t s) {
     if (count <= 0 || pr.np <= 0 || pr.nf <= 0) return;
     const int blk = 128;
-    dim3 g1((pr.nf + blk - 1) / blk, count);
-    k_dft_phasor<<<g1, blk, 0, s>>>(pr.freq, pr.nf, pr.phasor, step, count, pr.dt);
-    dim3 g2((pr.nf + blk - 1) / blk, pr.np * 3);
-    k_dft_accumulate<T><<<g2, blk, 0, s>>>(pr.samples, pr.phasor, pr.F, pr.np, pr.nf, pr.mask, step, count,
-                                           pr.dt);
+    k_dft_phasor<<<dim3((pr.nf + blk - 1) / blk, (count + PHASE_RUN - 1) / PHASE_RUN), blk, 0, s>>>(
+        pr.freq, pr.nf, pr.phasor, step, count, pr.dt);
+    dim3 g2((pr.nf + blk - 1) / blk, (pr.np * 3 + DFT_ROWS - 1) / DFT_ROWS);
+    k_dft_accumulate<T><<<g2, blk, 0, s>>>(pr.samples, pr.phasor, pr.F, pr.np, pr.nf, pr.mask, step, count, pr.dt);
 }
 
 template void launch_sources<float>(const Grid<float> &, const Fields<float> &, const Source *, int, double,

@@ -113,3 +113,21 @@ def edge_wp2(w, comp, values=None):
 
     s1 = shift_back(wp2, a1)
     return 0.25 * (wp2 + s1 + shift_back(wp2, a2) + shift_back(s1, a2))
+
+
+def spectral_peak(freqs, power, band=None):
+    """Frequency of the largest value of power (optionally inside band =
+    (f_lo, f_hi)), refined by the vertex of the parabola through the
+    maximum and its two neighbours."""
+    f = np.asarray(freqs, np.float64)
+    p = np.asarray(power, np.float64)
+    idx = np.arange(f.size)
+    if band is not None:
+        idx = idx[(f >= band[0]) & (f <= band[1])]
+    m = idx[np.argmax(p[idx])]
+    if 0 < m < f.size - 1:
+        y0, y1, y2 = p[m - 1], p[m], p[m + 1]
+        den = y0 - 2 * y1 + y2
+        shift = 0.5 * (y0 - y2) / den if den != 0 else 0.0
+        return f[m] + shift * (f[1] - f[0])
+    return f[m]
