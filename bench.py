@@ -29,9 +29,6 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 FALLBACK_HBM_GBS = 6800.0
-KERNELS_PER_STEP = 4          # update_H, push_deposit, update_E, step_tail
-DFT_KERNELS_PER_FLUSH = 2     # phasor table, accumulate
-DFT_BLOCK = 64
 
 
 def parse():
@@ -242,6 +239,7 @@ def main():
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    k0 = sim.stats().kernel_launches
     e0.record(stream)
     sim.step(args.steps)
     e1.record(stream)
@@ -255,7 +253,7 @@ def main():
         ms = float(t.item())
     cells_total = w.ncells * args.steps * world
     value = cells_total / (ms / 1e3) / 1e9
-    launches = KERNELS_PER_STEP * args.steps + DFT_KERNELS_PER_FLUSH * (args.steps // DFT_BLOCK)
+    launches = sim.stats().kernel_launches - k0  # counted by the library (graph replays count their kernels)
 
     # ------------------------------ per-kernel durations (CUDA events, live)
     prof = sim.profile(min(args.steps, 1024))

@@ -99,6 +99,7 @@ typedef struct {
     int64_t n_frozen;      /* particles stopped by the boundary/metal rule */
     int32_t device_error;  /* bit set reported by kernels (0 = none) */
     int32_t n_edge_classes;
+    int64_t kernel_launches; /* kernels pic_step has launched (graph replays count their kernels) */
 } pic_stats;
 
 typedef struct pic_handle pic_handle;

@@ -36,6 +36,11 @@ static int fail(int code, const char *fmt, ...) {
 }
 
 namespace pic {
+long long &launch_count() {
+    static thread_local long long n = 0;
+    return n;
+}
+
 int set_last_error(int code, const char *fmt, ...) {
     char buf[512];
     va_list ap;
@@ -159,6 +164,8 @@ struct Sim : SimBase {
     double q = 0, m = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    long long graph_kernels = 0;   // kernels in one replay of the step graph
+    long long kernels = 0;         // kernels launched by this simulation so far
 
     // all device buffers, in one pass; base == nullptr only measures
     void plan(Arena &a) {
@@ -471,8 +478,11 @@ struct Sim : SimBase {
     int ensure_graph() {
         if (gexec) return PIC_OK;
         CUDA_TRY(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+        const long long before = launch_count();
         for (int s = 0; s < DFT_BLOCK; s++) launch_step(s % SORT_EVERY == 0);
         launch_dft_flush<T>(pr, d_step, DFT_BLOCK, stream);
+        graph_kernels = launch_count() - before;
+        launch_count() = before;  // captured, not launched
         cudaError_t e = cudaStreamEndCapture(stream, &graph);
         if (e != cudaSuccess) { graph = nullptr; return fail(PIC_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e)); }
         e = cudaGraphInstantiate(&gexec, graph, 0);
@@ -491,6 +501,13 @@ struct Sim : SimBase {
 
     int step(long long nsteps) {
         if (nsteps < 0) return fail(PIC_ERR_ARG, "negative step count");
+        const long long direct0 = launch_count();
+        int rc = step_inner(nsteps);
+        kernels += launch_count() - direct0;
+        return rc;
+    }
+
+    int step_inner(long long nsteps) {
         int rc = refresh_bold();
         if (rc) return rc;
         while (nsteps > 0) {
@@ -498,6 +515,7 @@ struct Sim : SimBase {
                 rc = ensure_graph();
                 if (rc) return rc;
                 CUDA_TRY(cudaGraphLaunch(gexec, stream));
+                kernels += graph_kernels;
                 nsteps -= DFT_BLOCK;
                 step_host += DFT_BLOCK;
                 since_sort = DFT_BLOCK - (DFT_BLOCK - 1) / SORT_EVERY * SORT_EVERY;  // steps since its last sort
@@ -825,6 +843,7 @@ static int stats_t(Sim<T> *s, pic_stats *out) {
     out->n_frozen = fr;
     out->device_error = err;
     out->n_edge_classes = s->n_classes;
+    out->kernel_launches = s->kernels;
     return PIC_OK;
 }
 

@@ -200,12 +200,14 @@ template <typename T>
 void launch_update_H(const Grid<T> &g, const Fields<T> &f, const FieldPlan *, cudaStream_t s) {
     dim3 blk(32, 4, 2);
     k_update_H<T><<<field_grid(g.n, blk), blk, 0, s>>>(g, f);
+    launch_count() += 1;
 }
 
 template <typename T>
 void launch_update_E(const Grid<T> &g, const Fields<T> &f, const FieldPlan *, cudaStream_t s) {
     dim3 blk(32, 4, 2);
     k_update_E<T><<<field_grid(g.n, blk), blk, 0, s>>>(g, f);
+    launch_count() += 1;
 }
 
 // FP32 with a plan (nx a multiple of 4): the four-cells-per-thread kernels of fields_v4.cu.
@@ -216,6 +218,7 @@ void launch_update_H<float>(const Grid<float> &g, const Fields<float> &f, const 
         launch_v4_H(g, f, *plan, s);
     } else {
         k_update_H<float><<<field_grid(g.n, blk), blk, 0, s>>>(g, f);
+        launch_count() += 1;
     }
 }
 
@@ -226,6 +229,7 @@ void launch_update_E<float>(const Grid<float> &g, const Fields<float> &f, const 
         launch_v4_E(g, f, *plan, s);
     } else {
         k_update_E<float><<<field_grid(g.n, blk), blk, 0, s>>>(g, f);
+        launch_count() += 1;
     }
 }
 

@@ -346,7 +346,10 @@ template <typename K>
 void launch_list(K kernel, const Grid<float> &g, const Fields<float> &f, const BoxList &bl, cudaStream_t s) {
     const int blk = 256;
     const long long total = bl.first[bl.n];
-    if (total > 0) kernel<<<(unsigned)((total + blk - 1) / blk), blk, 0, s>>>(g, f, bl);
+    if (total > 0) {
+        kernel<<<(unsigned)((total + blk - 1) / blk), blk, 0, s>>>(g, f, bl);
+        launch_count() += 1;
+    }
 }
 
 bool add_box(BoxList &bl, int x0, int x1, int y0, int y1, int z0, int z1, float cE) {

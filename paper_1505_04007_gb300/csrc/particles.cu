@@ -426,6 +426,7 @@ void launch_push_deposit(const Grid<T> &g, const Fields<T> &f, const Particles<T
                          cudaStream_t s) {
     if (p.n <= 0) return;
     k_push_deposit<T><<<(unsigned)((p.n + PUSH_BLOCK - 1) / PUSH_BLOCK), PUSH_BLOCK, DEP_SMEM_BYTES, s>>>(g, f, p, pp);
+    launch_count() += 1;
 }
 
 template <typename T>
@@ -433,6 +434,7 @@ void launch_gather_bold(const Grid<T> &g, const Fields<T> &f, const Particles<T>
     if (p.n <= 0) return;
     const int blk = 256;
     k_gather_bold<T><<<(unsigned)((p.n + blk - 1) / blk), blk, 0, s>>>(g, f, p);
+    launch_count() += 1;
 }
 
 template <typename T>
@@ -442,13 +444,19 @@ void launch_sort(const Particles<T> &p, const Particles<T> &scratch, const SortB
     const unsigned gp = (unsigned)((p.n + blk - 1) / blk);
     const int nbins = sb.nbricks + 1;
     const int ntiles = (nbins + SCAN_TILE - 1) / SCAN_TILE;
-    cudaMemsetAsync(sb.count, 0, sizeof(int) * nbins, s);
+    cudaMemsetAsync(sb.count, 0, sizeof(int) * nbins, s);  // a memset node, not a kernel
     k_sort_hist<T><<<gp, blk, 0, s>>>(p, sb);
+    launch_count() += 1;
     k_scan_tiles<<<ntiles, 1024, 0, s>>>(sb.count, nbins, sb.part);
+    launch_count() += 1;
     k_scan_parts<<<1, 1024, 0, s>>>(sb.part, ntiles);
+    launch_count() += 1;
     k_scan_add<<<ntiles, 1024, 0, s>>>(sb.count, nbins, sb.part);
+    launch_count() += 1;
     k_sort_scatter<T><<<gp, blk, 0, s>>>(p, scratch, sb);
+    launch_count() += 1;
     k_sort_copyback<T><<<gp, blk, 0, s>>>(p, scratch);
+    launch_count() += 1;
 }
 
 template void launch_push_deposit<float>(const Grid<float> &, const Fields<float> &, const Particles<float> &,

@@ -111,6 +111,9 @@ struct Source {
     double amp, t0, tau, f0;
 };
 
+// Kernels launched on this host thread (every launcher adds its launches).
+long long &launch_count();
+
 // Record the message returned by pic_last_error() on this thread; returns code.
 int set_last_error(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
 

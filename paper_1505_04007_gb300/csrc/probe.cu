@@ -53,6 +53,7 @@ void launch_sources(const Grid<T> &g, const Fields<T> &f, const Source *src, int
     long long nblk = (most + blk - 1) / blk;
     if (nblk > 1024) nblk = 1024;
     k_sources<T><<<dim3((unsigned)nblk, (unsigned)nsrc), blk, 0, s>>>(g, f, sl, dt);
+    launch_count() += 1;
 }
 
 // One block: each warp interpolates whole probes (24 lanes = 3 components x
@@ -83,6 +84,7 @@ void launch_step_tail(const Grid<T> &g, const Fields<T> &f, const Probes<T> &pr,
     int blk = 32 * pr.np;
     blk = blk < 32 ? 32 : (blk > 1024 ? 1024 : blk);
     k_step_tail<T><<<1, blk, 0, s>>>(g, f, pr, step);
+    launch_count() += 1;
 }
 
 // Phase table phasor[s][f] = exp(+i 2 pi f (n_s+1) dt) for the count most
@@ -159,8 +161,10 @@ void launch_dft_flush(const Probes<T> &pr, const long long *step, int count, cud
     const int blk = 128;
     k_dft_phasor<<<dim3((pr.nf + blk - 1) / blk, (count + PHASE_RUN - 1) / PHASE_RUN), blk, 0, s>>>(
         pr.freq, pr.nf, pr.phasor, step, count, pr.dt);
+    launch_count() += 1;
     dim3 g2((pr.nf + blk - 1) / blk, (pr.np * 3 + DFT_ROWS - 1) / DFT_ROWS);
     k_dft_accumulate<T><<<g2, blk, 0, s>>>(pr.samples, pr.phasor, pr.F, pr.np, pr.nf, pr.mask, step, count, pr.dt);
+    launch_count() += 1;
 }
 
 template void launch_sources<float>(const Grid<float> &, const Fields<float> &, const Source *, int, double,

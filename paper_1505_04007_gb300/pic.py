@@ -52,7 +52,7 @@ class pic_config(C.Structure):
 
 class pic_stats(C.Structure):
     _fields_ = [("step", C.c_int64), ("n_particles", C.c_int64), ("n_frozen", C.c_int64),
-                ("device_error", C.c_int32), ("n_edge_classes", C.c_int32)]
+                ("device_error", C.c_int32), ("n_edge_classes", C.c_int32), ("kernel_launches", C.c_int64)]
 
 
 class PicError(RuntimeError):

@@ -33,7 +33,7 @@ def test_struct_layout_matches_header():
     # offsets of the trailing fields pin the ctypes mirror to the C layout
     assert C.sizeof(P.pic_material) == 24
     assert P.pic_config.flags.offset == C.sizeof(P.pic_config) - 8
-    assert C.sizeof(P.pic_stats) == 32
+    assert C.sizeof(P.pic_stats) == 40
 
 
 def _cfg(**kw):
