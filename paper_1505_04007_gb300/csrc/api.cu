@@ -143,6 +143,7 @@ struct Sim : SimBase {
     uint8_t *d_mat = nullptr, *d_mat_metal = nullptr;
     uint8_t *d_ecls[3] = {nullptr, nullptr, nullptr};
     uint8_t *d_cls_metal = nullptr;
+    float4 *d_cls_pack = nullptr;
     FieldPlan fplan{};
     bool use_plan = false;
     T *d_cls[3] = {nullptr, nullptr, nullptr};
@@ -191,6 +192,7 @@ struct Sim : SimBase {
         for (int c = 0; c < 3; c++) d_ecls[c] = a.take<uint8_t>(Ts);
         for (int q3 = 0; q3 < 3; q3++) d_cls[q3] = a.take<T>(256);
         d_cls_metal = a.take<uint8_t>(256);
+        d_cls_pack = a.take<float4>(256);
         d_flag = a.take<int>(n_tiles);
         d_step = a.take<long long>(1);
         d_err = a.take<int>(1);
@@ -384,6 +386,10 @@ struct Sim : SimBase {
             CUDA_TRY(cudaMemcpyAsync(d_ecls[comp], ecls[comp].data(), (size_t)N, cudaMemcpyHostToDevice, stream));
         for (int q3 = 0; q3 < 3; q3++)
             CUDA_TRY(cudaMemcpyAsync(d_cls[q3], cls[q3].data(), 256 * sizeof(T), cudaMemcpyHostToDevice, stream));
+        std::vector<float4> pack(256);
+        for (int q = 0; q < 256; q++)
+            pack[q] = make_float4((float)cls[0][q], (float)cls[1][q], (float)cls[2][q], cls_metal[q] ? 1.f : 0.f);
+        CUDA_TRY(cudaMemcpyAsync(d_cls_pack, pack.data(), 256 * sizeof(float4), cudaMemcpyHostToDevice, stream));
         CUDA_TRY(cudaMemcpyAsync(d_cls_metal, cls_metal.data(), 256, cudaMemcpyHostToDevice, stream));
         // FP32 with whole four-cell groups per row: cut the grid for the
         // four-cells-per-thread kernels (planes of one non-metal material
@@ -432,6 +438,7 @@ struct Sim : SimBase {
         }
         f.cls_kJm1 = d_cls[0]; f.cls_bJ = d_cls[1]; f.cls_cE = d_cls[2];
         f.cls_metal = d_cls_metal;
+        f.cls_pack = d_cls_pack;
         f.jf_flag = d_flag;
         f.step = d_step;
         p.n = 0;

@@ -30,7 +30,6 @@ __device__ __forceinline__ void st4(float *p, const F4 &a) {
     *reinterpret_cast<float4 *>(p) = make_float4(a.v[0], a.v[1], a.v[2], a.v[3]);
 }
 __device__ __forceinline__ F4 zero4() { return F4{{0.f, 0.f, 0.f, 0.f}}; }
-__device__ __forceinline__ F4 fill4(float x) { return F4{{x, x, x, x}}; }
 
 __device__ __forceinline__ int slab(const Grid<float> &g, int a, int x) {
     if (!g.cpml[a]) return -1;
@@ -43,48 +42,6 @@ __device__ __forceinline__ long long psi_idx(const Grid<float> &g, int a, int s,
     if (a == 0) return ((long long)k * g.n[1] + j) * L2 + s;
     if (a == 1) return ((long long)k * L2 + s) * g.n[0] + i;
     return ((long long)s * g.n[1] + j) * g.n[0] + i;
-}
-
-// CPML state of one four-cell group for one derivative axis: the profile
-// (b-1, a, 1/kappa) per cell and where its two psi components live.
-struct Slab4 {
-    bool on;
-    F4 b, a, ik;
-    long long q;
-};
-
-__device__ __forceinline__ Slab4 slab4(const Grid<float> &g, const float *const *bp, const float *const *ap,
-                                       const float *const *kp, int axis, int i0, int j, int k) {
-    Slab4 s;
-    const int x = axis == 0 ? i0 : (axis == 1 ? j : k);
-    const int sp = slab(g, axis, x);
-    s.on = sp >= 0;
-    s.q = 0;
-    s.b = zero4();
-    s.a = zero4();
-    s.ik = fill4(1.f);
-    if (s.on) {
-        s.q = psi_idx(g, axis, sp, i0, j, k);
-        if (axis == 0) {
-            s.b = ld4(bp[0] + i0);
-            s.a = ld4(ap[0] + i0);
-            s.ik = ld4(kp[0] + i0);
-        } else {
-            s.b = fill4(bp[axis][x]);
-            s.a = fill4(ap[axis][x]);
-            s.ik = fill4(kp[axis][x]);
-        }
-    }
-    return s;
-}
-
-// psi += (b-1) psi + a dF for the four cells; returns the new psi.
-__device__ __forceinline__ F4 advance(const Slab4 &s, float *psi, const float d[4], bool store) {
-    F4 p = ld4(psi + s.q);
-#pragma unroll
-    for (int m = 0; m < 4; m++) p.v[m] = p.v[m] + (s.b.v[m] * p.v[m] + s.a.v[m] * d[m]);
-    if (store) st4(psi + s.q, p);
-    return p;
 }
 
 // H^{n+1/2} for cells i0..i0+3 of row (j, k).
@@ -139,28 +96,75 @@ __device__ __forceinline__ void h4(const Grid<float> &g, const Fields<float> &f,
             hz.v[m] -= g.cH * (dEy_dx[m] - dEx_dy[m]);
         }
     } else {
-        const Slab4 sx = slab4(g, f.bH, f.aH, f.ikH, 0, i0, j, k);
-        const Slab4 syl = slab4(g, f.bH, f.aH, f.ikH, 1, i0, j, k);
-        const Slab4 szl = slab4(g, f.bH, f.aH, f.ikH, 2, i0, j, k);
-        F4 pxy = zero4(), pxz = zero4(), pyz = zero4(), pyx = zero4(), pzx = zero4(), pzy = zero4();
-        if (sx.on) {
-            pxy = advance(sx, f.psiH[0][0], dEz_dx, true);   // Hy's d/dx
-            pxz = advance(sx, f.psiH[0][1], dEy_dx, true);   // Hz's d/dx
+        // Each axis adds its terms to the three curl sums in turn (its
+        // profile and psi values are dead once added), which keeps the
+        // register count close to the interior kernel's.
+        float cx[4] = {0.f, 0.f, 0.f, 0.f}, cy[4] = {0.f, 0.f, 0.f, 0.f}, cz[4] = {0.f, 0.f, 0.f, 0.f};
+        {   // x: Hy -= d/dx Ez, Hz += d/dx Ey
+            const int sp = slab(g, 0, i0);
+            if (sp >= 0) {
+                const long long q = psi_idx(g, 0, sp, i0, j, k);
+                const F4 b = ld4(f.bH[0] + i0), a = ld4(f.aH[0] + i0), ik = ld4(f.ikH[0] + i0);
+                F4 p0 = ld4(f.psiH[0][0] + q), p1 = ld4(f.psiH[0][1] + q);
+#pragma unroll
+                for (int m = 0; m < 4; m++) {
+                    p0.v[m] += b.v[m] * p0.v[m] + a.v[m] * dEz_dx[m];
+                    p1.v[m] += b.v[m] * p1.v[m] + a.v[m] * dEy_dx[m];
+                    cy[m] -= ik.v[m] * dEz_dx[m] + p0.v[m];
+                    cz[m] += ik.v[m] * dEy_dx[m] + p1.v[m];
+                }
+                st4(f.psiH[0][0] + q, p0);
+                st4(f.psiH[0][1] + q, p1);
+            } else {
+#pragma unroll
+                for (int m = 0; m < 4; m++) { cy[m] -= dEz_dx[m]; cz[m] += dEy_dx[m]; }
+            }
         }
-        if (syl.on) {
-            pyz = advance(syl, f.psiH[1][0], dEx_dy, true);  // Hz's d/dy
-            pyx = advance(syl, f.psiH[1][1], dEz_dy, true);  // Hx's d/dy
+        {   // y: Hz -= d/dy Ex, Hx += d/dy Ez
+            const int sp = slab(g, 1, j);
+            if (sp >= 0) {
+                const long long q = psi_idx(g, 1, sp, i0, j, k);
+                const float b = f.bH[1][j], a = f.aH[1][j], ik = f.ikH[1][j];
+                F4 p0 = ld4(f.psiH[1][0] + q), p1 = ld4(f.psiH[1][1] + q);
+#pragma unroll
+                for (int m = 0; m < 4; m++) {
+                    p0.v[m] += b * p0.v[m] + a * dEx_dy[m];
+                    p1.v[m] += b * p1.v[m] + a * dEz_dy[m];
+                    cz[m] -= ik * dEx_dy[m] + p0.v[m];
+                    cx[m] += ik * dEz_dy[m] + p1.v[m];
+                }
+                st4(f.psiH[1][0] + q, p0);
+                st4(f.psiH[1][1] + q, p1);
+            } else {
+#pragma unroll
+                for (int m = 0; m < 4; m++) { cz[m] -= dEx_dy[m]; cx[m] += dEz_dy[m]; }
+            }
         }
-        if (szl.on) {
-            pzx = advance(szl, f.psiH[2][0], dEy_dz, true);  // Hx's d/dz
-            pzy = advance(szl, f.psiH[2][1], dEx_dz, true);  // Hy's d/dz
+        {   // z: Hx -= d/dz Ey, Hy += d/dz Ex
+            const int sp = slab(g, 2, k);
+            if (sp >= 0) {
+                const long long q = psi_idx(g, 2, sp, i0, j, k);
+                const float b = f.bH[2][k], a = f.aH[2][k], ik = f.ikH[2][k];
+                F4 p0 = ld4(f.psiH[2][0] + q), p1 = ld4(f.psiH[2][1] + q);
+#pragma unroll
+                for (int m = 0; m < 4; m++) {
+                    p0.v[m] += b * p0.v[m] + a * dEy_dz[m];
+                    p1.v[m] += b * p1.v[m] + a * dEx_dz[m];
+                    cx[m] -= ik * dEy_dz[m] + p0.v[m];
+                    cy[m] += ik * dEx_dz[m] + p1.v[m];
+                }
+                st4(f.psiH[2][0] + q, p0);
+                st4(f.psiH[2][1] + q, p1);
+            } else {
+#pragma unroll
+                for (int m = 0; m < 4; m++) { cx[m] -= dEy_dz[m]; cy[m] += dEx_dz[m]; }
+            }
         }
 #pragma unroll
         for (int m = 0; m < 4; m++) {
-            const float kx = sx.ik.v[m], ky = syl.ik.v[m], kz = szl.ik.v[m];
-            hx.v[m] -= g.cH * (ky * dEz_dy[m] + pyx.v[m] - kz * dEy_dz[m] - pzx.v[m]);
-            hy.v[m] -= g.cH * (kz * dEx_dz[m] + pzy.v[m] - kx * dEz_dx[m] - pxy.v[m]);
-            hz.v[m] -= g.cH * (kx * dEy_dx[m] + pxz.v[m] - ky * dEx_dy[m] - pyz.v[m]);
+            hx.v[m] -= g.cH * cx[m];
+            hy.v[m] -= g.cH * cy[m];
+            hz.v[m] -= g.cH * cz[m];
         }
     }
     st4(f.H[0] + e, hx);
@@ -168,16 +172,27 @@ __device__ __forceinline__ void h4(const Grid<float> &g, const Fields<float> &f,
     st4(f.H[2] + e, hz);
 }
 
-// Eq. 6 (increment form) on a metal edge, then Eq. 8.
-__device__ __forceinline__ float ampere1(const Fields<float> &f, int comp, int cls, long long em, float E, float curl,
-                                         float jf) {
-    float jp = 0.f;
-    if (f.cls_metal[cls]) {
-        const float j0 = f.Jp[comp][em];
-        jp = j0 + (f.cls_kJm1[cls] * j0 + f.cls_bJ[cls] * E);
-        f.Jp[comp][em] = jp;
+// Eq. 6 (increment form) on the metal edges among the four, then Eq. 8, for
+// component comp of cells e..e+3 with edge classes cl; J_p moves as one
+// 16-byte access when any of the four edges is metal.
+__device__ __forceinline__ void ampere4(const Fields<float> &f, int comp, uchar4 cl, long long e, F4 &E, const float curl[4],
+                                        const F4 &jf, const bool doit[4]) {
+    const float4 t0 = f.cls_pack[cl.x], t1 = f.cls_pack[cl.y], t2 = f.cls_pack[cl.z], t3 = f.cls_pack[cl.w];
+    const float4 t[4] = {t0, t1, t2, t3};
+    const bool metal = (t0.w + t1.w + t2.w + t3.w) != 0.f;
+    F4 jp = zero4();
+    if (metal) {
+        jp = ld4(f.Jp[comp] + e);
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            const float j0 = jp.v[m];
+            jp.v[m] = (t[m].w != 0.f && doit[m]) ? j0 + (t[m].x * j0 + t[m].y * E.v[m]) : j0;
+        }
+        st4(f.Jp[comp] + e, jp);
     }
-    return E + f.cls_cE[cls] * (curl - jp - jf);
+#pragma unroll
+    for (int m = 0; m < 4; m++)
+        if (doit[m]) E.v[m] += t[m].z * (curl[m] - (t[m].w != 0.f ? jp.v[m] : 0.f) - jf.v[m]);
 }
 
 // E^{n+1} (with the Drude current of Eq. 6) for cells i0..i0+3 of row (j, k).
@@ -213,7 +228,6 @@ __device__ __forceinline__ void e4(const Grid<float> &g, const Fields<float> &f,
         cl1 = *reinterpret_cast<const uchar4 *>(f.ecls[1] + e);
         cl2 = *reinterpret_cast<const uchar4 *>(f.ecls[2] + e);
     }
-    const int cls[3][4] = {{cl0.x, cl0.y, cl0.z, cl0.w}, {cl1.x, cl1.y, cl1.z, cl1.w}, {cl2.x, cl2.y, cl2.z, cl2.w}};
 
     const float rx = g.r[0], ry = g.r[1], rz = g.r[2];
     float dHz_dy[4], dHy_dz[4], dHx_dz[4], dHz_dx[4], dHy_dx[4], dHx_dy[4];
@@ -228,59 +242,92 @@ __device__ __forceinline__ void e4(const Grid<float> &g, const Fields<float> &f,
         dHy_dx[m] = (hy.v[m] - hym) * rx;
         dHx_dy[m] = (hx.v[m] - hx_jm.v[m]) * ry;
     }
-    // psi and 1/kappa terms; held edges (E stays zero) leave their psi untouched
-    F4 pxy = zero4(), pxz = zero4(), pyx = zero4(), pyz = zero4(), pzx = zero4(), pzy = zero4();
-    F4 kx = fill4(1.f), ky = fill4(1.f), kz = fill4(1.f);
+    // curl sums, one axis at a time (in the absorbing slabs with psi and
+    // 1/kappa); a held edge (E stays zero) leaves its psi untouched
+    float cx[4], cy[4], cz[4];
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+        cx[m] = dHz_dy[m] - dHy_dz[m];
+        cy[m] = dHx_dz[m] - dHz_dx[m];
+        cz[m] = dHy_dx[m] - dHx_dy[m];
+    }
     if (CPML) {
-        const Slab4 sx = slab4(g, f.bE, f.aE, f.ikE, 0, i0, j, k);
-        const Slab4 syl = slab4(g, f.bE, f.aE, f.ikE, 1, i0, j, k);
-        const Slab4 szl = slab4(g, f.bE, f.aE, f.ikE, 2, i0, j, k);
-        kx = sx.ik;
-        ky = syl.ik;
-        kz = szl.ik;
-        if (sx.on) {
-            // Ey's and Ez's d/dx: cell 0 is held when it sits on the x face
-            const F4 o0 = ld4(f.psiE[0][0] + sx.q), o1 = ld4(f.psiE[0][1] + sx.q);
-            pxy = advance(sx, f.psiE[0][0], dHz_dx, false);
-            pxz = advance(sx, f.psiE[0][1], dHy_dx, false);
-            if (fx0) {
-                pxy.v[0] = o0.v[0];
-                pxz.v[0] = o1.v[0];
+        {   // x: Ey -= d/dx Hz, Ez += d/dx Hy
+            const int sp = slab(g, 0, i0);
+            if (sp >= 0) {
+                const long long q = psi_idx(g, 0, sp, i0, j, k);
+                const F4 b = ld4(f.bE[0] + i0), a = ld4(f.aE[0] + i0), ik = ld4(f.ikE[0] + i0);
+                F4 p0 = ld4(f.psiE[0][0] + q), p1 = ld4(f.psiE[0][1] + q);
+                const float o0 = p0.v[0], o1 = p1.v[0];
+#pragma unroll
+                for (int m = 0; m < 4; m++) {
+                    p0.v[m] += b.v[m] * p0.v[m] + a.v[m] * dHz_dx[m];
+                    p1.v[m] += b.v[m] * p1.v[m] + a.v[m] * dHy_dx[m];
+                    cy[m] += (1.f - ik.v[m]) * dHz_dx[m] - p0.v[m];
+                    cz[m] += (ik.v[m] - 1.f) * dHy_dx[m] + p1.v[m];
+                }
+                if (fx0) { p0.v[0] = o0; p1.v[0] = o1; }
+                if (!fz) st4(f.psiE[0][0] + q, p0);
+                if (!fy) st4(f.psiE[0][1] + q, p1);
             }
-            if (!fz) st4(f.psiE[0][0] + sx.q, pxy);
-            if (!fy) st4(f.psiE[0][1] + sx.q, pxz);
         }
-        if (syl.on) {
-            pyx = advance(syl, f.psiE[1][1], dHz_dy, !(fy || fz));  // Ex's d/dy
-            const F4 o0 = ld4(f.psiE[1][0] + syl.q);
-            pyz = advance(syl, f.psiE[1][0], dHx_dy, false);        // Ez's d/dy
-            if (fx0) pyz.v[0] = o0.v[0];
-            if (!fy) st4(f.psiE[1][0] + syl.q, pyz);
+        {   // y: Ez -= d/dy Hx, Ex += d/dy Hz
+            const int sp = slab(g, 1, j);
+            if (sp >= 0) {
+                const long long q = psi_idx(g, 1, sp, i0, j, k);
+                const float b = f.bE[1][j], a = f.aE[1][j], ik = f.ikE[1][j];
+                F4 p0 = ld4(f.psiE[1][0] + q), p1 = ld4(f.psiE[1][1] + q);
+                const float o0 = p0.v[0];
+#pragma unroll
+                for (int m = 0; m < 4; m++) {
+                    p0.v[m] += b * p0.v[m] + a * dHx_dy[m];
+                    p1.v[m] += b * p1.v[m] + a * dHz_dy[m];
+                    cz[m] += (1.f - ik) * dHx_dy[m] - p0.v[m];
+                    cx[m] += (ik - 1.f) * dHz_dy[m] + p1.v[m];
+                }
+                if (fx0) p0.v[0] = o0;
+                if (!fy) st4(f.psiE[1][0] + q, p0);
+                if (!(fy || fz)) st4(f.psiE[1][1] + q, p1);
+            }
         }
-        if (szl.on) {
-            pzx = advance(szl, f.psiE[2][0], dHy_dz, !(fy || fz));  // Ex's d/dz
-            const F4 o1 = ld4(f.psiE[2][1] + szl.q);
-            pzy = advance(szl, f.psiE[2][1], dHx_dz, false);        // Ey's d/dz
-            if (fx0) pzy.v[0] = o1.v[0];
-            if (!fz) st4(f.psiE[2][1] + szl.q, pzy);
+        {   // z: Ex -= d/dz Hy, Ey += d/dz Hx
+            const int sp = slab(g, 2, k);
+            if (sp >= 0) {
+                const long long q = psi_idx(g, 2, sp, i0, j, k);
+                const float b = f.bE[2][k], a = f.aE[2][k], ik = f.ikE[2][k];
+                F4 p0 = ld4(f.psiE[2][0] + q), p1 = ld4(f.psiE[2][1] + q);
+                const float o1 = p1.v[0];
+#pragma unroll
+                for (int m = 0; m < 4; m++) {
+                    p0.v[m] += b * p0.v[m] + a * dHy_dz[m];
+                    p1.v[m] += b * p1.v[m] + a * dHx_dz[m];
+                    cx[m] += (1.f - ik) * dHy_dz[m] - p0.v[m];
+                    cy[m] += (ik - 1.f) * dHx_dz[m] + p1.v[m];
+                }
+                if (fx0) p1.v[0] = o1;
+                if (!(fy || fz)) st4(f.psiE[2][0] + q, p0);
+                if (!fz) st4(f.psiE[2][1] + q, p1);
+            }
         }
     }
+    bool doX[4], doY[4], doZ[4];
 #pragma unroll
     for (int m = 0; m < 4; m++) {
         const bool fx = fx0 && m == 0;
-        const bool doX = !(fy || fz), doY = !(fx || fz), doZ = !(fx || fy);
-        const long long em = e + m;
-        const float cx = ky.v[m] * dHz_dy[m] + pyx.v[m] - kz.v[m] * dHy_dz[m] - pzx.v[m];
-        const float cy = kz.v[m] * dHx_dz[m] + pzy.v[m] - kx.v[m] * dHz_dx[m] - pxy.v[m];
-        const float cz = kx.v[m] * dHy_dx[m] + pxz.v[m] - ky.v[m] * dHx_dy[m] - pyz.v[m];
-        if (MAT) {
-            if (doX) ex.v[m] = ampere1(f, 0, cls[0][m], em, ex.v[m], cx, jfx.v[m]);
-            if (doY) ey.v[m] = ampere1(f, 1, cls[1][m], em, ey.v[m], cy, jfy.v[m]);
-            if (doZ) ez.v[m] = ampere1(f, 2, cls[2][m], em, ez.v[m], cz, jfz.v[m]);
-        } else {
-            if (doX) ex.v[m] += cEu * (cx - jfx.v[m]);
-            if (doY) ey.v[m] += cEu * (cy - jfy.v[m]);
-            if (doZ) ez.v[m] += cEu * (cz - jfz.v[m]);
+        doX[m] = !(fy || fz);
+        doY[m] = !(fx || fz);
+        doZ[m] = !(fx || fy);
+    }
+    if (MAT) {
+        ampere4(f, 0, cl0, e, ex, cx, jfx, doX);
+        ampere4(f, 1, cl1, e, ey, cy, jfy, doY);
+        ampere4(f, 2, cl2, e, ez, cz, jfz, doZ);
+    } else {
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            if (doX[m]) ex.v[m] += cEu * (cx[m] - jfx.v[m]);
+            if (doY[m]) ey.v[m] += cEu * (cy[m] - jfy.v[m]);
+            if (doZ[m]) ez.v[m] += cEu * (cz[m] - jfz.v[m]);
         }
     }
     st4(f.E[0] + e, ex);
@@ -313,7 +360,7 @@ __global__ void __launch_bounds__(256) k_H4_bulk(Grid<float> g, Fields<float> f,
     BOX_CELL(bl);
     h4<false>(g, f, i0, j, k, *f.step);
 }
-__global__ void __launch_bounds__(256) k_H4_cpml(Grid<float> g, Fields<float> f, BoxList bl) {
+__global__ void __launch_bounds__(256, 3) k_H4_cpml(Grid<float> g, Fields<float> f, BoxList bl) {
     BOX_CELL(bl);
     h4<true>(g, f, i0, j, k, *f.step);
 }
@@ -328,7 +375,7 @@ __global__ void __launch_bounds__(256) k_E4_mat(Grid<float> g, Fields<float> f, 
     e4<false, true>(g, f, i0, j, k, *f.step, 0.f);
 }
 // one non-metal material inside the absorbing slabs
-__global__ void __launch_bounds__(256) k_E4_cpml_vac(Grid<float> g, Fields<float> f, BoxList bl) {
+__global__ void __launch_bounds__(256, 3) k_E4_cpml_vac(Grid<float> g, Fields<float> f, BoxList bl) {
     BOX_CELL(bl);
     e4<true, false>(g, f, i0, j, k, *f.step, b.cE);
 }

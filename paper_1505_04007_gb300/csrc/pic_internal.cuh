@@ -52,6 +52,7 @@ struct Fields {
     const uint8_t *ecls[3];           // edge class per E component
     const T *cls_kJm1, *cls_bJ, *cls_cE; // per-class Eq. 6 (kJ-1, bJ) and Eq. 8 factors
     const uint8_t *cls_metal;         // per-class: wp^2 > 0
+    const float4 *cls_pack;           // per-class (kJ-1, bJ, cE, metal) in float (FP32 kernels)
     int *jf_flag;                     // per tile: step+1 when J_f was written
     const long long *step;            // device step counter n
 };

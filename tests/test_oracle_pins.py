@@ -17,6 +17,10 @@ time level, a transposed index) breaks at least one of them:
 * CPML: reflection below -40 dB against a larger domain.
 * Probe DFT: equals the direct sum of the recorded probe series, and the
   closed-form geometric series of the plasma oscillation.
+* Bulk Drude permittivity (Eq. 1) recovered from a plane wave in a metal:
+  the two-probe ratio gives the numerical wavenumber, and
+  eps = (c K/Omega)^2 must equal the discrete Drude-Yee permittivity
+  1 - wp^2/(Omega(Omega + i gamma cos(w dt/2))) and, to O((w dt)^2), Eq. 1.
 """
 import math
 
@@ -119,6 +123,39 @@ def test_probe_dft_matches_direct_and_closed_form():
     assert np.abs(F - cf).max() <= 1e-9 * np.abs(cf).max()
     # untouched components stay zero
     assert np.all(o.probe_read()[0, 1:] == 0)
+
+
+def test_bulk_drude_permittivity_from_plane_wave():
+    # Metal everywhere, periodic x and y (plane wave along z), absorbing z ends
+    # far away; a sheet current launches a pulse centred at 3.5 PHz whose
+    # spectrum stays well above the plasma frequency (2.18 PHz), so nothing
+    # rings near cut-off inside the window.
+    nz = 4000
+    bc = (W.BC_PERIODIC,) * 4 + (W.BC_CPML, W.BC_CPML)
+    w = box_workload(2, 2, nz, bc=bc, material=np.ones((nz, 2, 2), np.uint8), table=[[0, 0, 1], [WP, GAM, 1.0]])
+    o = O.Oracle(w)
+    zs, z1, z2 = 1500, 1600, 1610
+    o.add_source(0, (0, 2, 0, 2, zs, zs + 1), 1e16, 1800 * w.dt, 420 * w.dt, 3.5e15)
+    freqs = np.linspace(3.1e15, 3.9e15, 41)
+    o.probe_dft([[0.5 * w.dx, 0, z1 * w.dz], [0.5 * w.dx, 0, z2 * w.dz]], freqs, 0b001)
+    prev = O.set_threads(0)
+    O.set_threads(2)  # a 2x2-cell cross-section: more threads only add overhead
+    try:
+        o.step(12000)  # the reflections from the z ends have not come back yet
+    finally:
+        O.set_threads(prev)
+    F = o.probe_read()[:, 0, :]
+    kt = -1j * np.log(F[1] / F[0]) / ((z2 - z1) * w.dz)   # exp(+i k z) with the e^{-i w t} convention
+    K = 2 / w.dz * np.sin(kt * w.dz / 2)
+    om = 2 * np.pi * freqs
+    Om = 2 / w.dt * np.sin(om * w.dt / 2)
+    eps = (W.C0 * K / Om) ** 2
+    eps_num = 1 - WP**2 / (Om * (Om + 1j * GAM * np.cos(om * w.dt / 2)))
+    eps_eq1 = 1 - WP**2 / (om * (om + 1j * GAM))
+    assert np.abs(eps - eps_num).max() <= 1e-5 * np.abs(eps_num).min()
+    # the collision term (imaginary part, ~1e-3) is resolved too
+    assert np.abs(eps.imag - eps_num.imag).max() <= 0.02 * np.abs(eps_num.imag).min()
+    assert (np.abs(eps - eps_eq1) / np.abs(1 - eps_eq1)).max() <= 1e-3
 
 
 # ----------------------------------------------------------------- energy --
