@@ -191,6 +191,20 @@ int pic_set_field(pic_handle *h, int which, const double *in);
 /* Counters and the device error word.  Synchronises. */
 int pic_get_stats(pic_handle *h, pic_stats *out);
 
+/* Write the complete state of the simulation to the file `path`: fields,
+ * J, CPML memory, particles, probe accumulators and buffered samples, sources
+ * and the step counter (the whole device arena plus the host-side counters).
+ * Synchronises.  Errors: PIC_ERR_ARG (file cannot be written), PIC_ERR_CUDA. */
+int pic_save(pic_handle *h, const char *path);
+
+/* Restore a state written by pic_save into h, which must have been created
+ * with the same configuration (grid, precision, boundaries, materials,
+ * capacities); stepping then continues exactly where the saved run stood
+ * (up to the summation order of atomic current deposits).  Synchronises.
+ * Errors: PIC_ERR_ARG (missing/truncated file or a different configuration),
+ * PIC_ERR_CUDA. */
+int pic_load(pic_handle *h, const char *path);
+
 /* Time the given number of steps on the handle's stream with CUDA events and
  * return the average duration of each kernel kind in microseconds:
  * out[0] H update, out[1] push+deposit, out[2] E update, out[3] step tail

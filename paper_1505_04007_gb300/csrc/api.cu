@@ -561,6 +561,131 @@ struct Sim : SimBase {
         return PIC_OK;
     }
 
+    // ------------------------------------------------------ checkpoint --
+    // File: magic, fixed header (geometry, precision, arena size, host-side
+    // counters), the source list, then the whole device arena.  The arena's
+    // layout is a function of the configuration alone, so a handle created
+    // with the same configuration restores every array exactly.
+    struct SaveHeader {
+        char magic[8];
+        uint32_t version;
+        int32_t precision;
+        int64_t n[3];
+        uint64_t arena_bytes;
+        int64_t max_particles;
+        int32_t max_probes, max_freqs;
+        int64_t step_host, np;
+        int32_t buffered, since_sort, bold_stale, have_q, deposit, probe_np, probe_nf, nsources;
+        uint32_t probe_mask, pad;
+        double q, m;
+    };
+
+    int save(const char *path) {
+        int rc = sync();
+        if (rc) return rc;
+        SaveHeader hd{};
+        memcpy(hd.magic, "PICSAVE1", 8);
+        hd.version = 1;
+        hd.precision = cfg.precision;
+        for (int a = 0; a < 3; a++) hd.n[a] = n[a];
+        hd.arena_bytes = arena_bytes;
+        hd.max_particles = cfg.max_particles;
+        hd.max_probes = cfg.max_probes;
+        hd.max_freqs = cfg.max_freqs;
+        hd.step_host = step_host;
+        hd.np = p.n;
+        hd.buffered = buffered;
+        hd.since_sort = since_sort;
+        hd.bold_stale = bold_stale;
+        hd.have_q = have_q;
+        hd.deposit = pp.deposit;
+        hd.probe_np = pr.np;
+        hd.probe_nf = pr.nf;
+        hd.probe_mask = pr.mask;
+        hd.nsources = (int)sources.size();
+        hd.q = q;
+        hd.m = m;
+        FILE *fp = fopen(path, "wb");
+        if (!fp) return fail(PIC_ERR_ARG, "cannot open %s for writing", path);
+        bool ok = fwrite(&hd, sizeof hd, 1, fp) == 1;
+        if (ok && !sources.empty()) ok = fwrite(sources.data(), sizeof(Source), sources.size(), fp) == sources.size();
+        std::vector<char> buf;
+        const size_t chunk = (size_t)64 << 20;
+        for (size_t off = 0; ok && off < arena_bytes; off += chunk) {
+            const size_t len = std::min(chunk, arena_bytes - off);
+            buf.resize(len);
+            if (cudaMemcpy(buf.data(), (char *)arena + off, len, cudaMemcpyDeviceToHost) != cudaSuccess) {
+                fclose(fp);
+                return fail(PIC_ERR_CUDA, "reading the device state failed");
+            }
+            ok = fwrite(buf.data(), 1, len, fp) == len;
+        }
+        if (fclose(fp) != 0) ok = false;
+        if (!ok) return fail(PIC_ERR_ARG, "writing %s failed", path);
+        return PIC_OK;
+    }
+
+    int load(const char *path) {
+        FILE *fp = fopen(path, "rb");
+        if (!fp) return fail(PIC_ERR_ARG, "cannot open %s", path);
+        SaveHeader hd{};
+        if (fread(&hd, sizeof hd, 1, fp) != 1 || memcmp(hd.magic, "PICSAVE1", 8) != 0 || hd.version != 1) {
+            fclose(fp);
+            return fail(PIC_ERR_ARG, "%s is not a checkpoint of this library", path);
+        }
+        if (hd.precision != cfg.precision || hd.n[0] != n[0] || hd.n[1] != n[1] || hd.n[2] != n[2] ||
+            hd.arena_bytes != arena_bytes || hd.max_particles != cfg.max_particles ||
+            hd.max_probes != cfg.max_probes || hd.max_freqs != cfg.max_freqs || hd.nsources < 0 ||
+            hd.nsources > MAX_SOURCES) {
+            fclose(fp);
+            return fail(PIC_ERR_ARG, "checkpoint %s was written by a differently configured simulation", path);
+        }
+        std::vector<Source> src((size_t)hd.nsources);
+        if (hd.nsources && fread(src.data(), sizeof(Source), src.size(), fp) != src.size()) {
+            fclose(fp);
+            return fail(PIC_ERR_ARG, "truncated checkpoint %s", path);
+        }
+        int rc = sync();
+        if (rc) { fclose(fp); return rc; }
+        std::vector<char> buf;
+        const size_t chunk = (size_t)64 << 20;
+        for (size_t off = 0; off < arena_bytes; off += chunk) {
+            const size_t len = std::min(chunk, arena_bytes - off);
+            buf.resize(len);
+            if (fread(buf.data(), 1, len, fp) != len) {
+                fclose(fp);
+                return fail(PIC_ERR_ARG, "truncated checkpoint %s", path);
+            }
+            if (cudaMemcpy((char *)arena + off, buf.data(), len, cudaMemcpyHostToDevice) != cudaSuccess) {
+                fclose(fp);
+                return fail(PIC_ERR_CUDA, "writing the device state failed");
+            }
+        }
+        fclose(fp);
+        drop_graph();
+        sources = src;
+        step_host = hd.step_host;
+        p.n = hd.np;
+        buffered = hd.buffered;
+        since_sort = hd.since_sort;
+        bold_stale = hd.bold_stale != 0;
+        have_q = hd.have_q != 0;
+        q = hd.q;
+        m = hd.m;
+        pp.deposit = hd.deposit;
+        pr.np = hd.probe_np;
+        pr.nf = hd.probe_nf;
+        pr.mask = hd.probe_mask;
+        if (have_q) {
+            pp.qmdt2 = (T)(q * cfg.dt / (2.0 * m));
+            for (int c = 0; c < 3; c++) {
+                const int a1 = (c + 1) % 3, a2 = (c + 2) % 3;
+                pp.jscale[c] = (T)(-q / (cfg.dt * d[a1] * d[a2]));
+            }
+        }
+        return PIC_OK;
+    }
+
     int profile_steps(long long nsteps, double *out) {
         int rc = refresh_bold();
         if (rc) return rc;
@@ -1017,6 +1142,18 @@ int pic_get_stats(pic_handle *h, pic_stats *out) {
     g_err.clear();
     if (!h || !out) return fail(PIC_ERR_ARG, "NULL argument");
     return h->precision == PIC_FP64 ? stats_t(S<double>(h), out) : stats_t(S<float>(h), out);
+}
+
+int pic_save(pic_handle *h, const char *path) {
+    g_err.clear();
+    if (!h || !path) return fail(PIC_ERR_ARG, "NULL argument");
+    return DISPATCH(h, save(path));
+}
+
+int pic_load(pic_handle *h, const char *path) {
+    g_err.clear();
+    if (!h || !path) return fail(PIC_ERR_ARG, "NULL argument");
+    return DISPATCH(h, load(path));
 }
 
 int pic_profile_steps(pic_handle *h, int64_t nsteps, double *out_us) {

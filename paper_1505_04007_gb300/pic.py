@@ -30,7 +30,7 @@ ERRORS = {-1: "PIC_ERR_ARG", -2: "PIC_ERR_CFL", -3: "PIC_ERR_OOM", -4: "PIC_ERR_
 EXPORTS = ("pic_last_error", "pic_workspace_size", "pic_create", "pic_destroy", "pic_set_stream",
            "pic_add_particles", "pic_get_particles", "pic_set_deposit", "pic_add_source", "pic_probe_dft",
            "pic_step", "pic_sync", "pic_probe_read", "pic_get_field", "pic_set_field", "pic_get_stats",
-           "pic_profile_steps", "pic_dft_fold_static")
+           "pic_save", "pic_load", "pic_profile_steps", "pic_dft_fold_static")
 
 
 class pic_material(C.Structure):
@@ -94,6 +94,8 @@ def load(path: str | None = None):
     L.pic_set_field.argtypes = [h, C.c_int, dp]
     L.pic_get_stats.argtypes = [h, C.POINTER(pic_stats)]
     L.pic_profile_steps.argtypes = [h, C.c_int64, dp]
+    L.pic_save.argtypes = [h, C.c_char_p]
+    L.pic_load.argtypes = [h, C.c_char_p]
     L.pic_dft_fold_static.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_uint32, C.c_void_p, C.c_int,
                                       C.c_int64, C.c_double, C.c_void_p, C.c_void_p]
     _lib = L
@@ -194,6 +196,14 @@ def pic_get_stats(h) -> pic_stats:
     s = pic_stats()
     _check(load().pic_get_stats(h, C.byref(s)), "pic_get_stats")
     return s
+
+
+def pic_save(h, path: str) -> None:
+    _check(load().pic_save(h, os.fsencode(path)), "pic_save")
+
+
+def pic_load(h, path: str) -> None:
+    _check(load().pic_load(h, os.fsencode(path)), "pic_load")
 
 
 def pic_profile_steps(h, nsteps: int) -> dict:
@@ -310,6 +320,12 @@ class Simulation:
 
     def profile(self, nsteps):
         return pic_profile_steps(self.h, nsteps)
+
+    def save(self, path):
+        pic_save(self.h, path)
+
+    def load(self, path):
+        pic_load(self.h, path)
 
     def close(self):
         if getattr(self, "h", None):
