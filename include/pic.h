@@ -205,11 +205,16 @@ int pic_save(pic_handle *h, const char *path);
  * PIC_ERR_CUDA. */
 int pic_load(pic_handle *h, const char *path);
 
-/* Time the given number of steps on the handle's stream with CUDA events and
- * return the average duration of each kernel kind in microseconds:
- * out[0] H update, out[1] push+deposit, out[2] E update, out[3] step tail
- * (probe sampling), out[4] probe DFT flush per step, out[5] whole step.
- * Runs real steps (the simulation advances).  Synchronises. */
+/* Time the given number of steps with CUDA events placed between the phases
+ * of steps run exactly as pic_step runs them (the push and deposit overlap
+ * the E update on a second stream, the absorbing-slab part of each field
+ * update runs beside the interior part).  Returns per-step averages in
+ * microseconds: out[0] H update (from the start of the step to the end of
+ * the H update on both streams), out[1] push + deposit (its own stream),
+ * out[2] E update (both streams), out[3] wait for the deposit + free-current
+ * term + probe sampling, out[4] probe DFT flush per step, out[5] whole step
+ * (without the brick sort that precedes every 16th step).  Runs real steps
+ * (the simulation advances).  Synchronises. */
 int pic_profile_steps(pic_handle *h, int64_t nsteps, double *out_us);
 
 /* Probe-DFT fold that allocates no device memory.  The paper has no

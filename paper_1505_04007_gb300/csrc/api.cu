@@ -128,6 +128,10 @@ struct Sim : SimBase {
     long long N = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t side = nullptr;  // electron kernels, beside the field updates
+    cudaStream_t aux = nullptr;   // field updates over the absorbing slabs, beside the interior ones
+    cudaEvent_t ev_fork = nullptr, ev_gathered = nullptr, ev_h = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_hf = nullptr, ev_hj = nullptr, ev_ef = nullptr, ev_ej = nullptr;
     void *arena = nullptr;
     bool own_arena = false;
     size_t arena_bytes = 0;
@@ -149,6 +153,7 @@ struct Sim : SimBase {
     T *d_cls[3] = {nullptr, nullptr, nullptr};
     T *d_prof[18];
     int *d_flag = nullptr;
+    int *d_jf_list = nullptr, *d_jf_count = nullptr;
     long long *d_step = nullptr;
     int *d_err = nullptr;
     double *d_probe_xyz = nullptr, *d_freq = nullptr, *d_samples = nullptr, *d_F = nullptr, *d_phasor = nullptr;
@@ -194,6 +199,8 @@ struct Sim : SimBase {
         d_cls_metal = a.take<uint8_t>(256);
         d_cls_pack = a.take<float4>(256);
         d_flag = a.take<int>(n_tiles);
+        d_jf_list = a.take<int>(n_tiles);
+        d_jf_count = a.take<int>(1);
         d_step = a.take<long long>(1);
         d_err = a.take<int>(1);
         const size_t mp = (size_t)cfg.max_particles;
@@ -203,6 +210,7 @@ struct Sim : SimBase {
             p.u[c] = a.take<T>(mp);
             p.ulo[c] = a.take<T>(mp);
             p.bold[c] = a.take<T>(mp);
+            p.eg[c] = a.take<T>(mp);
         }
         p.status = a.take<uint8_t>(mp);
         p.id = a.take<long long>(mp);
@@ -376,6 +384,14 @@ struct Sim : SimBase {
             own_stream = true;
         }
         CUDA_TRY(cudaMemsetAsync(arena, 0, arena_bytes, stream));
+        {
+            int least = 0, greatest = 0;
+            CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+            CUDA_TRY(cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, greatest));
+            CUDA_TRY(cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking));
+            for (cudaEvent_t *e : {&ev_fork, &ev_gathered, &ev_h, &ev_join, &ev_hf, &ev_hj, &ev_ef, &ev_ej})
+                CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+        }
 
         // material map and per-material metal flag (particle absorption)
         std::vector<uint8_t> metal(256, 0);
@@ -440,6 +456,8 @@ struct Sim : SimBase {
         f.cls_metal = d_cls_metal;
         f.cls_pack = d_cls_pack;
         f.jf_flag = d_flag;
+        f.jf_list = d_jf_list;
+        f.jf_count = d_jf_count;
         f.step = d_step;
         p.n = 0;
         pp.mat = d_mat;
@@ -458,8 +476,14 @@ struct Sim : SimBase {
     ~Sim() override {
         if (stream) cudaStreamSynchronize(stream);
         drop_graph();
+        if (side) cudaStreamSynchronize(side);
+        if (aux) cudaStreamSynchronize(aux);
         if (own_arena && arena) cudaFree(arena);
         if (own_stream && stream) cudaStreamDestroy(stream);
+        if (side) cudaStreamDestroy(side);
+        if (aux) cudaStreamDestroy(aux);
+        for (cudaEvent_t e : {ev_fork, ev_gathered, ev_h, ev_join, ev_hf, ev_hj, ev_ef, ev_ej})
+            if (e) cudaEventDestroy(e);
     }
 
     void drop_graph() {
@@ -470,16 +494,63 @@ struct Sim : SimBase {
     }
 
     // ---------------------------------------------------------- stepping --
-    void launch_step(bool sort) {
+    // Work queued on `to` after this waits for the work queued on `from` so far.
+    static void fork_join(cudaStream_t from, cudaStream_t to, cudaEvent_t ev) {
+        cudaEventRecord(ev, from);
+        cudaStreamWaitEvent(to, ev, 0);
+    }
+
+    // One step.  On the side stream the electrons' E^n is gathered while
+    // the main stream updates H (which leaves E alone); once H^{n+1/2} is
+    // final the push and deposit run there while the main stream updates E
+    // without the free current; k_jf_apply adds the free current once both
+    // are done.  With concurrent = false everything runs in that order on
+    // the main stream.  pe (optional) receives 7 timing events: step start,
+    // H done, push start, push done, E start, E done, tail done.
+    void launch_step(bool sort, bool concurrent = true, cudaEvent_t *pe = nullptr) {
         if (sort) {
             psort.n = p.n;
             launch_sort<T>(p, psort, sb, stream);
         }
-        launch_update_H<T>(g, f, use_plan ? &fplan : nullptr, stream);
-        launch_push_deposit<T>(g, f, p, pp, stream);
+        if (pe) cudaEventRecord(pe[0], stream);
+        const bool parts = p.n > 0, fork = concurrent && parts;
+        if (fork) {
+            cudaEventRecord(ev_fork, stream);
+            cudaStreamWaitEvent(side, ev_fork, 0);
+            launch_gather_E<T>(g, f, p, side);
+            cudaEventRecord(ev_gathered, side);
+        } else if (parts) {
+            launch_gather_E<T>(g, f, p, stream);
+        }
+        // the absorbing-slab boxes of each field update run on aux beside the interior boxes
+        const bool split = concurrent && use_plan;
+        if (split) fork_join(stream, aux, ev_hf);
+        launch_update_H<T>(g, f, use_plan ? &fplan : nullptr, stream, split ? aux : stream);
+        if (split) fork_join(aux, stream, ev_hj);
+        if (pe) cudaEventRecord(pe[1], stream);
         launch_sources<T>(g, f, sources.data(), (int)sources.size(), cfg.dt, stream);
-        launch_update_E<T>(g, f, use_plan ? &fplan : nullptr, stream);
+        if (fork) {
+            cudaEventRecord(ev_h, stream);
+            cudaStreamWaitEvent(side, ev_h, 0);
+            if (pe) cudaEventRecord(pe[2], side);
+            launch_push_deposit<T>(g, f, p, pp, side);
+            if (pe) cudaEventRecord(pe[3], side);
+            cudaEventRecord(ev_join, side);
+            cudaStreamWaitEvent(stream, ev_gathered, 0);
+        } else {
+            if (pe) cudaEventRecord(pe[2], stream);
+            if (parts) launch_push_deposit<T>(g, f, p, pp, stream);
+            if (pe) cudaEventRecord(pe[3], stream);
+        }
+        if (pe) cudaEventRecord(pe[4], stream);
+        if (split) fork_join(stream, aux, ev_ef);
+        launch_update_E<T>(g, f, use_plan ? &fplan : nullptr, stream, split ? aux : stream);
+        if (split) fork_join(aux, stream, ev_ej);
+        if (pe) cudaEventRecord(pe[5], stream);
+        if (fork) cudaStreamWaitEvent(stream, ev_join, 0);
+        launch_jf_apply<T>(g, f, (int)n_tiles, stream);
         launch_step_tail<T>(g, f, pr, d_step, stream);
+        if (pe) cudaEventRecord(pe[6], stream);
     }
 
     int ensure_graph() {
@@ -691,50 +762,39 @@ struct Sim : SimBase {
         if (rc) return rc;
         for (int q6 = 0; q6 < 6; q6++) out[q6] = 0.0;
         if (nsteps <= 0) return PIC_OK;
+        // The steps run exactly as pic_step runs them (same streams and
+        // overlap), with timing events at the phase boundaries.
+        constexpr int NE = 8;
         const int B = DFT_BLOCK;
-        std::vector<cudaEvent_t> ev((size_t)B * 6);
+        std::vector<cudaEvent_t> ev((size_t)B * NE);
         for (auto &e : ev) CUDA_TRY(cudaEventCreate(&e));
         long long done = 0;
         double acc[6] = {0, 0, 0, 0, 0, 0};
         while (done < nsteps) {
             const int cnt = (int)std::min<long long>(B, nsteps - done);
             for (int s = 0; s < cnt; s++) {
-                cudaEvent_t *e = &ev[(size_t)s * 6];
+                cudaEvent_t *e = &ev[(size_t)s * NE];
                 const bool sort = since_sort >= SORT_EVERY;
-                if (sort) {
-                    psort.n = p.n;
-                    launch_sort<T>(p, psort, sb, stream);
-                }
+                launch_step(sort, true, e);
                 since_sort = sort ? 1 : since_sort + 1;
-                cudaEventRecord(e[0], stream);
-                launch_update_H<T>(g, f, use_plan ? &fplan : nullptr, stream);
-                cudaEventRecord(e[1], stream);
-                launch_push_deposit<T>(g, f, p, pp, stream);
-                launch_sources<T>(g, f, sources.data(), (int)sources.size(), cfg.dt, stream);
-                cudaEventRecord(e[2], stream);
-                launch_update_E<T>(g, f, use_plan ? &fplan : nullptr, stream);
-                cudaEventRecord(e[3], stream);
-                launch_step_tail<T>(g, f, pr, d_step, stream);
-                cudaEventRecord(e[4], stream);
                 buffered++;
                 step_host++;
                 if (buffered == DFT_BLOCK) {
                     launch_dft_flush<T>(pr, d_step, DFT_BLOCK, stream);
                     buffered = 0;
                 }
-                cudaEventRecord(e[5], stream);
+                cudaEventRecord(e[7], stream);
             }
             CUDA_TRY(cudaGetLastError());
-            CUDA_TRY(cudaEventSynchronize(ev[(size_t)(cnt - 1) * 6 + 5]));
+            CUDA_TRY(cudaEventSynchronize(ev[(size_t)(cnt - 1) * NE + 7]));
             for (int s = 0; s < cnt; s++) {
-                cudaEvent_t *e = &ev[(size_t)s * 6];
-                float ms;
-                for (int q5 = 0; q5 < 5; q5++) {
-                    cudaEventElapsedTime(&ms, e[q5], e[q5 + 1]);
-                    acc[q5] += ms;
+                cudaEvent_t *e = &ev[(size_t)s * NE];
+                const int from[6] = {0, 2, 4, 5, 6, 0}, to[6] = {1, 3, 5, 6, 7, 7};
+                for (int q6 = 0; q6 < 6; q6++) {
+                    float ms;
+                    cudaEventElapsedTime(&ms, e[from[q6]], e[to[q6]]);
+                    acc[q6] += ms;
                 }
-                cudaEventElapsedTime(&ms, e[0], e[5]);
-                acc[5] += ms;
             }
             done += cnt;
         }

@@ -94,9 +94,10 @@ __global__ void __launch_bounds__(256) k_update_H(Grid<T> g, Fields<T> f) {
     f.H[2][e] -= g.cH * cz;
 }
 
-// Eq. 6 on metal edges, then Eq. 8, for one E component at linear index e.
+// Eq. 6 on metal edges, then Eq. 8 without the free current (k_jf_apply
+// subtracts that once the deposit of the step is complete).
 template <typename T>
-__device__ __forceinline__ void ampere(const Fields<T> &f, int c, long long e, T curl, T jf) {
+__device__ __forceinline__ void ampere(const Fields<T> &f, int c, long long e, T curl) {
     const int cls = f.ecls[c][e];
     T E = f.E[c][e];
     T jp = T(0);
@@ -108,7 +109,7 @@ __device__ __forceinline__ void ampere(const Fields<T> &f, int c, long long e, T
         jp = j0 + (f.cls_kJm1[cls] * j0 + f.cls_bJ[cls] * E);
         f.Jp[c][e] = jp;
     }
-    f.E[c][e] = E + f.cls_cE[cls] * (curl - jp - jf);
+    f.E[c][e] = E + f.cls_cE[cls] * (curl - jp);
 }
 
 template <typename T>
@@ -130,14 +131,6 @@ __global__ void __launch_bounds__(256) k_update_E(Grid<T> g, Fields<T> f) {
     const long long ojm = j > 0 ? sy : (g.per[1] ? -(long long)(ny - 1) * sy : 0);
     const long long okm = k > 0 ? sz : (g.per[2] ? -(long long)(nz - 1) * sz : 0);
 
-    const long long t = ((long long)(k / TILE_Z) * g.nt[1] + j / TILE_Y) * g.nt[0] + i / TILE_X;
-    const bool jf_here = f.jf_flag[t] == (int)(*f.step + 1);
-    T jf[3] = {T(0), T(0), T(0)};
-    if (jf_here) {
-#pragma unroll
-        for (int c = 0; c < 3; c++) jf[c] = f.Jf[c][e];
-    }
-
     const T *Hx = f.H[0], *Hy = f.H[1], *Hz = f.H[2];
     const T hx = Hx[e], hy = Hy[e], hz = Hz[e];
     const int s0 = slab_pos(g, 0, i), s1 = slab_pos(g, 1, j), s2 = slab_pos(g, 2, k);
@@ -156,7 +149,7 @@ __global__ void __launch_bounds__(256) k_update_E(Grid<T> g, Fields<T> f) {
             const long long q = psi_at(g, 2, s2, i, j, k);
             pz = f.psiE[2][0][q] + (f.bE[2][k] * f.psiE[2][0][q] + f.aE[2][k] * dHy_dz); f.psiE[2][0][q] = pz;
         }
-        ampere(f, 0, e, ky * dHz_dy + py - kz * dHy_dz - pz, jf[0]);
+        ampere(f, 0, e, ky * dHz_dy + py - kz * dHy_dz - pz);
     }
     if (doY) {
         const T dHx_dz = (hx - Hx[e - okm]) * g.r[2];
@@ -172,7 +165,7 @@ __global__ void __launch_bounds__(256) k_update_E(Grid<T> g, Fields<T> f) {
             const long long q = psi_at(g, 0, s0, i, j, k);
             px = f.psiE[0][0][q] + (f.bE[0][i] * f.psiE[0][0][q] + f.aE[0][i] * dHz_dx); f.psiE[0][0][q] = px;
         }
-        ampere(f, 1, e, kz * dHx_dz + pz - kx * dHz_dx - px, jf[1]);
+        ampere(f, 1, e, kz * dHx_dz + pz - kx * dHz_dx - px);
     }
     if (doZ) {
         const T dHy_dx = (hy - Hy[e - oim]) * g.r[0];
@@ -188,7 +181,32 @@ __global__ void __launch_bounds__(256) k_update_E(Grid<T> g, Fields<T> f) {
             const long long q = psi_at(g, 1, s1, i, j, k);
             py = f.psiE[1][0][q] + (f.bE[1][j] * f.psiE[1][0][q] + f.aE[1][j] * dHx_dy); f.psiE[1][0][q] = py;
         }
-        ampere(f, 2, e, kx * dHy_dx + px - ky * dHx_dy - py, jf[2]);
+        ampere(f, 2, e, kx * dHy_dx + px - ky * dHx_dy - py);
+    }
+}
+
+// The free-current term of Eq. 8, applied after the E update of the same
+// step: E -= (dt/(eps0 eps_inf)) J_f on every updated edge of the tiles the
+// deposit and the sources wrote this step (each listed once).  One thread per
+// cell of a TILE_X x TILE_Y x TILE_Z tile; blocks stride over the list.
+template <typename T>
+__global__ void __launch_bounds__(TILE_X *TILE_Y *TILE_Z) k_jf_apply(Grid<T> g, Fields<T> f) {
+    const int count = *f.jf_count;
+    const int i0 = threadIdx.x % TILE_X, j0 = (threadIdx.x / TILE_X) % TILE_Y, k0 = threadIdx.x / (TILE_X * TILE_Y);
+    for (int q = blockIdx.x; q < count; q += gridDim.x) {
+        const long long t = f.jf_list[q];
+        const int tx = (int)(t % g.nt[0]), ty = (int)((t / g.nt[0]) % g.nt[1]);
+        const int tz = (int)(t / ((long long)g.nt[0] * g.nt[1]));
+        const int i = tx * TILE_X + i0, j = ty * TILE_Y + j0, k = tz * TILE_Z + k0;
+        if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) continue;
+        const long long e = ((long long)k * g.n[1] + j) * g.n[0] + i;
+        const bool fx = !g.per[0] && i == 0, fy = !g.per[1] && j == 0, fz = !g.per[2] && k == 0;
+        const bool upd[3] = {!(fy || fz), !(fx || fz), !(fx || fy)};
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const T jf = f.Jf[c][e];
+            if (upd[c] && jf != T(0)) f.E[c][e] -= f.cls_cE[f.ecls[c][e]] * jf;
+        }
     }
 }
 
@@ -197,14 +215,14 @@ static dim3 field_grid(const int n[3], dim3 blk) {
 }
 
 template <typename T>
-void launch_update_H(const Grid<T> &g, const Fields<T> &f, const FieldPlan *, cudaStream_t s) {
+void launch_update_H(const Grid<T> &g, const Fields<T> &f, const FieldPlan *, cudaStream_t s, cudaStream_t) {
     dim3 blk(32, 4, 2);
     k_update_H<T><<<field_grid(g.n, blk), blk, 0, s>>>(g, f);
     launch_count() += 1;
 }
 
 template <typename T>
-void launch_update_E(const Grid<T> &g, const Fields<T> &f, const FieldPlan *, cudaStream_t s) {
+void launch_update_E(const Grid<T> &g, const Fields<T> &f, const FieldPlan *, cudaStream_t s, cudaStream_t) {
     dim3 blk(32, 4, 2);
     k_update_E<T><<<field_grid(g.n, blk), blk, 0, s>>>(g, f);
     launch_count() += 1;
@@ -212,10 +230,11 @@ void launch_update_E(const Grid<T> &g, const Fields<T> &f, const FieldPlan *, cu
 
 // FP32 with a plan (nx a multiple of 4): the four-cells-per-thread kernels of fields_v4.cu.
 template <>
-void launch_update_H<float>(const Grid<float> &g, const Fields<float> &f, const FieldPlan *plan, cudaStream_t s) {
+void launch_update_H<float>(const Grid<float> &g, const Fields<float> &f, const FieldPlan *plan, cudaStream_t s,
+                            cudaStream_t s2) {
     dim3 blk(32, 4, 2);
     if (plan) {
-        launch_v4_H(g, f, *plan, s);
+        launch_v4_H(g, f, *plan, s, s2);
     } else {
         k_update_H<float><<<field_grid(g.n, blk), blk, 0, s>>>(g, f);
         launch_count() += 1;
@@ -223,17 +242,31 @@ void launch_update_H<float>(const Grid<float> &g, const Fields<float> &f, const 
 }
 
 template <>
-void launch_update_E<float>(const Grid<float> &g, const Fields<float> &f, const FieldPlan *plan, cudaStream_t s) {
+void launch_update_E<float>(const Grid<float> &g, const Fields<float> &f, const FieldPlan *plan, cudaStream_t s,
+                            cudaStream_t s2) {
     dim3 blk(32, 4, 2);
     if (plan) {
-        launch_v4_E(g, f, *plan, s);
+        launch_v4_E(g, f, *plan, s, s2);
     } else {
         k_update_E<float><<<field_grid(g.n, blk), blk, 0, s>>>(g, f);
         launch_count() += 1;
     }
 }
 
-template void launch_update_H<double>(const Grid<double> &, const Fields<double> &, const FieldPlan *, cudaStream_t);
-template void launch_update_E<double>(const Grid<double> &, const Fields<double> &, const FieldPlan *, cudaStream_t);
+template <typename T>
+void launch_jf_apply(const Grid<T> &g, const Fields<T> &f, int max_tiles, cudaStream_t s) {
+    int nblk = max_tiles < 4 * 152 ? max_tiles : 4 * 152;
+    if (nblk < 1) nblk = 1;
+    k_jf_apply<T><<<nblk, TILE_X * TILE_Y * TILE_Z, 0, s>>>(g, f);
+    launch_count() += 1;
+}
+
+template void launch_update_H<double>(const Grid<double> &, const Fields<double> &, const FieldPlan *, cudaStream_t,
+                                      cudaStream_t);
+template void launch_update_E<double>(const Grid<double> &, const Fields<double> &, const FieldPlan *, cudaStream_t,
+                                      cudaStream_t);
+
+template void launch_jf_apply<float>(const Grid<float> &, const Fields<float> &, int, cudaStream_t);
+template void launch_jf_apply<double>(const Grid<double> &, const Fields<double> &, int, cudaStream_t);
 
 }  // namespace pic

@@ -172,11 +172,12 @@ __device__ __forceinline__ void h4(const Grid<float> &g, const Fields<float> &f,
     st4(f.H[2] + e, hz);
 }
 
-// Eq. 6 (increment form) on the metal edges among the four, then Eq. 8, for
+// Eq. 6 (increment form) on the metal edges among the four, then Eq. 8
+// without the free current (applied by k_jf_apply after the deposit), for
 // component comp of cells e..e+3 with edge classes cl; J_p moves as one
 // 16-byte access when any of the four edges is metal.
 __device__ __forceinline__ void ampere4(const Fields<float> &f, int comp, uchar4 cl, long long e, F4 &E, const float curl[4],
-                                        const F4 &jf, const bool doit[4]) {
+                                        const bool doit[4]) {
     const float4 t0 = f.cls_pack[cl.x], t1 = f.cls_pack[cl.y], t2 = f.cls_pack[cl.z], t3 = f.cls_pack[cl.w];
     const float4 t[4] = {t0, t1, t2, t3};
     const bool metal = (t0.w + t1.w + t2.w + t3.w) != 0.f;
@@ -192,7 +193,7 @@ __device__ __forceinline__ void ampere4(const Fields<float> &f, int comp, uchar4
     }
 #pragma unroll
     for (int m = 0; m < 4; m++)
-        if (doit[m]) E.v[m] += t[m].z * (curl[m] - (t[m].w != 0.f ? jp.v[m] : 0.f) - jf.v[m]);
+        if (doit[m]) E.v[m] += t[m].z * (curl[m] - (t[m].w != 0.f ? jp.v[m] : 0.f));
 }
 
 // E^{n+1} (with the Drude current of Eq. 6) for cells i0..i0+3 of row (j, k).
@@ -211,11 +212,7 @@ __device__ __forceinline__ void e4(const Grid<float> &g, const Fields<float> &f,
     const long long okm = k > 0 ? sz : (g.per[2] ? -(long long)(nz - 1) * sz : 0);
     const long long oim = i0 > 0 ? 1 : (g.per[0] ? -(long long)(nx - 1) : 0);
 
-    const long long t = ((long long)(k / TILE_Z) * g.nt[1] + j / TILE_Y) * g.nt[0] + i0 / TILE_X;
-    const bool jf_here = f.jf_flag[t] == (int)(step + 1);
-    const F4 jfx = jf_here ? ld4(f.Jf[0] + e) : zero4();
-    const F4 jfy = jf_here ? ld4(f.Jf[1] + e) : zero4();
-    const F4 jfz = jf_here ? ld4(f.Jf[2] + e) : zero4();
+    (void)step;
 
     const F4 hx = ld4(f.H[0] + e), hy = ld4(f.H[1] + e), hz = ld4(f.H[2] + e);
     const F4 hz_jm = ld4(f.H[2] + e - ojm), hx_jm = ld4(f.H[0] + e - ojm);
@@ -319,15 +316,15 @@ __device__ __forceinline__ void e4(const Grid<float> &g, const Fields<float> &f,
         doZ[m] = !(fx || fy);
     }
     if (MAT) {
-        ampere4(f, 0, cl0, e, ex, cx, jfx, doX);
-        ampere4(f, 1, cl1, e, ey, cy, jfy, doY);
-        ampere4(f, 2, cl2, e, ez, cz, jfz, doZ);
+        ampere4(f, 0, cl0, e, ex, cx, doX);
+        ampere4(f, 1, cl1, e, ey, cy, doY);
+        ampere4(f, 2, cl2, e, ez, cz, doZ);
     } else {
 #pragma unroll
         for (int m = 0; m < 4; m++) {
-            if (doX[m]) ex.v[m] += cEu * (cx[m] - jfx.v[m]);
-            if (doY[m]) ey.v[m] += cEu * (cy[m] - jfy.v[m]);
-            if (doZ[m]) ez.v[m] += cEu * (cz[m] - jfz.v[m]);
+            if (doX[m]) ex.v[m] += cEu * cx[m];
+            if (doY[m]) ey.v[m] += cEu * cy[m];
+            if (doZ[m]) ez.v[m] += cEu * cz[m];
         }
     }
     st4(f.E[0] + e, ex);
@@ -342,11 +339,13 @@ __device__ __forceinline__ bool list_cell(const BoxList &bl, long long q, int &b
     bi = 0;
     while (q >= bl.first[bi + 1]) bi++;
     const Box &b = bl.b[bi];
-    const long long r = q - bl.first[bi];
-    const int wx = (b.hi[0] - b.lo[0]) / 4, wy = b.hi[1] - b.lo[1];
-    i0 = b.lo[0] + 4 * (int)(r % wx);
-    j = b.lo[1] + (int)((r / wx) % wy);
-    k = b.lo[2] + (int)(r / ((long long)wx * wy));
+    // 32-bit arithmetic: a plan exists only for grids of fewer than 2^31 four-cell groups
+    const unsigned r = (unsigned)(q - bl.first[bi]);
+    const unsigned wx = (unsigned)(b.hi[0] - b.lo[0]) / 4u, wy = (unsigned)(b.hi[1] - b.lo[1]);
+    const unsigned row = r / wx, kk = row / wy;
+    i0 = b.lo[0] + 4 * (int)(r - row * wx);
+    j = b.lo[1] + (int)(row - kk * wy);
+    k = b.lo[2] + (int)kk;
     return true;
 }
 
@@ -429,6 +428,7 @@ bool split_by_planes(const int lo[3], const int hi[3], const uint8_t *plane_cls,
 bool make_field_plan(const Grid<float> &g, const uint8_t *plane_cls, const float *cls_cE, FieldPlan &p) {
     p = FieldPlan{};
     if (g.n[0] % 4 != 0 || (g.cpml[0] && g.L % 4 != 0)) return false;
+    if ((long long)g.n[0] * g.n[1] * g.n[2] / 4 >= (1LL << 31)) return false;  // list_cell indexes in 32 bits
     int lo[3], hi[3];
     for (int a = 0; a < 3; a++) {
         lo[a] = g.cpml[a] ? g.L : 0;
@@ -454,16 +454,16 @@ bool make_field_plan(const Grid<float> &g, const uint8_t *plane_cls, const float
     return true;
 }
 
-void launch_v4_H(const Grid<float> &g, const Fields<float> &f, const FieldPlan &plan, cudaStream_t s) {
+void launch_v4_H(const Grid<float> &g, const Fields<float> &f, const FieldPlan &plan, cudaStream_t s, cudaStream_t s2) {
+    launch_list(k_H4_cpml, g, f, plan.faces, s2);
     launch_list(k_H4_bulk, g, f, plan.bulk, s);
-    launch_list(k_H4_cpml, g, f, plan.faces, s);
 }
 
-void launch_v4_E(const Grid<float> &g, const Fields<float> &f, const FieldPlan &plan, cudaStream_t s) {
+void launch_v4_E(const Grid<float> &g, const Fields<float> &f, const FieldPlan &plan, cudaStream_t s, cudaStream_t s2) {
+    launch_list(k_E4_cpml_vac, g, f, plan.fvac, s2);
+    launch_list(k_E4_cpml_mat, g, f, plan.fmat, s2);
     launch_list(k_E4_vac, g, f, plan.vac, s);
     launch_list(k_E4_mat, g, f, plan.mat, s);
-    launch_list(k_E4_cpml_vac, g, f, plan.fvac, s);
-    launch_list(k_E4_cpml_mat, g, f, plan.fmat, s);
 }
 
 }  // namespace pic

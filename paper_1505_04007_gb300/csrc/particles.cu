@@ -2,10 +2,13 @@
 // periodic brick sort that keeps neighbouring electrons in neighbouring
 // threads.
 //
-// Per live electron, one thread:
-//   gather E^n and B^n = mu0 (H^{n-1/2} + H^{n+1/2})/2 at x^n (staggered
-//   trilinear; H^{n-1/2}(x^n) is the value the previous push left in bold),
-//   relativistic Boris rotation u^{n-1/2} -> u^{n+1/2}, x^{n+1} = x^n + dt u/gamma,
+// Per live electron, one thread in each of two kernels:
+//   k_gather_E (beside the H update, which does not touch E): E^n at x^n
+//   (staggered trilinear), stored per electron;
+//   k_push_deposit (beside the E update, once H^{n+1/2} is final): B^n =
+//   mu0 (H^{n-1/2} + H^{n+1/2})/2 at x^n (H^{n-1/2}(x^n) is the value the
+//   previous push left in bold), relativistic Boris rotation
+//   u^{n-1/2} -> u^{n+1/2}, x^{n+1} = x^n + dt u/gamma,
 //   the boundary/metal freeze rule, the Esirkepov current of the move
 //   (linear node shapes, 4-node window per axis), and finally
 //   bold <- H^{n+1/2}(x^{n+1}) for the next step.
@@ -36,50 +39,54 @@ __device__ __forceinline__ int wrap_or_clamp(int x, int n, int per) {
     return x < 0 ? 0 : (x >= n ? n - 1 : x);
 }
 
-// Trilinear interpolation of F on a lattice shifted by half a cell along the
-// axes flagged in stag (bit a).
+// Trilinear interpolation at one position on the Yee lattices.  Per axis a
+// component lives either on the cell nodes (index c, weight o) or half a
+// cell over (index c or c-1, weight o -+ 1/2); the stencil holds both, so
+// the six field components share one set of index computations.
 template <typename T>
-__device__ __forceinline__ T gather(const T *__restrict__ F, const Grid<T> &g, const int c[3], const T o[3],
-                                    int stag) {
-    int i0[3], i1[3];
-    T w[3];
+struct Stencil {
+    int i0[3][2], i1[3][2];  // [axis][0 unshifted, 1 half-shifted]: lower / upper index
+    T w[3][2];               // weight of the upper index
+};
+
+template <typename T>
+__device__ __forceinline__ void make_stencil(const Grid<T> &g, const int c[3], const T o[3], Stencil<T> &s) {
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        int b;
-        T wa;
-        if (stag & (1 << a)) {
-            if (o[a] >= T(0.5)) { b = c[a]; wa = o[a] - T(0.5); }
-            else { b = c[a] - 1; wa = o[a] + T(0.5); }
-        } else {
-            b = c[a];
-            wa = o[a];
-        }
-        i0[a] = wrap_or_clamp<T>(b, g.n[a], g.per[a]);
-        i1[a] = wrap_or_clamp<T>(b + 1, g.n[a], g.per[a]);
-        w[a] = wa;
+        s.i0[a][0] = c[a];
+        s.i1[a][0] = wrap_or_clamp<T>(c[a] + 1, g.n[a], g.per[a]);
+        s.w[a][0] = o[a];
+        const bool up = o[a] >= T(0.5);
+        const int b = up ? c[a] : c[a] - 1;
+        s.i0[a][1] = wrap_or_clamp<T>(b, g.n[a], g.per[a]);
+        s.i1[a][1] = wrap_or_clamp<T>(b + 1, g.n[a], g.per[a]);
+        s.w[a][1] = up ? o[a] - T(0.5) : o[a] + T(0.5);
     }
-    const long long nx = g.n[0], nxy = (long long)g.n[0] * g.n[1];
-    const long long r00 = i0[2] * nxy + i0[1] * nx, r01 = i0[2] * nxy + i1[1] * nx;
-    const long long r10 = i1[2] * nxy + i0[1] * nx, r11 = i1[2] * nxy + i1[1] * nx;
-    const T ux = T(1) - w[0], uy = T(1) - w[1], uz = T(1) - w[2];
-    const T v00 = ux * F[r00 + i0[0]] + w[0] * F[r00 + i1[0]];
-    const T v01 = ux * F[r01 + i0[0]] + w[0] * F[r01 + i1[0]];
-    const T v10 = ux * F[r10 + i0[0]] + w[0] * F[r10 + i1[0]];
-    const T v11 = ux * F[r11 + i0[0]] + w[0] * F[r11 + i1[0]];
-    return uz * (uy * v00 + w[1] * v01) + w[2] * (uy * v10 + w[1] * v11);
 }
 
-// stagger bits: Ex x, Ey y, Ez z; Hx y|z, Hy x|z, Hz x|y
-__device__ __constant__ int STAG_E[3] = {1, 2, 4};
-__device__ __constant__ int STAG_H[3] = {6, 5, 3};
+// F on the lattice shifted by half a cell along the axes flagged in STAG
+// (bit a): Ex 1, Ey 2, Ez 4; Hx 6, Hy 5, Hz 3.
+template <int STAG, typename T>
+__device__ __forceinline__ T interp(const T *__restrict__ F, const Grid<T> &g, const Stencil<T> &s) {
+    constexpr int sx = STAG & 1, sy = (STAG >> 1) & 1, sz = (STAG >> 2) & 1;
+    const long long nx = g.n[0], nxy = (long long)g.n[0] * g.n[1];
+    const int x0 = s.i0[0][sx], x1 = s.i1[0][sx];
+    const long long r00 = s.i0[2][sz] * nxy + s.i0[1][sy] * nx, r01 = s.i0[2][sz] * nxy + s.i1[1][sy] * nx;
+    const long long r10 = s.i1[2][sz] * nxy + s.i0[1][sy] * nx, r11 = s.i1[2][sz] * nxy + s.i1[1][sy] * nx;
+    const T wx = s.w[0][sx], wy = s.w[1][sy], wz = s.w[2][sz];
+    const T ux = T(1) - wx, uy = T(1) - wy, uz = T(1) - wz;
+    const T v00 = ux * F[r00 + x0] + wx * F[r00 + x1];
+    const T v01 = ux * F[r01 + x0] + wx * F[r01 + x1];
+    const T v10 = ux * F[r10 + x0] + wx * F[r10 + x1];
+    const T v11 = ux * F[r11 + x0] + wx * F[r11 + x1];
+    return uz * (uy * v00 + wy * v01) + wz * (uy * v10 + wy * v11);
+}
 
 template <typename T>
-__device__ __forceinline__ void shape4(T x, T S[4]) {
-#pragma unroll
-    for (int m = 0; m < 4; m++) {
-        T r = T(1) - fabs(x - T(m));
-        S[m] = r > T(0) ? r : T(0);
-    }
+__device__ __forceinline__ void interp_H(const Fields<T> &f, const Grid<T> &g, const Stencil<T> &s, T h[3]) {
+    h[0] = interp<6>(f.H[0], g, s);
+    h[1] = interp<5>(f.H[1], g, s);
+    h[2] = interp<3>(f.H[2], g, s);
 }
 
 constexpr int PUSH_BLOCK = 256;
@@ -87,6 +94,48 @@ constexpr int DEP_SMEM_BYTES = 40 * 1024;  // stays under the 48 KB default with
 
 __device__ __forceinline__ long long tile_of(const int idx[3], const int nt[3]) {
     return ((long long)(idx[2] / TILE_Z) * nt[1] + idx[1] / TILE_Y) * nt[0] + idx[0] / TILE_X;
+}
+
+// The Esirkepov contributions of one electron on a window of WX x WY x WZ
+// nodes (2 along an axis no electron of the warp changed cell on, else 3):
+// J_c on edge m0 = jscale_c (dS_c[0] + .. + dS_c[m0]) W(m1, m2), with the
+// transverse weight W = S0 S0 + (dS S0 + S0 dS)/2 + dS dS/3 written as
+// P P + dS dS/12, P = S0 + dS/2.  The cumulative sum is exactly zero past
+// the last node with weight, so only edge 0 (and edge 1 when the electron
+// changed cell along c) is issued.  Shared path: l0 and st[] index the
+// block's node box in acc; direct path: gofs[a][m] is the grid offset of
+// window node m along axis a.
+template <int WX, int WY, int WZ, typename T>
+__device__ __forceinline__ void esirkepov_sites(const T (&P)[3][3], const T (&dS)[3][3], const int (&shv)[3],
+                                                const T (&jscale)[3], bool in_smem, T *acc, int vol, int l0,
+                                                const int (&st)[3], T *const (&Jf)[3], const long long (&gofs)[3][3]) {
+    const T twelfth = T(1) / T(12);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const int a1 = (c + 1) % 3, a2 = (c + 2) % 3;
+        const int wc = c == 0 ? WX : (c == 1 ? WY : WZ);
+        const int w1 = a1 == 0 ? WX : (a1 == 1 ? WY : WZ);
+        const int w2 = a2 == 0 ? WX : (a2 == 1 ? WY : WZ);
+        const int nedge = shv[c] != 0 ? 2 : 1;
+        const T kc[2] = {jscale[c] * dS[c][0], jscale[c] * (dS[c][0] + dS[c][1])};
+#pragma unroll
+        for (int m2 = 0; m2 < w2; m2++) {
+#pragma unroll
+            for (int m1 = 0; m1 < w1; m1++) {
+                const T tr = P[a1][m1] * P[a2][m2] + twelfth * (dS[a1][m1] * dS[a2][m2]);
+                if ((w1 == 3 || w2 == 3) && tr == T(0)) continue;  // a third node with no weight
+#pragma unroll
+                for (int m0 = 0; m0 < wc - 1; m0++) {
+                    if (m0 >= nedge) break;
+                    const T v = kc[m0] * tr;
+                    if (in_smem)
+                        atomicAdd(&acc[c * vol + l0 + m0 * st[c] + m1 * st[a1] + m2 * st[a2]], v);
+                    else
+                        atomicAdd(&Jf[c][gofs[c][m0] + gofs[a1][m1] + gofs[a2][m2]], v);
+                }
+            }
+        }
+    }
 }
 
 template <typename T>
@@ -106,12 +155,15 @@ __global__ void __launch_bounds__(PUSH_BLOCK) k_push_deposit(Grid<T> g, Fields<T
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             c0[a] = p.cell[a][q]; o0[a] = p.off[a][q]; u[a] = p.u[a][q]; ul[a] = p.ulo[a][q];
+            E[a] = p.eg[a][q];
         }
+        {
+            Stencil<T> st0;
+            make_stencil(g, c0, o0, st0);
+            T hnew[3];
+            interp_H(f, g, st0, hnew);
 #pragma unroll
-        for (int a = 0; a < 3; a++) {
-            E[a] = gather(f.E[a], g, c0, o0, STAG_E[a]);
-            const T hnew = gather(f.H[a], g, c0, o0, STAG_H[a]);
-            B[a] = pp.mu0 * T(0.5) * (p.bold[a][q] + hnew);
+            for (int a = 0; a < 3; a++) B[a] = pp.mu0 * T(0.5) * (p.bold[a][q] + hnew[a]);
         }
         // relativistic Boris rotation, as an increment of u
         T um[3], t[3], s[3], up[3], du[3];
@@ -183,104 +235,161 @@ __global__ void __launch_bounds__(PUSH_BLOCK) k_push_deposit(Grid<T> g, Fields<T
                 p.u[a][q] = un[a];
                 p.ulo[a][q] = unl[a];
             }
+            Stencil<T> st1;
+            make_stencil(g, c1w, o1, st1);
+            T hb[3];
+            interp_H(f, g, st1, hb);
 #pragma unroll
-            for (int a = 0; a < 3; a++) p.bold[a][q] = gather(f.H[a], g, c1w, o1, STAG_H[a]);
+            for (int a = 0; a < 3; a++) p.bold[a][q] = hb[a];
             dep = pp.deposit != 0;
         }
     }
 
-    // ---- deposit: bounding box of the block's stencil windows (nodes c0-1 .. c0+2)
+    // ---- deposit window per axis: the three nodes from start = c0 + min(sh, 0)
+    // hold the old and the new shape (sh = cell shift, -1..1); positions in
+    // that window: old x0 = o0 + max(-sh, 0), new x1 = o1 + max(sh, 0).
+    int start[3], shv[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        shv[a] = dep ? c1[a] - c0[a] : 0;
+        start[a] = c0[a] + (shv[a] < 0 ? shv[a] : 0);
+    }
+    // bounding box of the touched nodes (start .. c0 + 1 + max(sh, 0)):
+    // warp minima/maxima first, then one shared atomic per warp
     if (threadIdx.x < 3) {
         bb_lo[threadIdx.x] = 0x7fffffff;
         bb_hi[threadIdx.x] = -0x7fffffff;
     }
     __syncthreads();
-    if (dep) {
 #pragma unroll
-        for (int a = 0; a < 3; a++) {
-            atomicMin(&bb_lo[a], c0[a] - 1);
-            atomicMax(&bb_hi[a], c0[a] + 2);
+    for (int a = 0; a < 3; a++) {
+        const int lo_a = __reduce_min_sync(0xffffffffu, dep ? start[a] : 0x7fffffff);
+        const int hi_a = __reduce_max_sync(0xffffffffu, dep ? c0[a] + 1 + (shv[a] > 0 ? shv[a] : 0) : -0x7fffffff);
+        if ((threadIdx.x & 31) == 0 && lo_a <= hi_a) {
+            atomicMin(&bb_lo[a], lo_a);
+            atomicMax(&bb_hi[a], hi_a);
         }
     }
     __syncthreads();
     const int w0 = bb_hi[0] - bb_lo[0] + 1, w1 = bb_hi[1] - bb_lo[1] + 1, w2 = bb_hi[2] - bb_lo[2] + 1;
     const bool any = bb_hi[0] >= bb_lo[0];
-    const long long vol = any ? (long long)w0 * w1 * w2 : 0;
-    const bool in_smem = any && 3 * vol * (long long)sizeof(T) <= DEP_SMEM_BYTES;
+    const long long box = any ? (long long)w0 * w1 * w2 : 0;
+    const bool in_smem = any && 3 * box * (long long)sizeof(T) <= DEP_SMEM_BYTES;
+    const int vol = in_smem ? (int)box : 0;  // nodes in the shared box (32-bit indexing from here)
     if (in_smem) {
-        for (long long e = threadIdx.x; e < 3 * vol; e += blockDim.x) acc[e] = T(0);
+        for (int e = threadIdx.x; e < 3 * vol; e += blockDim.x) acc[e] = T(0);
         __syncthreads();
     }
     const int flagv = (int)(step + 1);
+    // window width per axis, uniform over the warp: 3 nodes only where some
+    // electron of the warp changed cell (mostly along the beam)
+    const bool wide_x = __any_sync(0xffffffffu, shv[0] != 0), wide_y = __any_sync(0xffffffffu, shv[1] != 0),
+               wide_z = __any_sync(0xffffffffu, shv[2] != 0);
     if (dep) {
-        // Esirkepov on the 4-node window base = c0-1.  The old shape covers
-        // nodes 1..2 of the window, the new one nodes 1+sh..2+sh (sh = cell
-        // shift, -1..1), so only nodes lo..hi carry weight; the cumulative
-        // sum along the current's own axis is non-zero only on the edges
-        // between them (exactly zero elsewhere, so those are not issued).
-        T S0[3][4], dS[3][4];
-        int base[3], lo[3], hi[3];
+        // Esirkepov (linear shapes): old and new shape on the 3-node window
+        // (the third node carries no weight when the electron kept its cell)
+        T P[3][3], dS[3][3];
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            const int sh = c1[a] - c0[a];
-            base[a] = c0[a] - 1;
-            lo[a] = 1 + (sh < 0 ? sh : 0);
-            hi[a] = 2 + (sh > 0 ? sh : 0);
-            T S1[4];
-            shape4(T(1) + o0[a], S0[a]);
-            shape4(T(sh + 1) + o1[a], S1);
+            const T x0 = o0[a] + T(shv[a] < 0 ? -shv[a] : 0);
+            const T x1 = o1[a] + T(shv[a] > 0 ? shv[a] : 0);
 #pragma unroll
-            for (int m = 0; m < 4; m++) dS[a][m] = S1[m] - S0[a][m];
+            for (int m = 0; m < 3; m++) {
+                const T r0 = T(1) - fabs(x0 - T(m)), r1 = T(1) - fabs(x1 - T(m));
+                const T s0 = r0 > T(0) ? r0 : T(0);
+                dS[a][m] = (r1 > T(0) ? r1 : T(0)) - s0;
+                P[a][m] = s0 + T(0.5) * dS[a][m];
+            }
         }
-        const T third = T(1) / T(3);
+        // shared path: offsets in the block's node box; direct path: offsets
+        // of the (wrapped or clamped) window nodes in the grid
+        int st[3], l0 = 0;
+        long long gofs[3][3];
+        if (in_smem) {
+            st[0] = 1; st[1] = w0; st[2] = w0 * w1;
+            l0 = ((start[2] - bb_lo[2]) * w1 + (start[1] - bb_lo[1])) * w0 + (start[0] - bb_lo[0]);
+        } else {
+            const long long gs[3] = {1, g.n[0], (long long)g.n[0] * g.n[1]};
+            int tl[3][2];
 #pragma unroll
-        for (int c = 0; c < 3; c++) {
-            const int a1 = (c + 1) % 3, a2 = (c + 2) % 3;
-            T *J = f.Jf[c];
-            for (int m2 = lo[a2]; m2 <= hi[a2]; m2++) {
-                for (int m1 = lo[a1]; m1 <= hi[a1]; m1++) {
-                    const T tr = S0[a1][m1] * S0[a2][m2] + T(0.5) * dS[a1][m1] * S0[a2][m2] +
-                                 T(0.5) * S0[a1][m1] * dS[a2][m2] + third * dS[a1][m1] * dS[a2][m2];
-                    if (tr == T(0)) continue;
-                    int node[3];
-                    node[a1] = base[a1] + m1;
-                    node[a2] = base[a2] + m2;
-                    T run = T(0);
-                    for (int m0 = lo[c]; m0 < hi[c]; m0++) {
-                        run += dS[c][m0] * tr;
-                        node[c] = base[c] + m0;
-                        const T v = pp.jscale[c] * run;
-                        if (in_smem) {
-                            const long long l = ((long long)(node[2] - bb_lo[2]) * w1 + (node[1] - bb_lo[1])) * w0 +
-                                                (node[0] - bb_lo[0]);
-                            atomicAdd(&acc[c * vol + l], v);
-                        } else {
-                            int idx[3];
+            for (int a = 0; a < 3; a++) {
+                const int tsz = a == 0 ? TILE_X : (a == 1 ? TILE_Y : TILE_Z);
 #pragma unroll
-                            for (int a = 0; a < 3; a++) idx[a] = wrap_or_clamp<T>(node[a], g.n[a], g.per[a]);
-                            atomicAdd(&J[((long long)idx[2] * g.n[1] + idx[1]) * g.n[0] + idx[0]], v);
-                            f.jf_flag[tile_of(idx, g.nt)] = flagv;
-                        }
-                    }
+                for (int m = 0; m < 3; m++) {
+                    const int w = wrap_or_clamp<T>(start[a] + m, g.n[a], g.per[a]);
+                    gofs[a][m] = w * gs[a];
+                    if (m != 1) tl[a][m >> 1] = w / tsz;
                 }
             }
+            // the window's nodes lie in at most two tiles per axis (its end nodes' tiles)
+#pragma unroll
+            for (int z = 0; z < 2; z++)
+#pragma unroll
+                for (int y = 0; y < 2; y++)
+#pragma unroll
+                    for (int x = 0; x < 2; x++) {
+                        if ((z && tl[2][1] == tl[2][0]) || (y && tl[1][1] == tl[1][0]) || (x && tl[0][1] == tl[0][0]))
+                            continue;
+                        mark_jf_tile(f.jf_flag, f.jf_list, f.jf_count,
+                                     ((long long)tl[2][z] * g.nt[1] + tl[1][y]) * g.nt[0] + tl[0][x], flagv);
+                    }
+        }
+        if (!wide_y && !wide_z) {
+            if (wide_x)
+                esirkepov_sites<3, 2, 2>(P, dS, shv, pp.jscale, in_smem, acc, vol, l0, st, f.Jf, gofs);
+            else
+                esirkepov_sites<2, 2, 2>(P, dS, shv, pp.jscale, in_smem, acc, vol, l0, st, f.Jf, gofs);
+        } else {
+            esirkepov_sites<3, 3, 3>(P, dS, shv, pp.jscale, in_smem, acc, vol, l0, st, f.Jf, gofs);
         }
     }
     if (in_smem) {
+        // Flush: each non-zero entry goes to J_f once.  Lanes of a warp that
+        // wrote into the same tile mark it once (the trip count is uniform
+        // over the block, so whole warps reach the vote together).
         __syncthreads();
-        for (long long e = threadIdx.x; e < 3 * vol; e += blockDim.x) {
-            const T v = acc[e];
-            if (v == T(0)) continue;
-            const int c = (int)(e / vol);
-            const long long r = e - c * vol;
-            int idx[3];
-            idx[0] = wrap_or_clamp<T>(bb_lo[0] + (int)(r % w0), g.n[0], g.per[0]);
-            idx[1] = wrap_or_clamp<T>(bb_lo[1] + (int)((r / w0) % w1), g.n[1], g.per[1]);
-            idx[2] = wrap_or_clamp<T>(bb_lo[2] + (int)(r / ((long long)w0 * w1)), g.n[2], g.per[2]);
-            atomicAdd(&f.Jf[c][((long long)idx[2] * g.n[1] + idx[1]) * g.n[0] + idx[0]], v);
-            f.jf_flag[tile_of(idx, g.nt)] = flagv;
+        const int lane = threadIdx.x & 31;
+        for (int e0 = 0; e0 < 3 * vol; e0 += blockDim.x) {
+            const int e = e0 + threadIdx.x;
+            int tile = -1;
+            if (e < 3 * vol) {
+                const T v = acc[e];
+                if (v != T(0)) {
+                    const unsigned c = (unsigned)e / (unsigned)vol;
+                    const unsigned r = (unsigned)e - c * (unsigned)vol;
+                    const unsigned yz = r / (unsigned)w0, z = yz / (unsigned)w1;
+                    int idx[3];
+                    idx[0] = wrap_or_clamp<T>(bb_lo[0] + (int)(r - yz * (unsigned)w0), g.n[0], g.per[0]);
+                    idx[1] = wrap_or_clamp<T>(bb_lo[1] + (int)(yz - z * (unsigned)w1), g.n[1], g.per[1]);
+                    idx[2] = wrap_or_clamp<T>(bb_lo[2] + (int)z, g.n[2], g.per[2]);
+                    atomicAdd(&f.Jf[c][((long long)idx[2] * g.n[1] + idx[1]) * g.n[0] + idx[0]], v);
+                    tile = (int)tile_of(idx, g.nt);
+                }
+            }
+            const unsigned act = __ballot_sync(0xffffffffu, tile >= 0);
+            if (tile >= 0) {
+                const unsigned grp = __match_any_sync(act, tile);
+                if (lane == __ffs(grp) - 1) mark_jf_tile(f.jf_flag, f.jf_list, f.jf_count, tile, flagv);
+            }
         }
     }
+}
+
+// E^n at x^n for every live electron, taken before the E update
+// overwrites E^n (it runs beside the H update, which leaves E alone).
+template <typename T>
+__global__ void __launch_bounds__(PUSH_BLOCK) k_gather_E(Grid<T> g, Fields<T> f, Particles<T> p) {
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= p.n || p.status[q]) return;
+    int c[3];
+    T o[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) { c[a] = p.cell[a][q]; o[a] = p.off[a][q]; }
+    Stencil<T> st;
+    make_stencil(g, c, o, st);
+    p.eg[0][q] = interp<1>(f.E[0], g, st);
+    p.eg[1][q] = interp<2>(f.E[1], g, st);
+    p.eg[2][q] = interp<4>(f.E[2], g, st);
 }
 
 template <typename T>
@@ -291,8 +400,12 @@ __global__ void k_gather_bold(Grid<T> g, Fields<T> f, Particles<T> p) {
     T o[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) { c[a] = p.cell[a][q]; o[a] = p.off[a][q]; }
+    Stencil<T> st;
+    make_stencil(g, c, o, st);
+    T hb[3];
+    interp_H(f, g, st, hb);
 #pragma unroll
-    for (int a = 0; a < 3; a++) p.bold[a][q] = gather(f.H[a], g, c, o, STAG_H[a]);
+    for (int a = 0; a < 3; a++) p.bold[a][q] = hb[a];
 }
 
 // ------------------------------------------------------------ brick sort --
@@ -430,6 +543,13 @@ void launch_push_deposit(const Grid<T> &g, const Fields<T> &f, const Particles<T
 }
 
 template <typename T>
+void launch_gather_E(const Grid<T> &g, const Fields<T> &f, const Particles<T> &p, cudaStream_t s) {
+    if (p.n <= 0) return;
+    k_gather_E<T><<<(unsigned)((p.n + PUSH_BLOCK - 1) / PUSH_BLOCK), PUSH_BLOCK, 0, s>>>(g, f, p);
+    launch_count() += 1;
+}
+
+template <typename T>
 void launch_gather_bold(const Grid<T> &g, const Fields<T> &f, const Particles<T> &p, cudaStream_t s) {
     if (p.n <= 0) return;
     const int blk = 256;
@@ -463,6 +583,10 @@ template void launch_push_deposit<float>(const Grid<float> &, const Fields<float
                                          const PushParams<float> &, cudaStream_t);
 template void launch_push_deposit<double>(const Grid<double> &, const Fields<double> &, const Particles<double> &,
                                           const PushParams<double> &, cudaStream_t);
+template void launch_gather_E<float>(const Grid<float> &, const Fields<float> &, const Particles<float> &,
+                                     cudaStream_t);
+template void launch_gather_E<double>(const Grid<double> &, const Fields<double> &, const Particles<double> &,
+                                      cudaStream_t);
 template void launch_gather_bold<float>(const Grid<float> &, const Fields<float> &, const Particles<float> &,
                                         cudaStream_t);
 template void launch_gather_bold<double>(const Grid<double> &, const Fields<double> &, const Particles<double> &,

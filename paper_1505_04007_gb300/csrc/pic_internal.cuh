@@ -54,6 +54,8 @@ struct Fields {
     const uint8_t *cls_metal;         // per-class: wp^2 > 0
     const float4 *cls_pack;           // per-class (kJ-1, bJ, cE, metal) in float (FP32 kernels)
     int *jf_flag;                     // per tile: step+1 when J_f was written
+    int *jf_list;                     // tiles written this step (each once), for the J_f correction
+    int *jf_count;                    // length of jf_list
     const long long *step;            // device step counter n
 };
 
@@ -64,6 +66,7 @@ struct Particles {
     T *u[3];           // gamma*v [m/s], leading part
     T *ulo[3];         // trailing part: gamma*v = u + ulo (compensated sum)
     T *bold[3];        // H^{n-1/2} gathered at x^n (carried from the last push)
+    T *eg[3];          // E^n at x^n, gathered beside the H update
     uint8_t *status;   // 0 live, 1 frozen
     long long *id;     // input order
     long long n;
@@ -140,19 +143,30 @@ struct FieldPlan {
     BoxList bulk, faces, vac, mat, fvac, fmat;
 };
 // FP32 four-cells-per-thread field kernels (nx % 4 == 0), fields_v4.cu
-void launch_v4_H(const Grid<float> &g, const Fields<float> &f, const FieldPlan &plan, cudaStream_t s);
-void launch_v4_E(const Grid<float> &g, const Fields<float> &f, const FieldPlan &plan, cudaStream_t s);
+// bulk/interior boxes on s, boxes over the absorbing slabs on s2 (may be s)
+void launch_v4_H(const Grid<float> &g, const Fields<float> &f, const FieldPlan &plan, cudaStream_t s, cudaStream_t s2);
+void launch_v4_E(const Grid<float> &g, const Fields<float> &f, const FieldPlan &plan, cudaStream_t s, cudaStream_t s2);
 // plane_cls[k]: the class all edges of plane k share if it is non-metal, else
 // 255.  Returns false when the grid does not suit these kernels.
 bool make_field_plan(const Grid<float> &g, const uint8_t *plane_cls, const float *cls_cE, FieldPlan &p);
+
+// Mark tile t as holding free current of the step flagged v, and append it
+// to the step's tile list the first time.
+__device__ __forceinline__ void mark_jf_tile(int *flag, int *list, int *count, long long t, int v) {
+    if (flag[t] != v && atomicExch(&flag[t], v) != v) list[atomicAdd(count, 1)] = (int)t;
+}
 
 // ---------------------------------------------------------------- launchers
 // Field updates; with a plan (FP32) the four-cells-per-thread kernels run,
 // otherwise the one-cell-per-thread kernels of fields.cu.
 template <typename T>
-void launch_update_H(const Grid<T> &g, const Fields<T> &f, const FieldPlan *plan, cudaStream_t s);
+void launch_update_H(const Grid<T> &g, const Fields<T> &f, const FieldPlan *plan, cudaStream_t s, cudaStream_t s2);
 template <typename T>
-void launch_update_E(const Grid<T> &g, const Fields<T> &f, const FieldPlan *plan, cudaStream_t s);
+void launch_update_E(const Grid<T> &g, const Fields<T> &f, const FieldPlan *plan, cudaStream_t s, cudaStream_t s2);
+template <typename T>
+void launch_gather_E(const Grid<T> &g, const Fields<T> &f, const Particles<T> &p, cudaStream_t s);
+template <typename T>
+void launch_jf_apply(const Grid<T> &g, const Fields<T> &f, int max_tiles, cudaStream_t s);
 template <typename T>
 void launch_push_deposit(const Grid<T> &g, const Fields<T> &f, const Particles<T> &p,
                          const PushParams<T> &pp, cudaStream_t s);

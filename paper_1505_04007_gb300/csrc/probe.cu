@@ -34,7 +34,8 @@ __global__ void k_sources(Grid<T> g, Fields<T> f, SourceList sl, double dt) {
         const int k = s.box[4] + (int)(q / ((long long)wi * wj));
         const long long e = ((long long)k * g.n[1] + j) * g.n[0] + i;
         atomicAdd(&f.Jf[s.comp][e], (T)v);
-        f.jf_flag[((long long)(k / TILE_Z) * g.nt[1] + j / TILE_Y) * g.nt[0] + i / TILE_X] = (int)(step + 1);
+        mark_jf_tile(f.jf_flag, f.jf_list, f.jf_count,
+                     ((long long)(k / TILE_Z) * g.nt[1] + j / TILE_Y) * g.nt[0] + i / TILE_X, (int)(step + 1));
     }
 }
 
@@ -76,7 +77,10 @@ __global__ void __launch_bounds__(1024) k_step_tail(Grid<T> g, Fields<T> f, Prob
         if ((lane & 7) == 0 && c < 3) pr.samples[((long long)slot * pr.np + p) * 3 + c] = (double)v;
     }
     __syncthreads();
-    if (threadIdx.x == 0) *step = n + 1;
+    if (threadIdx.x == 0) {
+        *step = n + 1;
+        *f.jf_count = 0;  // the J_f tile list of the next step starts empty
+    }
 }
 
 template <typename T>
