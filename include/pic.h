@@ -217,6 +217,37 @@ int pic_load(pic_handle *h, const char *path);
  * (the simulation advances).  Synchronises. */
 int pic_profile_steps(pic_handle *h, int64_t nsteps, double *out_us);
 
+/* ---------------------------------------------------------------- batch --
+ * Several independent simulations (same device, any sizes and precisions)
+ * stepped together.  The paper has no counterpart; it serves parameter sweeps
+ * (films of different thicknesses, bunches of different energies): every
+ * whole block of 64 steps of every instance is captured into one CUDA graph,
+ * one branch per instance on that instance's own streams, so instances too
+ * small to fill the GPU run side by side instead of one after another.  The
+ * arithmetic of each instance is exactly that of pic_step. */
+typedef struct pic_batch pic_batch;
+
+/* Group n handles (not owned; each must outlive the batch and appear once).
+ * stream: the CUDA stream the batch graph is launched on (NULL: the batch
+ * creates its own).  Errors: PIC_ERR_ARG, PIC_ERR_CUDA. */
+int pic_batch_create(int n, pic_handle *const *handles, void *stream, pic_batch **out);
+
+/* Advance every instance by nsteps.  While every instance sits at a 64-step
+ * block boundary (no probe samples buffered), whole blocks go through the
+ * batch graph; the rest run per instance as pic_step does.  The graph is
+ * captured again when an instance changed in a way that invalidates captured
+ * steps (particles added, deposit switched, sources or stream changed).
+ * Asynchronous; each instance's stream is ordered after the batch, so its own
+ * calls (pic_probe_read, pic_get_field, ...) see the result.  Errors:
+ * PIC_ERR_ARG, PIC_ERR_CUDA. */
+int pic_batch_step(pic_batch *b, int64_t nsteps);
+
+/* Wait for the batch and every instance; reports device errors as pic_sync. */
+int pic_batch_sync(pic_batch *b);
+
+/* Release the batch (not its instances).  NULL is accepted. */
+int pic_batch_destroy(pic_batch *b);
+
 /* Probe-DFT fold that allocates no device memory.  The paper has no
  * counterpart; this is a service for callers that cannot call cudaMalloc:
  * code whose device memory is owned entirely by another allocator (a

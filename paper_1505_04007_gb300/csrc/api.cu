@@ -12,6 +12,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <type_traits>
 #include <unordered_map>
@@ -118,6 +119,15 @@ static int validate(const pic_config *c) {
 // ---------------------------------------------------------------- the sim --
 struct SimBase {
     virtual ~SimBase() {}
+    // for pic_batch: the batch captures whole DFT_BLOCK-step blocks of its
+    // instances into one graph
+    virtual int batch_prepare() = 0;                  // pending host-side work (outside any capture)
+    virtual bool batch_ready() const = 0;             // at a block boundary (no buffered samples)
+    virtual long long launch_block_on(cudaStream_t from) = 0;  // one block on own streams, joined to `from`
+    virtual void after_block(long long kernels) = 0;  // host bookkeeping once the block is enqueued
+    virtual long long graph_epoch() const = 0;        // changes whenever captured steps go stale
+    virtual int step_direct(long long n) = 0;
+    virtual cudaStream_t main_stream() const = 0;
 };
 
 template <typename T>
@@ -129,6 +139,8 @@ struct Sim : SimBase {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaStream_t side = nullptr;  // electron kernels, beside the field updates
+    cudaEvent_t ev_bfork = nullptr, ev_bjoin = nullptr;  // joins to a batch capture
+    long long epoch = 0;          // bumped by drop_graph
     cudaStream_t aux = nullptr;   // field updates over the absorbing slabs, beside the interior ones
     cudaEvent_t ev_fork = nullptr, ev_gathered = nullptr, ev_h = nullptr, ev_join = nullptr;
     cudaEvent_t ev_hf = nullptr, ev_hj = nullptr, ev_ef = nullptr, ev_ej = nullptr;
@@ -389,7 +401,8 @@ struct Sim : SimBase {
             CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
             CUDA_TRY(cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, greatest));
             CUDA_TRY(cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking));
-            for (cudaEvent_t *e : {&ev_fork, &ev_gathered, &ev_h, &ev_join, &ev_hf, &ev_hj, &ev_ef, &ev_ej})
+            for (cudaEvent_t *e : {&ev_fork, &ev_gathered, &ev_h, &ev_join, &ev_hf, &ev_hj, &ev_ef, &ev_ej, &ev_bfork,
+                                   &ev_bjoin})
                 CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
         }
 
@@ -482,7 +495,7 @@ struct Sim : SimBase {
         if (own_stream && stream) cudaStreamDestroy(stream);
         if (side) cudaStreamDestroy(side);
         if (aux) cudaStreamDestroy(aux);
-        for (cudaEvent_t e : {ev_fork, ev_gathered, ev_h, ev_join, ev_hf, ev_hj, ev_ef, ev_ej})
+        for (cudaEvent_t e : {ev_fork, ev_gathered, ev_h, ev_join, ev_hf, ev_hj, ev_ef, ev_ej, ev_bfork, ev_bjoin})
             if (e) cudaEventDestroy(e);
     }
 
@@ -491,6 +504,36 @@ struct Sim : SimBase {
         if (graph) cudaGraphDestroy(graph);
         gexec = nullptr;
         graph = nullptr;
+        epoch++;
+    }
+
+    // ------------------------------------------------------------ batch --
+    int batch_prepare() override { return refresh_bold(); }
+    bool batch_ready() const override { return buffered == 0; }
+    long long launch_block_on(cudaStream_t from) override {
+        const long long before = launch_count();
+        cudaEventRecord(ev_bfork, from);
+        cudaStreamWaitEvent(stream, ev_bfork, 0);
+        launch_block();
+        cudaEventRecord(ev_bjoin, stream);
+        cudaStreamWaitEvent(from, ev_bjoin, 0);
+        const long long k = launch_count() - before;
+        launch_count() = before;  // captured, not launched
+        return k;
+    }
+    void after_block(long long k) override {
+        kernels += k;
+        step_host += DFT_BLOCK;
+        since_sort = DFT_BLOCK - (DFT_BLOCK - 1) / SORT_EVERY * SORT_EVERY;  // steps since its last sort
+    }
+    long long graph_epoch() const override { return epoch; }
+    int step_direct(long long n) override { return step(n); }
+    cudaStream_t main_stream() const override { return stream; }
+
+    // DFT_BLOCK steps (a sort every SORT_EVERY, the first one included) and the DFT flush
+    void launch_block() {
+        for (int s = 0; s < DFT_BLOCK; s++) launch_step(s % SORT_EVERY == 0);
+        launch_dft_flush<T>(pr, d_step, DFT_BLOCK, stream);
     }
 
     // ---------------------------------------------------------- stepping --
@@ -557,8 +600,7 @@ struct Sim : SimBase {
         if (gexec) return PIC_OK;
         CUDA_TRY(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
         const long long before = launch_count();
-        for (int s = 0; s < DFT_BLOCK; s++) launch_step(s % SORT_EVERY == 0);
-        launch_dft_flush<T>(pr, d_step, DFT_BLOCK, stream);
+        launch_block();
         graph_kernels = launch_count() - before;
         launch_count() = before;  // captured, not launched
         cudaError_t e = cudaStreamEndCapture(stream, &graph);
@@ -1220,6 +1262,143 @@ int pic_profile_steps(pic_handle *h, int64_t nsteps, double *out_us) {
     g_err.clear();
     if (!h || !out_us) return fail(PIC_ERR_ARG, "NULL argument");
     return DISPATCH(h, profile_steps(nsteps, out_us));
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batch --
+// Several independent simulations stepped together: whole DFT_BLOCK-step
+// blocks of every instance are captured into one CUDA graph (one branch per
+// instance, each on its own streams), so small grids share the GPU instead
+// of running one after another.
+struct pic_batch {
+    std::vector<pic_handle *> h;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaEvent_t ev = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<long long> epochs, kernels;
+
+    void drop() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+    }
+    bool stale() const {
+        if (!exec) return true;
+        for (size_t i = 0; i < h.size(); i++)
+            if (h[i]->sim->graph_epoch() != epochs[i]) return true;
+        return false;
+    }
+    int capture() {
+        drop();
+        CUDA_TRY(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+        for (size_t i = 0; i < h.size(); i++) kernels[i] = h[i]->sim->launch_block_on(stream);
+        cudaError_t e = cudaStreamEndCapture(stream, &graph);
+        if (e != cudaSuccess) { graph = nullptr; return fail(PIC_ERR_CUDA, "batch graph capture: %s", cudaGetErrorString(e)); }
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e != cudaSuccess) { exec = nullptr; return fail(PIC_ERR_CUDA, "batch graph instantiate: %s", cudaGetErrorString(e)); }
+        for (size_t i = 0; i < h.size(); i++) epochs[i] = h[i]->sim->graph_epoch();
+        return PIC_OK;
+    }
+    // `to` waits for the work queued on `from` so far
+    int order(cudaStream_t from, cudaStream_t to) {
+        CUDA_TRY(cudaEventRecord(ev, from));
+        CUDA_TRY(cudaStreamWaitEvent(to, ev, 0));
+        return PIC_OK;
+    }
+    int step(long long n) {
+        for (auto *x : h) {  // the batch stream starts after everything queued on the instances
+            int rc = x->sim->batch_prepare();
+            if (rc) return rc;
+            rc = order(x->sim->main_stream(), stream);
+            if (rc) return rc;
+        }
+        bool ready = true;
+        for (auto *x : h) ready = ready && x->sim->batch_ready();
+        while (ready && n >= DFT_BLOCK) {
+            if (stale()) {
+                int rc = capture();
+                if (rc) return rc;
+            }
+            CUDA_TRY(cudaGraphLaunch(exec, stream));
+            for (size_t i = 0; i < h.size(); i++) h[i]->sim->after_block(kernels[i]);
+            n -= DFT_BLOCK;
+        }
+        for (auto *x : h) {  // instance streams wait for the batch; any remainder steps there
+            int rc = order(stream, x->sim->main_stream());
+            if (rc) return rc;
+            if (n > 0) {
+                rc = x->sim->step_direct(n);
+                if (rc) return rc;
+                rc = order(x->sim->main_stream(), stream);
+                if (rc) return rc;
+            }
+        }
+        CUDA_TRY(cudaGetLastError());
+        return PIC_OK;
+    }
+    ~pic_batch() {
+        if (stream) cudaStreamSynchronize(stream);
+        drop();
+        if (ev) cudaEventDestroy(ev);
+        if (own_stream && stream) cudaStreamDestroy(stream);
+    }
+};
+
+extern "C" {
+
+int pic_batch_create(int n, pic_handle *const *handles, void *stream, pic_batch **out) {
+    g_err.clear();
+    if (!out) return fail(PIC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || !handles) return fail(PIC_ERR_ARG, "need at least one handle");
+    int dev = -1;
+    CUDA_TRY(cudaGetDevice(&dev));
+    std::unique_ptr<pic_batch> b(new pic_batch());
+    for (int i = 0; i < n; i++) {
+        if (!handles[i]) return fail(PIC_ERR_ARG, "handle %d is NULL", i);
+        for (int q = 0; q < i; q++)
+            if (handles[q] == handles[i]) return fail(PIC_ERR_ARG, "handle %d appears twice", i);
+        b->h.push_back(handles[i]);
+    }
+    b->epochs.assign(n, -1);
+    b->kernels.assign(n, 0);
+    if (stream) {
+        b->stream = (cudaStream_t)stream;
+    } else {
+        CUDA_TRY(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+        b->own_stream = true;
+    }
+    CUDA_TRY(cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming));
+    *out = b.release();
+    return PIC_OK;
+}
+
+int pic_batch_step(pic_batch *b, int64_t nsteps) {
+    g_err.clear();
+    if (!b) return fail(PIC_ERR_ARG, "NULL batch");
+    if (nsteps < 0) return fail(PIC_ERR_ARG, "negative step count");
+    return b->step(nsteps);
+}
+
+int pic_batch_sync(pic_batch *b) {
+    g_err.clear();
+    if (!b) return fail(PIC_ERR_ARG, "NULL batch");
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    for (auto *x : b->h) {
+        const int rc = x->precision == PIC_FP64 ? S<double>(x)->sync() : S<float>(x)->sync();
+        if (rc) return rc;
+    }
+    return PIC_OK;
+}
+
+int pic_batch_destroy(pic_batch *b) {
+    g_err.clear();
+    delete b;
+    return PIC_OK;
 }
 
 }  // extern "C"

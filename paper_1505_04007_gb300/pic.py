@@ -30,7 +30,8 @@ ERRORS = {-1: "PIC_ERR_ARG", -2: "PIC_ERR_CFL", -3: "PIC_ERR_OOM", -4: "PIC_ERR_
 EXPORTS = ("pic_last_error", "pic_workspace_size", "pic_create", "pic_destroy", "pic_set_stream",
            "pic_add_particles", "pic_get_particles", "pic_set_deposit", "pic_add_source", "pic_probe_dft",
            "pic_step", "pic_sync", "pic_probe_read", "pic_get_field", "pic_set_field", "pic_get_stats",
-           "pic_save", "pic_load", "pic_profile_steps", "pic_dft_fold_static")
+           "pic_save", "pic_load", "pic_profile_steps", "pic_dft_fold_static", "pic_batch_create",
+           "pic_batch_step", "pic_batch_sync", "pic_batch_destroy")
 
 
 class pic_material(C.Structure):
@@ -98,6 +99,10 @@ def load(path: str | None = None):
     L.pic_load.argtypes = [h, C.c_char_p]
     L.pic_dft_fold_static.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_uint32, C.c_void_p, C.c_int,
                                       C.c_int64, C.c_double, C.c_void_p, C.c_void_p]
+    L.pic_batch_create.argtypes = [C.c_int, C.POINTER(h), C.c_void_p, C.POINTER(h)]
+    L.pic_batch_step.argtypes = [h, C.c_int64]
+    L.pic_batch_sync.argtypes = [h]
+    L.pic_batch_destroy.argtypes = [h]
     _lib = L
     return L
 
@@ -223,6 +228,26 @@ def pic_dft_fold_static(samples_ptr: int, count: int, np_: int, comp_mask: int, 
 
 
 # ------------------------------------------------------------ convenience --
+def pic_batch_create(handles, stream: int | None = None) -> C.c_void_p:
+    arr = (C.c_void_p * len(handles))(*[hh.value if isinstance(hh, C.c_void_p) else hh for hh in handles])
+    out = C.c_void_p()
+    _check(load().pic_batch_create(len(handles), arr, C.c_void_p(stream) if stream else None, C.byref(out)),
+           "pic_batch_create")
+    return out
+
+
+def pic_batch_step(b, nsteps: int) -> None:
+    _check(load().pic_batch_step(b, int(nsteps)), "pic_batch_step")
+
+
+def pic_batch_sync(b) -> None:
+    _check(load().pic_batch_sync(b), "pic_batch_sync")
+
+
+def pic_batch_destroy(b) -> None:
+    _check(load().pic_batch_destroy(b), "pic_batch_destroy")
+
+
 def make_config(w, precision=PIC_FP32, max_particles=None, max_probes=None, max_freqs=None,
                 eps0=None, mu0=None) -> tuple[pic_config, tuple]:
     """pic_config for a Workload; returns (cfg, keepalive) where keepalive
@@ -332,6 +357,37 @@ class Simulation:
             pic_destroy(self.h)
             self.h = None
             self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several Simulations stepped together through one pic_batch."""
+
+    def __init__(self, sims, stream=None):
+        import torch
+        self.sims = list(sims)
+        self._stream = stream if stream is not None else torch.cuda.Stream()
+        self.b = pic_batch_create([x.h for x in self.sims], self._stream.cuda_stream)
+
+    @property
+    def stream(self):
+        return self._stream
+
+    def step(self, n):
+        pic_batch_step(self.b, n)
+
+    def sync(self):
+        pic_batch_sync(self.b)
+
+    def close(self):
+        if getattr(self, "b", None):
+            pic_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

@@ -18,6 +18,9 @@ sizes below are the three single-instance workloads the project benchmarks:
   at 50 keV, a line of 64 probes (paper-scale run, the timed workload).
 * ``c3`` 768x256x256 cells, dx=1 nm, 12000 steps, 10 nm film, 1e6 electrons
   at 30 keV, one probe (streaming-limit size).
+* ``sweep`` 48 independent instances on uneven grids (128..320 x 64..128 x
+  64..96 cells), films 10-60 nm, 10-100 keV, gaps 5-20 nm, 2e4 electrons
+  each, 4000 steps (batched stepping).
 
 Positions come from ``numpy.random.default_rng(seed)`` (PCG64) with a fixed
 rejection order, so every consumer sees identical arrays.
@@ -213,6 +216,43 @@ def c3(seed: int = 1505, nsteps: int = 12000, nparticles: int = 1000000) -> Work
     probe = [(L + 0.75 * (nx - 2 * L)) * dx, 0.5 * ny * dx, top + 5e-9]
     return _bunch_workload("c3", nx, ny, nz, dx, nsteps, 8, 18, nparticles, 2e-15, 30.0,
                            (25e-9, 0.5 * ny * dx, top + 5e-9), 5e-9, [probe], seed)
+
+
+def sweep(n: int = 48, seed: int = 1505, nsteps: int = 4000, nparticles: int = 20000,
+          sizes: tuple = ((128, 320), (64, 128), (64, 96))) -> list:
+    """A sweep of n independent film instances for batched stepping: silver
+    films 10-60 nm thick (uniform), electrons of 10-100 keV (log-uniform),
+    bunch centres 5-20 nm above the film (uniform), grids of uneven sizes in
+    the given (lo, hi) cell ranges per axis (x a multiple of 32, y and z of
+    16; z raised where the film, gap and bunch need it), dx = 2 nm, 1 fC and
+    `nparticles` electrons per bunch (sigma 5 nm), one probe 5 nm above the
+    film top.  Draws come from one PCG64 stream in a fixed order per
+    instance: nx, ny, nz, thickness, energy, gap; instance i's bunch uses
+    seed + 1 + i."""
+    rng = np.random.default_rng(seed)
+    dx = 2e-9
+    L = 8
+    sigma = 5e-9
+    out = []
+    for i in range(n):
+        nx = 32 * int(rng.integers(sizes[0][0] // 32, sizes[0][1] // 32 + 1))
+        ny = 16 * int(rng.integers(sizes[1][0] // 16, sizes[1][1] // 16 + 1))
+        nz = 16 * int(rng.integers(sizes[2][0] // 16, sizes[2][1] // 16 + 1))
+        d = rng.uniform(10e-9, 60e-9)
+        kev = float(np.exp(rng.uniform(np.log(10.0), np.log(100.0))))
+        gap = rng.uniform(5e-9, 20e-9)
+        k0 = L
+        k1 = k0 + max(1, int(round(d / dx)))
+        top = k1 * dx
+        need = int(np.ceil((top + gap + 3 * sigma) / dx)) + MARGIN_CELLS + 1 + L
+        nz = max(nz, 16 * ((need + 15) // 16))
+        probe = [(L + 0.75 * (nx - 2 * L)) * dx, 0.5 * ny * dx, top + 5e-9]
+        centre = ((L + MARGIN_CELLS) * dx + 3 * sigma, 0.5 * ny * dx, top + gap)
+        w = _bunch_workload(f"sweep{i:02d}", nx, ny, nz, dx, nsteps, k0, k1, nparticles, 1e-15, kev,
+                            centre, sigma, [probe], seed + 1 + i)
+        w.info.update(thickness=d, gap=gap)
+        out.append(w)
+    return out
 
 
 def scaled(w: Workload, nx: int, ny: int, nz: int, nparticles: int, nsteps: int,

@@ -1,0 +1,89 @@
+"""Batched stepping (pic_batch): several independent film instances stepped
+through one captured graph must each give what the FP64 oracle gives for that
+instance alone (same tolerances as the single-instance parity tests: rel-L2
+<= 1e-10 for an FP64 instance, <= 2e-5 for FP32; probe spectra likewise).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1505_04007_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+ETA0 = (W.MU0 / W.EPS0) ** 0.5
+
+# small uneven grids, a few hundred electrons each: the oracle runs them in seconds
+SMALL = dict(sizes=((64, 96), (32, 48), (48, 64)), nparticles=384)
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    from paper_1505_04007_gb300 import pic
+    pic.load()
+    return pic
+
+
+def rel_l2(a, b):
+    nb = np.sqrt(sum((x ** 2).sum() for x in b))
+    na = np.sqrt(sum(((x - y) ** 2).sum() for x, y in zip(a, b)))
+    return na / nb if nb > 0 else na
+
+
+def fields_of(getter):
+    return [getter(c) for c in range(3)] + [ETA0 * getter(3 + c) for c in range(3)]
+
+
+def check(o, s, tol):
+    f = rel_l2(fields_of(s.field), fields_of(o.get_field))
+    p = rel_l2([s.probe_read()], [o.probe_read()])
+    assert f <= tol and p <= tol, (f, p)
+    return f, p
+
+
+def test_batch_fp32_matches_oracle(P):
+    ws = W.sweep(n=3, seed=7, nsteps=128, **SMALL)
+    sims = [P.Simulation(w, P.PIC_FP32) for w in ws]
+    b = P.Batch(sims)
+    b.step(128)  # two whole blocks through the batch graph
+    b.sync()
+    for w, s in zip(ws, sims):
+        o = O.from_workload(w)
+        o.step(128)
+        check(o, s, 2e-5)
+        assert s.stats().step == 128
+    b.close()
+
+
+def test_batch_mixed_precision_with_remainder(P):
+    ws = W.sweep(n=2, seed=9, nsteps=80, **SMALL)
+    sims = [P.Simulation(ws[0], P.PIC_FP64), P.Simulation(ws[1], P.PIC_FP32)]
+    b = P.Batch(sims)
+    b.step(64 + 13)  # one block through the graph, then 13 steps per instance
+    b.sync()
+    for w, s, tol in zip(ws, sims, (1e-10, 2e-5)):
+        o = O.from_workload(w)
+        o.step(77)
+        check(o, s, tol)
+    b.close()
+
+
+def test_batch_recaptures_after_change(P):
+    ws = W.sweep(n=2, seed=5, nsteps=192, **SMALL)
+    sims = [P.Simulation(w, P.PIC_FP32) for w in ws]
+    orcs = [O.from_workload(w) for w in ws]
+    b = P.Batch(sims)
+    b.step(64)
+    P.pic_set_deposit(sims[1].h, False)  # invalidates the captured steps of instance 1
+    orcs[1].step(64)
+    orcs[1].set_deposit(False)
+    orcs[0].step(64)
+    b.step(128)
+    b.sync()
+    for o, s in zip(orcs, sims):
+        o.step(128)
+        check(o, s, 2e-5)
+    b.close()
