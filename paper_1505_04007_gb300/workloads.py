@@ -255,6 +255,61 @@ def sweep(n: int = 48, seed: int = 1505, nsteps: int = 4000, nparticles: int = 2
     return out
 
 
+# The paper's film model for its mode study (Sec. IV, Table 1): silver with
+# these Drude parameters, a 100 keV bunch, films 20-150 nm thick.
+TABLE1_WP = 1.2e16
+TABLE1_GAMMA = 1.45e13
+TABLE1_KEV = 100.0
+TABLE1_THICKNESS_NM = (20, 30, 40, 50, 60, 70, 80, 150)
+
+
+def film_plasmon(thick_cells: int, nsteps: int, nx: int = 256, npart: int = 1024, charge: float = 1e-18,
+                 wp: float = TABLE1_WP, gamma: float = TABLE1_GAMMA, kev: float = TABLE1_KEV, seed: int = 5,
+                 freqs=None, comp_mask: int = 0b101, below: int = 0) -> Workload:
+    """Quasi-2D version of the paper's film model (Sec. III-IV): a silver film
+    of thick_cells x 2 nm, `below` vacuum cells above the z-low CPML (0: on
+    it), periodic in y (2 cells), and a sheet of electrons at kev moving +x
+    20 nm above it (small total charge: linear response, no Coulomb
+    explosion); one probe 5 nm above the film at 3/4 of the x extent."""
+    dx = 2e-9
+    k0 = 8 + below
+    k1 = k0 + thick_cells
+    ny = 2
+    nz = k1 + 32 + 8
+    w = Workload(name=f"film{2 * thick_cells}nm", nx=nx, ny=ny, nz=nz, dx=dx, dy=dx, dz=dx,
+                 dt=yee_dt(dx, dx, dx), nsteps=nsteps,
+                 bc=(BC_CPML, BC_CPML, BC_PERIODIC, BC_PERIODIC, BC_CPML, BC_CPML))
+    w.cpml_alpha_max = 0.05 * EPS0 * wp
+    w.material = slab_material(nx, ny, nz, k0, k1)
+    w.table = np.array([[0.0, 0.0, 1.0], [wp, gamma, 1.0]])
+    rng = np.random.default_rng(seed)
+    x = rng.normal(30 * dx, 8 * dx, npart)
+    y = rng.uniform(0, ny * dx, npart)
+    z = rng.normal((k1 + 10) * dx, 1.0 * dx, npart)
+    w.xyz = np.stack([x, y, z], 1)
+    w.u = np.zeros_like(w.xyz)
+    w.u[:, 0] = electron_momentum(kev)
+    w.q_macro = -charge / npart
+    w.m_macro = ME * (charge / npart) / QE
+    w.probes = np.array([[0.75 * nx * dx, 0.5 * ny * dx, k1 * dx + 5e-9]])
+    w.freqs = np.arange(1.0e15, 1.5e15, 1e12) if freqs is None else np.asarray(freqs, np.float64)
+    w.comp_mask = comp_mask
+    w.info.update(film_cells=(k0, k1), kev=kev, wp=wp, thickness=thick_cells * dx)
+    return w
+
+
+def table1(nsteps: int, nx: int = 2048, below: int = 24) -> list:
+    """The paper's thickness series: one film_plasmon instance per thickness
+    of TABLE1_THICKNESS_NM, Ez probed from 0.7 to 1.6 PHz in 1 THz steps.
+    The film is a free film in vacuum (the theory the paper compares with
+    has vacuum on both sides): `below` vacuum cells separate it from the
+    z-low CPML, which also keeps the Drude metal away from the absorbing
+    layer (with the metal on the CPML the late-time fields grow)."""
+    freqs = np.arange(0.7e15, 1.6e15 + 0.5e12, 1e12)
+    return [film_plasmon(d // 2, nsteps, nx=nx, freqs=freqs, comp_mask=0b100, below=below)
+            for d in TABLE1_THICKNESS_NM]
+
+
 def scaled(w: Workload, nx: int, ny: int, nz: int, nparticles: int, nsteps: int,
            seed: int = 1505) -> Workload:
     """A smaller instance with the same film planes, bunch recipe and probe

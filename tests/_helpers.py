@@ -165,34 +165,11 @@ def cic_charge_fast(w, xyz, q):
 
 def film_spp_workload(thick_cells, nsteps, nx=256, npart=1024, charge=1e-18, wp=1.2e16, gamma=1.45e13,
                       kev=100.0, seed=5):
-    """Quasi-2D version of the paper's model (Sec. III): a silver film (the
-    paper's wp and gamma) of thick_cells x 2 nm on the z-low CPML, periodic
-    in y, and a sheet of electrons at kev moving +x 20 nm above it (small
-    total charge: linear response, no Coulomb explosion); one probe 5 nm
-    above the film at 3/4 of the x extent, Ex and Ez."""
-    dx = 2e-9
-    k0 = 8
-    k1 = k0 + thick_cells
-    ny = 2
-    nz = k1 + 32 + 8
-    w = W.Workload(name="film_spp", nx=nx, ny=ny, nz=nz, dx=dx, dy=dx, dz=dx, dt=W.yee_dt(dx, dx, dx),
-                   nsteps=nsteps, bc=(W.BC_CPML, W.BC_CPML, W.BC_PERIODIC, W.BC_PERIODIC, W.BC_CPML, W.BC_CPML))
-    w.cpml_alpha_max = 0.05 * W.EPS0 * wp
-    w.material = W.slab_material(nx, ny, nz, k0, k1)
-    w.table = np.array([[0.0, 0.0, 1.0], [wp, gamma, 1.0]])
-    rng = np.random.default_rng(seed)
-    x = rng.normal(30 * dx, 8 * dx, npart)
-    y = rng.uniform(0, ny * dx, npart)
-    z = rng.normal((k1 + 10) * dx, 1.0 * dx, npart)
-    w.xyz = np.stack([x, y, z], 1)
-    w.u = np.zeros_like(w.xyz)
-    w.u[:, 0] = W.electron_momentum(kev)
-    w.q_macro = -charge / npart
-    w.m_macro = W.ME * (charge / npart) / W.QE
-    w.probes = np.array([[0.75 * nx * dx, 0.5 * ny * dx, k1 * dx + 5e-9]])
-    w.freqs = np.arange(1.0e15, 1.5e15, 1e12)
-    w.comp_mask = 0b101
-    w.info.update(film_cells=(k0, k1), kev=kev, wp=wp)
+    """The quasi-2D film model of workloads.film_plasmon with Ex and Ez probed
+    from 1.0 to 1.5 PHz."""
+    w = W.film_plasmon(thick_cells, nsteps, nx=nx, npart=npart, charge=charge, wp=wp, gamma=gamma, kev=kev,
+                       seed=seed)
+    w.name = "film_spp"
     return w
 
 
