@@ -179,6 +179,17 @@ int pic_sync(pic_handle *h);
  * the mask are zero).  Synchronises. */
 int pic_probe_read(pic_handle *h, double *out);
 
+/* Space-time spectrum of the probe line (the paper's dispersion picture,
+ * Sec. II / Fig. 2): for the wavenumbers k[0..nk) (rad/m) along axis `axis`
+ * (0 x, 1 y, 2 z),
+ *     out[q][f] = | sum_p F[p][comp][f] exp(-i k[q] s_p) |^2   (nk x nf, row-major)
+ * with F the probe spectra of pic_probe_read and s_p the coordinate of probe
+ * p along the axis in metres.  Meaningful for probes on a line along that
+ * axis.  Flushes buffered samples; synchronises; allocates two temporary
+ * device buffers (k and out).  Errors: PIC_ERR_STATE (no probes), PIC_ERR_ARG
+ * (comp/axis out of range, nk > 65535, NULL arrays), PIC_ERR_OOM, PIC_ERR_CUDA. */
+int pic_probe_kw(pic_handle *h, int comp, int axis, int nk, const double *k, double *out);
+
 /* Copy grid array `which` (PIC_EX..PIC_JFZ) to out [nz][ny][nx] as double.
  * Synchronises. */
 int pic_get_field(pic_handle *h, int which, double *out);

@@ -76,3 +76,36 @@ def film_modes(wp: float, d: float, kev: float, n_scan: int = 4000):
 def film_modes_thz(wp: float, d: float, kev: float):
     lo, hi = film_modes(wp, d, kev)
     return lo / (2 * math.pi) / 1e12, hi / (2 * math.pi) / 1e12
+
+
+def branch_omega(wp: float, d: float, k: float, branch: str, n_scan: int = 4000) -> float:
+    """omega (rad/s) of a bound film mode of real wavenumber k (rad/m) on the
+    given branch ("upper" or "lower"): the same two equations as above with k
+    independent of omega, on 0 < omega < min(wp, c k) (below the light line,
+    eps < 0).  nan if the branch has no mode at this k."""
+    top = min(wp, C0 * k) * (1 - 1e-12)
+
+    def res(omega):
+        eps = 1.0 - (wp / omega) ** 2
+        kd = math.sqrt(max(k * k - (omega / C0) ** 2, 0.0))
+        km = math.sqrt(k * k - eps * (omega / C0) ** 2)
+        x = 0.5 * km * d
+        if branch == "upper":
+            return km * math.tanh(x) + eps * kd
+        return km + eps * kd * math.tanh(x)
+
+    grid = np.linspace(1e-3 * top, top, n_scan)
+    vals = [res(w) for w in grid]
+    for a in range(n_scan - 1):
+        if vals[a] == 0.0 or vals[a] * vals[a + 1] < 0:
+            return brentq(res, grid[a], grid[a + 1], xtol=1e-6, rtol=1e-15)
+    return float("nan")
+
+
+def single_interface_omega(wp: float, k: float) -> float:
+    """Closed form of the lossless Drude surface plasmon on one metal-vacuum
+    interface, k^2 = (omega/c)^2 eps/(1+eps): omega^2 = wp^2/2 + (ck)^2 -
+    sqrt(wp^4/4 + (ck)^4)."""
+    ck = C0 * k
+    return math.sqrt(0.5 * wp * wp + ck * ck - math.sqrt(0.25 * wp ** 4 + ck ** 4))
+

@@ -1029,6 +1029,36 @@ static int probe_read_t(Sim<T> *s, double *out) {
 }
 
 template <typename T>
+static int probe_kw_t(Sim<T> *s, int comp, int axis, int nk, const double *k, double *out) {
+    if (s->pr.np == 0 || s->pr.nf == 0) return fail(PIC_ERR_STATE, "no probes configured");
+    if (comp < 0 || comp > 2 || axis < 0 || axis > 2 || nk < 0 || (nk > 0 && (!k || !out)))
+        return fail(PIC_ERR_ARG, "bad k-omega arguments");
+    if (nk > 65535) return fail(PIC_ERR_ARG, "at most 65535 wavenumbers");
+    if (nk == 0) return PIC_OK;
+    int rc = s->flush_probes();
+    if (rc) return rc;
+    const size_t kb = (size_t)nk * sizeof(double), ob = (size_t)nk * s->pr.nf * sizeof(double);
+    double *dk = nullptr, *dout = nullptr;
+    CUDA_TRY(cudaMalloc(&dk, kb));
+    if (cudaMalloc(&dout, ob) != cudaSuccess) {
+        cudaFree(dk);
+        return fail(PIC_ERR_OOM, "k-omega output of %zu bytes", ob);
+    }
+    cudaError_t e = cudaMemcpyAsync(dk, k, kb, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) {
+        launch_probe_kw(s->d_F, s->d_probe_xyz, s->d[axis], axis, s->pr.np, s->pr.nf, comp, dk, nk, dout, s->stream);
+        s->kernels += 1;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, ob, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    cudaFree(dk);
+    cudaFree(dout);
+    if (e != cudaSuccess) return fail(PIC_ERR_CUDA, "k-omega map: %s", cudaGetErrorString(e));
+    return s->sync();
+}
+
+template <typename T>
 static T *field_of(Sim<T> *s, int which) {
     const int c = which % 3;
     switch (which / 3) {
@@ -1226,6 +1256,13 @@ int pic_probe_read(pic_handle *h, double *out) {
     g_err.clear();
     if (!h || !out) return fail(PIC_ERR_ARG, "NULL argument");
     return h->precision == PIC_FP64 ? probe_read_t(S<double>(h), out) : probe_read_t(S<float>(h), out);
+}
+
+int pic_probe_kw(pic_handle *h, int comp, int axis, int nk, const double *k, double *out) {
+    g_err.clear();
+    if (!h) return fail(PIC_ERR_ARG, "NULL handle");
+    return h->precision == PIC_FP64 ? probe_kw_t(S<double>(h), comp, axis, nk, k, out)
+                                    : probe_kw_t(S<float>(h), comp, axis, nk, k, out);
 }
 
 int pic_get_field(pic_handle *h, int which, double *out) {

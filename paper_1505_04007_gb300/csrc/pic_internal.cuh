@@ -150,6 +150,10 @@ void launch_v4_E(const Grid<float> &g, const Fields<float> &f, const FieldPlan &
 // 255.  Returns false when the grid does not suit these kernels.
 bool make_field_plan(const Grid<float> &g, const uint8_t *plane_cls, const float *cls_cE, FieldPlan &p);
 
+// k-omega map of the probe line (probe.cu): out[q][f] = |sum_p F_p e^{-i k_q s_p}|^2.
+void launch_probe_kw(const double *F, const double *xyz_cells, double cell, int axis, int np, int nf, int comp,
+                     const double *k, int nk, double *out, cudaStream_t s);
+
 // Mark tile t as holding free current of the step flagged v, and append it
 // to the step's tile list the first time.
 __device__ __forceinline__ void mark_jf_tile(int *flag, int *list, int *count, long long t, int v) {

@@ -182,4 +182,31 @@ template void launch_step_tail<double>(const Grid<double> &, const Fields<double
 template void launch_dft_flush<float>(const Probes<float> &, const long long *, int, cudaStream_t);
 template void launch_dft_flush<double>(const Probes<double> &, const long long *, int, cudaStream_t);
 
+// Space-time spectrum of the probe line (the dispersion picture of Sec. II,
+// Fig. 2): out[q][f] = |sum_p F[p][comp][f] exp(-i k_q s_p)|^2, s_p the
+// probe coordinate along the line's axis.  One thread per (k, f); FP64.
+__global__ void k_probe_kw(const double *F, const double *xyz_cells, double cell, int axis, int np, int nf,
+                           int comp, const double *k, int nk, double *out) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = blockIdx.y;
+    if (f >= nf || q >= nk) return;
+    double re = 0.0, im = 0.0;
+    for (int p = 0; p < np; p++) {
+        const double sp = xyz_cells[3 * p + axis] * cell;
+        double sn, cs;
+        sincos(-k[q] * sp, &sn, &cs);
+        const double *z = F + (((long long)p * 3 + comp) * nf + f) * 2;
+        re += z[0] * cs - z[1] * sn;
+        im += z[0] * sn + z[1] * cs;
+    }
+    out[(long long)q * nf + f] = re * re + im * im;
+}
+
+void launch_probe_kw(const double *F, const double *xyz_cells, double cell, int axis, int np, int nf, int comp,
+                     const double *k, int nk, double *out, cudaStream_t s) {
+    const int blk = 128;
+    k_probe_kw<<<dim3((nf + blk - 1) / blk, nk), blk, 0, s>>>(F, xyz_cells, cell, axis, np, nf, comp, k, nk, out);
+    launch_count() += 1;
+}
+
 }  // namespace pic

@@ -31,7 +31,7 @@ EXPORTS = ("pic_last_error", "pic_workspace_size", "pic_create", "pic_destroy", 
            "pic_add_particles", "pic_get_particles", "pic_set_deposit", "pic_add_source", "pic_probe_dft",
            "pic_step", "pic_sync", "pic_probe_read", "pic_get_field", "pic_set_field", "pic_get_stats",
            "pic_save", "pic_load", "pic_profile_steps", "pic_dft_fold_static", "pic_batch_create",
-           "pic_batch_step", "pic_batch_sync", "pic_batch_destroy")
+           "pic_batch_step", "pic_batch_sync", "pic_batch_destroy", "pic_probe_kw")
 
 
 class pic_material(C.Structure):
@@ -99,6 +99,7 @@ def load(path: str | None = None):
     L.pic_load.argtypes = [h, C.c_char_p]
     L.pic_dft_fold_static.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_uint32, C.c_void_p, C.c_int,
                                       C.c_int64, C.c_double, C.c_void_p, C.c_void_p]
+    L.pic_probe_kw.argtypes = [h, C.c_int, C.c_int, C.c_int, dp, dp]
     L.pic_batch_create.argtypes = [C.c_int, C.POINTER(h), C.c_void_p, C.POINTER(h)]
     L.pic_batch_step.argtypes = [h, C.c_int64]
     L.pic_batch_sync.argtypes = [h]
@@ -184,6 +185,13 @@ def pic_probe_read(h, nprobe: int, nfreq: int) -> np.ndarray:
     _check(load().pic_probe_read(h, _dp(out)), "pic_probe_read")
     z = out.reshape(nprobe, 3, nfreq, 2)
     return z[..., 0] + 1j * z[..., 1]
+
+
+def pic_probe_kw(h, comp: int, k, nfreq: int, axis: int = 0) -> np.ndarray:
+    k = np.ascontiguousarray(k, dtype=np.float64)
+    out = np.empty((k.size, nfreq))
+    _check(load().pic_probe_kw(h, comp, axis, k.size, _dp(k), _dp(out)), "pic_probe_kw")
+    return out
 
 
 def pic_get_field(h, which: int, shape) -> np.ndarray:
@@ -339,6 +347,9 @@ class Simulation:
 
     def probe_read(self):
         return pic_probe_read(self.h, self.nprobe, self.nfreq)
+
+    def probe_kw(self, comp, k, axis=0):
+        return pic_probe_kw(self.h, comp, k, self.nfreq, axis)
 
     def stats(self):
         return pic_get_stats(self.h)

@@ -289,12 +289,28 @@ def film_plasmon(thick_cells: int, nsteps: int, nx: int = 256, npart: int = 1024
     w.xyz = np.stack([x, y, z], 1)
     w.u = np.zeros_like(w.xyz)
     w.u[:, 0] = electron_momentum(kev)
-    w.q_macro = -charge / npart
-    w.m_macro = ME * (charge / npart) / QE
+    w.q_macro = -charge / max(npart, 1)
+    w.m_macro = ME * (charge / max(npart, 1)) / QE
     w.probes = np.array([[0.75 * nx * dx, 0.5 * ny * dx, k1 * dx + 5e-9]])
     w.freqs = np.arange(1.0e15, 1.5e15, 1e12) if freqs is None else np.asarray(freqs, np.float64)
     w.comp_mask = comp_mask
     w.info.update(film_cells=(k0, k1), kev=kev, wp=wp, thickness=thick_cells * dx)
+    return w
+
+
+def film_line(thick_cells: int, nsteps: int, nx: int = 1024, nprobes: int = 64, first: int = 200,
+              spacing: int = 11, below: int = 24, freqs=None) -> Workload:
+    """A free film (film_plasmon geometry, no electrons) with a line of
+    nprobes probes along x, 5 nm above the film, from cell `first` every
+    `spacing` cells: the input of the k-omega readout (Fig. 2 analogue).  The
+    excitation is left to the caller (a prescribed source pulse)."""
+    fq = np.arange(0.5e15, 1.7e15 + 0.5e12, 2e12) if freqs is None else freqs
+    w = film_plasmon(thick_cells, nsteps, nx=nx, npart=0, freqs=fq, comp_mask=0b100, below=below)
+    w.xyz = np.zeros((0, 3))
+    w.u = np.zeros((0, 3))
+    top = w.info["film_cells"][1] * w.dx
+    w.probes = np.array([[(first + spacing * p) * w.dx, 0.5 * w.ny * w.dx, top + 5e-9] for p in range(nprobes)])
+    w.name = f"film_line{2 * thick_cells}nm"
     return w
 
 

@@ -67,3 +67,29 @@ def test_modes_bracket_thick_limit():
     w = T.thick_film_omega(1.37e16, 30.0)
     lo, hi = T.film_modes(1.37e16, 20e-9, 30.0)
     assert lo < w < hi
+
+
+def test_branch_omega_on_the_electron_line_gives_the_table_modes():
+    # k = omega/(beta c) at each electron-line crossing returns that crossing
+    beta = T.beta_of(100.0)
+    for d in (20e-9, 50e-9, 80e-9):
+        lo, hi = T.film_modes(1.2e16, d, 100.0)
+        assert abs(T.branch_omega(1.2e16, d, lo / (beta * T.C0), "lower") / lo - 1) < 1e-6
+        assert abs(T.branch_omega(1.2e16, d, hi / (beta * T.C0), "upper") / hi - 1) < 1e-6
+
+
+def test_branch_omega_thick_film_and_large_k_limits():
+    wp = 1.2e16
+    for k in (3e7, 6e7, 1.2e8):  # a 2 um film: both branches on the single-interface curve
+        w1 = T.single_interface_omega(wp, k)
+        for br in ("lower", "upper"):
+            assert abs(T.branch_omega(wp, 2e-6, k, br) / w1 - 1) < 1e-6
+    # the closed form itself: k -> infinity gives wp/sqrt(2); small k hugs the light line
+    assert abs(T.single_interface_omega(wp, 1e11) / (wp / math.sqrt(2)) - 1) < 1e-6
+    ck = T.C0 * 1e5  # far below wp: omega = ck (1 - (ck/wp)^2 / 2 + ...)
+    assert abs(T.single_interface_omega(wp, 1e5) / (ck * (1 - 0.5 * (ck / wp) ** 2)) - 1) < 1e-8
+    # thin film: the branches straddle the single-interface curve
+    for k in (4e7, 8e7):
+        w1 = T.single_interface_omega(wp, k)
+        assert T.branch_omega(wp, 20e-9, k, "lower") < w1 < T.branch_omega(wp, 20e-9, k, "upper")
+
