@@ -37,8 +37,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=4096)
     ap.add_argument("--warmup", type=int, default=128)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["c1", "c2", "c3", "sweep"], default="c2",
-                    help="sweep: 48 uneven film instances stepped through one batch graph vs one after another")
+    ap.add_argument("--workload", choices=["c1", "c2", "c3", "sweep", "adjoint"], default="c2",
+                    help="sweep: 48 uneven film instances stepped through one batch graph vs one after another; "
+                         "adjoint: gradient of the plasmon probe energy (192x96x96, 4000 steps) vs the plain step")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -244,8 +245,75 @@ def bench_sweep(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_adjoint(args):
+    """Forward + adjoint of the film study (192x96x96 cells, 30 nm design
+    slab, 4000 steps, FP32 state) against the plain FP32 step of the same
+    grid, with the FP32 gradient's error against the FP64 one."""
+    import torch
+    import numpy as np
+    from paper_1505_04007_gb300 import adjoint as A
+    from paper_1505_04007_gb300 import pic
+    from paper_1505_04007_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    wp, gamma = W.TABLE1_WP, W.TABLE1_GAMMA
+    res = {}
+    for prec in ("fp32", "fp64"):
+        cfg = A.film_config(precision=pic.PIC_FP32 if prec == "fp32" else pic.PIC_FP64)
+        st = A.Adjoint(cfg)
+        mask = np.random.default_rng(1505).uniform(0.2, 0.8, st.n)
+        st.forward(mask, wp, gamma)  # warm-up
+        t0 = time.perf_counter()
+        loss = st.forward(mask, wp, gamma)
+        t1 = time.perf_counter()
+        dm, dwp, dga = st.backward()
+        t2 = time.perf_counter()
+        res[prec] = dict(loss=loss, dm=dm, dwp=dwp, dga=dga, fwd=t1 - t0, bwd=t2 - t1, cfg=cfg)
+        st.close()
+    cfg = res["fp32"]["cfg"]
+    cells = cfg.nx * cfg.ny * cfg.nz
+    steps = cfg.nsteps
+    # the plain FP32 step of the same grid (film of the design slab at m = 1, no electrons)
+    w = W.Workload(name="adjoint_grid", nx=cfg.nx, ny=cfg.ny, nz=cfg.nz, dx=cfg.dx, dy=cfg.dx, dz=cfg.dx,
+                   dt=cfg.dt, nsteps=steps)
+    w.cpml_alpha_max = cfg.cpml_alpha_max
+    w.material = W.slab_material(cfg.nx, cfg.ny, cfg.nz, cfg.design_k0, cfg.design_k1)
+    w.table = np.array([[0.0, 0.0, 1.0], [wp, gamma, 1.0]])
+    w.xyz, w.u = np.zeros((0, 3)), np.zeros((0, 3))
+    w.probes = np.array([list(cfg.probe)])
+    w.freqs = np.array([cfg.omega0 / (2 * np.pi)])
+    sim = pic.Simulation(w, pic.PIC_FP32, particles=False)
+    sim.step(256)
+    sim.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(sim.stream)
+    sim.step(steps)
+    e1.record(sim.stream)
+    sim.sync()
+    plain_s = e0.elapsed_time(e1) / 1e3
+    sim.close()
+    r32, r64 = res["fp32"], res["fp64"]
+    line = {"metric": "Gcell-upd/s", "value": cells * steps / (r32["fwd"] + r32["bwd"]) / 1e9, "unit": "Gcell-upd/s",
+            "n_gpus": 1, "steps": steps, "warmup": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"adjoint: {cfg.nx}x{cfg.ny}x{cfg.nz} cells, design slab planes "
+                                   f"[{cfg.design_k0}, {cfg.design_k1}) (30 nm), rigid 40 keV bunch, "
+                                   f"{steps} steps, loss |F(wp/sqrt2)|^2 of Ez",
+                       "note": "value counts one forward + one backward step as one cell-update; host wall clock"},
+            "forward_s": r32["fwd"], "backward_s": r32["bwd"], "plain_step_s": plain_s,
+            "forward_plus_backward_vs_plain": (r32["fwd"] + r32["bwd"]) / plain_s,
+            "fp32_vs_fp64": {"loss_rel": abs(r32["loss"] / r64["loss"] - 1),
+                             "dmask_rel_l2": float(np.linalg.norm(r32["dm"] - r64["dm"]) / np.linalg.norm(r64["dm"])),
+                             "dwp_rel": abs(r32["dwp"] / r64["dwp"] - 1), "dgamma_rel": abs(r32["dga"] / r64["dga"] - 1)},
+            "fp64_forward_s": r64["fwd"], "fp64_backward_s": r64["bwd"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "adjoint":
+        if int(os.environ.get("RANK", "0")) == 0 and args.impl == "ours":
+            bench_adjoint(args)
+        return
     if args.workload == "sweep":
         if int(os.environ.get("RANK", "0")) == 0 and args.impl == "ours":
             bench_sweep(args)

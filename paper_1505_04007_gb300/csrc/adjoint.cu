@@ -1,0 +1,756 @@
+// adjoint.cu -- gradient of a probe's plasmon spectral energy with respect
+// to the film's Drude mask, wp and gamma (include/pic_adjoint.h).
+//
+// Forward: the field part of the PIC step (H with CPML; Eq. 6 then Eq. 8
+// with CPML), the electrons replaced by a rigid Gaussian bunch current, a
+// per-edge Drude factor bJ built from a per-cell mask.  Backward: the exact
+// transpose of that step, run from the last step to the first.  Each
+// forward update is a sum of terms "target += c * source"; its transpose
+// adds c * adjoint(target) to adjoint(source).  The transposed H and E
+// updates scatter into the neighbours' adjoint values with atomics (several
+// cells read the same neighbour in the forward step), the CPML psi and the
+// Drude current J are per-edge states whose adjoints stay in place.
+// Every E^n and J^n on the design edges is stored during the forward run
+// (nothing is recomputed); gradients of bJ and kJ accumulate in FP64 per
+// design edge and are reduced to the mask, wp and gamma on the host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "../../include/pic.h"
+#include "../../include/pic_adjoint.h"
+#include "pic_internal.cuh"
+
+namespace pic {
+namespace {
+
+template <typename T>
+struct AGrid {
+    int n[3];
+    int L;       // CPML cells on every face
+    T r[3];      // 1/dx per axis
+    T cH, cE;    // dt/mu0, dt/eps0
+    T kJm1;      // kJ - 1 (uniform gamma)
+};
+
+template <typename T>
+struct AState {
+    T *E[3], *H[3], *J[3];
+    T *psiH[3][2], *psiE[3][2];  // same compact slab layout as the main path
+    T *lE[3], *lH[3], *lJ[3];    // adjoints
+    T *lpsiH[3][2], *lpsiE[3][2];
+    const T *bE[3], *aE[3], *ikE[3], *bH[3], *aH[3], *ikH[3];  // b-1, a, 1/kappa
+    const int *slot[3];          // per edge: design-edge slot, or -1
+    const long long *eidx;       // per slot: linear edge index
+    long long soff[4];           // slots of component c are [soff[c], soff[c+1])
+    const T *beta;               // per slot: bJ
+    T *stE, *stJ;                // per step and slot: E^n, J^n
+    double *gb, *gk;             // per slot: dL/dbJ, dL/dkJ contributions
+};
+
+struct Bunch {
+    double qv_norm;  // q v (2 pi sigma^2)^{-3/2}
+    double inv2s2, cut2;
+    double v, x0, y0, z0, dx;
+};
+
+struct Probe {
+    long long idx[8];
+    double w[8];
+    int comp;
+    double omega, dt;
+};
+
+__device__ __forceinline__ int aslab(int L, int n, int x) {
+    if (x < L) return x;
+    if (x >= n - L) return x - (n - 2 * L);
+    return -1;
+}
+__device__ __forceinline__ long long apsi(const int n[3], int L, int a, int s, int i, int j, int k) {
+    const long long L2 = 2 * L;
+    if (a == 0) return ((long long)k * n[1] + j) * L2 + s;
+    if (a == 1) return ((long long)k * L2 + s) * n[0] + i;
+    return ((long long)s * n[1] + j) * n[0] + i;
+}
+
+// ------------------------------------------------------------ forward --
+template <typename T>
+__global__ void __launch_bounds__(256) k_fwd_H(AGrid<T> g, AState<T> f) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    if (i >= nx) return;
+    const long long sy = nx, sz = (long long)nx * ny, e = k * sz + j * sy + i;
+    const T ex = f.E[0][e], ey = f.E[1][e], ez = f.E[2][e];
+    const T dEz_dy = ((j + 1 < ny ? f.E[2][e + sy] : T(0)) - ez) * g.r[1];
+    const T dEy_dz = ((k + 1 < nz ? f.E[1][e + sz] : T(0)) - ey) * g.r[2];
+    const T dEx_dz = ((k + 1 < nz ? f.E[0][e + sz] : T(0)) - ex) * g.r[2];
+    const T dEz_dx = ((i + 1 < nx ? f.E[2][e + 1] : T(0)) - ez) * g.r[0];
+    const T dEy_dx = ((i + 1 < nx ? f.E[1][e + 1] : T(0)) - ey) * g.r[0];
+    const T dEx_dy = ((j + 1 < ny ? f.E[0][e + sy] : T(0)) - ex) * g.r[1];
+    T kx = 1, ky = 1, kz = 1, pxy = 0, pxz = 0, pyz = 0, pyx = 0, pzx = 0, pzy = 0;
+    const int s0 = aslab(g.L, nx, i), s1 = aslab(g.L, ny, j), s2 = aslab(g.L, nz, k);
+    if (s0 >= 0) {
+        const T b = f.bH[0][i], a = f.aH[0][i];
+        kx = f.ikH[0][i];
+        const long long q = apsi(g.n, g.L, 0, s0, i, j, k);
+        pxy = f.psiH[0][0][q] + (b * f.psiH[0][0][q] + a * dEz_dx); f.psiH[0][0][q] = pxy;
+        pxz = f.psiH[0][1][q] + (b * f.psiH[0][1][q] + a * dEy_dx); f.psiH[0][1][q] = pxz;
+    }
+    if (s1 >= 0) {
+        const T b = f.bH[1][j], a = f.aH[1][j];
+        ky = f.ikH[1][j];
+        const long long q = apsi(g.n, g.L, 1, s1, i, j, k);
+        pyz = f.psiH[1][0][q] + (b * f.psiH[1][0][q] + a * dEx_dy); f.psiH[1][0][q] = pyz;
+        pyx = f.psiH[1][1][q] + (b * f.psiH[1][1][q] + a * dEz_dy); f.psiH[1][1][q] = pyx;
+    }
+    if (s2 >= 0) {
+        const T b = f.bH[2][k], a = f.aH[2][k];
+        kz = f.ikH[2][k];
+        const long long q = apsi(g.n, g.L, 2, s2, i, j, k);
+        pzx = f.psiH[2][0][q] + (b * f.psiH[2][0][q] + a * dEy_dz); f.psiH[2][0][q] = pzx;
+        pzy = f.psiH[2][1][q] + (b * f.psiH[2][1][q] + a * dEx_dz); f.psiH[2][1][q] = pzy;
+    }
+    f.H[0][e] -= g.cH * (ky * dEz_dy + pyx - kz * dEy_dz - pzx);
+    f.H[1][e] -= g.cH * (kz * dEx_dz + pzy - kx * dEz_dx - pxy);
+    f.H[2][e] -= g.cH * (kx * dEy_dx + pxz - ky * dEx_dy - pyz);
+}
+
+// the rigid bunch current J_x at the Ex edge (i+1/2, j, k) at time t
+__device__ __forceinline__ double bunch_jx(const Bunch &b, int i, int j, int k, double t) {
+    const double x = (i + 0.5) * b.dx - (b.x0 + b.v * t), y = j * b.dx - b.y0, z = k * b.dx - b.z0;
+    const double r2 = x * x + y * y + z * z;
+    return r2 > b.cut2 ? 0.0 : b.qv_norm * exp(-r2 * b.inv2s2);
+}
+
+// Eq. 6 (design edges) then Eq. 8 for component c of edge e
+template <typename T>
+__device__ __forceinline__ void fwd_ampere(const AGrid<T> &g, const AState<T> &f, int c, long long e, T curl, T js) {
+    T E = f.E[c][e], jp = T(0);
+    const int sl = f.slot[c][e];
+    if (sl >= 0) {
+        const T j0 = f.J[c][e];
+        jp = j0 + (g.kJm1 * j0 + f.beta[sl] * E);
+        f.J[c][e] = jp;
+    }
+    f.E[c][e] = E + g.cE * (curl - jp - js);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fwd_E(AGrid<T> g, AState<T> f, Bunch bu, double t_half) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    if (i >= nx) return;
+    const long long sy = nx, sz = (long long)nx * ny, e = k * sz + j * sy + i;
+    const bool fx = i == 0, fy = j == 0, fz = k == 0;  // held tangential E on the low faces
+    const long long oim = i > 0 ? 1 : 0, ojm = j > 0 ? sy : 0, okm = k > 0 ? sz : 0;
+    const T hx = f.H[0][e], hy = f.H[1][e], hz = f.H[2][e];
+    const int s0 = aslab(g.L, nx, i), s1 = aslab(g.L, ny, j), s2 = aslab(g.L, nz, k);
+    if (!(fy || fz)) {
+        const T dHz_dy = (hz - f.H[2][e - ojm]) * g.r[1], dHy_dz = (hy - f.H[1][e - okm]) * g.r[2];
+        T ky = 1, kz = 1, py = 0, pz = 0;
+        if (s1 >= 0) {
+            ky = f.ikE[1][j];
+            const long long q = apsi(g.n, g.L, 1, s1, i, j, k);
+            py = f.psiE[1][1][q] + (f.bE[1][j] * f.psiE[1][1][q] + f.aE[1][j] * dHz_dy); f.psiE[1][1][q] = py;
+        }
+        if (s2 >= 0) {
+            kz = f.ikE[2][k];
+            const long long q = apsi(g.n, g.L, 2, s2, i, j, k);
+            pz = f.psiE[2][0][q] + (f.bE[2][k] * f.psiE[2][0][q] + f.aE[2][k] * dHy_dz); f.psiE[2][0][q] = pz;
+        }
+        fwd_ampere(g, f, 0, e, ky * dHz_dy + py - kz * dHy_dz - pz, (T)bunch_jx(bu, i, j, k, t_half));
+    }
+    if (!(fx || fz)) {
+        const T dHx_dz = (hx - f.H[0][e - okm]) * g.r[2], dHz_dx = (hz - f.H[2][e - oim]) * g.r[0];
+        T kz = 1, kx = 1, pz = 0, px = 0;
+        if (s2 >= 0) {
+            kz = f.ikE[2][k];
+            const long long q = apsi(g.n, g.L, 2, s2, i, j, k);
+            pz = f.psiE[2][1][q] + (f.bE[2][k] * f.psiE[2][1][q] + f.aE[2][k] * dHx_dz); f.psiE[2][1][q] = pz;
+        }
+        if (s0 >= 0) {
+            kx = f.ikE[0][i];
+            const long long q = apsi(g.n, g.L, 0, s0, i, j, k);
+            px = f.psiE[0][0][q] + (f.bE[0][i] * f.psiE[0][0][q] + f.aE[0][i] * dHz_dx); f.psiE[0][0][q] = px;
+        }
+        fwd_ampere(g, f, 1, e, kz * dHx_dz + pz - kx * dHz_dx - px, T(0));
+    }
+    if (!(fx || fy)) {
+        const T dHy_dx = (hy - f.H[1][e - oim]) * g.r[0], dHx_dy = (hx - f.H[0][e - ojm]) * g.r[1];
+        T kx = 1, ky = 1, px = 0, py = 0;
+        if (s0 >= 0) {
+            kx = f.ikE[0][i];
+            const long long q = apsi(g.n, g.L, 0, s0, i, j, k);
+            px = f.psiE[0][1][q] + (f.bE[0][i] * f.psiE[0][1][q] + f.aE[0][i] * dHy_dx); f.psiE[0][1][q] = px;
+        }
+        if (s1 >= 0) {
+            ky = f.ikE[1][j];
+            const long long q = apsi(g.n, g.L, 1, s1, i, j, k);
+            py = f.psiE[1][0][q] + (f.bE[1][j] * f.psiE[1][0][q] + f.aE[1][j] * dHx_dy); f.psiE[1][0][q] = py;
+        }
+        fwd_ampere(g, f, 2, e, kx * dHy_dx + px - ky * dHx_dy - py, T(0));
+    }
+}
+
+// E^n and J^n of every design edge into storage row n
+template <typename T>
+__global__ void k_store(AState<T> f, long long n) {
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long ne = f.soff[3];
+    if (q >= ne) return;
+    const int c = q < f.soff[1] ? 0 : (q < f.soff[2] ? 1 : 2);
+    const long long e = f.eidx[q];
+    f.stE[n * ne + q] = f.E[c][e];
+    f.stJ[n * ne + q] = f.J[c][e];
+}
+
+// F += E_c(x_p, t) exp(+i omega t) dt
+template <typename T>
+__global__ void k_probe(AState<T> f, Probe p, double t, double *F) {
+    if (threadIdx.x != 0) return;
+    double v = 0.0;
+    for (int q = 0; q < 8; q++) v += p.w[q] * (double)f.E[p.comp][p.idx[q]];
+    double sn, cs;
+    sincos(p.omega * t, &sn, &cs);
+    F[0] += v * cs * p.dt;
+    F[1] += v * sn * p.dt;
+}
+
+// ----------------------------------------------------------- backward --
+// adjoint of the probe term at time t: dL/dE = 2 Re(conj(F) e^{i omega t}) dt w
+template <typename T>
+__global__ void k_src(AState<T> f, Probe p, double t, const double *F) {
+    if (threadIdx.x != 0) return;
+    double sn, cs;
+    sincos(p.omega * t, &sn, &cs);
+    const double s = 2.0 * p.dt * (F[0] * cs + F[1] * sn);
+    for (int q = 0; q < 8; q++) f.lE[p.comp][p.idx[q]] += (T)(s * p.w[q]);
+}
+
+// Transpose of the Eq. 6 + Eq. 8 update of component c at edge e (updated
+// edges only).  Returns nothing; updates the adjoints of E, J (in place) and
+// accumulates the bJ / kJ gradients with the stored E^n, J^n.
+template <typename T>
+__device__ __forceinline__ void adj_ampere(const AGrid<T> &g, const AState<T> &f, int c, long long e, T lE,
+                                           long long n) {
+    const int sl = f.slot[c][e];
+    if (sl < 0) return;  // lambda_E passes through unchanged
+    const long long ne = f.soff[3];
+    const T LJ = f.lJ[c][e] - g.cE * lE;  // adjoint of J^{n+1}
+    f.gb[sl] += (double)LJ * (double)f.stE[n * ne + sl];
+    f.gk[sl] += (double)LJ * (double)f.stJ[n * ne + sl];
+    f.lJ[c][e] = (T(1) + g.kJm1) * LJ;
+    f.lE[c][e] = lE + f.beta[sl] * LJ;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_E(AGrid<T> g, AState<T> f, long long n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    if (i >= nx) return;
+    const long long sy = nx, sz = (long long)nx * ny, e = k * sz + j * sy + i;
+    const bool fx = i == 0, fy = j == 0, fz = k == 0;
+    const int s0 = aslab(g.L, nx, i), s1 = aslab(g.L, ny, j), s2 = aslab(g.L, nz, k);
+    const T cE = g.cE;
+    // scatter A * d(H_c)/d... for a backward difference (H[e] - H[e - off]) * r
+    auto scat = [&](T *lH, long long off, bool has, T r, T A) {
+        atomicAdd(&lH[e], r * A);
+        if (has) atomicAdd(&lH[e - off], -r * A);
+    };
+    if (!(fy || fz)) {  // Ex: curl = ky dHz/dy + py - kz dHy/dz - pz
+        const T lE = f.lE[0][e];
+        T Ay = cE * lE, Az = -cE * lE;
+        if (s1 >= 0) {
+            const long long q = apsi(g.n, g.L, 1, s1, i, j, k);
+            const T ap = f.lpsiE[1][1][q] + cE * lE;
+            Ay = cE * f.ikE[1][j] * lE + f.aE[1][j] * ap;
+            f.lpsiE[1][1][q] = (T(1) + f.bE[1][j]) * ap;
+        }
+        if (s2 >= 0) {
+            const long long q = apsi(g.n, g.L, 2, s2, i, j, k);
+            const T ap = f.lpsiE[2][0][q] - cE * lE;
+            Az = -cE * f.ikE[2][k] * lE + f.aE[2][k] * ap;
+            f.lpsiE[2][0][q] = (T(1) + f.bE[2][k]) * ap;
+        }
+        scat(f.lH[2], sy, j > 0, g.r[1], Ay);
+        scat(f.lH[1], sz, k > 0, g.r[2], Az);
+        adj_ampere(g, f, 0, e, lE, n);
+    }
+    if (!(fx || fz)) {  // Ey: curl = kz dHx/dz + pz - kx dHz/dx - px
+        const T lE = f.lE[1][e];
+        T Az = cE * lE, Ax = -cE * lE;
+        if (s2 >= 0) {
+            const long long q = apsi(g.n, g.L, 2, s2, i, j, k);
+            const T ap = f.lpsiE[2][1][q] + cE * lE;
+            Az = cE * f.ikE[2][k] * lE + f.aE[2][k] * ap;
+            f.lpsiE[2][1][q] = (T(1) + f.bE[2][k]) * ap;
+        }
+        if (s0 >= 0) {
+            const long long q = apsi(g.n, g.L, 0, s0, i, j, k);
+            const T ap = f.lpsiE[0][0][q] - cE * lE;
+            Ax = -cE * f.ikE[0][i] * lE + f.aE[0][i] * ap;
+            f.lpsiE[0][0][q] = (T(1) + f.bE[0][i]) * ap;
+        }
+        scat(f.lH[0], sz, k > 0, g.r[2], Az);
+        scat(f.lH[2], 1, i > 0, g.r[0], Ax);
+        adj_ampere(g, f, 1, e, lE, n);
+    }
+    if (!(fx || fy)) {  // Ez: curl = kx dHy/dx + px - ky dHx/dy - py
+        const T lE = f.lE[2][e];
+        T Ax = cE * lE, Ay = -cE * lE;
+        if (s0 >= 0) {
+            const long long q = apsi(g.n, g.L, 0, s0, i, j, k);
+            const T ap = f.lpsiE[0][1][q] + cE * lE;
+            Ax = cE * f.ikE[0][i] * lE + f.aE[0][i] * ap;
+            f.lpsiE[0][1][q] = (T(1) + f.bE[0][i]) * ap;
+        }
+        if (s1 >= 0) {
+            const long long q = apsi(g.n, g.L, 1, s1, i, j, k);
+            const T ap = f.lpsiE[1][0][q] - cE * lE;
+            Ay = -cE * f.ikE[1][j] * lE + f.aE[1][j] * ap;
+            f.lpsiE[1][0][q] = (T(1) + f.bE[1][j]) * ap;
+        }
+        scat(f.lH[1], 1, i > 0, g.r[0], Ax);
+        scat(f.lH[0], sy, j > 0, g.r[1], Ay);
+        adj_ampere(g, f, 2, e, lE, n);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_H(AGrid<T> g, AState<T> f) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    if (i >= nx) return;
+    const long long sy = nx, sz = (long long)nx * ny, e = k * sz + j * sy + i;
+    const T lx = f.lH[0][e], ly = f.lH[1][e], lz = f.lH[2][e], cH = g.cH;
+    // adjoints of the six differences (forward differences of E)
+    T Azy = -cH * lx, Ayz = cH * lx, Axz = -cH * ly, Azx = cH * ly, Ayx = -cH * lz, Axy = cH * lz;
+    const int s0 = aslab(g.L, nx, i), s1 = aslab(g.L, ny, j), s2 = aslab(g.L, nz, k);
+    if (s0 >= 0) {
+        const T a = f.aH[0][i], k0 = f.ikH[0][i], b1 = T(1) + f.bH[0][i];
+        const long long q = apsi(g.n, g.L, 0, s0, i, j, k);
+        const T pxy = f.lpsiH[0][0][q] + cH * ly, pxz = f.lpsiH[0][1][q] - cH * lz;
+        Azx = cH * k0 * ly + a * pxy;
+        Ayx = -cH * k0 * lz + a * pxz;
+        f.lpsiH[0][0][q] = b1 * pxy;
+        f.lpsiH[0][1][q] = b1 * pxz;
+    }
+    if (s1 >= 0) {
+        const T a = f.aH[1][j], k1 = f.ikH[1][j], b1 = T(1) + f.bH[1][j];
+        const long long q = apsi(g.n, g.L, 1, s1, i, j, k);
+        const T pyz = f.lpsiH[1][0][q] + cH * lz, pyx = f.lpsiH[1][1][q] - cH * lx;
+        Axy = cH * k1 * lz + a * pyz;
+        Azy = -cH * k1 * lx + a * pyx;
+        f.lpsiH[1][0][q] = b1 * pyz;
+        f.lpsiH[1][1][q] = b1 * pyx;
+    }
+    if (s2 >= 0) {
+        const T a = f.aH[2][k], k2 = f.ikH[2][k], b1 = T(1) + f.bH[2][k];
+        const long long q = apsi(g.n, g.L, 2, s2, i, j, k);
+        const T pzx = f.lpsiH[2][0][q] + cH * lx, pzy = f.lpsiH[2][1][q] - cH * ly;
+        Ayz = cH * k2 * lx + a * pzx;
+        Axz = -cH * k2 * ly + a * pzy;
+        f.lpsiH[2][0][q] = b1 * pzx;
+        f.lpsiH[2][1][q] = b1 * pzy;
+    }
+    // d = (E[e + off] - E[e]) * r, E[e + off] = 0 beyond the high face
+    auto scat = [&](T *lE, long long off, bool has, T r, T A) {
+        if (has) atomicAdd(&lE[e + off], r * A);
+        atomicAdd(&lE[e], -r * A);
+    };
+    scat(f.lE[2], sy, j + 1 < ny, g.r[1], Azy);
+    scat(f.lE[1], sz, k + 1 < nz, g.r[2], Ayz);
+    scat(f.lE[0], sz, k + 1 < nz, g.r[2], Axz);
+    scat(f.lE[2], 1, i + 1 < nx, g.r[0], Azx);
+    scat(f.lE[1], 1, i + 1 < nx, g.r[0], Ayx);
+    scat(f.lE[0], sy, j + 1 < ny, g.r[1], Axy);
+}
+
+// ------------------------------------------------------------------ host --
+struct AdjBase {
+    virtual ~AdjBase() {}
+    virtual int forward(const double *mask, double wp, double gamma, double *loss) = 0;
+    virtual int backward(double *dmask, double *dwp, double *dgamma) = 0;
+    long long nmask = 0;
+};
+
+template <typename T>
+struct AdjSim : AdjBase {
+    pic_adj_config cfg{};
+    AGrid<T> g{};
+    AState<T> f{};
+    Bunch bu{};
+    Probe pr{};
+    long long N = 0, ne = 0;
+    std::vector<void *> allocs;
+    std::vector<long long> eidx_h;       // per slot: edge index
+    std::vector<int> comp_h;             // per slot: component
+    std::vector<T> beta_h;
+    std::vector<double> mbar_h;          // per slot: mean mask over its four cells (last forward)
+    std::vector<std::array<long long, 4>> cells_h;  // per slot: its four cells as mask indices (-1: outside)
+    double *d_F = nullptr;
+    double F[2] = {0, 0};
+    double wp_last = 0, gamma_last = 0;
+    bool have_forward = false;
+
+    ~AdjSim() override {
+        cudaDeviceSynchronize();
+        for (void *p : allocs) cudaFree(p);
+    }
+
+    template <typename P>
+    int take(P **out, size_t count) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, count * sizeof(P) + 16) != cudaSuccess)
+            return set_last_error(PIC_ERR_OOM, "adjoint: cudaMalloc of %zu bytes failed", count * sizeof(P));
+        allocs.push_back(p);
+        *out = static_cast<P *>(p);
+        return PIC_OK;
+    }
+
+    void profile(int a, double pos, double &b, double &aa, double &ik) const {
+        const double L = cfg.cpml_cells, n = (double)g.n[a];
+        double rho = 0.0;
+        if (pos < L) rho = L - pos;
+        if (pos > n - L) rho = std::max(rho, pos - (n - L));
+        if (rho <= 0.0) { b = 0.0; aa = 0.0; ik = 1.0; return; }
+        const double eta0 = std::sqrt(cfg.mu0 / cfg.eps0);
+        const double x = rho / L, xm = std::pow(x, cfg.cpml_order);
+        const double sigma = cfg.cpml_sigma_fac * (cfg.cpml_order + 1.0) / (eta0 * cfg.dx) * xm;
+        const double kappa = 1.0 + (cfg.cpml_kappa_max - 1.0) * xm;
+        const double alpha = cfg.cpml_alpha_max * (1.0 - x);
+        b = std::expm1(-(sigma / kappa + alpha) * cfg.dt / cfg.eps0);
+        const double den = sigma * kappa + kappa * kappa * alpha;
+        aa = (sigma > 0.0 && den > 0.0) ? sigma * b / den : 0.0;
+        ik = 1.0 / kappa;
+    }
+
+    int create(const pic_adj_config *c) {
+        cfg = *c;
+        for (int a = 0; a < 3; a++) g.n[a] = (int)(a == 0 ? c->nx : a == 1 ? c->ny : c->nz);
+        g.L = c->cpml_cells;
+        for (int a = 0; a < 3; a++) g.r[a] = (T)(1.0 / c->dx);
+        g.cH = (T)(c->dt / c->mu0);
+        g.cE = (T)(c->dt / c->eps0);
+        N = (long long)g.n[0] * g.n[1] * g.n[2];
+        const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+        nmask = (long long)nx * ny * (c->design_k1 - c->design_k0);
+        // design edges: any of the four cells around the edge inside the slab
+        // (cells beyond a face are clamped to the face, as for the materials)
+        auto cell_mask_index = [&](int i, int j, int k) -> long long {
+            i = std::min(std::max(i, 0), nx - 1);
+            j = std::min(std::max(j, 0), ny - 1);
+            k = std::min(std::max(k, 0), nz - 1);
+            if (k < c->design_k0 || k >= c->design_k1) return -1;
+            return ((long long)(k - c->design_k0) * ny + j) * nx + i;
+        };
+        std::vector<int> slot_h[3];
+        long long soff[4] = {0, 0, 0, 0};
+        for (int comp = 0; comp < 3; comp++) {
+            slot_h[comp].assign((size_t)N, -1);
+            const int a1 = (comp + 1) % 3, a2 = (comp + 2) % 3;
+            const int klo = std::max(0, (int)c->design_k0 - 1), khi = std::min(nz, (int)c->design_k1 + 1);
+            for (int k = klo; k < khi; k++)
+                for (int j = 0; j < ny; j++)
+                    for (int i = 0; i < nx; i++) {
+                        std::array<long long, 4> cl;
+                        bool any = false;
+                        int t = 0;
+                        for (int s1 = -1; s1 <= 0; s1++)
+                            for (int s2 = -1; s2 <= 0; s2++) {
+                                int p3[3] = {i, j, k};
+                                p3[a1] += s1;
+                                p3[a2] += s2;
+                                cl[t] = cell_mask_index(p3[0], p3[1], p3[2]);
+                                any = any || cl[t] >= 0;
+                                t++;
+                            }
+                        if (!any) continue;
+                        const long long e = ((long long)k * ny + j) * nx + i;
+                        slot_h[comp][(size_t)e] = (int)eidx_h.size();
+                        eidx_h.push_back(e);
+                        comp_h.push_back(comp);
+                        cells_h.push_back(cl);
+                    }
+            soff[comp + 1] = (long long)eidx_h.size();
+        }
+        ne = (long long)eidx_h.size();
+        const size_t per_step = (size_t)ne * 2 * sizeof(T);
+        if (per_step && (size_t)c->nsteps > ((size_t)1 << 40) / per_step)
+            return set_last_error(PIC_ERR_OOM, "adjoint storage of %lld steps x %lld edges is too large",
+                                  (long long)c->nsteps, ne);
+        // device arrays
+        int rc = 0;
+        for (int a = 0; a < 3 && !rc; a++) {
+            rc = rc ? rc : take(&f.E[a], N);
+            rc = rc ? rc : take(&f.H[a], N);
+            rc = rc ? rc : take(&f.J[a], N);
+            rc = rc ? rc : take(&f.lE[a], N);
+            rc = rc ? rc : take(&f.lH[a], N);
+            rc = rc ? rc : take(&f.lJ[a], N);
+            const size_t slab = (size_t)(N / g.n[a]) * 2 * g.L;
+            for (int s = 0; s < 2 && !rc; s++) {
+                rc = rc ? rc : take(&f.psiH[a][s], slab);
+                rc = rc ? rc : take(&f.psiE[a][s], slab);
+                rc = rc ? rc : take(&f.lpsiH[a][s], slab);
+                rc = rc ? rc : take(&f.lpsiE[a][s], slab);
+            }
+        }
+        T *prof[3][6];
+        int *slot_d[3];
+        long long *eidx_d = nullptr;
+        T *beta_d = nullptr;
+        for (int a = 0; a < 3 && !rc; a++) {
+            for (int q6 = 0; q6 < 6 && !rc; q6++) rc = take(&prof[a][q6], g.n[a]);
+            rc = rc ? rc : take(&slot_d[a], N);
+        }
+        rc = rc ? rc : take(&eidx_d, ne + 1);
+        rc = rc ? rc : take(&beta_d, ne + 1);
+        rc = rc ? rc : take(&f.gb, ne + 1);
+        rc = rc ? rc : take(&f.gk, ne + 1);
+        rc = rc ? rc : take(&f.stE, (size_t)ne * c->nsteps + 1);
+        rc = rc ? rc : take(&f.stJ, (size_t)ne * c->nsteps + 1);
+        rc = rc ? rc : take(&d_F, 2);
+        if (rc) return rc;
+        for (int a = 0; a < 3; a++) {
+            std::vector<T> pf[6];
+            for (auto &v : pf) v.resize(g.n[a]);
+            for (int x = 0; x < g.n[a]; x++) {
+                double b, aa, ik;
+                profile(a, (double)x, b, aa, ik);
+                pf[0][x] = (T)b; pf[1][x] = (T)aa; pf[2][x] = (T)ik;
+                profile(a, x + 0.5, b, aa, ik);
+                pf[3][x] = (T)b; pf[4][x] = (T)aa; pf[5][x] = (T)ik;
+            }
+            for (int q6 = 0; q6 < 6; q6++)
+                if (cudaMemcpy(prof[a][q6], pf[q6].data(), g.n[a] * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+                    return set_last_error(PIC_ERR_CUDA, "adjoint: profile upload failed");
+            f.bE[a] = prof[a][0]; f.aE[a] = prof[a][1]; f.ikE[a] = prof[a][2];
+            f.bH[a] = prof[a][3]; f.aH[a] = prof[a][4]; f.ikH[a] = prof[a][5];
+            if (cudaMemcpy(slot_d[a], slot_h[a].data(), (size_t)N * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+                return set_last_error(PIC_ERR_CUDA, "adjoint: edge map upload failed");
+            f.slot[a] = slot_d[a];
+        }
+        if (ne && cudaMemcpy(eidx_d, eidx_h.data(), (size_t)ne * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess)
+            return set_last_error(PIC_ERR_CUDA, "adjoint: edge list upload failed");
+        f.eidx = eidx_d;
+        f.beta = beta_d;
+        for (int q4 = 0; q4 < 4; q4++) f.soff[q4] = soff[q4];
+        // bunch
+        const double s = c->bunch_sigma;
+        bu.qv_norm = c->bunch_q * c->bunch_v / std::pow(2.0 * M_PI * s * s, 1.5);
+        bu.inv2s2 = 1.0 / (2.0 * s * s);
+        bu.cut2 = 36.0 * s * s;
+        bu.v = c->bunch_v; bu.x0 = c->bunch_x0; bu.y0 = c->bunch_y0; bu.z0 = c->bunch_z0; bu.dx = c->dx;
+        // probe stencil on the component's staggered lattice
+        pr.comp = c->probe_comp;
+        pr.omega = c->omega0;
+        pr.dt = c->dt;
+        for (int corner = 0; corner < 8; corner++) {
+            long long idx = 0, stride = 1;
+            double wt = 1.0;
+            for (int a = 0; a < 3; a++) {
+                const double sa = c->probe[a] / c->dx - (a == pr.comp ? 0.5 : 0.0);
+                const double fl = std::floor(sa);
+                const int bit = (corner >> a) & 1;
+                const int ib = std::min(std::max((int)fl + bit, 0), g.n[a] - 1);
+                wt *= bit ? (sa - fl) : 1.0 - (sa - fl);
+                idx += (long long)ib * stride;
+                stride *= g.n[a];
+            }
+            pr.idx[corner] = idx;
+            pr.w[corner] = wt;
+        }
+        return PIC_OK;
+    }
+
+    void clear_forward() {
+        for (int a = 0; a < 3; a++) {
+            cudaMemset(f.E[a], 0, N * sizeof(T));
+            cudaMemset(f.H[a], 0, N * sizeof(T));
+            cudaMemset(f.J[a], 0, N * sizeof(T));
+            const size_t slab = (size_t)(N / g.n[a]) * 2 * g.L;
+            for (int s = 0; s < 2; s++) {
+                cudaMemset(f.psiH[a][s], 0, slab * sizeof(T));
+                cudaMemset(f.psiE[a][s], 0, slab * sizeof(T));
+            }
+        }
+        cudaMemset(d_F, 0, 2 * sizeof(double));
+    }
+    void clear_adjoint() {
+        for (int a = 0; a < 3; a++) {
+            cudaMemset(f.lE[a], 0, N * sizeof(T));
+            cudaMemset(f.lH[a], 0, N * sizeof(T));
+            cudaMemset(f.lJ[a], 0, N * sizeof(T));
+            const size_t slab = (size_t)(N / g.n[a]) * 2 * g.L;
+            for (int s = 0; s < 2; s++) {
+                cudaMemset(f.lpsiH[a][s], 0, slab * sizeof(T));
+                cudaMemset(f.lpsiE[a][s], 0, slab * sizeof(T));
+            }
+        }
+        cudaMemset(f.gb, 0, ne * sizeof(double));
+        cudaMemset(f.gk, 0, ne * sizeof(double));
+    }
+
+    dim3 grid3() const { return dim3((g.n[0] + 255) / 256, g.n[1], g.n[2]); }
+
+    int forward(const double *mask, double wp, double gamma, double *loss) override {
+        if (!mask || !loss) return set_last_error(PIC_ERR_ARG, "NULL argument");
+        if (!(wp >= 0.0) || !(gamma >= 0.0) || !std::isfinite(wp) || !std::isfinite(gamma))
+            return set_last_error(PIC_ERR_ARG, "need finite wp >= 0 and gamma >= 0");
+        for (long long q = 0; q < nmask; q++)
+            if (!(mask[q] >= 0.0 && mask[q] <= 1.0)) return set_last_error(PIC_ERR_ARG, "mask[%lld] outside [0, 1]", q);
+        const double dt = cfg.dt, c2 = 1.0 / (cfg.eps0 * cfg.mu0);
+        if (!(c2 * dt * dt * 3.0 / (cfg.dx * cfg.dx) + 0.25 * wp * wp * dt * dt < 1.0))
+            return set_last_error(PIC_ERR_CFL, "dt=%g violates the time-step bound with wp=%g", dt, wp);
+        g.kJm1 = (T)(-2.0 * gamma * dt / (2.0 + gamma * dt));
+        beta_h.resize(ne);
+        mbar_h.resize(ne);
+        for (long long q = 0; q < ne; q++) {
+            double m = 0.0;
+            for (int t = 0; t < 4; t++) m += cells_h[q][t] >= 0 ? mask[cells_h[q][t]] : 0.0;
+            mbar_h[q] = 0.25 * m;
+            beta_h[q] = (T)(2.0 * dt * cfg.eps0 * wp * wp * mbar_h[q] / (2.0 + gamma * dt));
+        }
+        if (ne && cudaMemcpy((void *)f.beta, beta_h.data(), ne * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+            return set_last_error(PIC_ERR_CUDA, "adjoint: bJ upload failed");
+        clear_forward();
+        const dim3 gr = grid3();
+        const unsigned ns = (unsigned)((ne + 255) / 256);
+        for (long long n = 0; n < cfg.nsteps; n++) {
+            if (ne) k_store<T><<<ns, 256>>>(f, n);
+            k_fwd_H<T><<<gr, 256>>>(g, f);
+            k_fwd_E<T><<<gr, 256>>>(g, f, bu, (n + 0.5) * dt);
+            k_probe<T><<<1, 32>>>(f, pr, (n + 1) * dt, d_F);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpy(F, d_F, 2 * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return set_last_error(PIC_ERR_CUDA, "adjoint forward: %s", cudaGetErrorString(e));
+        *loss = F[0] * F[0] + F[1] * F[1];
+        wp_last = wp;
+        gamma_last = gamma;
+        have_forward = true;
+        return PIC_OK;
+    }
+
+    int backward(double *dmask, double *dwp, double *dgamma) override {
+        if (!have_forward) return set_last_error(PIC_ERR_STATE, "pic_adj_backward needs a forward run first");
+        if (!dmask || !dwp || !dgamma) return set_last_error(PIC_ERR_ARG, "NULL argument");
+        clear_adjoint();
+        const dim3 gr = grid3();
+        for (long long n = cfg.nsteps - 1; n >= 0; n--) {
+            k_src<T><<<1, 32>>>(f, pr, (n + 1) * cfg.dt, d_F);
+            k_adj_E<T><<<gr, 256>>>(g, f, n);
+            k_adj_H<T><<<gr, 256>>>(g, f);
+        }
+        std::vector<double> gb(ne), gk(ne);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess && ne) e = cudaMemcpy(gb.data(), f.gb, ne * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && ne) e = cudaMemcpy(gk.data(), f.gk, ne * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return set_last_error(PIC_ERR_CUDA, "adjoint backward: %s", cudaGetErrorString(e));
+        // chain rule: bJ = 2 dt eps0 wp^2 mbar / (2 + gamma dt), kJ = (2 - gamma dt) / (2 + gamma dt)
+        const double dt = cfg.dt, wp = wp_last, ga = gamma_last, den = 2.0 + ga * dt;
+        const double dbeta_dm = 2.0 * dt * cfg.eps0 * wp * wp * 0.25 / den;  // per cell of the four
+        const double dkJ_dga = -4.0 * dt / (den * den);
+        for (long long q = 0; q < nmask; q++) dmask[q] = 0.0;
+        double gwp = 0.0, gga = 0.0;
+        for (long long q = 0; q < ne; q++) {
+            for (int t = 0; t < 4; t++)
+                if (cells_h[q][t] >= 0) dmask[cells_h[q][t]] += gb[q] * dbeta_dm;
+            const double beta = 2.0 * dt * cfg.eps0 * wp * wp * mbar_h[q] / den;
+            gwp += gb[q] * 2.0 * dt * cfg.eps0 * 2.0 * wp * mbar_h[q] / den;
+            gga += gb[q] * (-beta * dt / den) + gk[q] * dkJ_dga;
+        }
+        *dwp = gwp;
+        *dgamma = gga;
+        return PIC_OK;
+    }
+};
+
+}  // namespace
+}  // namespace pic
+
+struct pic_adj {
+    pic::AdjBase *sim;
+};
+
+extern "C" {
+
+int pic_adj_create(const pic_adj_config *c, pic_adj **out) {
+    using namespace pic;
+    set_last_error(PIC_OK, "%s", "");
+    if (!out) return set_last_error(PIC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!c) return set_last_error(PIC_ERR_ARG, "config is NULL");
+    if (c->precision != PIC_FP32 && c->precision != PIC_FP64) return set_last_error(PIC_ERR_ARG, "unknown precision");
+    const int64_t n[3] = {c->nx, c->ny, c->nz};
+    for (int a = 0; a < 3; a++)
+        if (n[a] < 2 * (int64_t)c->cpml_cells + 4 || n[a] > 65535)
+            return set_last_error(PIC_ERR_ARG, "axis %d: %lld cells do not hold two CPML slabs", a, (long long)n[a]);
+    if (c->cpml_cells < 1) return set_last_error(PIC_ERR_ARG, "cpml_cells must be >= 1");
+    if (!(c->dx > 0.0) || !(c->dt > 0.0) || !(c->eps0 > 0.0) || !(c->mu0 > 0.0))
+        return set_last_error(PIC_ERR_ARG, "dx, dt, eps0, mu0 must be > 0");
+    if (1.0 / (c->eps0 * c->mu0) * c->dt * c->dt * 3.0 / (c->dx * c->dx) >= 1.0)
+        return set_last_error(PIC_ERR_CFL, "dt=%g violates the vacuum time-step bound", c->dt);
+    if (c->design_k0 < 1 || c->design_k1 <= c->design_k0 || c->design_k1 > c->nz - 1)
+        return set_last_error(PIC_ERR_ARG, "design slab [%lld, %lld) must lie inside the grid",
+                              (long long)c->design_k0, (long long)c->design_k1);
+    if (c->nsteps < 1) return set_last_error(PIC_ERR_ARG, "nsteps must be >= 1");
+    if (c->probe_comp < 0 || c->probe_comp > 2) return set_last_error(PIC_ERR_ARG, "probe_comp must be 0..2");
+    for (int a = 0; a < 3; a++) {
+        const double xi = c->probe[a] / c->dx;
+        if (!(xi >= 1.0 && xi < n[a] - 1.0)) return set_last_error(PIC_ERR_ARG, "probe outside the grid interior");
+    }
+    if (!(c->bunch_sigma > 0.0)) return set_last_error(PIC_ERR_ARG, "bunch_sigma must be > 0");
+    pic_adj *h = new pic_adj{nullptr};
+    int rc;
+    if (c->precision == PIC_FP64) {
+        auto *s = new AdjSim<double>();
+        h->sim = s;
+        rc = s->create(c);
+    } else {
+        auto *s = new AdjSim<float>();
+        h->sim = s;
+        rc = s->create(c);
+    }
+    if (rc) {
+        delete h->sim;
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return PIC_OK;
+}
+
+int pic_adj_mask_size(const pic_adj *a, int64_t *n) {
+    pic::set_last_error(PIC_OK, "%s", "");
+    if (!a || !n) return pic::set_last_error(PIC_ERR_ARG, "NULL argument");
+    *n = a->sim->nmask;
+    return PIC_OK;
+}
+
+int pic_adj_forward(pic_adj *a, const double *mask, double wp, double gamma, double *loss) {
+    pic::set_last_error(PIC_OK, "%s", "");
+    if (!a) return pic::set_last_error(PIC_ERR_ARG, "NULL handle");
+    return a->sim->forward(mask, wp, gamma, loss);
+}
+
+int pic_adj_backward(pic_adj *a, double *dmask, double *dwp, double *dgamma) {
+    pic::set_last_error(PIC_OK, "%s", "");
+    if (!a) return pic::set_last_error(PIC_ERR_ARG, "NULL handle");
+    return a->sim->backward(dmask, dwp, dgamma);
+}
+
+int pic_adj_destroy(pic_adj *a) {
+    pic::set_last_error(PIC_OK, "%s", "");
+    if (!a) return PIC_OK;
+    delete a->sim;
+    delete a;
+    return PIC_OK;
+}
+
+}  // extern "C"

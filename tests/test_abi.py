@@ -79,3 +79,35 @@ def test_cfl_bound_includes_drude_term():
     cfg.materials = tab
     h = C.c_void_p()
     assert P.load().pic_create(C.byref(cfg), C.byref(h)) == -2
+
+
+def test_adjoint_header_matches_binding_and_library():
+    from paper_1505_04007_gb300 import adjoint as A
+    src = open(os.path.join(ROOT, "include", "pic_adjoint.h")).read()
+    declared = sorted(set(re.findall(r"^\s*int\s*(pic_\w+)\s*\(", src, re.M)))
+    assert declared == sorted(A.ADJ_EXPORTS)
+    L = A.load()
+    for name in declared:
+        assert hasattr(L, name), name
+
+
+ERR_ARG, ERR_CFL = -1, -2  # PIC_ERR_ARG, PIC_ERR_CFL of include/pic.h
+
+
+@pytest.mark.parametrize("field, value, code", [
+    ("nsteps", 0, ERR_ARG),
+    ("design_k1", 5, ERR_ARG),          # slab of no planes
+    ("probe_comp", 3, ERR_ARG),
+    ("cpml_cells", 30, ERR_ARG),        # two slabs do not fit
+    ("dt", 1e-16, ERR_CFL),
+])
+def test_adjoint_create_rejects_invalid_config_on_host(field, value, code):
+    from paper_1505_04007_gb300 import adjoint as A
+    cfg = A.film_config(nx=48, ny=24, nz=40, design=(10, 16), nsteps=10)
+    if field == "design_k1":
+        cfg.design_k0 = 5
+    setattr(cfg, field, value)
+    out = C.c_void_p()
+    assert A.load().pic_adj_create(C.byref(cfg), C.byref(out)) == code
+    assert out.value is None
+

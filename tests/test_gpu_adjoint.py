@@ -1,0 +1,93 @@
+"""Adjoint gradients (include/pic_adjoint.h) against central finite
+differences of the forward model, in FP64 on the GPU.
+
+A small film study (48x24x40 cells, 6-plane design slab, 400 steps, a 40 keV
+rigid bunch, Ez probe at wp/sqrt(2)) with a seeded mask in [0.2, 0.8]:
+the mask gradient at 8 cells (drawn from the 200 with the largest gradient),
+d/dwp and d/dgamma each agree with central differences at a relative step of
+1e-4 to 1e-5 of the largest mask gradient (mask) or of the derivative itself
+(wp, gamma).  The FP32 path's gradient is compared with the FP64 one, and the
+torch.autograd wrapper with the direct call.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+WP, GAMMA = 1.2e16, 1.45e13
+
+
+@pytest.fixture(scope="module")
+def A():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    from paper_1505_04007_gb300 import adjoint
+    adjoint.load()
+    return adjoint
+
+
+def small(A, precision):
+    from paper_1505_04007_gb300 import pic
+    prec = pic.PIC_FP64 if precision == "fp64" else pic.PIC_FP32
+    return A.Adjoint(A.film_config(nx=48, ny=24, nz=40, design=(10, 16), nsteps=400, sigma=4e-9, cpml=6,
+                                   precision=prec))
+
+
+@pytest.fixture(scope="module")
+def fp64_grad(A):
+    st = small(A, "fp64")
+    mask = np.random.default_rng(7).uniform(0.2, 0.8, st.n)
+    loss = st.forward(mask, WP, GAMMA)
+    dm, dwp, dga = st.backward()
+    return st, mask, loss, dm, dwp, dga
+
+
+def test_mask_gradient_matches_central_differences(fp64_grad):
+    st, mask, loss, dm, _, _ = fp64_grad
+    assert loss > 0 and np.isfinite(dm).all()
+    rng = np.random.default_rng(11)
+    cells = rng.choice(np.argsort(-np.abs(dm))[:200], 8, replace=False)
+    for c in cells:
+        h = 1e-4 * mask[c]
+        mp, mm = mask.copy(), mask.copy()
+        mp[c] += h
+        mm[c] -= h
+        fd = (st.forward(mp, WP, GAMMA) - st.forward(mm, WP, GAMMA)) / (2 * h)
+        assert abs(fd - dm[c]) <= 1e-5 * np.abs(dm).max(), (c, fd, dm[c])
+
+
+def test_wp_and_gamma_gradients_match_central_differences(fp64_grad):
+    st, mask, loss, _, dwp, dga = fp64_grad
+    for val, grad, f in ((WP, dwp, lambda v: st.forward(mask, v, GAMMA)),
+                         (GAMMA, dga, lambda v: st.forward(mask, WP, v))):
+        h = 1e-4 * val
+        fd = (f(val + h) - f(val - h)) / (2 * h)
+        assert abs(fd - grad) <= 1e-5 * abs(grad), (fd, grad)
+
+
+def test_fp32_gradient_close_to_fp64(A, fp64_grad):
+    _, mask, loss64, dm64, dwp64, dga64 = fp64_grad
+    st = small(A, "fp32")
+    loss = st.forward(mask, WP, GAMMA)
+    dm, dwp, dga = st.backward()
+    st.close()
+    assert abs(loss / loss64 - 1) <= 1e-4
+    assert np.linalg.norm(dm - dm64) <= 1e-3 * np.linalg.norm(dm64)
+    assert abs(dwp / dwp64 - 1) <= 1e-3 and abs(dga / dga64 - 1) <= 1e-3
+
+
+def test_autograd_wrapper(A, fp64_grad):
+    import torch
+    st, mask, loss, dm, dwp, dga = fp64_grad
+    f = A.plasmon_loss(st)
+    m = torch.tensor(mask, dtype=torch.float64, requires_grad=True)
+    w = torch.tensor(WP, dtype=torch.float64, requires_grad=True)
+    g = torch.tensor(GAMMA, dtype=torch.float64, requires_grad=True)
+    out = f(m, w, g)
+    (3.0 * out).backward()
+    # a second forward/backward: equal up to the order of the atomic sums
+    assert float(out.detach()) == pytest.approx(loss, rel=1e-12)
+    assert np.abs(m.grad.numpy() - 3.0 * dm).max() <= 1e-9 * 3.0 * np.abs(dm).max()
+    assert float(w.grad) == pytest.approx(3.0 * dwp, rel=1e-9)
+    assert float(g.grad) == pytest.approx(3.0 * dga, rel=1e-9)
