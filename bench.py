@@ -153,9 +153,9 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def traffic_for(kernel):
+def traffic_for(kernel, workload):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source; else None."""
+    on the current kernel source and on this workload; else None."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
@@ -165,7 +165,7 @@ def traffic_for(kernel):
         src = os.path.join(ROOT, "paper_1505_04007_gb300", "csrc", d["source"])
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         k = d["kernels"].get(kernel)
-        if k is None or d.get("source_sha") != sha:
+        if k is None or d.get("source_sha") != sha or d.get("workload_key") != workload:
             return None
         return float(k["dram_bytes_per_launch_full"])
     except Exception:
@@ -391,7 +391,7 @@ def main():
     achieved = ab[dom] / (prof[dom] * 1e-6) / 1e9
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": f"{peak_kind} copy bandwidth",
-            "traffic": traffic_for(dom), "algorithmic_bytes_per_launch": ab[dom],
+            "traffic": traffic_for(dom, args.workload), "algorithmic_bytes_per_launch": ab[dom],
             "kernel_us": {k: round(v, 3) for k, v in prof.items()}}
     sim.close()
 
