@@ -191,6 +191,8 @@ __global__ void __launch_bounds__(256) k_update_E(Grid<T> g, Fields<T> f) {
 // cell of a TILE_X x TILE_Y x TILE_Z tile; blocks stride over the list.
 template <typename T>
 __global__ void __launch_bounds__(TILE_X *TILE_Y *TILE_Z) k_jf_apply(Grid<T> g, Fields<T> f) {
+    pdl_wait();
+    pdl_release();
     const int count = *f.jf_count;
     const int i0 = threadIdx.x % TILE_X, j0 = (threadIdx.x / TILE_X) % TILE_Y, k0 = threadIdx.x / (TILE_X * TILE_Y);
     for (int q = blockIdx.x; q < count; q += gridDim.x) {
@@ -257,7 +259,7 @@ template <typename T>
 void launch_jf_apply(const Grid<T> &g, const Fields<T> &f, int max_tiles, cudaStream_t s) {
     int nblk = max_tiles < 4 * 152 ? max_tiles : 4 * 152;
     if (nblk < 1) nblk = 1;
-    k_jf_apply<T><<<nblk, TILE_X * TILE_Y * TILE_Z, 0, s>>>(g, f);
+    launch_pdl(k_jf_apply<T>, dim3(nblk), dim3(TILE_X * TILE_Y * TILE_Z), 0, s, g, f);
     launch_count() += 1;
 }
 

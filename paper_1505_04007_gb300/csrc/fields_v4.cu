@@ -350,6 +350,8 @@ __device__ __forceinline__ bool list_cell(const BoxList &bl, long long q, int &b
 }
 
 #define BOX_CELL(bl)                                                                                   \
+    pdl_wait();                                                                                        \
+    pdl_release();                                                                                     \
     int bi, i0, j, k;                                                                                  \
     if (!list_cell((bl), blockIdx.x * (long long)blockDim.x + threadIdx.x, bi, i0, j, k)) return;      \
     const Box &b = (bl).b[bi];                                                                         \
@@ -393,7 +395,7 @@ void launch_list(K kernel, const Grid<float> &g, const Fields<float> &f, const B
     const int blk = 256;
     const long long total = bl.first[bl.n];
     if (total > 0) {
-        kernel<<<(unsigned)((total + blk - 1) / blk), blk, 0, s>>>(g, f, bl);
+        launch_pdl(kernel, dim3((unsigned)((total + blk - 1) / blk)), dim3(blk), 0, s, g, f, bl);
         launch_count() += 1;
     }
 }

@@ -160,6 +160,31 @@ __device__ __forceinline__ void mark_jf_tile(int *flag, int *list, int *count, l
     if (flag[t] != v && atomicExch(&flag[t], v) != v) list[atomicAdd(count, 1)] = (int)t;
 }
 
+// Programmatic dependent launch: a kernel launched with launch_pdl may be
+// scheduled while the kernel before it in the stream is still finishing.
+// pdl_wait() blocks until that kernel has completed and its writes are
+// visible (a no-op for a kernel launched normally), so it comes before any
+// global memory access; pdl_release() then lets the next such kernel be
+// scheduled early in turn (it still waits for this one to complete).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // ---------------------------------------------------------------- launchers
 // Field updates; with a plan (FP32) the four-cells-per-thread kernels run,
 // otherwise the one-cell-per-thread kernels of fields.cu.

@@ -62,6 +62,8 @@ void launch_sources(const Grid<T> &g, const Fields<T> &f, const Source *src, int
 // advances the step counter once every sample of step n is written.
 template <typename T>
 __global__ void __launch_bounds__(1024) k_step_tail(Grid<T> g, Fields<T> f, Probes<T> pr, long long *step) {
+    pdl_wait();
+    pdl_release();
     const long long n = *step;
     const int slot = (int)(n % DFT_BLOCK);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -87,7 +89,7 @@ template <typename T>
 void launch_step_tail(const Grid<T> &g, const Fields<T> &f, const Probes<T> &pr, long long *step, cudaStream_t s) {
     int blk = 32 * pr.np;
     blk = blk < 32 ? 32 : (blk > 1024 ? 1024 : blk);
-    k_step_tail<T><<<1, blk, 0, s>>>(g, f, pr, step);
+    launch_pdl(k_step_tail<T>, dim3(1), dim3(blk), 0, s, g, f, pr, step);
     launch_count() += 1;
 }
 
