@@ -48,15 +48,34 @@ def refine(freqs, power, m: int) -> float:
     return float(freqs[m])
 
 
-def peak_in(freqs, power, band) -> float:
-    """Refined frequency of the largest sample inside band = (f_lo, f_hi)."""
+SMOOTH_HZ = 4e12  # about half the 1/T resolution of a 65 536-step (126 fs) record
+
+
+def smooth(freqs, power, width_hz: float = SMOOTH_HZ):
+    """power convolved with a normalised Gaussian of rms width width_hz: a
+    record of length T resolves lines only to ~1/T, and the side lobes of a
+    line cut off by the end of the record can outgrow its centre sample."""
+    if width_hz <= 0:
+        return np.asarray(power, np.float64)
+    s = width_hz / (freqs[1] - freqs[0])
+    half = int(4 * s) + 1
+    x = np.arange(-half, half + 1)
+    k = np.exp(-0.5 * (x / s) ** 2)
+    return np.convolve(np.asarray(power, np.float64), k / k.sum(), mode="same")
+
+
+def peak_in(freqs, power, band, width_hz: float = SMOOTH_HZ) -> float:
+    """Refined frequency of the largest sample of the smoothed power inside
+    band = (f_lo, f_hi)."""
+    p = smooth(freqs, power, width_hz)
     idx = np.nonzero((freqs >= band[0]) & (freqs <= band[1]))[0]
-    return refine(freqs, power, int(idx[np.argmax(power[idx])]))
+    return refine(freqs, p, int(idx[np.argmax(p[idx])]))
 
 
-def top_peaks(freqs, power, n: int = 2) -> list:
-    """The n largest local maxima, refined, in increasing frequency."""
-    p = np.asarray(power)
+def top_peaks(freqs, power, n: int = 2, width_hz: float = SMOOTH_HZ) -> list:
+    """The n largest local maxima of the smoothed power, refined, in
+    increasing frequency."""
+    p = smooth(freqs, power, width_hz)
     lm = [i for i in range(1, len(p) - 1) if p[i] > p[i - 1] and p[i] >= p[i + 1]]
     lm = sorted(lm, key=lambda i: -p[i])[:n]
     return sorted(refine(freqs, p, i) for i in lm)
