@@ -197,9 +197,9 @@ def bench_sweep(args):
     from paper_1505_04007_gb300 import pic
     from paper_1505_04007_gb300 import workloads as W
     torch.cuda.set_device(0)
-    steps = max(64, args.steps // 64 * 64)
-    warm = max(64, args.warmup // 64 * 64)
     ws = W.sweep()
+    steps = max(64, min(args.steps, ws[0].nsteps) // 64 * 64)  # whole 64-step blocks of the 4000-step sweep
+    warm = max(64, args.warmup // 64 * 64)
     cells = sum(w.ncells for w in ws)
     sims = [pic.Simulation(w, pic.PIC_FP32) for w in ws]
     b = pic.Batch(sims)

@@ -142,8 +142,9 @@ struct Sim : SimBase {
     cudaEvent_t ev_bfork = nullptr, ev_bjoin = nullptr;  // joins to a batch capture
     long long epoch = 0;          // bumped by drop_graph
     cudaStream_t aux = nullptr;   // field updates over the absorbing slabs, beside the interior ones
+    cudaStream_t aux2 = nullptr, aux3 = nullptr;  // E over material planes (interior, slabs)
     cudaEvent_t ev_fork = nullptr, ev_gathered = nullptr, ev_h = nullptr, ev_join = nullptr;
-    cudaEvent_t ev_hf = nullptr, ev_hj = nullptr, ev_ef = nullptr, ev_ej = nullptr;
+    cudaEvent_t ev_hf = nullptr, ev_hj = nullptr, ev_ef = nullptr, ev_ej = nullptr, ev_ej2 = nullptr, ev_ej3 = nullptr;
     void *arena = nullptr;
     bool own_arena = false;
     size_t arena_bytes = 0;
@@ -401,7 +402,9 @@ struct Sim : SimBase {
             CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
             CUDA_TRY(cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, greatest));
             CUDA_TRY(cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking));
-            for (cudaEvent_t *e : {&ev_fork, &ev_gathered, &ev_h, &ev_join, &ev_hf, &ev_hj, &ev_ef, &ev_ej, &ev_bfork,
+            CUDA_TRY(cudaStreamCreateWithFlags(&aux2, cudaStreamNonBlocking));
+            CUDA_TRY(cudaStreamCreateWithFlags(&aux3, cudaStreamNonBlocking));
+            for (cudaEvent_t *e : {&ev_fork, &ev_gathered, &ev_h, &ev_join, &ev_hf, &ev_hj, &ev_ef, &ev_ej, &ev_ej2, &ev_ej3, &ev_bfork,
                                    &ev_bjoin})
                 CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
         }
@@ -490,12 +493,14 @@ struct Sim : SimBase {
         if (stream) cudaStreamSynchronize(stream);
         drop_graph();
         if (side) cudaStreamSynchronize(side);
-        if (aux) cudaStreamSynchronize(aux);
+        for (cudaStream_t x : {aux, aux2, aux3})
+            if (x) cudaStreamSynchronize(x);
         if (own_arena && arena) cudaFree(arena);
         if (own_stream && stream) cudaStreamDestroy(stream);
         if (side) cudaStreamDestroy(side);
-        if (aux) cudaStreamDestroy(aux);
-        for (cudaEvent_t e : {ev_fork, ev_gathered, ev_h, ev_join, ev_hf, ev_hj, ev_ef, ev_ej, ev_bfork, ev_bjoin})
+        for (cudaStream_t x : {aux, aux2, aux3})
+            if (x) cudaStreamDestroy(x);
+        for (cudaEvent_t e : {ev_fork, ev_gathered, ev_h, ev_join, ev_hf, ev_hj, ev_ef, ev_ej, ev_ej2, ev_ej3, ev_bfork, ev_bjoin})
             if (e) cudaEventDestroy(e);
     }
 
@@ -586,9 +591,17 @@ struct Sim : SimBase {
             if (pe) cudaEventRecord(pe[3], stream);
         }
         if (pe) cudaEventRecord(pe[4], stream);
-        if (split) fork_join(stream, aux, ev_ef);
-        launch_update_E<T>(g, f, use_plan ? &fplan : nullptr, stream, split ? aux : stream);
-        if (split) fork_join(aux, stream, ev_ej);
+        if (split) {  // the four E pieces write disjoint cells: each on its own stream
+            cudaEventRecord(ev_ef, stream);
+            for (cudaStream_t x : {aux, aux2, aux3}) cudaStreamWaitEvent(x, ev_ef, 0);
+        }
+        launch_update_E<T>(g, f, use_plan ? &fplan : nullptr, stream, split ? aux : stream, split ? aux2 : stream,
+                           split ? aux3 : stream);
+        if (split) {
+            fork_join(aux, stream, ev_ej);
+            fork_join(aux2, stream, ev_ej2);
+            fork_join(aux3, stream, ev_ej3);
+        }
         if (pe) cudaEventRecord(pe[5], stream);
         if (fork) cudaStreamWaitEvent(stream, ev_join, 0);
         launch_jf_apply<T>(g, f, (int)n_tiles, stream);

@@ -224,7 +224,8 @@ void launch_update_H(const Grid<T> &g, const Fields<T> &f, const FieldPlan *, cu
 }
 
 template <typename T>
-void launch_update_E(const Grid<T> &g, const Fields<T> &f, const FieldPlan *, cudaStream_t s, cudaStream_t) {
+void launch_update_E(const Grid<T> &g, const Fields<T> &f, const FieldPlan *, cudaStream_t s, cudaStream_t,
+                     cudaStream_t, cudaStream_t) {
     dim3 blk(32, 4, 2);
     k_update_E<T><<<field_grid(g.n, blk), blk, 0, s>>>(g, f);
     launch_count() += 1;
@@ -245,10 +246,10 @@ void launch_update_H<float>(const Grid<float> &g, const Fields<float> &f, const 
 
 template <>
 void launch_update_E<float>(const Grid<float> &g, const Fields<float> &f, const FieldPlan *plan, cudaStream_t s,
-                            cudaStream_t s2) {
+                            cudaStream_t s2, cudaStream_t s3, cudaStream_t s4) {
     dim3 blk(32, 4, 2);
     if (plan) {
-        launch_v4_E(g, f, *plan, s, s2);
+        launch_v4_E(g, f, *plan, s, s2, s3, s4);
     } else {
         k_update_E<float><<<field_grid(g.n, blk), blk, 0, s>>>(g, f);
         launch_count() += 1;
@@ -266,7 +267,7 @@ void launch_jf_apply(const Grid<T> &g, const Fields<T> &f, int max_tiles, cudaSt
 template void launch_update_H<double>(const Grid<double> &, const Fields<double> &, const FieldPlan *, cudaStream_t,
                                       cudaStream_t);
 template void launch_update_E<double>(const Grid<double> &, const Fields<double> &, const FieldPlan *, cudaStream_t,
-                                      cudaStream_t);
+                                      cudaStream_t, cudaStream_t, cudaStream_t);
 
 template void launch_jf_apply<float>(const Grid<float> &, const Fields<float> &, int, cudaStream_t);
 template void launch_jf_apply<double>(const Grid<double> &, const Fields<double> &, int, cudaStream_t);

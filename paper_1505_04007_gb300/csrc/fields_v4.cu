@@ -461,11 +461,12 @@ void launch_v4_H(const Grid<float> &g, const Fields<float> &f, const FieldPlan &
     launch_list(k_H4_bulk, g, f, plan.bulk, s);
 }
 
-void launch_v4_E(const Grid<float> &g, const Fields<float> &f, const FieldPlan &plan, cudaStream_t s, cudaStream_t s2) {
+void launch_v4_E(const Grid<float> &g, const Fields<float> &f, const FieldPlan &plan, cudaStream_t s, cudaStream_t s2,
+                 cudaStream_t s3, cudaStream_t s4) {
     launch_list(k_E4_cpml_vac, g, f, plan.fvac, s2);
-    launch_list(k_E4_cpml_mat, g, f, plan.fmat, s2);
+    launch_list(k_E4_cpml_mat, g, f, plan.fmat, s4);
     launch_list(k_E4_vac, g, f, plan.vac, s);
-    launch_list(k_E4_mat, g, f, plan.mat, s);
+    launch_list(k_E4_mat, g, f, plan.mat, s3);
 }
 
 }  // namespace pic

@@ -145,7 +145,9 @@ struct FieldPlan {
 // FP32 four-cells-per-thread field kernels (nx % 4 == 0), fields_v4.cu
 // bulk/interior boxes on s, boxes over the absorbing slabs on s2 (may be s)
 void launch_v4_H(const Grid<float> &g, const Fields<float> &f, const FieldPlan &plan, cudaStream_t s, cudaStream_t s2);
-void launch_v4_E(const Grid<float> &g, const Fields<float> &f, const FieldPlan &plan, cudaStream_t s, cudaStream_t s2);
+// E: vacuum interior on s, absorbing-slab vacuum on s2, material interior on s3, absorbing-slab material on s4
+void launch_v4_E(const Grid<float> &g, const Fields<float> &f, const FieldPlan &plan, cudaStream_t s, cudaStream_t s2,
+                 cudaStream_t s3, cudaStream_t s4);
 // plane_cls[k]: the class all edges of plane k share if it is non-metal, else
 // 255.  Returns false when the grid does not suit these kernels.
 bool make_field_plan(const Grid<float> &g, const uint8_t *plane_cls, const float *cls_cE, FieldPlan &p);
@@ -191,7 +193,8 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 template <typename T>
 void launch_update_H(const Grid<T> &g, const Fields<T> &f, const FieldPlan *plan, cudaStream_t s, cudaStream_t s2);
 template <typename T>
-void launch_update_E(const Grid<T> &g, const Fields<T> &f, const FieldPlan *plan, cudaStream_t s, cudaStream_t s2);
+void launch_update_E(const Grid<T> &g, const Fields<T> &f, const FieldPlan *plan, cudaStream_t s, cudaStream_t s2,
+                     cudaStream_t s3, cudaStream_t s4);
 template <typename T>
 void launch_gather_E(const Grid<T> &g, const Fields<T> &f, const Particles<T> &p, cudaStream_t s);
 template <typename T>
