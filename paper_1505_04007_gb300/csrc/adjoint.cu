@@ -50,6 +50,7 @@ struct AState {
     const T *beta;               // per slot: bJ
     T *stE, *stJ;                // per step and slot: E^n, J^n
     double *gb, *gk;             // per slot: dL/dbJ, dL/dkJ contributions
+    long long *n;                // device step counter (forward: next step; backward: steps left)
 };
 
 struct Bunch {
@@ -140,7 +141,8 @@ __device__ __forceinline__ void fwd_ampere(const AGrid<T> &g, const AState<T> &f
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_fwd_E(AGrid<T> g, AState<T> f, Bunch bu, double t_half) {
+__global__ void __launch_bounds__(256) k_fwd_E(AGrid<T> g, AState<T> f, Bunch bu, double dt) {
+    const double t_half = (*f.n + 0.5) * dt;
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     if (i >= nx) return;
@@ -198,7 +200,8 @@ __global__ void __launch_bounds__(256) k_fwd_E(AGrid<T> g, AState<T> f, Bunch bu
 
 // E^n and J^n of every design edge into storage row n
 template <typename T>
-__global__ void k_store(AState<T> f, long long n) {
+__global__ void k_store(AState<T> f) {
+    const long long n = *f.n;
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long ne = f.soff[3];
     if (q >= ne) return;
@@ -208,10 +211,13 @@ __global__ void k_store(AState<T> f, long long n) {
     f.stJ[n * ne + q] = f.J[c][e];
 }
 
-// F += E_c(x_p, t) exp(+i omega t) dt
+// F += E_c(x_p, t) exp(+i omega t) dt at t = (n+1) dt, then n += 1
 template <typename T>
-__global__ void k_probe(AState<T> f, Probe p, double t, double *F) {
+__global__ void k_probe(AState<T> f, Probe p, double *F) {
     if (threadIdx.x != 0) return;
+    const long long n = *f.n;
+    const double t = (n + 1) * p.dt;
+    *f.n = n + 1;
     double v = 0.0;
     for (int q = 0; q < 8; q++) v += p.w[q] * (double)f.E[p.comp][p.idx[q]];
     double sn, cs;
@@ -221,10 +227,14 @@ __global__ void k_probe(AState<T> f, Probe p, double t, double *F) {
 }
 
 // ----------------------------------------------------------- backward --
-// adjoint of the probe term at time t: dL/dE = 2 Re(conj(F) e^{i omega t}) dt w
+// Start of backward step n (n = steps left - 1, then stored as the counter):
+// adjoint of the probe term at t = (n+1) dt, dL/dE = 2 Re(conj(F) e^{i omega t}) dt w
 template <typename T>
-__global__ void k_src(AState<T> f, Probe p, double t, const double *F) {
+__global__ void k_src(AState<T> f, Probe p, const double *F) {
     if (threadIdx.x != 0) return;
+    const long long n = *f.n - 1;
+    *f.n = n;
+    const double t = (n + 1) * p.dt;
     double sn, cs;
     sincos(p.omega * t, &sn, &cs);
     const double s = 2.0 * p.dt * (F[0] * cs + F[1] * sn);
@@ -248,7 +258,8 @@ __device__ __forceinline__ void adj_ampere(const AGrid<T> &g, const AState<T> &f
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_adj_E(AGrid<T> g, AState<T> f, long long n) {
+__global__ void __launch_bounds__(256) k_adj_E(AGrid<T> g, AState<T> f) {
+    const long long n = *f.n;
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     if (i >= nx) return;
@@ -394,12 +405,18 @@ struct AdjSim : AdjBase {
     std::vector<std::array<long long, 4>> cells_h;  // per slot: its four cells as mask indices (-1: outside)
     double *d_F = nullptr;
     double F[2] = {0, 0};
+    cudaStream_t stream = nullptr;
+    static constexpr int GRAPH_STEPS = 64;  // steps per captured graph (forward and backward)
+    cudaGraphExec_t gfwd = nullptr, gbwd = nullptr;
     double wp_last = 0, gamma_last = 0;
     bool have_forward = false;
 
     ~AdjSim() override {
-        cudaDeviceSynchronize();
+        if (stream) cudaStreamSynchronize(stream);
+        if (gfwd) cudaGraphExecDestroy(gfwd);
+        if (gbwd) cudaGraphExecDestroy(gbwd);
         for (void *p : allocs) cudaFree(p);
+        if (stream) cudaStreamDestroy(stream);
     }
 
     template <typename P>
@@ -515,7 +532,10 @@ struct AdjSim : AdjBase {
         rc = rc ? rc : take(&f.stE, (size_t)ne * c->nsteps + 1);
         rc = rc ? rc : take(&f.stJ, (size_t)ne * c->nsteps + 1);
         rc = rc ? rc : take(&d_F, 2);
+        rc = rc ? rc : take(&f.n, 1);
         if (rc) return rc;
+        if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess)
+            return set_last_error(PIC_ERR_CUDA, "adjoint: stream creation failed");
         for (int a = 0; a < 3; a++) {
             std::vector<T> pf[6];
             for (auto &v : pf) v.resize(g.n[a]);
@@ -570,33 +590,81 @@ struct AdjSim : AdjBase {
 
     void clear_forward() {
         for (int a = 0; a < 3; a++) {
-            cudaMemset(f.E[a], 0, N * sizeof(T));
-            cudaMemset(f.H[a], 0, N * sizeof(T));
-            cudaMemset(f.J[a], 0, N * sizeof(T));
+            cudaMemsetAsync(f.E[a], 0, N * sizeof(T), stream);
+            cudaMemsetAsync(f.H[a], 0, N * sizeof(T), stream);
+            cudaMemsetAsync(f.J[a], 0, N * sizeof(T), stream);
             const size_t slab = (size_t)(N / g.n[a]) * 2 * g.L;
             for (int s = 0; s < 2; s++) {
-                cudaMemset(f.psiH[a][s], 0, slab * sizeof(T));
-                cudaMemset(f.psiE[a][s], 0, slab * sizeof(T));
+                cudaMemsetAsync(f.psiH[a][s], 0, slab * sizeof(T), stream);
+                cudaMemsetAsync(f.psiE[a][s], 0, slab * sizeof(T), stream);
             }
         }
-        cudaMemset(d_F, 0, 2 * sizeof(double));
+        cudaMemsetAsync(d_F, 0, 2 * sizeof(double), stream);
+        cudaMemsetAsync(f.n, 0, sizeof(long long), stream);
     }
     void clear_adjoint() {
         for (int a = 0; a < 3; a++) {
-            cudaMemset(f.lE[a], 0, N * sizeof(T));
-            cudaMemset(f.lH[a], 0, N * sizeof(T));
-            cudaMemset(f.lJ[a], 0, N * sizeof(T));
+            cudaMemsetAsync(f.lE[a], 0, N * sizeof(T), stream);
+            cudaMemsetAsync(f.lH[a], 0, N * sizeof(T), stream);
+            cudaMemsetAsync(f.lJ[a], 0, N * sizeof(T), stream);
             const size_t slab = (size_t)(N / g.n[a]) * 2 * g.L;
             for (int s = 0; s < 2; s++) {
-                cudaMemset(f.lpsiH[a][s], 0, slab * sizeof(T));
-                cudaMemset(f.lpsiE[a][s], 0, slab * sizeof(T));
+                cudaMemsetAsync(f.lpsiH[a][s], 0, slab * sizeof(T), stream);
+                cudaMemsetAsync(f.lpsiE[a][s], 0, slab * sizeof(T), stream);
             }
         }
-        cudaMemset(f.gb, 0, ne * sizeof(double));
-        cudaMemset(f.gk, 0, ne * sizeof(double));
+        cudaMemsetAsync(f.gb, 0, ne * sizeof(double), stream);
+        cudaMemsetAsync(f.gk, 0, ne * sizeof(double), stream);
     }
 
     dim3 grid3() const { return dim3((g.n[0] + 255) / 256, g.n[1], g.n[2]); }
+
+    T kJm1_captured = T(0);
+    void drop_graphs() {
+        if (gfwd) cudaGraphExecDestroy(gfwd);
+        if (gbwd) cudaGraphExecDestroy(gbwd);
+        gfwd = gbwd = nullptr;
+    }
+    void launch_forward_steps(int count) {
+        const dim3 gr = grid3();
+        const unsigned ns = (unsigned)((ne + 255) / 256);
+        for (int q = 0; q < count; q++) {
+            if (ne) k_store<T><<<ns, 256, 0, stream>>>(f);
+            k_fwd_H<T><<<gr, 256, 0, stream>>>(g, f);
+            k_fwd_E<T><<<gr, 256, 0, stream>>>(g, f, bu, cfg.dt);
+            k_probe<T><<<1, 32, 0, stream>>>(f, pr, d_F);
+        }
+    }
+    void launch_backward_steps(int count) {
+        const dim3 gr = grid3();
+        for (int q = 0; q < count; q++) {
+            k_src<T><<<1, 32, 0, stream>>>(f, pr, d_F);
+            k_adj_E<T><<<gr, 256, 0, stream>>>(g, f);
+            k_adj_H<T><<<gr, 256, 0, stream>>>(g, f);
+        }
+    }
+    // one block of GRAPH_STEPS steps from a graph captured on first use (the
+    // step index lives in device memory, so one graph serves every block)
+    int run_block(bool fwd, cudaGraphExec_t &exec) {
+        if (!exec) {
+            cudaGraph_t graph = nullptr;
+            if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                return set_last_error(PIC_ERR_CUDA, "adjoint: graph capture failed to start");
+            if (fwd) launch_forward_steps(GRAPH_STEPS);
+            else launch_backward_steps(GRAPH_STEPS);
+            cudaError_t e = cudaStreamEndCapture(stream, &graph);
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                exec = nullptr;
+                return set_last_error(PIC_ERR_CUDA, "adjoint graph: %s", cudaGetErrorString(e));
+            }
+            if (fwd) kJm1_captured = g.kJm1;
+        }
+        if (cudaGraphLaunch(exec, stream) != cudaSuccess)
+            return set_last_error(PIC_ERR_CUDA, "adjoint: graph launch failed");
+        return PIC_OK;
+    }
 
     int forward(const double *mask, double wp, double gamma, double *loss) override {
         if (!mask || !loss) return set_last_error(PIC_ERR_ARG, "NULL argument");
@@ -618,17 +686,26 @@ struct AdjSim : AdjBase {
         }
         if (ne && cudaMemcpy((void *)f.beta, beta_h.data(), ne * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
             return set_last_error(PIC_ERR_CUDA, "adjoint: bJ upload failed");
+        // the bJ table above is uploaded by value into device memory, and the
+        // kernels read kJ-1 from their arguments: graphs captured before
+        // hold the old kJ-1, so they are rebuilt when gamma changes
+        if (gfwd && kJm1_captured != g.kJm1) drop_graphs();
         clear_forward();
-        const dim3 gr = grid3();
-        const unsigned ns = (unsigned)((ne + 255) / 256);
-        for (long long n = 0; n < cfg.nsteps; n++) {
-            if (ne) k_store<T><<<ns, 256>>>(f, n);
-            k_fwd_H<T><<<gr, 256>>>(g, f);
-            k_fwd_E<T><<<gr, 256>>>(g, f, bu, (n + 0.5) * dt);
-            k_probe<T><<<1, 32>>>(f, pr, (n + 1) * dt, d_F);
+        long long left = cfg.nsteps;
+        int rc = 0;
+        while (left > 0 && !rc) {
+            if (left >= GRAPH_STEPS) {
+                rc = run_block(true, gfwd);
+                left -= GRAPH_STEPS;
+            } else {
+                launch_forward_steps((int)left);
+                left = 0;
+            }
         }
+        if (rc) return rc;
         cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaMemcpy(F, d_F, 2 * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(F, d_F, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
         if (e != cudaSuccess) return set_last_error(PIC_ERR_CUDA, "adjoint forward: %s", cudaGetErrorString(e));
         *loss = F[0] * F[0] + F[1] * F[1];
         wp_last = wp;
@@ -641,14 +718,26 @@ struct AdjSim : AdjBase {
         if (!have_forward) return set_last_error(PIC_ERR_STATE, "pic_adj_backward needs a forward run first");
         if (!dmask || !dwp || !dgamma) return set_last_error(PIC_ERR_ARG, "NULL argument");
         clear_adjoint();
-        const dim3 gr = grid3();
-        for (long long n = cfg.nsteps - 1; n >= 0; n--) {
-            k_src<T><<<1, 32>>>(f, pr, (n + 1) * cfg.dt, d_F);
-            k_adj_E<T><<<gr, 256>>>(g, f, n);
-            k_adj_H<T><<<gr, 256>>>(g, f);
+        {
+            const long long nst = cfg.nsteps;
+            cudaMemcpyAsync(f.n, &nst, sizeof(long long), cudaMemcpyHostToDevice, stream);
+            cudaStreamSynchronize(stream);  // nst lives on this stack frame
         }
+        long long left = cfg.nsteps;
+        int rc = 0;
+        while (left > 0 && !rc) {
+            if (left >= GRAPH_STEPS) {
+                rc = run_block(false, gbwd);
+                left -= GRAPH_STEPS;
+            } else {
+                launch_backward_steps((int)left);
+                left = 0;
+            }
+        }
+        if (rc) return rc;
         std::vector<double> gb(ne), gk(ne);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = cudaStreamSynchronize(stream);
+        if (e == cudaSuccess) e = cudaGetLastError();
         if (e == cudaSuccess && ne) e = cudaMemcpy(gb.data(), f.gb, ne * sizeof(double), cudaMemcpyDeviceToHost);
         if (e == cudaSuccess && ne) e = cudaMemcpy(gk.data(), f.gk, ne * sizeof(double), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return set_last_error(PIC_ERR_CUDA, "adjoint backward: %s", cudaGetErrorString(e));
