@@ -35,6 +35,7 @@ struct AGrid {
     T r[3];      // 1/dx per axis
     T cH, cE;    // dt/mu0, dt/eps0
     T kJm1;      // kJ - 1 (uniform gamma)
+    int ks0, ks1;  // cell planes [ks0, ks1) hold every design edge
 };
 
 template <typename T>
@@ -57,6 +58,7 @@ struct Bunch {
     double qv_norm;  // q v (2 pi sigma^2)^{-3/2}
     double inv2s2, cut2;
     double v, x0, y0, z0, dx;
+    int j0, j1, k0, k1;  // rows [j0, j1] x planes [k0, k1] hold every edge within the cut
 };
 
 struct Probe {
@@ -81,9 +83,9 @@ __device__ __forceinline__ long long apsi(const int n[3], int L, int a, int s, i
 // ------------------------------------------------------------ forward --
 template <typename T>
 __global__ void __launch_bounds__(256) k_fwd_H(AGrid<T> g, AState<T> f) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    if (i >= nx) return;
+    if (i >= nx || j >= ny) return;
     const long long sy = nx, sz = (long long)nx * ny, e = k * sz + j * sy + i;
     const T ex = f.E[0][e], ey = f.E[1][e], ez = f.E[2][e];
     const T dEz_dy = ((j + 1 < ny ? f.E[2][e + sy] : T(0)) - ez) * g.r[1];
@@ -122,18 +124,29 @@ __global__ void __launch_bounds__(256) k_fwd_H(AGrid<T> g, AState<T> f) {
 
 // the rigid bunch current J_x at the Ex edge (i+1/2, j, k) at time t
 __device__ __forceinline__ double bunch_jx(const Bunch &b, int i, int j, int k, double t) {
+    if (j < b.j0 || j > b.j1 || k < b.k0 || k > b.k1) return 0.0;  // FP64 is slow: integer test first
     const double x = (i + 0.5) * b.dx - (b.x0 + b.v * t), y = j * b.dx - b.y0, z = k * b.dx - b.z0;
     const double r2 = x * x + y * y + z * z;
     return r2 > b.cut2 ? 0.0 : b.qv_norm * exp(-r2 * b.inv2s2);
 }
 
-// Eq. 6 (design edges) then Eq. 8 for component c of edge e
 template <typename T>
-__device__ __forceinline__ void fwd_ampere(const AGrid<T> &g, const AState<T> &f, int c, long long e, T curl, T js) {
+__device__ __forceinline__ int design_slot(const AGrid<T> &g, const AState<T> &f, int c, long long e, int k) {
+    return (k >= g.ks0 && k < g.ks1) ? f.slot[c][e] : -1;
+}
+
+// Eq. 6 (design edges) then Eq. 8 for component c of edge e at plane k;
+// E^n and J^n of a design edge go to storage row n on the way
+template <typename T>
+__device__ __forceinline__ void fwd_ampere(const AGrid<T> &g, const AState<T> &f, int c, long long e, int k,
+                                           long long n, T curl, T js) {
     T E = f.E[c][e], jp = T(0);
-    const int sl = f.slot[c][e];
+    const int sl = design_slot(g, f, c, e, k);
     if (sl >= 0) {
         const T j0 = f.J[c][e];
+        const long long row = n * f.soff[3] + sl;
+        f.stE[row] = E;
+        f.stJ[row] = j0;
         jp = j0 + (g.kJm1 * j0 + f.beta[sl] * E);
         f.J[c][e] = jp;
     }
@@ -142,10 +155,11 @@ __device__ __forceinline__ void fwd_ampere(const AGrid<T> &g, const AState<T> &f
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_fwd_E(AGrid<T> g, AState<T> f, Bunch bu, double dt) {
-    const double t_half = (*f.n + 0.5) * dt;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    const long long n = *f.n;
+    const double t_half = (n + 0.5) * dt;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    if (i >= nx) return;
+    if (i >= nx || j >= ny) return;
     const long long sy = nx, sz = (long long)nx * ny, e = k * sz + j * sy + i;
     const bool fx = i == 0, fy = j == 0, fz = k == 0;  // held tangential E on the low faces
     const long long oim = i > 0 ? 1 : 0, ojm = j > 0 ? sy : 0, okm = k > 0 ? sz : 0;
@@ -164,7 +178,7 @@ __global__ void __launch_bounds__(256) k_fwd_E(AGrid<T> g, AState<T> f, Bunch bu
             const long long q = apsi(g.n, g.L, 2, s2, i, j, k);
             pz = f.psiE[2][0][q] + (f.bE[2][k] * f.psiE[2][0][q] + f.aE[2][k] * dHy_dz); f.psiE[2][0][q] = pz;
         }
-        fwd_ampere(g, f, 0, e, ky * dHz_dy + py - kz * dHy_dz - pz, (T)bunch_jx(bu, i, j, k, t_half));
+        fwd_ampere(g, f, 0, e, k, n, ky * dHz_dy + py - kz * dHy_dz - pz, (T)bunch_jx(bu, i, j, k, t_half));
     }
     if (!(fx || fz)) {
         const T dHx_dz = (hx - f.H[0][e - okm]) * g.r[2], dHz_dx = (hz - f.H[2][e - oim]) * g.r[0];
@@ -179,7 +193,7 @@ __global__ void __launch_bounds__(256) k_fwd_E(AGrid<T> g, AState<T> f, Bunch bu
             const long long q = apsi(g.n, g.L, 0, s0, i, j, k);
             px = f.psiE[0][0][q] + (f.bE[0][i] * f.psiE[0][0][q] + f.aE[0][i] * dHz_dx); f.psiE[0][0][q] = px;
         }
-        fwd_ampere(g, f, 1, e, kz * dHx_dz + pz - kx * dHz_dx - px, T(0));
+        fwd_ampere(g, f, 1, e, k, n, kz * dHx_dz + pz - kx * dHz_dx - px, T(0));
     }
     if (!(fx || fy)) {
         const T dHy_dx = (hy - f.H[1][e - oim]) * g.r[0], dHx_dy = (hx - f.H[0][e - ojm]) * g.r[1];
@@ -194,21 +208,8 @@ __global__ void __launch_bounds__(256) k_fwd_E(AGrid<T> g, AState<T> f, Bunch bu
             const long long q = apsi(g.n, g.L, 1, s1, i, j, k);
             py = f.psiE[1][0][q] + (f.bE[1][j] * f.psiE[1][0][q] + f.aE[1][j] * dHx_dy); f.psiE[1][0][q] = py;
         }
-        fwd_ampere(g, f, 2, e, kx * dHy_dx + px - ky * dHx_dy - py, T(0));
+        fwd_ampere(g, f, 2, e, k, n, kx * dHy_dx + px - ky * dHx_dy - py, T(0));
     }
-}
-
-// E^n and J^n of every design edge into storage row n
-template <typename T>
-__global__ void k_store(AState<T> f) {
-    const long long n = *f.n;
-    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long ne = f.soff[3];
-    if (q >= ne) return;
-    const int c = q < f.soff[1] ? 0 : (q < f.soff[2] ? 1 : 2);
-    const long long e = f.eidx[q];
-    f.stE[n * ne + q] = f.E[c][e];
-    f.stJ[n * ne + q] = f.J[c][e];
 }
 
 // F += E_c(x_p, t) exp(+i omega t) dt at t = (n+1) dt, then n += 1
@@ -245,9 +246,9 @@ __global__ void k_src(AState<T> f, Probe p, const double *F) {
 // edges only).  Returns nothing; updates the adjoints of E, J (in place) and
 // accumulates the bJ / kJ gradients with the stored E^n, J^n.
 template <typename T>
-__device__ __forceinline__ void adj_ampere(const AGrid<T> &g, const AState<T> &f, int c, long long e, T lE,
+__device__ __forceinline__ void adj_ampere(const AGrid<T> &g, const AState<T> &f, int c, long long e, int k, T lE,
                                            long long n) {
-    const int sl = f.slot[c][e];
+    const int sl = design_slot(g, f, c, e, k);
     if (sl < 0) return;  // lambda_E passes through unchanged
     const long long ne = f.soff[3];
     const T LJ = f.lJ[c][e] - g.cE * lE;  // adjoint of J^{n+1}
@@ -260,9 +261,9 @@ __device__ __forceinline__ void adj_ampere(const AGrid<T> &g, const AState<T> &f
 template <typename T>
 __global__ void __launch_bounds__(256) k_adj_E(AGrid<T> g, AState<T> f) {
     const long long n = *f.n;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    if (i >= nx) return;
+    if (i >= nx || j >= ny) return;
     const long long sy = nx, sz = (long long)nx * ny, e = k * sz + j * sy + i;
     const bool fx = i == 0, fy = j == 0, fz = k == 0;
     const int s0 = aslab(g.L, nx, i), s1 = aslab(g.L, ny, j), s2 = aslab(g.L, nz, k);
@@ -289,7 +290,7 @@ __global__ void __launch_bounds__(256) k_adj_E(AGrid<T> g, AState<T> f) {
         }
         scat(f.lH[2], sy, j > 0, g.r[1], Ay);
         scat(f.lH[1], sz, k > 0, g.r[2], Az);
-        adj_ampere(g, f, 0, e, lE, n);
+        adj_ampere(g, f, 0, e, k, lE, n);
     }
     if (!(fx || fz)) {  // Ey: curl = kz dHx/dz + pz - kx dHz/dx - px
         const T lE = f.lE[1][e];
@@ -308,7 +309,7 @@ __global__ void __launch_bounds__(256) k_adj_E(AGrid<T> g, AState<T> f) {
         }
         scat(f.lH[0], sz, k > 0, g.r[2], Az);
         scat(f.lH[2], 1, i > 0, g.r[0], Ax);
-        adj_ampere(g, f, 1, e, lE, n);
+        adj_ampere(g, f, 1, e, k, lE, n);
     }
     if (!(fx || fy)) {  // Ez: curl = kx dHy/dx + px - ky dHx/dy - py
         const T lE = f.lE[2][e];
@@ -327,15 +328,15 @@ __global__ void __launch_bounds__(256) k_adj_E(AGrid<T> g, AState<T> f) {
         }
         scat(f.lH[1], 1, i > 0, g.r[0], Ax);
         scat(f.lH[0], sy, j > 0, g.r[1], Ay);
-        adj_ampere(g, f, 2, e, lE, n);
+        adj_ampere(g, f, 2, e, k, lE, n);
     }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_adj_H(AGrid<T> g, AState<T> f) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    if (i >= nx) return;
+    if (i >= nx || j >= ny) return;
     const long long sy = nx, sz = (long long)nx * ny, e = k * sz + j * sy + i;
     const T lx = f.lH[0][e], ly = f.lH[1][e], lz = f.lH[2][e], cH = g.cH;
     // adjoints of the six differences (forward differences of E)
@@ -465,12 +466,14 @@ struct AdjSim : AdjBase {
             if (k < c->design_k0 || k >= c->design_k1) return -1;
             return ((long long)(k - c->design_k0) * ny + j) * nx + i;
         };
+        g.ks0 = std::max(0, (int)c->design_k0 - 1);
+        g.ks1 = std::min(nz, (int)c->design_k1 + 1);
         std::vector<int> slot_h[3];
         long long soff[4] = {0, 0, 0, 0};
         for (int comp = 0; comp < 3; comp++) {
             slot_h[comp].assign((size_t)N, -1);
             const int a1 = (comp + 1) % 3, a2 = (comp + 2) % 3;
-            const int klo = std::max(0, (int)c->design_k0 - 1), khi = std::min(nz, (int)c->design_k1 + 1);
+            const int klo = g.ks0, khi = g.ks1;
             for (int k = klo; k < khi; k++)
                 for (int j = 0; j < ny; j++)
                     for (int i = 0; i < nx; i++) {
@@ -566,6 +569,12 @@ struct AdjSim : AdjBase {
         bu.inv2s2 = 1.0 / (2.0 * s * s);
         bu.cut2 = 36.0 * s * s;
         bu.v = c->bunch_v; bu.x0 = c->bunch_x0; bu.y0 = c->bunch_y0; bu.z0 = c->bunch_z0; bu.dx = c->dx;
+        // rows and planes within the cut radius (6 sigma), one cell wider on each side
+        const double cut = 6.0 * s / c->dx;
+        bu.j0 = (int)std::floor(c->bunch_y0 / c->dx - cut) - 1;
+        bu.j1 = (int)std::ceil(c->bunch_y0 / c->dx + cut) + 1;
+        bu.k0 = (int)std::floor(c->bunch_z0 / c->dx - cut) - 1;
+        bu.k1 = (int)std::ceil(c->bunch_z0 / c->dx + cut) + 1;
         // probe stencil on the component's staggered lattice
         pr.comp = c->probe_comp;
         pr.omega = c->omega0;
@@ -617,7 +626,9 @@ struct AdjSim : AdjBase {
         cudaMemsetAsync(f.gk, 0, ne * sizeof(double), stream);
     }
 
-    dim3 grid3() const { return dim3((g.n[0] + 255) / 256, g.n[1], g.n[2]); }
+    // 32 x 8 threads over (x, y), one plane z per grid layer
+    static dim3 block3() { return dim3(32, 8, 1); }
+    dim3 grid3() const { return dim3((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, g.n[2]); }
 
     T kJm1_captured = T(0);
     void drop_graphs() {
@@ -626,21 +637,19 @@ struct AdjSim : AdjBase {
         gfwd = gbwd = nullptr;
     }
     void launch_forward_steps(int count) {
-        const dim3 gr = grid3();
-        const unsigned ns = (unsigned)((ne + 255) / 256);
+        const dim3 gr = grid3(), bl = block3();
         for (int q = 0; q < count; q++) {
-            if (ne) k_store<T><<<ns, 256, 0, stream>>>(f);
-            k_fwd_H<T><<<gr, 256, 0, stream>>>(g, f);
-            k_fwd_E<T><<<gr, 256, 0, stream>>>(g, f, bu, cfg.dt);
+            k_fwd_H<T><<<gr, bl, 0, stream>>>(g, f);
+            k_fwd_E<T><<<gr, bl, 0, stream>>>(g, f, bu, cfg.dt);
             k_probe<T><<<1, 32, 0, stream>>>(f, pr, d_F);
         }
     }
     void launch_backward_steps(int count) {
-        const dim3 gr = grid3();
+        const dim3 gr = grid3(), bl = block3();
         for (int q = 0; q < count; q++) {
             k_src<T><<<1, 32, 0, stream>>>(f, pr, d_F);
-            k_adj_E<T><<<gr, 256, 0, stream>>>(g, f);
-            k_adj_H<T><<<gr, 256, 0, stream>>>(g, f);
+            k_adj_E<T><<<gr, bl, 0, stream>>>(g, f);
+            k_adj_H<T><<<gr, bl, 0, stream>>>(g, f);
         }
     }
     // one block of GRAPH_STEPS steps from a graph captured on first use (the
