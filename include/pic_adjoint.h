@@ -16,7 +16,9 @@
  * the slab), eps_inf = 1, tangential E held at 0 on the low faces, and Js the
  * current of a rigid Gaussian bunch (charge q, rms radius sigma) moving along
  * +x at speed v:
- *   Js_x(x, t) = q v (2 pi sigma^2)^{-3/2} exp(-|x - x0 - v t e_x|^2 / (2 sigma^2)).
+ *   Js_x(x, t) = q v (2 pi sigma^2)^{-3/2} exp(-|x - x0 - v t e_x|^2 / (2 sigma^2)),
+ * set to zero where |x - x0 - v t e_x| > 6 sigma, evaluated on the Ex edges at
+ * t = (n + 1/2) dt.
  * Loss:  L = |F|^2,  F = sum_n E_c(x_p, t_{n+1}) exp(+i omega0 t_{n+1}) dt,
  * E_c interpolated trilinearly on its staggered lattice at the probe x_p
  * (the probe DFT of pic_probe_dft at one frequency).

@@ -1,13 +1,17 @@
-"""Adjoint gradients (include/pic_adjoint.h) against central finite
-differences of the forward model, in FP64 on the GPU.
+"""Adjoint gradients (include/pic_adjoint.h) on the GPU.
 
-A small film study (48x24x40 cells, 6-plane design slab, 400 steps, a 40 keV
-rigid bunch, Ez probe at wp/sqrt(2)) with a seeded mask in [0.2, 0.8]:
-the mask gradient at 8 cells (drawn from the 200 with the largest gradient),
-d/dwp and d/dgamma each agree with central differences at a relative step of
-1e-4 to 1e-5 of the largest mask gradient (mask) or of the derivative itself
-(wp, gamma).  The FP32 path's gradient is compared with the FP64 one, and the
-torch.autograd wrapper with the direct call.
+- Against the FP64 oracle (oracle/adjoint_oracle.py: the same forward model
+  in plain PyTorch CPU ops, differentiated by reverse mode) on a 24x16x24
+  study of 120 steps: loss and every mask cell's gradient within 1e-10 (FP64
+  path, rel. L2) and 1e-3 (FP32 path).
+- Against central finite differences of the library's own forward model, in
+  FP64, on a 48x24x40 study (6-plane design slab, 400 steps, 40 keV rigid
+  bunch, Ez probe at wp/sqrt(2), seeded mask in [0.2, 0.8]): the mask gradient
+  at 32 cells (drawn from the 200 with the largest gradient), d/dwp and
+  d/dgamma within 1e-5 of the largest mask gradient (mask) or of the
+  derivative itself (wp, gamma), at a relative step of 1e-4.
+- The FP32 path's gradient against the FP64 one, and the torch.autograd
+  wrapper against the direct call.
 """
 import numpy as np
 import pytest
@@ -47,7 +51,7 @@ def test_mask_gradient_matches_central_differences(fp64_grad):
     st, mask, loss, dm, _, _ = fp64_grad
     assert loss > 0 and np.isfinite(dm).all()
     rng = np.random.default_rng(11)
-    cells = rng.choice(np.argsort(-np.abs(dm))[:200], 8, replace=False)
+    cells = rng.choice(np.argsort(-np.abs(dm))[:200], 32, replace=False)
     for c in cells:
         h = 1e-4 * mask[c]
         mp, mm = mask.copy(), mask.copy()
@@ -91,3 +95,21 @@ def test_autograd_wrapper(A, fp64_grad):
     assert np.abs(m.grad.numpy() - 3.0 * dm).max() <= 1e-9 * 3.0 * np.abs(dm).max()
     assert float(w.grad) == pytest.approx(3.0 * dwp, rel=1e-9)
     assert float(g.grad) == pytest.approx(3.0 * dga, rel=1e-9)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-3)])
+def test_gradient_matches_the_oracle(A, precision, tol):
+    from oracle import adjoint_oracle as AO
+    from paper_1505_04007_gb300 import pic
+    prec = pic.PIC_FP64 if precision == "fp64" else pic.PIC_FP32
+    cfg = A.film_config(nx=24, ny=16, nz=24, design=(8, 11), nsteps=120, sigma=4e-9, cpml=4, precision=prec)
+    st = A.Adjoint(cfg)
+    mask = np.random.default_rng(13).uniform(0.2, 0.8, st.n)
+    loss = st.forward(mask, WP, GAMMA)
+    dm, dwp, dga = st.backward()
+    st.close()
+    L0, dm0, dwp0, dga0 = AO.loss_and_grad(cfg, mask, WP, GAMMA)
+    assert abs(loss / L0 - 1) <= tol, (loss, L0)
+    assert np.linalg.norm(dm - dm0) <= tol * np.linalg.norm(dm0)
+    assert abs(dwp / dwp0 - 1) <= tol, (dwp, dwp0)
+    assert abs(dga / dga0 - 1) <= tol, (dga, dga0)
