@@ -190,24 +190,20 @@ def cpu_reference(w, target_s, warm=1):
     return w.ncells * nsteps / dt / 1e9, nsteps, threads, dt
 
 
-def bench_sweep(args):
-    """Batched stepping of the 48-instance sweep against the same instances
-    stepped one after another (same GPU, same FP32 arithmetic)."""
+def batched_and_sequential(ws, warm, steps, clocks=None):
+    """Time `steps` steps (after `warm`) of the instances ws stepped through one
+    pic_batch, then fresh copies of the same instances stepped alone, one after
+    another, over the same steps.  Returns (ms_batch, ms_seq, launches, clock
+    record or None)."""
     import torch
     from paper_1505_04007_gb300 import pic
-    from paper_1505_04007_gb300 import workloads as W
-    torch.cuda.set_device(0)
-    ws = W.sweep()
-    warm = max(64, args.warmup // 64 * 64)
-    steps = max(64, min(args.steps, ws[0].nsteps - warm) // 64 * 64)  # whole 64-step blocks within the 4000 steps
-    cells = sum(w.ncells for w in ws)
     sims = [pic.Simulation(w, pic.PIC_FP32) for w in ws]
     b = pic.Batch(sims)
     b.step(warm)
     b.sync()
-    clocks = ClockSampler(0)
-    clocks.start()
-    time.sleep(0.3)
+    if clocks is not None:
+        clocks.start()
+        time.sleep(0.3)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     k0 = sum(x.stats().kernel_launches for x in sims)
@@ -217,13 +213,11 @@ def bench_sweep(args):
     b.sync()
     torch.cuda.synchronize()
     ms_batch = e0.elapsed_time(e1)
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks is not None else None
     launches = sum(x.stats().kernel_launches for x in sims) - k0
     b.close()
     for x in sims:
         x.close()
-    # fresh copies of the same instances, each stepped alone over the same
-    # step range (same warm-up), one after another, timed on its own stream
     ms_seq = 0.0
     for w in ws:
         x = pic.Simulation(w, pic.PIC_FP32)
@@ -236,8 +230,28 @@ def bench_sweep(args):
         x.sync()
         ms_seq += a0.elapsed_time(a1)
         x.close()
+    return ms_batch, ms_seq, launches, clk
+
+
+def bench_sweep(args):
+    """Batched stepping of the 48-instance sweep against the same instances
+    stepped one after another (same GPU, same FP32 arithmetic); the same
+    comparison on the eight quasi-2D grids of the Table 1 series, each far too
+    small to fill the GPU."""
+    import torch
+    from paper_1505_04007_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    ws = W.sweep()
+    warm = max(64, args.warmup // 64 * 64)
+    steps = max(64, min(args.steps, ws[0].nsteps - warm) // 64 * 64)  # whole 64-step blocks within the 4000 steps
+    cells = sum(w.ncells for w in ws)
+    ms_batch, ms_seq, launches, clk = batched_and_sequential(ws, warm, steps, ClockSampler(0))
     value = cells * steps / (ms_batch / 1e3) / 1e9
     seq = cells * steps / (ms_seq / 1e3) / 1e9
+    t1 = W.table1(65536)
+    t1_steps = 1024
+    t1_cells = sum(w.ncells for w in t1)
+    tb, ts, _, _ = batched_and_sequential(t1, 128, t1_steps)
     line = {"metric": "Gcell-upd/s", "value": value, "unit": "Gcell-upd/s", "n_gpus": 1, "steps": steps,
             "warmup": warm, "ms_per_step": ms_batch / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -249,7 +263,13 @@ def bench_sweep(args):
             "sequential": {"value": seq, "unit": "Gcell-upd/s", "ms_per_step": ms_seq / steps,
                            "note": "fresh copies of the same instances over the same step range, each stepped "
                                    "alone (own 64-step graphs), one after another"},
-            "batched_vs_sequential": value / seq, "gpu_launches": launches, "clocks": clk}
+            "batched_vs_sequential": value / seq,
+            "small_grids": {"workload": f"Table 1 series: {len(t1)} quasi-2D films, 2048 x 2 x 82..147 cells "
+                                        f"({t1_cells / 1e6:.2f}M in all), 1024 e- each, steps 128..{128 + t1_steps}",
+                            "batched": t1_cells * t1_steps / (tb / 1e3) / 1e9,
+                            "sequential": t1_cells * t1_steps / (ts / 1e3) / 1e9,
+                            "unit": "Gcell-upd/s", "batched_vs_sequential": ts / tb},
+            "gpu_launches": launches, "clocks": clk}
     print(json.dumps(line), flush=True)
 
 

@@ -123,7 +123,8 @@ struct SimBase {
     // instances into one graph
     virtual int batch_prepare() = 0;                  // pending host-side work (outside any capture)
     virtual bool batch_ready() const = 0;             // at a block boundary (no buffered samples)
-    virtual long long launch_block_on(cudaStream_t from) = 0;  // one block on own streams, joined to `from`
+    virtual long long launch_block_on(cudaStream_t from) = 0;  // one block on own streams, forked from `from`
+    virtual void join_to(cudaStream_t to) = 0;                 // `to` waits for the block launched last
     virtual void after_block(long long kernels) = 0;  // host bookkeeping once the block is enqueued
     virtual long long graph_epoch() const = 0;        // changes whenever captured steps go stale
     virtual int step_direct(long long n) = 0;
@@ -520,11 +521,13 @@ struct Sim : SimBase {
         cudaEventRecord(ev_bfork, from);
         cudaStreamWaitEvent(stream, ev_bfork, 0);
         launch_block();
-        cudaEventRecord(ev_bjoin, stream);
-        cudaStreamWaitEvent(from, ev_bjoin, 0);
         const long long k = launch_count() - before;
         launch_count() = before;  // captured, not launched
         return k;
+    }
+    void join_to(cudaStream_t to) override {
+        cudaEventRecord(ev_bjoin, stream);
+        cudaStreamWaitEvent(to, ev_bjoin, 0);
     }
     void after_block(long long k) override {
         kernels += k;
@@ -1345,7 +1348,10 @@ struct pic_batch {
     int capture() {
         drop();
         CUDA_TRY(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+        // every instance forks from the start of the capture and joins at its
+        // end, so the branches depend on nothing but that start
         for (size_t i = 0; i < h.size(); i++) kernels[i] = h[i]->sim->launch_block_on(stream);
+        for (size_t i = 0; i < h.size(); i++) h[i]->sim->join_to(stream);
         cudaError_t e = cudaStreamEndCapture(stream, &graph);
         if (e != cudaSuccess) { graph = nullptr; return fail(PIC_ERR_CUDA, "batch graph capture: %s", cudaGetErrorString(e)); }
         e = cudaGraphInstantiate(&exec, graph, 0);
