@@ -273,6 +273,24 @@ def bench_sweep(args):
     print(json.dumps(line), flush=True)
 
 
+def adjoint_bytes(cfg, elem):
+    """Algorithmic DRAM bytes of one forward and one backward step of the
+    film study: every field, adjoint and psi value read and written once per
+    update (E, H, their adjoints: 9 values per cell per update; psi: 2 values
+    rw per slab cell and axis), the design-edge map on the planes that hold
+    design edges, and per design edge J (rw), bJ and the stored E^n, J^n
+    (written forward, read backward), plus the FP64 dL/dbJ, dL/dkJ (rw)
+    backward."""
+    n = (cfg.nx, cfg.ny, cfg.nz)
+    N = n[0] * n[1] * n[2]
+    slab = sum(N * 2 * cfg.cpml_cells // n[a] for a in range(3))
+    k0, k1 = cfg.design_k0, cfg.design_k1
+    planes = min(cfg.nz, k1 + 1) - max(0, k0 - 1)
+    edges = n[0] * n[1] * (2 * (k1 - k0 + 1) + (k1 - k0))
+    common = 18 * elem * N + 8 * elem * slab + 3 * 4 * n[0] * n[1] * planes + 5 * elem * edges
+    return common, common + 32 * edges
+
+
 def bench_adjoint(args):
     """Forward + adjoint of the film study (192x96x96 cells, 30 nm design
     slab, 4000 steps, FP32 state) against the plain FP32 step of the same
@@ -333,6 +351,15 @@ def bench_adjoint(args):
                              "dmask_rel_l2": float(np.linalg.norm(r32["dm"] - r64["dm"]) / np.linalg.norm(r64["dm"])),
                              "dwp_rel": abs(r32["dwp"] / r64["dwp"] - 1), "dgamma_rel": abs(r32["dga"] / r64["dga"] - 1)},
             "fp64_forward_s": r64["fwd"], "fp64_backward_s": r64["bwd"]}
+    peak, src = measured_peak()
+    fb, bb = adjoint_bytes(cfg, 4)
+    f_gbs = fb / (r32["fwd"] / steps) / 1e9
+    b_gbs = bb / (r32["bwd"] / steps) / 1e9
+    line["roofline"] = {"bound": "hbm", "kernel": "adjoint backward step (k_src + k_adj_E + k_adj_H)",
+                        "achieved": b_gbs, "peak": peak, "unit": "GB/s", "frac": b_gbs / peak,
+                        "peak_source": src, "traffic": None, "algorithmic_bytes_per_launch": bb,
+                        "forward": {"achieved": f_gbs, "frac": f_gbs / peak, "algorithmic_bytes_per_step": fb},
+                        "note": "per-step durations from the host wall clock of whole 4000-step runs"}
     print(json.dumps(line), flush=True)
 
 
