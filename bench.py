@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the library's default launch settings instead of choosing them with pic_tune")
     ap.add_argument("--ref-seconds", type=float, default=20.0,
                     help="target CPU seconds of the oracle sample")
     return ap.parse_args()
@@ -407,6 +409,11 @@ def main():
     real = 4 if prec == pic.PIC_FP32 else 8
     stream = torch.cuda.Stream()
     sim = pic.Simulation(w, prec, stream=stream)
+    tuned = None
+    if not args.no_tune:  # launch settings chosen on this workload's own steps, before the warm-up
+        rep = sim.tune(rounds=2)
+        tuned = {"dep_smem_bytes": rep["best"][0], "sort_every": rep["best"][1],
+                 "chosen_by": f"pic_tune, 2 rounds on steps 0..{rep['steps']} (before the warm-up)"}
     sim.step(args.warmup)
     sim.sync()
 
@@ -456,6 +463,8 @@ def main():
         barrier()
         t0 = time.perf_counter()
         s2 = pic.Simulation(w, prec, stream=stream)
+        if tuned is not None:
+            s2.set_tuning(tuned["dep_smem_bytes"], tuned["sort_every"])
         s2.step(args.steps)
         spec = s2.probe_read()
         t1 = time.perf_counter()
@@ -484,7 +493,8 @@ def main():
                 "dtype": "f32" if prec == pic.PIC_FP32 else "f64", "data": "synthetic",
                 "config": {"workload": desc, "global_batch": world, "parallelism": f"replicas x{world}",
                            "l2": "state larger than the 129 MB L2 (no flush)",
-                           "particle_pushes_per_s": w.nparticles * args.steps * world / (ms / 1e3)},
+                           "particle_pushes_per_s": w.nparticles * args.steps * world / (ms / 1e3),
+                           "launch_settings": tuned or "library defaults (dep_smem_bytes 4096, sort_every 16)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk}
         print(json.dumps(line), flush=True)

@@ -228,6 +228,48 @@ int pic_load(pic_handle *h, const char *path);
  * (the simulation advances).  Synchronises. */
 int pic_profile_steps(pic_handle *h, int64_t nsteps, double *out_us);
 
+/* ---------------------------------------------------------------- tuning --
+ * Launch settings that change how fast a step runs, never what it computes
+ * (the paper has no counterpart; results stay those of pic_step up to the
+ * summation order of the atomic current deposits):
+ *   dep_smem_bytes  largest node box (three current components) a block of
+ *                   the deposit accumulates in shared memory before adding
+ *                   it to J_f; blocks whose electrons span more nodes add
+ *                   straight to J_f.  0 .. 16384, a multiple of 16.
+ *                   Default 4096.
+ *   sort_every      electrons are re-sorted by 4x4x4-cell brick every this
+ *                   many steps: 1, 2, 4, 8, 16, 32 or 64.  Default 16. */
+typedef struct {
+    int32_t dep_smem_bytes;
+    int32_t sort_every;
+} pic_tuning;
+
+int pic_get_tuning(pic_handle *h, pic_tuning *out);
+
+/* Errors: PIC_ERR_ARG (NULL or a value outside the ranges above). */
+int pic_set_tuning(pic_handle *h, const pic_tuning *t);
+
+/* Candidates pic_tune times: dep_smem_bytes over {0, 2048, 4096, 8192, 16384}
+ * with sort_every held, then sort_every over {8, 16, 32, 64} with the best
+ * box held. */
+#define PIC_TUNE_MAX_CANDIDATES 12
+typedef struct {
+    pic_tuning best;
+    int32_t n;                                    /* candidates timed */
+    pic_tuning cand[PIC_TUNE_MAX_CANDIDATES];
+    double us_per_step[PIC_TUNE_MAX_CANDIDATES];  /* best block of each, per step */
+    int64_t steps;                                /* simulation steps taken */
+} pic_tune_report;
+
+/* Choose the tuning for this simulation by timing it: `rounds` (1..16)
+ * passes of the candidates above, each candidate stepping one whole 64-step
+ * block (CUDA events on the simulation's stream); each candidate keeps its
+ * fastest block, and the fastest candidate is kept.  The blocks are real
+ * steps of the simulation (it advances by report->steps = rounds x 9 x 64
+ * steps, plus up to 63 steps to reach a block boundary first).  `report`
+ * may be NULL.  Synchronises.  Errors: PIC_ERR_ARG, PIC_ERR_CUDA. */
+int pic_tune(pic_handle *h, int32_t rounds, pic_tune_report *report);
+
 /* ---------------------------------------------------------------- batch --
  * Several independent simulations (same device, any sizes and precisions)
  * stepped together.  The paper has no counterpart; it serves parameter sweeps

@@ -155,6 +155,7 @@ struct Sim : SimBase {
     Particles<T> p{};
     Particles<T> psort{};  // scratch arrays the sort scatters into
     SortBuffers sb{};
+    int sort_every = SORT_EVERY;  // a divisor of DFT_BLOCK
     int since_sort = SORT_EVERY;
     PushParams<T> pp{};
     Probes<T> pr{};
@@ -480,6 +481,7 @@ struct Sim : SimBase {
         pp.mat = d_mat;
         pp.mat_metal = d_mat_metal;
         pp.deposit = 1;
+        pp.dep_smem = DEP_SMEM_DEFAULT;
         pp.err = d_err;
         pp.mu0 = (T)c->mu0;
         pp.inv_c2 = (T)(c->eps0 * c->mu0);
@@ -532,15 +534,15 @@ struct Sim : SimBase {
     void after_block(long long k) override {
         kernels += k;
         step_host += DFT_BLOCK;
-        since_sort = DFT_BLOCK - (DFT_BLOCK - 1) / SORT_EVERY * SORT_EVERY;  // steps since its last sort
+        since_sort = DFT_BLOCK - (DFT_BLOCK - 1) / sort_every * sort_every;  // steps since its last sort
     }
     long long graph_epoch() const override { return epoch; }
     int step_direct(long long n) override { return step(n); }
     cudaStream_t main_stream() const override { return stream; }
 
-    // DFT_BLOCK steps (a sort every SORT_EVERY, the first one included) and the DFT flush
+    // DFT_BLOCK steps (a sort every sort_every, the first one included) and the DFT flush
     void launch_block() {
-        for (int s = 0; s < DFT_BLOCK; s++) launch_step(s % SORT_EVERY == 0);
+        for (int s = 0; s < DFT_BLOCK; s++) launch_step(s % sort_every == 0);
         launch_dft_flush<T>(pr, d_step, DFT_BLOCK, stream);
     }
 
@@ -654,10 +656,10 @@ struct Sim : SimBase {
                 kernels += graph_kernels;
                 nsteps -= DFT_BLOCK;
                 step_host += DFT_BLOCK;
-                since_sort = DFT_BLOCK - (DFT_BLOCK - 1) / SORT_EVERY * SORT_EVERY;  // steps since its last sort
+                since_sort = DFT_BLOCK - (DFT_BLOCK - 1) / sort_every * sort_every;  // steps since its last sort
                 continue;
             }
-            const bool sort = since_sort >= SORT_EVERY;
+            const bool sort = since_sort >= sort_every;
             launch_step(sort);
             since_sort = sort ? 1 : since_sort + 1;
             CUDA_TRY(cudaGetLastError());
@@ -815,6 +817,92 @@ struct Sim : SimBase {
         return PIC_OK;
     }
 
+    // ---------------------------------------------------------- tuning --
+    int set_tuning(int dep, int every) {
+        if (dep < 0 || dep > DEP_SMEM_MAX || dep % 16 != 0)
+            return fail(PIC_ERR_ARG, "dep_smem_bytes %d outside 0..%d or not a multiple of 16", dep, DEP_SMEM_MAX);
+        if (every < 1 || every > DFT_BLOCK || DFT_BLOCK % every != 0)
+            return fail(PIC_ERR_ARG, "sort_every %d does not divide %d", every, DFT_BLOCK);
+        if (dep != pp.dep_smem || every != sort_every) {
+            pp.dep_smem = dep;
+            sort_every = every;
+            drop_graph();  // the captured launches hold the old settings
+        }
+        return PIC_OK;
+    }
+
+    // one whole block under the current tuning, timed on the stream (the
+    // graph is captured before the start event)
+    int time_block(cudaEvent_t e0, cudaEvent_t e1, double *us) {
+        int rc = refresh_bold();
+        if (rc) return rc;
+        rc = ensure_graph();
+        if (rc) return rc;
+        CUDA_TRY(cudaEventRecord(e0, stream));
+        rc = step(DFT_BLOCK);
+        if (rc) return rc;
+        CUDA_TRY(cudaEventRecord(e1, stream));
+        CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        *us = 1e3 * ms / DFT_BLOCK;
+        return PIC_OK;
+    }
+
+    int tune(int rounds, pic_tune_report *rep) {
+        if (rounds < 1 || rounds > 16) return fail(PIC_ERR_ARG, "rounds must be 1..16");
+        const long long s0 = step_host;
+        int rc = PIC_OK;
+        if (buffered) rc = step(DFT_BLOCK - buffered);  // reach a block boundary
+        if (rc) return rc;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        CUDA_TRY(cudaEventCreate(&e0));
+        CUDA_TRY(cudaEventCreate(&e1));
+        const int deps[5] = {0, 2048, 4096, 8192, 16384}, everies[4] = {8, 16, 32, 64};
+        pic_tuning cand[PIC_TUNE_MAX_CANDIDATES];
+        double best_us[PIC_TUNE_MAX_CANDIDATES];
+        int nc = 0;
+        // time candidates [first, first + count) `rounds` times each; *win = the fastest
+        auto pass = [&](int first, int count, int *win) -> int {
+            for (int r = 0; r < rounds; r++)
+                for (int c = first; c < first + count; c++) {
+                    int q = set_tuning(cand[c].dep_smem_bytes, cand[c].sort_every);
+                    if (q) return q;
+                    double us = 0.0;
+                    q = time_block(e0, e1, &us);
+                    if (q) return q;
+                    best_us[c] = std::min(best_us[c], us);
+                }
+            *win = first;
+            for (int c = first; c < first + count; c++)
+                if (best_us[c] < best_us[*win]) *win = c;
+            return PIC_OK;
+        };
+        const int every0 = sort_every;
+        for (int d : deps) { cand[nc] = pic_tuning{d, every0}; best_us[nc++] = 1e300; }
+        int win = 0;
+        rc = pass(0, 5, &win);
+        if (!rc) {
+            const int dep_best = cand[win].dep_smem_bytes;
+            for (int e : everies) { cand[nc] = pic_tuning{dep_best, e}; best_us[nc++] = 1e300; }
+            rc = pass(5, 4, &win);
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc) return rc;
+        const pic_tuning best = cand[win];
+        rc = set_tuning(best.dep_smem_bytes, best.sort_every);
+        if (rc) return rc;
+        if (rep) {
+            std::memset(rep, 0, sizeof(*rep));
+            rep->best = best;
+            rep->n = nc;
+            for (int c = 0; c < nc; c++) { rep->cand[c] = cand[c]; rep->us_per_step[c] = best_us[c]; }
+            rep->steps = step_host - s0;
+        }
+        return sync();
+    }
+
     int profile_steps(long long nsteps, double *out) {
         int rc = refresh_bold();
         if (rc) return rc;
@@ -832,7 +920,7 @@ struct Sim : SimBase {
             const int cnt = (int)std::min<long long>(B, nsteps - done);
             for (int s = 0; s < cnt; s++) {
                 cudaEvent_t *e = &ev[(size_t)s * NE];
-                const bool sort = since_sort >= SORT_EVERY;
+                const bool sort = since_sort >= sort_every;
                 launch_step(sort, true, e);
                 since_sort = sort ? 1 : since_sort + 1;
                 buffered++;
@@ -1315,6 +1403,26 @@ int pic_profile_steps(pic_handle *h, int64_t nsteps, double *out_us) {
     g_err.clear();
     if (!h || !out_us) return fail(PIC_ERR_ARG, "NULL argument");
     return DISPATCH(h, profile_steps(nsteps, out_us));
+}
+
+int pic_get_tuning(pic_handle *h, pic_tuning *out) {
+    g_err.clear();
+    if (!h || !out) return fail(PIC_ERR_ARG, "NULL argument");
+    if (h->precision == PIC_FP64) *out = pic_tuning{S<double>(h)->pp.dep_smem, S<double>(h)->sort_every};
+    else *out = pic_tuning{S<float>(h)->pp.dep_smem, S<float>(h)->sort_every};
+    return PIC_OK;
+}
+
+int pic_set_tuning(pic_handle *h, const pic_tuning *t) {
+    g_err.clear();
+    if (!h || !t) return fail(PIC_ERR_ARG, "NULL argument");
+    return DISPATCH(h, set_tuning(t->dep_smem_bytes, t->sort_every));
+}
+
+int pic_tune(pic_handle *h, int32_t rounds, pic_tune_report *report) {
+    g_err.clear();
+    if (!h) return fail(PIC_ERR_ARG, "NULL handle");
+    return DISPATCH(h, tune(rounds, report));
 }
 
 }  // extern "C"

@@ -90,12 +90,6 @@ __device__ __forceinline__ void interp_H(const Fields<T> &f, const Grid<T> &g, c
 }
 
 constexpr int PUSH_BLOCK = 256;
-// Largest node box (3 components) a block accumulates in shared memory.  A
-// block whose box is larger adds its contributions straight to J_f: clearing
-// and flushing a large, mostly empty box (the sparse tails of a sorted bunch)
-// costs more than the global atomics it saves (measured: 4 KB beats 2, 8, 16
-// and 40 KB, and direct-only, on the c2 step and on the 48-instance sweep).
-constexpr int DEP_SMEM_BYTES = 4 * 1024;
 
 __device__ __forceinline__ long long tile_of(const int idx[3], const int nt[3]) {
     return ((long long)(idx[2] / TILE_Z) * nt[1] + idx[1] / TILE_Y) * nt[0] + idx[0] / TILE_X;
@@ -279,7 +273,7 @@ __global__ void __launch_bounds__(PUSH_BLOCK) k_push_deposit(Grid<T> g, Fields<T
     const int w0 = bb_hi[0] - bb_lo[0] + 1, w1 = bb_hi[1] - bb_lo[1] + 1, w2 = bb_hi[2] - bb_lo[2] + 1;
     const bool any = bb_hi[0] >= bb_lo[0];
     const long long box = any ? (long long)w0 * w1 * w2 : 0;
-    const bool in_smem = any && 3 * box * (long long)sizeof(T) <= DEP_SMEM_BYTES;
+    const bool in_smem = any && 3 * box * (long long)sizeof(T) <= pp.dep_smem;
     const int vol = in_smem ? (int)box : 0;  // nodes in the shared box (32-bit indexing from here)
     if (in_smem) {
         for (int e = threadIdx.x; e < 3 * vol; e += blockDim.x) acc[e] = T(0);
@@ -543,7 +537,7 @@ template <typename T>
 void launch_push_deposit(const Grid<T> &g, const Fields<T> &f, const Particles<T> &p, const PushParams<T> &pp,
                          cudaStream_t s) {
     if (p.n <= 0) return;
-    k_push_deposit<T><<<(unsigned)((p.n + PUSH_BLOCK - 1) / PUSH_BLOCK), PUSH_BLOCK, DEP_SMEM_BYTES, s>>>(g, f, p, pp);
+    k_push_deposit<T><<<(unsigned)((p.n + PUSH_BLOCK - 1) / PUSH_BLOCK), PUSH_BLOCK, (size_t)pp.dep_smem, s>>>(g, f, p, pp);
     launch_count() += 1;
 }
 

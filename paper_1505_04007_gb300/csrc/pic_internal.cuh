@@ -12,7 +12,8 @@ constexpr int TILE_X = 32, TILE_Y = 4, TILE_Z = 4;
 // Probe samples buffered on the device between DFT flushes (one graph).
 constexpr int DFT_BLOCK = 64;
 constexpr int MAX_SOURCES = 16;
-// Electrons are re-sorted by 4x4x4-cell brick every SORT_EVERY steps.
+// Electrons are re-sorted by 4x4x4-cell brick every SORT_EVERY steps (the
+// default; a simulation may change it, to a divisor of DFT_BLOCK).
 constexpr int SORT_BRICK = 4;
 constexpr int SORT_EVERY = 16;
 constexpr int SCAN_TILE = 4096;  // entries per block of the prefix scan
@@ -82,8 +83,16 @@ struct PushParams {
     const uint8_t *mat;       // cell material id
     const uint8_t *mat_metal; // per material id: wp > 0
     int deposit;
+    int dep_smem;   // largest node box (bytes, three components) a deposit block accumulates in shared memory
     int *err;
 };
+// Default of PushParams::dep_smem.  A block whose box is larger adds its
+// contributions straight to J_f: clearing and flushing a large, mostly empty
+// box (the sparse tails of a sorted bunch) costs more than the global atomics
+// it saves (measured: 4 KB beats 2, 8, 16 and 40 KB, and direct-only, on the
+// c2 step and on the 48-instance sweep).
+constexpr int DEP_SMEM_DEFAULT = 4 * 1024;
+constexpr int DEP_SMEM_MAX = 16 * 1024;
 
 template <typename T>
 struct Probes {

@@ -31,7 +31,8 @@ EXPORTS = ("pic_last_error", "pic_workspace_size", "pic_create", "pic_destroy", 
            "pic_add_particles", "pic_get_particles", "pic_set_deposit", "pic_add_source", "pic_probe_dft",
            "pic_step", "pic_sync", "pic_probe_read", "pic_get_field", "pic_set_field", "pic_get_stats",
            "pic_save", "pic_load", "pic_profile_steps", "pic_dft_fold_static", "pic_batch_create",
-           "pic_batch_step", "pic_batch_sync", "pic_batch_destroy", "pic_probe_kw")
+           "pic_batch_step", "pic_batch_sync", "pic_batch_destroy", "pic_probe_kw", "pic_get_tuning",
+           "pic_set_tuning", "pic_tune")
 
 
 class pic_material(C.Structure):
@@ -54,6 +55,18 @@ class pic_config(C.Structure):
 class pic_stats(C.Structure):
     _fields_ = [("step", C.c_int64), ("n_particles", C.c_int64), ("n_frozen", C.c_int64),
                 ("device_error", C.c_int32), ("n_edge_classes", C.c_int32), ("kernel_launches", C.c_int64)]
+
+
+class pic_tuning(C.Structure):
+    _fields_ = [("dep_smem_bytes", C.c_int32), ("sort_every", C.c_int32)]
+
+
+PIC_TUNE_MAX_CANDIDATES = 12
+
+
+class pic_tune_report(C.Structure):
+    _fields_ = [("best", pic_tuning), ("n", C.c_int32), ("cand", pic_tuning * PIC_TUNE_MAX_CANDIDATES),
+                ("us_per_step", C.c_double * PIC_TUNE_MAX_CANDIDATES), ("steps", C.c_int64)]
 
 
 class PicError(RuntimeError):
@@ -95,6 +108,9 @@ def load(path: str | None = None):
     L.pic_set_field.argtypes = [h, C.c_int, dp]
     L.pic_get_stats.argtypes = [h, C.POINTER(pic_stats)]
     L.pic_profile_steps.argtypes = [h, C.c_int64, dp]
+    L.pic_get_tuning.argtypes = [h, C.POINTER(pic_tuning)]
+    L.pic_set_tuning.argtypes = [h, C.POINTER(pic_tuning)]
+    L.pic_tune.argtypes = [h, C.c_int32, C.POINTER(pic_tune_report)]
     L.pic_save.argtypes = [h, C.c_char_p]
     L.pic_load.argtypes = [h, C.c_char_p]
     L.pic_dft_fold_static.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_uint32, C.c_void_p, C.c_int,
@@ -224,6 +240,24 @@ def pic_profile_steps(h, nsteps: int) -> dict:
     _check(load().pic_profile_steps(h, int(nsteps), _dp(out)), "pic_profile_steps")
     keys = ("update_H", "push_deposit", "update_E", "step_tail", "dft_flush", "step")
     return dict(zip(keys, out.tolist()))
+
+
+def pic_get_tuning(h) -> tuple:
+    t = pic_tuning()
+    _check(load().pic_get_tuning(h, C.byref(t)), "pic_get_tuning")
+    return t.dep_smem_bytes, t.sort_every
+
+
+def pic_set_tuning(h, dep_smem_bytes: int, sort_every: int) -> None:
+    t = pic_tuning(int(dep_smem_bytes), int(sort_every))
+    _check(load().pic_set_tuning(h, C.byref(t)), "pic_set_tuning")
+
+
+def pic_tune(h, rounds: int = 1) -> dict:
+    r = pic_tune_report()
+    _check(load().pic_tune(h, int(rounds), C.byref(r)), "pic_tune")
+    return {"best": (r.best.dep_smem_bytes, r.best.sort_every), "steps": r.steps,
+            "candidates": [((r.cand[i].dep_smem_bytes, r.cand[i].sort_every), r.us_per_step[i]) for i in range(r.n)]}
 
 
 def pic_dft_fold_static(samples_ptr: int, count: int, np_: int, comp_mask: int, freq_ptr: int, nf: int,
@@ -356,6 +390,18 @@ class Simulation:
 
     def profile(self, nsteps):
         return pic_profile_steps(self.h, nsteps)
+
+    @property
+    def tuning(self):
+        return pic_get_tuning(self.h)
+
+    def set_tuning(self, dep_smem_bytes, sort_every):
+        pic_set_tuning(self.h, dep_smem_bytes, sort_every)
+
+    def tune(self, rounds=1):
+        """Time the deposit box and sort interval candidates on real steps of
+        this simulation and keep the fastest (the simulation advances)."""
+        return pic_tune(self.h, rounds)
 
     def save(self, path):
         pic_save(self.h, path)

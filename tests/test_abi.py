@@ -34,6 +34,8 @@ def test_struct_layout_matches_header():
     assert C.sizeof(P.pic_material) == 24
     assert P.pic_config.flags.offset == C.sizeof(P.pic_config) - 8
     assert C.sizeof(P.pic_stats) == 40
+    assert C.sizeof(P.pic_tuning) == 8
+    assert P.pic_tune_report.us_per_step.offset == 112 and C.sizeof(P.pic_tune_report) == 216
 
 
 def _cfg(**kw):

@@ -1,0 +1,110 @@
+"""Launch tuning (pic_get_tuning / pic_set_tuning / pic_tune, include/pic.h):
+settings that change how fast a step runs, never what it computes.
+
+- Switching the deposit's shared-memory box and the sort interval in the
+  middle of a run (after a captured 64-step block, so the graph is rebuilt)
+  keeps the FP64 path within 1e-10 of the FP64 oracle and the FP32 path
+  within 2e-5, on a dense bunch (4096 electrons on a 64x24x40 grid), for box
+  sizes that send every block to global atomics (0) or let the densest blocks
+  accumulate in shared memory (16 KB), and for sort intervals from every step
+  to once per block.
+- pic_tune started off a block boundary steps to the boundary, times its
+  nine candidates on real steps, keeps the fastest, and the run it leaves
+  behind still equals the oracle stepped the same number of steps.
+- Invalid settings are rejected and leave the current ones in place.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1505_04007_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+ETA0 = (W.MU0 / W.EPS0) ** 0.5
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    from paper_1505_04007_gb300 import pic
+    pic.load()
+    return pic
+
+
+def dense(nsteps):
+    return W.scaled(W.c1(), 64, 24, 40, 4096, nsteps)
+
+
+def rel(s, o):
+    num = sum(np.linalg.norm(s.field(c) * (ETA0 if c >= 3 else 1) - o.get_field(c) * (ETA0 if c >= 3 else 1)) ** 2
+              for c in range(6))
+    den = sum(np.linalg.norm(o.get_field(c) * (ETA0 if c >= 3 else 1)) ** 2 for c in range(6))
+    return float(np.sqrt(num / den))
+
+
+@pytest.fixture(scope="module")
+def oracle200():
+    w = dense(200)
+    o = O.from_workload(w)
+    o.step(200)
+    return w, o
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
+@pytest.mark.parametrize("dep,every", [(0, 8), (16384, 1), (2048, 32), (8192, 64)])
+def test_tuning_changes_keep_parity(P, oracle200, prec, tol, dep, every):
+    w, o = oracle200
+    s = P.Simulation(w, P.PIC_FP64 if prec == "fp64" else P.PIC_FP32)
+    assert s.tuning == (4096, 16)
+    s.step(64)  # one captured block under the default settings
+    s.set_tuning(dep, every)
+    assert s.tuning == (dep, every)
+    s.step(136)
+    s.sync()
+    assert rel(s, o) <= tol
+    Fo, Fg = o.probe_read(), s.probe_read()
+    assert np.linalg.norm(Fg - Fo) <= tol * np.linalg.norm(Fo)
+    xo, _, so = o.particles()
+    xg, _, sg = s.particles()
+    if prec == "fp64":
+        assert np.array_equal(sg, so)
+        assert np.abs(xg - xo).max() <= 1e-12 * w.dx
+    s.close()
+
+
+def test_tune_off_a_block_boundary_keeps_parity(P):
+    s = P.Simulation(dense(0), P.PIC_FP64)
+    s.step(70)
+    rep = s.tune(rounds=1)
+    n = 70 + rep["steps"]
+    assert rep["steps"] == (64 - 70 % 64) + 9 * 64
+    assert s.stats().step == n
+    cands = [c for c, _ in rep["candidates"]]
+    assert len(cands) == 9 and rep["best"] in cands and s.tuning == rep["best"]
+    assert [c[0] for c in cands[:5]] == [0, 2048, 4096, 8192, 16384]
+    assert [c[1] for c in cands[5:]] == [8, 16, 32, 64]
+    assert all(us > 0 for _, us in rep["candidates"])
+    box_pass, sort_pass = rep["candidates"][:5], rep["candidates"][5:]
+    assert rep["best"][0] == min(box_pass, key=lambda cu: cu[1])[0][0]
+    assert rep["best"] == min(sort_pass, key=lambda cu: cu[1])[0]
+    s.step(30)
+    s.sync()
+    o = O.from_workload(dense(0))
+    o.step(n + 30)
+    assert rel(s, o) <= 1e-10
+    Fo, Fg = o.probe_read(), s.probe_read()
+    assert np.linalg.norm(Fg - Fo) <= 1e-10 * np.linalg.norm(Fo)
+    s.close()
+
+
+@pytest.mark.parametrize("dep,every", [(1000, 16), (32768, 16), (-16, 16), (4096, 3), (4096, 128), (4096, 0)])
+def test_invalid_tuning_rejected(P, dep, every):
+    s = P.Simulation(dense(0), P.PIC_FP32)
+    s.set_tuning(8192, 32)
+    with pytest.raises(P.PicError):
+        s.set_tuning(dep, every)
+    assert s.tuning == (8192, 32)
+    s.close()
