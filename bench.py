@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the library's default launch settings instead of choosing them with pic_tune")
+    ap.add_argument("--tuning", default=None, metavar="DEP_SMEM_BYTES,SORT_EVERY",
+                    help="use these launch settings instead of running pic_tune (e.g. 8192,32)")
     ap.add_argument("--ref-seconds", type=float, default=20.0,
                     help="target CPU seconds of the oracle sample")
     return ap.parse_args()
@@ -410,7 +412,11 @@ def main():
     stream = torch.cuda.Stream()
     sim = pic.Simulation(w, prec, stream=stream)
     tuned = None
-    if not args.no_tune:  # launch settings chosen on this workload's own steps, before the warm-up
+    if args.tuning:
+        dep, every = (int(v) for v in args.tuning.split(","))
+        sim.set_tuning(dep, every)
+        tuned = {"dep_smem_bytes": dep, "sort_every": every, "chosen_by": "--tuning"}
+    elif not args.no_tune:  # launch settings chosen on this workload's own steps, before the warm-up
         rep = sim.tune(rounds=2)
         tuned = {"dep_smem_bytes": rep["best"][0], "sort_every": rep["best"][1],
                  "chosen_by": f"pic_tune, 2 rounds on steps 0..{rep['steps']} (before the warm-up)"}
