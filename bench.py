@@ -194,15 +194,20 @@ def cpu_reference(w, target_s, warm=1):
     return w.ncells * nsteps / dt / 1e9, nsteps, threads, dt
 
 
-def batched_and_sequential(ws, warm, steps, clocks=None):
+def batched_and_sequential(ws, warm, steps, clocks=None, tune=False):
     """Time `steps` steps (after `warm`) of the instances ws stepped through one
     pic_batch, then fresh copies of the same instances stepped alone, one after
-    another, over the same steps.  Returns (ms_batch, ms_seq, launches, clock
-    record or None)."""
+    another, over the same steps.  With `tune`, pic_batch_tune first chooses the
+    launch settings on the batch (its steps count towards the warm-up; the
+    sequential copies get the same settings).  Returns (ms_batch, ms_seq,
+    launches, clock record or None, tuning or None, steps before the timed
+    region)."""
     import torch
     from paper_1505_04007_gb300 import pic
     sims = [pic.Simulation(w, pic.PIC_FP32) for w in ws]
     b = pic.Batch(sims)
+    rep = b.tune(rounds=1) if tune else None
+    before = warm + (rep["steps"] if rep else 0)
     b.step(warm)
     b.sync()
     if clocks is not None:
@@ -225,7 +230,9 @@ def batched_and_sequential(ws, warm, steps, clocks=None):
     ms_seq = 0.0
     for w in ws:
         x = pic.Simulation(w, pic.PIC_FP32)
-        x.step(warm)
+        if rep:
+            x.set_tuning(*rep["best"])
+        x.step(before)
         x.sync()
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record(x.stream)
@@ -234,7 +241,7 @@ def batched_and_sequential(ws, warm, steps, clocks=None):
         x.sync()
         ms_seq += a0.elapsed_time(a1)
         x.close()
-    return ms_batch, ms_seq, launches, clk
+    return ms_batch, ms_seq, launches, clk, (rep["best"] if rep else None), before
 
 
 def bench_sweep(args):
@@ -247,29 +254,37 @@ def bench_sweep(args):
     torch.cuda.set_device(0)
     ws = W.sweep()
     warm = max(64, args.warmup // 64 * 64)
-    steps = max(64, min(args.steps, ws[0].nsteps - warm) // 64 * 64)  # whole 64-step blocks within the 4000 steps
+    tune_steps = 0 if args.no_tune else 9 * 64  # pic_batch_tune, one round
+    # whole 64-step blocks within the 4000 steps
+    steps = max(64, min(args.steps, ws[0].nsteps - warm - tune_steps) // 64 * 64)
     cells = sum(w.ncells for w in ws)
-    ms_batch, ms_seq, launches, clk = batched_and_sequential(ws, warm, steps, ClockSampler(0))
+    ms_batch, ms_seq, launches, clk, tuned, before = batched_and_sequential(ws, warm, steps, ClockSampler(0),
+                                                                            tune=not args.no_tune)
     value = cells * steps / (ms_batch / 1e3) / 1e9
     seq = cells * steps / (ms_seq / 1e3) / 1e9
     t1 = W.table1(65536)
     t1_steps = 1024
     t1_cells = sum(w.ncells for w in t1)
-    tb, ts, _, _ = batched_and_sequential(t1, 128, t1_steps)
+    tb, ts, _, _, t1_tuned, t1_before = batched_and_sequential(t1, 128, t1_steps, tune=not args.no_tune)
     line = {"metric": "Gcell-upd/s", "value": value, "unit": "Gcell-upd/s", "n_gpus": 1, "steps": steps,
             "warmup": warm, "ms_per_step": ms_batch / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"sweep: {len(ws)} instances, {cells / 1e6:.1f}M cells in all "
                                    f"(128..320 x 64..128 x 64..96, films 10-60 nm, 10-100 keV, gaps 5-20 nm, "
-                                   f"2e4 e- each), steps {warm}..{warm + steps} of the 4000-step sweep timed",
+                                   f"2e4 e- each), steps {before}..{before + steps} of the 4000-step sweep timed",
                        "parallelism": "one batch graph (one branch per instance)",
-                       "l2": "state larger than the 129 MB L2 (no flush)"},
+                       "l2": "state larger than the 129 MB L2 (no flush)",
+                       "launch_settings": ({"dep_smem_bytes": tuned[0], "sort_every": tuned[1],
+                                            "chosen_by": f"pic_batch_tune, 1 round on steps 0..{tune_steps}"}
+                                           if tuned else "library defaults (dep_smem_bytes 4096, sort_every 16)")},
             "sequential": {"value": seq, "unit": "Gcell-upd/s", "ms_per_step": ms_seq / steps,
                            "note": "fresh copies of the same instances over the same step range, each stepped "
                                    "alone (own 64-step graphs), one after another"},
             "batched_vs_sequential": value / seq,
             "small_grids": {"workload": f"Table 1 series: {len(t1)} quasi-2D films, 2048 x 2 x 82..147 cells "
-                                        f"({t1_cells / 1e6:.2f}M in all), 1024 e- each, steps 128..{128 + t1_steps}",
+                                        f"({t1_cells / 1e6:.2f}M in all), 1024 e- each, "
+                                        f"steps {t1_before}..{t1_before + t1_steps}",
+                            "launch_settings": t1_tuned,
                             "batched": t1_cells * t1_steps / (tb / 1e3) / 1e9,
                             "sequential": t1_cells * t1_steps / (ts / 1e3) / 1e9,
                             "unit": "Gcell-upd/s", "batched_vs_sequential": ts / tb},

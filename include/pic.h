@@ -298,6 +298,15 @@ int pic_batch_step(pic_batch *b, int64_t nsteps);
 /* Wait for the batch and every instance; reports device errors as pic_sync. */
 int pic_batch_sync(pic_batch *b);
 
+/* pic_tune for the batch as a whole: each candidate is applied to every
+ * instance and timed on whole batch blocks (the box candidates at the first
+ * instance's sort interval); the fastest is applied to every instance.
+ * Instances not at a block boundary first step to it on their own (up to 63
+ * steps each); then every instance advances by report->steps = rounds x 9 x
+ * 64 steps.  `report` may be NULL.  Synchronises.  Errors: PIC_ERR_ARG,
+ * PIC_ERR_CUDA. */
+int pic_batch_tune(pic_batch *b, int32_t rounds, pic_tune_report *report);
+
 /* Release the batch (not its instances).  NULL is accepted. */
 int pic_batch_destroy(pic_batch *b);
 

@@ -129,6 +129,8 @@ struct SimBase {
     virtual long long graph_epoch() const = 0;        // changes whenever captured steps go stale
     virtual int step_direct(long long n) = 0;
     virtual cudaStream_t main_stream() const = 0;
+    virtual int steps_to_boundary() const = 0;        // steps left in the current block (0 at a boundary)
+    virtual int set_tuning(int dep_smem, int sort_every) = 0;
 };
 
 template <typename T>
@@ -538,6 +540,7 @@ struct Sim : SimBase {
     }
     long long graph_epoch() const override { return epoch; }
     int step_direct(long long n) override { return step(n); }
+    int steps_to_boundary() const override { return buffered ? DFT_BLOCK - buffered : 0; }
     cudaStream_t main_stream() const override { return stream; }
 
     // DFT_BLOCK steps (a sort every sort_every, the first one included) and the DFT flush
@@ -818,7 +821,7 @@ struct Sim : SimBase {
     }
 
     // ---------------------------------------------------------- tuning --
-    int set_tuning(int dep, int every) {
+    int set_tuning(int dep, int every) override {
         if (dep < 0 || dep > DEP_SMEM_MAX || dep % 16 != 0)
             return fail(PIC_ERR_ARG, "dep_smem_bytes %d outside 0..%d or not a multiple of 16", dep, DEP_SMEM_MAX);
         if (every < 1 || every > DFT_BLOCK || DFT_BLOCK % every != 0)
@@ -1504,6 +1507,104 @@ struct pic_batch {
         CUDA_TRY(cudaGetLastError());
         return PIC_OK;
     }
+    // one whole block of every instance under the current settings, timed on
+    // the batch stream (any capture happens before the start event)
+    int time_block(cudaEvent_t e0, cudaEvent_t e1, double *us) {
+        for (auto *x : h) {
+            int rc = x->sim->batch_prepare();
+            if (rc) return rc;
+            rc = order(x->sim->main_stream(), stream);
+            if (rc) return rc;
+        }
+        if (stale()) {
+            int rc = capture();
+            if (rc) return rc;
+        }
+        CUDA_TRY(cudaEventRecord(e0, stream));
+        CUDA_TRY(cudaGraphLaunch(exec, stream));
+        CUDA_TRY(cudaEventRecord(e1, stream));
+        for (size_t i = 0; i < h.size(); i++) h[i]->sim->after_block(kernels[i]);
+        for (auto *x : h) {
+            int rc = order(stream, x->sim->main_stream());
+            if (rc) return rc;
+        }
+        CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        *us = 1e3 * ms / DFT_BLOCK;
+        return PIC_OK;
+    }
+
+    int set_all(const pic_tuning &t) {
+        for (auto *x : h) {
+            const int rc = x->sim->set_tuning(t.dep_smem_bytes, t.sort_every);
+            if (rc) return rc;
+        }
+        return PIC_OK;
+    }
+
+    // the candidates of pic_tune, each applied to every instance and timed on
+    // whole batch blocks
+    int tune(int rounds, pic_tune_report *rep) {
+        if (rounds < 1 || rounds > 16) return fail(PIC_ERR_ARG, "rounds must be 1..16");
+        for (auto *x : h) {  // every instance to its own block boundary
+            const int left = x->sim->steps_to_boundary();
+            if (left) {
+                int rc = x->sim->step_direct(left);
+                if (rc) return rc;
+            }
+        }
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        CUDA_TRY(cudaEventCreate(&e0));
+        CUDA_TRY(cudaEventCreate(&e1));
+        const int deps[5] = {0, 2048, 4096, 8192, 16384}, everies[4] = {8, 16, 32, 64};
+        pic_tuning cand[PIC_TUNE_MAX_CANDIDATES];
+        double best_us[PIC_TUNE_MAX_CANDIDATES];
+        int nc = 0, rc = PIC_OK, win = 0;
+        auto pass = [&](int first, int count) -> int {
+            for (int r = 0; r < rounds; r++)
+                for (int c = first; c < first + count; c++) {
+                    int q = set_all(cand[c]);
+                    if (q) return q;
+                    double us = 0.0;
+                    q = time_block(e0, e1, &us);
+                    if (q) return q;
+                    best_us[c] = std::min(best_us[c], us);
+                }
+            win = first;
+            for (int c = first; c < first + count; c++)
+                if (best_us[c] < best_us[win]) win = c;
+            return PIC_OK;
+        };
+        const pic_tuning start = rep_start();
+        for (int d : deps) { cand[nc] = pic_tuning{d, start.sort_every}; best_us[nc++] = 1e300; }
+        rc = pass(0, 5);
+        if (!rc) {
+            const int dep_best = cand[win].dep_smem_bytes;
+            for (int e : everies) { cand[nc] = pic_tuning{dep_best, e}; best_us[nc++] = 1e300; }
+            rc = pass(5, 4);
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc) return rc;
+        rc = set_all(cand[win]);
+        if (rc) return rc;
+        if (rep) {
+            std::memset(rep, 0, sizeof(*rep));
+            rep->best = cand[win];
+            rep->n = nc;
+            for (int c = 0; c < nc; c++) { rep->cand[c] = cand[c]; rep->us_per_step[c] = best_us[c]; }
+            rep->steps = (long long)rounds * nc * DFT_BLOCK;
+        }
+        return PIC_OK;
+    }
+    // the first instance's sort interval (the box candidates are timed at it)
+    pic_tuning rep_start() const {
+        pic_tuning t{};
+        pic_get_tuning(h[0], &t);
+        return t;
+    }
+
     ~pic_batch() {
         if (stream) cudaStreamSynchronize(stream);
         drop();
@@ -1546,6 +1647,14 @@ int pic_batch_step(pic_batch *b, int64_t nsteps) {
     if (!b) return fail(PIC_ERR_ARG, "NULL batch");
     if (nsteps < 0) return fail(PIC_ERR_ARG, "negative step count");
     return b->step(nsteps);
+}
+
+int pic_batch_tune(pic_batch *b, int32_t rounds, pic_tune_report *report) {
+    g_err.clear();
+    if (!b) return fail(PIC_ERR_ARG, "NULL batch");
+    const int rc = b->tune(rounds, report);
+    if (rc) return rc;
+    return pic_batch_sync(b);
 }
 
 int pic_batch_sync(pic_batch *b) {

@@ -32,7 +32,7 @@ EXPORTS = ("pic_last_error", "pic_workspace_size", "pic_create", "pic_destroy", 
            "pic_step", "pic_sync", "pic_probe_read", "pic_get_field", "pic_set_field", "pic_get_stats",
            "pic_save", "pic_load", "pic_profile_steps", "pic_dft_fold_static", "pic_batch_create",
            "pic_batch_step", "pic_batch_sync", "pic_batch_destroy", "pic_probe_kw", "pic_get_tuning",
-           "pic_set_tuning", "pic_tune")
+           "pic_set_tuning", "pic_tune", "pic_batch_tune")
 
 
 class pic_material(C.Structure):
@@ -111,6 +111,7 @@ def load(path: str | None = None):
     L.pic_get_tuning.argtypes = [h, C.POINTER(pic_tuning)]
     L.pic_set_tuning.argtypes = [h, C.POINTER(pic_tuning)]
     L.pic_tune.argtypes = [h, C.c_int32, C.POINTER(pic_tune_report)]
+    L.pic_batch_tune.argtypes = [h, C.c_int32, C.POINTER(pic_tune_report)]
     L.pic_save.argtypes = [h, C.c_char_p]
     L.pic_load.argtypes = [h, C.c_char_p]
     L.pic_dft_fold_static.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_uint32, C.c_void_p, C.c_int,
@@ -253,11 +254,21 @@ def pic_set_tuning(h, dep_smem_bytes: int, sort_every: int) -> None:
     _check(load().pic_set_tuning(h, C.byref(t)), "pic_set_tuning")
 
 
+def _report(r: pic_tune_report) -> dict:
+    return {"best": (r.best.dep_smem_bytes, r.best.sort_every), "steps": r.steps,
+            "candidates": [((r.cand[i].dep_smem_bytes, r.cand[i].sort_every), r.us_per_step[i]) for i in range(r.n)]}
+
+
 def pic_tune(h, rounds: int = 1) -> dict:
     r = pic_tune_report()
     _check(load().pic_tune(h, int(rounds), C.byref(r)), "pic_tune")
-    return {"best": (r.best.dep_smem_bytes, r.best.sort_every), "steps": r.steps,
-            "candidates": [((r.cand[i].dep_smem_bytes, r.cand[i].sort_every), r.us_per_step[i]) for i in range(r.n)]}
+    return _report(r)
+
+
+def pic_batch_tune(b, rounds: int = 1) -> dict:
+    r = pic_tune_report()
+    _check(load().pic_batch_tune(b, int(rounds), C.byref(r)), "pic_batch_tune")
+    return _report(r)
 
 
 def pic_dft_fold_static(samples_ptr: int, count: int, np_: int, comp_mask: int, freq_ptr: int, nf: int,
@@ -440,6 +451,10 @@ class Batch:
 
     def sync(self):
         pic_batch_sync(self.b)
+
+    def tune(self, rounds=1):
+        """pic_tune over the whole batch (every instance advances)."""
+        return pic_batch_tune(self.b, rounds)
 
     def close(self):
         if getattr(self, "b", None):

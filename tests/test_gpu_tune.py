@@ -11,6 +11,8 @@ settings that change how fast a step runs, never what it computes.
 - pic_tune started off a block boundary steps to the boundary, times its
   nine candidates on real steps, keeps the fastest, and the run it leaves
   behind still equals the oracle stepped the same number of steps.
+- pic_batch_tune applies each candidate to every instance of a batch (one
+  of them started off a block boundary) and leaves runs equal to the oracle's.
 - Invalid settings are rejected and leave the current ones in place.
 """
 import numpy as np
@@ -98,6 +100,29 @@ def test_tune_off_a_block_boundary_keeps_parity(P):
     Fo, Fg = o.probe_read(), s.probe_read()
     assert np.linalg.norm(Fg - Fo) <= 1e-10 * np.linalg.norm(Fo)
     s.close()
+
+
+def test_batch_tune_keeps_parity(P):
+    ws = [dense(0), W.scaled(W.c1(), 48, 24, 40, 1024, 0)]
+    sims = [P.Simulation(ws[0], P.PIC_FP64), P.Simulation(ws[1], P.PIC_FP64)]
+    sims[1].step(10)  # off a block boundary
+    b = P.Batch(sims)
+    rep = b.tune(rounds=1)
+    assert rep["steps"] == 9 * 64 and len(rep["candidates"]) == 9
+    assert all(x.tuning == rep["best"] for x in sims)
+    b.step(64)
+    b.sync()
+    n = [x.stats().step for x in sims]
+    assert n == [9 * 64 + 64, 64 + 9 * 64 + 64]
+    for w, x, k in zip(ws, sims, n):
+        o = O.from_workload(w)
+        o.step(k)
+        assert rel(x, o) <= 1e-10
+        Fo, Fg = o.probe_read(), x.probe_read()
+        assert np.linalg.norm(Fg - Fo) <= 1e-10 * np.linalg.norm(Fo)
+    b.close()
+    for x in sims:
+        x.close()
 
 
 @pytest.mark.parametrize("dep,every", [(1000, 16), (32768, 16), (-16, 16), (4096, 3), (4096, 128), (4096, 0)])
