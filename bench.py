@@ -374,7 +374,7 @@ def bench_adjoint(args):
     fb, bb = adjoint_bytes(cfg, 4)
     f_gbs = fb / (r32["fwd"] / steps) / 1e9
     b_gbs = bb / (r32["bwd"] / steps) / 1e9
-    line["roofline"] = {"bound": "hbm", "kernel": "adjoint backward step (k_src + k_adj_E + k_adj_H)",
+    line["roofline"] = {"bound": "hbm", "kernel": "adjoint backward step (k_adj_E + k_adj_H)",
                         "achieved": b_gbs, "peak": peak, "unit": "GB/s", "frac": b_gbs / peak,
                         "peak_source": src, "traffic": None, "algorithmic_bytes_per_launch": bb,
                         "forward": {"achieved": f_gbs, "frac": f_gbs / peak, "algorithmic_bytes_per_step": fb},

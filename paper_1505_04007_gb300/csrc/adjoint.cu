@@ -64,9 +64,23 @@ struct Bunch {
 struct Probe {
     long long idx[8];
     double w[8];
+    int lo[3], hi[3];  // cell index range of the eight corners per axis
     int comp;
     double omega, dt;
 };
+
+// F += E_c(x_p, t) exp(+i omega t) dt at t = (n+1) dt (the probe DFT at one
+// frequency, from E^{n+1})
+template <typename T>
+__device__ __forceinline__ void probe_term(const AState<T> &f, const Probe &p, double *F, long long n) {
+    const double t = (n + 1) * p.dt;
+    double v = 0.0;
+    for (int q = 0; q < 8; q++) v += p.w[q] * (double)f.E[p.comp][p.idx[q]];
+    double sn, cs;
+    sincos(p.omega * t, &sn, &cs);
+    F[0] += v * cs * p.dt;
+    F[1] += v * sn * p.dt;
+}
 
 __device__ __forceinline__ int aslab(int L, int n, int x) {
     if (x < L) return x;
@@ -81,8 +95,18 @@ __device__ __forceinline__ long long apsi(const int n[3], int L, int a, int s, i
 }
 
 // ------------------------------------------------------------ forward --
+// Step m starts here.  Its first thread also takes the probe term of step
+// m-1 (E is E^m until the E update that follows) and advances the step
+// counter from m-1 to m (it starts at -1).
 template <typename T>
-__global__ void __launch_bounds__(256) k_fwd_H(AGrid<T> g, AState<T> f) {
+__global__ void __launch_bounds__(256) k_fwd_H(AGrid<T> g, AState<T> f, Probe pr, double *F) {
+    pdl_wait();
+    pdl_release();
+    if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0) {
+        const long long m1 = *f.n;
+        if (m1 >= 0) probe_term(f, pr, F, m1);
+        *f.n = m1 + 1;
+    }
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     if (i >= nx || j >= ny) return;
@@ -155,6 +179,8 @@ __device__ __forceinline__ void fwd_ampere(const AGrid<T> &g, const AState<T> &f
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_fwd_E(AGrid<T> g, AState<T> f, Bunch bu, double dt) {
+    pdl_wait();
+    pdl_release();
     const long long n = *f.n;
     const double t_half = (n + 0.5) * dt;
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
@@ -212,34 +238,29 @@ __global__ void __launch_bounds__(256) k_fwd_E(AGrid<T> g, AState<T> f, Bunch bu
     }
 }
 
-// F += E_c(x_p, t) exp(+i omega t) dt at t = (n+1) dt, then n += 1
+// the probe term of the last step, after the last E update
 template <typename T>
 __global__ void k_probe(AState<T> f, Probe p, double *F) {
     if (threadIdx.x != 0) return;
     const long long n = *f.n;
-    const double t = (n + 1) * p.dt;
+    probe_term(f, p, F, n);
     *f.n = n + 1;
-    double v = 0.0;
-    for (int q = 0; q < 8; q++) v += p.w[q] * (double)f.E[p.comp][p.idx[q]];
-    double sn, cs;
-    sincos(p.omega * t, &sn, &cs);
-    F[0] += v * cs * p.dt;
-    F[1] += v * sn * p.dt;
 }
 
 // ----------------------------------------------------------- backward --
-// Start of backward step n (n = steps left - 1, then stored as the counter):
-// adjoint of the probe term at t = (n+1) dt, dL/dE = 2 Re(conj(F) e^{i omega t}) dt w
+// Adjoint of the probe term of step n at t = (n+1) dt, added by the thread
+// that owns edge e of the probed component before it reads lambda_E:
+// dL/dE = 2 Re(conj(F) e^{i omega t}) dt w
 template <typename T>
-__global__ void k_src(AState<T> f, Probe p, const double *F) {
-    if (threadIdx.x != 0) return;
-    const long long n = *f.n - 1;
-    *f.n = n;
+__device__ __forceinline__ void probe_source(const AState<T> &f, const Probe &p, const double *F, long long n, int i,
+                                             int j, int k, long long e) {
+    if (i < p.lo[0] || i > p.hi[0] || j < p.lo[1] || j > p.hi[1] || k < p.lo[2] || k > p.hi[2]) return;
     const double t = (n + 1) * p.dt;
     double sn, cs;
     sincos(p.omega * t, &sn, &cs);
     const double s = 2.0 * p.dt * (F[0] * cs + F[1] * sn);
-    for (int q = 0; q < 8; q++) f.lE[p.comp][p.idx[q]] += (T)(s * p.w[q]);
+    for (int q = 0; q < 8; q++)
+        if (p.idx[q] == e) f.lE[p.comp][e] += (T)(s * p.w[q]);
 }
 
 // Transpose of the Eq. 6 + Eq. 8 update of component c at edge e (updated
@@ -258,13 +279,17 @@ __device__ __forceinline__ void adj_ampere(const AGrid<T> &g, const AState<T> &f
     f.lE[c][e] = lE + f.beta[sl] * LJ;
 }
 
+// Backward step n = (steps left) - 1; k_adj_H then stores n as the counter.
 template <typename T>
-__global__ void __launch_bounds__(256) k_adj_E(AGrid<T> g, AState<T> f) {
-    const long long n = *f.n;
+__global__ void __launch_bounds__(256) k_adj_E(AGrid<T> g, AState<T> f, Probe pr, const double *F) {
+    pdl_wait();
+    pdl_release();
+    const long long n = *f.n - 1;
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     if (i >= nx || j >= ny) return;
     const long long sy = nx, sz = (long long)nx * ny, e = k * sz + j * sy + i;
+    probe_source(f, pr, F, n, i, j, k, e);
     const bool fx = i == 0, fy = j == 0, fz = k == 0;
     const int s0 = aslab(g.L, nx, i), s1 = aslab(g.L, ny, j), s2 = aslab(g.L, nz, k);
     const T cE = g.cE;
@@ -334,6 +359,9 @@ __global__ void __launch_bounds__(256) k_adj_E(AGrid<T> g, AState<T> f) {
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_adj_H(AGrid<T> g, AState<T> f) {
+    pdl_wait();
+    pdl_release();
+    if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0) *f.n -= 1;
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     if (i >= nx || j >= ny) return;
@@ -594,6 +622,17 @@ struct AdjSim : AdjBase {
             pr.idx[corner] = idx;
             pr.w[corner] = wt;
         }
+        for (int a = 0; a < 3; a++) {  // index range of the corners along each axis
+            long long stride = 1;
+            for (int b = 0; b < a; b++) stride *= g.n[b];
+            pr.lo[a] = g.n[a];
+            pr.hi[a] = -1;
+            for (int corner = 0; corner < 8; corner++) {
+                const int x = (int)((pr.idx[corner] / stride) % g.n[a]);
+                pr.lo[a] = std::min(pr.lo[a], x);
+                pr.hi[a] = std::max(pr.hi[a], x);
+            }
+        }
         return PIC_OK;
     }
 
@@ -609,7 +648,7 @@ struct AdjSim : AdjBase {
             }
         }
         cudaMemsetAsync(d_F, 0, 2 * sizeof(double), stream);
-        cudaMemsetAsync(f.n, 0, sizeof(long long), stream);
+        cudaMemsetAsync(f.n, 0xff, sizeof(long long), stream);  // -1: no step taken yet
     }
     void clear_adjoint() {
         for (int a = 0; a < 3; a++) {
@@ -639,17 +678,15 @@ struct AdjSim : AdjBase {
     void launch_forward_steps(int count) {
         const dim3 gr = grid3(), bl = block3();
         for (int q = 0; q < count; q++) {
-            k_fwd_H<T><<<gr, bl, 0, stream>>>(g, f);
-            k_fwd_E<T><<<gr, bl, 0, stream>>>(g, f, bu, cfg.dt);
-            k_probe<T><<<1, 32, 0, stream>>>(f, pr, d_F);
+            launch_pdl(k_fwd_H<T>, gr, bl, 0, stream, g, f, pr, d_F);
+            launch_pdl(k_fwd_E<T>, gr, bl, 0, stream, g, f, bu, cfg.dt);
         }
     }
     void launch_backward_steps(int count) {
         const dim3 gr = grid3(), bl = block3();
         for (int q = 0; q < count; q++) {
-            k_src<T><<<1, 32, 0, stream>>>(f, pr, d_F);
-            k_adj_E<T><<<gr, bl, 0, stream>>>(g, f);
-            k_adj_H<T><<<gr, bl, 0, stream>>>(g, f);
+            launch_pdl(k_adj_E<T>, gr, bl, 0, stream, g, f, pr, (const double *)d_F);
+            launch_pdl(k_adj_H<T>, gr, bl, 0, stream, g, f);
         }
     }
     // one block of GRAPH_STEPS steps from a graph captured on first use (the
@@ -712,6 +749,7 @@ struct AdjSim : AdjBase {
             }
         }
         if (rc) return rc;
+        k_probe<T><<<1, 32, 0, stream>>>(f, pr, d_F);  // the last step's probe term
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(F, d_F, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
