@@ -298,7 +298,8 @@ struct Sim : SimBase {
 
     int build_tables(const pic_config *c, std::vector<uint8_t> ecls[3], std::vector<T> cls[3],
                      std::vector<uint8_t> &cls_metal) {
-        // distinct multisets of the four cell ids around an edge -> class
+        // distinct multisets of the four cell ids around an edge -> class,
+        // numbered in order of first appearance (components 0, 1, 2)
         std::unordered_map<uint32_t, int> classes;
         const uint8_t *mat = c->material_id;
         auto wrapc = [&](int a, int x) {
@@ -308,29 +309,46 @@ struct Sim : SimBase {
         };
         for (int q3 = 0; q3 < 3; q3++) cls[q3].assign(256, (T)0);
         cls_metal.assign(256, 0);
+        const int nx = n[0], ny = n[1], nz = n[2];
+        const size_t stride[3] = {1, (size_t)nx, (size_t)nx * ny};
         for (int comp = 0; comp < 3; comp++) {
             ecls[comp].resize((size_t)N);
+            uint8_t *out = ecls[comp].data();
             const int a1 = (comp + 1) % 3, a2 = (comp + 2) % 3;
+            const size_t o1 = stride[a1], o2 = stride[a2];
             uint32_t last_key = 0xffffffffu;
             int last_cls = -1;
-            for (int k = 0; k < n[2]; k++)
-                for (int j = 0; j < n[1]; j++)
-                    for (int i = 0; i < n[0]; i++) {
-                        int ids[4], t = 0;
-                        for (int s1 = -1; s1 <= 0; s1++)
-                            for (int s2 = -1; s2 <= 0; s2++) {
-                                int p3[3] = {i, j, k};
-                                p3[a1] = wrapc(a1, p3[a1] + s1);
-                                p3[a2] = wrapc(a2, p3[a2] + s2);
-                                ids[t++] = mat[((size_t)p3[2] * n[1] + p3[1]) * n[0] + p3[0]];
-                            }
-                        std::sort(ids, ids + 4);
-                        const uint32_t key = (uint32_t)ids[0] | (uint32_t)ids[1] << 8 | (uint32_t)ids[2] << 16 |
-                                             (uint32_t)ids[3] << 24;
-                        int cl;
-                        if (key == last_key) {
-                            cl = last_cls;
+            for (int k = 0; k < nz; k++)
+                for (int j = 0; j < ny; j++)
+                    for (int i = 0; i < nx; i++) {
+                        const int x3[3] = {i, j, k};
+                        const size_t e = ((size_t)k * ny + j) * nx + i;
+                        int ids[4];
+                        if (x3[a1] > 0 && x3[a2] > 0) {  // no face: the four cells by their offsets
+                            ids[0] = mat[e];
+                            ids[1] = mat[e - o1];
+                            ids[2] = mat[e - o2];
+                            ids[3] = mat[e - o1 - o2];
                         } else {
+                            int t = 0;
+                            for (int s1 = -1; s1 <= 0; s1++)
+                                for (int s2 = -1; s2 <= 0; s2++) {
+                                    int p3[3] = {i, j, k};
+                                    p3[a1] = wrapc(a1, p3[a1] + s1);
+                                    p3[a2] = wrapc(a2, p3[a2] + s2);
+                                    ids[t++] = mat[((size_t)p3[2] * ny + p3[1]) * nx + p3[0]];
+                                }
+                        }
+                        uint32_t key;
+                        if (ids[0] == ids[1] && ids[0] == ids[2] && ids[0] == ids[3]) {
+                            key = (uint32_t)ids[0] * 0x01010101u;  // one material (most edges)
+                        } else {
+                            std::sort(ids, ids + 4);
+                            key = (uint32_t)ids[0] | (uint32_t)ids[1] << 8 | (uint32_t)ids[2] << 16 |
+                                  (uint32_t)ids[3] << 24;
+                        }
+                        int cl = last_cls;
+                        if (key != last_key) {
                             auto it = classes.find(key);
                             if (it == classes.end()) {
                                 if ((int)classes.size() >= 256)
@@ -356,7 +374,7 @@ struct Sim : SimBase {
                             last_key = key;
                             last_cls = cl;
                         }
-                        ecls[comp][((size_t)k * n[1] + j) * n[0] + i] = (uint8_t)cl;
+                        out[e] = (uint8_t)cl;
                     }
         }
         n_classes = (int)classes.size();
