@@ -59,6 +59,19 @@ def dist_env():
     return rank, world, local
 
 
+def job_rate(ms_local, units_per_rank, dist=None, device="cpu"):
+    """(slowest rank's milliseconds, whole-job units per second): every rank
+    processed units_per_rank units; the job took as long as its slowest rank
+    (all-reduce MAX).  Without a process group: this process alone."""
+    ms, world = float(ms_local), 1
+    if dist is not None:
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, world = float(t.item()), dist.get_world_size()
+    return ms, units_per_rank * world / (ms / 1e3)
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -458,12 +471,9 @@ def main():
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     sim.sync()
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, rate = job_rate(ms, w.ncells * args.steps, dist, "cuda")
     cells_total = w.ncells * args.steps * world
-    value = cells_total / (ms / 1e3) / 1e9
+    value = rate / 1e9
     launches = sim.stats().kernel_launches - k0  # counted by the library (graph replays count their kernels)
 
     # ------------------------------ per-kernel durations (CUDA events, live)
@@ -490,11 +500,8 @@ def main():
         spec = s2.probe_read()
         t1 = time.perf_counter()
         s2.close()
-        secs = t1 - t0
-        if dist is not None:
-            t = torch.tensor([secs], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            secs = float(t.item())
+        ms_e2e, _ = job_rate((t1 - t0) * 1e3, w.ncells * args.steps, dist, "cuda")
+        secs = ms_e2e / 1e3
         h2d = w.ncells + w.nparticles * 3 * 2 * 8 + len(w.probes) * 24 + len(w.freqs) * 8
         d2h = spec.size * 16
         e2e = {"value": cells_total / secs / 1e9, "unit": "Gcell-upd/s",
