@@ -302,6 +302,15 @@ def bench_sweep(args):
                             "sequential": t1_cells * t1_steps / (ts / 1e3) / 1e9,
                             "unit": "Gcell-upd/s", "batched_vs_sequential": ts / tb},
             "gpu_launches": launches, "clocks": clk}
+    # the field updates of all instances per batched step against the copy rate
+    # (push, deposit, probe and sort bytes left out: a lower bound on the rate)
+    peak, src = measured_peak()
+    fb = sum(ab["update_H"] + ab["update_E"] for ab in (algorithmic_bytes(w, 4) for w in ws))
+    ach = fb / (ms_batch / steps * 1e-3) / 1e9
+    line["roofline"] = {"bound": "hbm", "kernel": "H + E updates of all 48 instances (one batched step)",
+                        "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                        "peak_source": src, "traffic": None, "algorithmic_bytes_per_launch": fb,
+                        "note": "per-step time of the whole batched step (particles included)"}
     print(json.dumps(line), flush=True)
 
 
