@@ -238,7 +238,9 @@ int pic_profile_steps(pic_handle *h, int64_t nsteps, double *out_us);
  *                   straight to J_f.  0 .. 16384, a multiple of 16.
  *                   Default 4096.
  *   sort_every      electrons are re-sorted by 4x4x4-cell brick every this
- *                   many steps: 1, 2, 4, 8, 16, 32 or 64.  Default 16. */
+ *                   many steps: 1, 2, 4, 8, 16, 32 or 64.  Default 16.
+ * The settings belong to the handle, not to the simulation state: pic_save
+ * does not write them and pic_load leaves the handle's settings as they are. */
 typedef struct {
     int32_t dep_smem_bytes;
     int32_t sort_every;
