@@ -1,5 +1,6 @@
 """Checks at the full sizes, in the launch configuration the bench times
-(FP32 state, graph replays of 64 steps, sorted deposit).
+(FP32 state, graph replays of 64 steps, sorted deposit, launch settings
+chosen by pic_tune on the run's first steps, as bench.py does).
 
 Field values at these sizes have no closed form and the oracle cannot follow
 the runs step by step, so they are checked through properties that hold at
@@ -50,7 +51,8 @@ def gauss_residual(P, s, w, mask):
 def test_gauss_law_full_size_fp32(P, name, steps):
     w = W.WORKLOADS[name](nsteps=0)
     s = P.Simulation(w, P.PIC_FP32)
-    s.step(steps)  # graph replays (64-step blocks), sorts every 16 steps
+    s.tune(rounds=2)  # as the bench: real steps under every candidate, then the fastest
+    s.step(steps)  # graph replays (64-step blocks) under the chosen settings
     st = s.stats()
     assert st.device_error == 0 and st.n_frozen < w.nparticles
     mask = interior_node_mask(w, margin=1)
@@ -66,7 +68,8 @@ def test_c2_plasmon_peak_vs_oracle_fp32(P):
     gold = json.load(open(GOLD))
     w = W.c2()
     s = P.Simulation(w, P.PIC_FP32)
-    s.step(w.nsteps)
+    rep = s.tune(rounds=2)  # the tuning steps are steps of the run
+    s.step(w.nsteps - rep["steps"])
     F = s.probe_read()
     st = s.stats()
     s.close()
