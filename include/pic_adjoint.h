@@ -52,7 +52,8 @@ typedef struct {
     double bunch_x0, bunch_y0, bunch_z0;   /* centre at t = 0 [m] */
     double probe[3];        /* [m] */
     int32_t probe_comp;     /* 0..2: Ex, Ey, Ez */
-    int32_t pad;
+    int32_t flags;          /* bit 0: keep the one-cell-per-thread kernels where the FP32
+                               four-cell ones would run (nx and cpml_cells multiples of 4) */
     double omega0;          /* loss frequency [rad/s] */
     int64_t nsteps;
 } pic_adj_config;

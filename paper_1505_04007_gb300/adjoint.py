@@ -26,7 +26,7 @@ class pic_adj_config(C.Structure):
                 ("design_k0", C.c_int64), ("design_k1", C.c_int64),
                 ("bunch_q", C.c_double), ("bunch_sigma", C.c_double), ("bunch_v", C.c_double),
                 ("bunch_x0", C.c_double), ("bunch_y0", C.c_double), ("bunch_z0", C.c_double),
-                ("probe", C.c_double * 3), ("probe_comp", C.c_int32), ("pad", C.c_int32),
+                ("probe", C.c_double * 3), ("probe_comp", C.c_int32), ("flags", C.c_int32),
                 ("omega0", C.c_double), ("nsteps", C.c_int64)]
 
 

@@ -19,6 +19,7 @@
 #include <array>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/pic.h"
@@ -410,6 +411,453 @@ __global__ void __launch_bounds__(256) k_adj_H(AGrid<T> g, AState<T> f) {
     scat(f.lE[0], sy, j + 1 < ny, g.r[1], Axy);
 }
 
+// ------------------------------------------- FP32, four cells per thread --
+// The same four kernels for FP32 state with four consecutive x cells per
+// thread (nx and the CPML width multiples of 4, so a group lies wholly
+// inside or outside the x slabs): every centre, row and plane access is one
+// 16-byte load or store, and the transposed updates add into a neighbouring
+// group with one 16-byte atomic instead of four (the contributions a group
+// makes to its own cells are summed first).  Per cell the arithmetic is that
+// of the kernels above; only the order of the atomic sums differs.
+struct V4 {
+    float v[4];
+};
+__device__ __forceinline__ V4 ld4(const float *p) {
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    return V4{{q.x, q.y, q.z, q.w}};
+}
+__device__ __forceinline__ void st4(float *p, const V4 &a) {
+    *reinterpret_cast<float4 *>(p) = make_float4(a.v[0], a.v[1], a.v[2], a.v[3]);
+}
+__device__ __forceinline__ void add4(float *p, const V4 &a) {
+    atomicAdd(reinterpret_cast<float4 *>(p), make_float4(a.v[0], a.v[1], a.v[2], a.v[3]));
+}
+__device__ __forceinline__ V4 zero4() { return V4{{0.f, 0.f, 0.f, 0.f}}; }
+
+__device__ __forceinline__ bool group_of(const AGrid<float> &g, int &i0, int &j, int &k) {
+    i0 = 4 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    j = blockIdx.y * blockDim.y + threadIdx.y;
+    k = blockIdx.z;
+    return i0 < g.n[0] && j < g.n[1];
+}
+
+__global__ void __launch_bounds__(256) k_fwd_H4(AGrid<float> g, AState<float> f, Probe pr, double *F) {
+    pdl_wait();
+    pdl_release();
+    if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0) {
+        const long long m1 = *f.n;
+        if (m1 >= 0) probe_term(f, pr, F, m1);
+        *f.n = m1 + 1;
+    }
+    int i0, j, k;
+    if (!group_of(g, i0, j, k)) return;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const long long sy = nx, sz = (long long)nx * ny, e = k * sz + j * sy + i0;
+    const V4 ex = ld4(f.E[0] + e), ey = ld4(f.E[1] + e), ez = ld4(f.E[2] + e);
+    const V4 ez_jp = j + 1 < ny ? ld4(f.E[2] + e + sy) : zero4(), ex_jp = j + 1 < ny ? ld4(f.E[0] + e + sy) : zero4();
+    const V4 ey_kp = k + 1 < nz ? ld4(f.E[1] + e + sz) : zero4(), ex_kp = k + 1 < nz ? ld4(f.E[0] + e + sz) : zero4();
+    const float ez_ip = i0 + 4 < nx ? f.E[2][e + 4] : 0.f, ey_ip = i0 + 4 < nx ? f.E[1][e + 4] : 0.f;
+    V4 hx = ld4(f.H[0] + e), hy = ld4(f.H[1] + e), hz = ld4(f.H[2] + e);
+    const float rx = g.r[0], ry = g.r[1], rz = g.r[2];
+    float dEz_dy[4], dEy_dz[4], dEx_dz[4], dEz_dx[4], dEy_dx[4], dEx_dy[4];
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+        dEz_dy[m] = (ez_jp.v[m] - ez.v[m]) * ry;
+        dEy_dz[m] = (ey_kp.v[m] - ey.v[m]) * rz;
+        dEx_dz[m] = (ex_kp.v[m] - ex.v[m]) * rz;
+        dEz_dx[m] = ((m < 3 ? ez.v[m + 1] : ez_ip) - ez.v[m]) * rx;
+        dEy_dx[m] = ((m < 3 ? ey.v[m + 1] : ey_ip) - ey.v[m]) * rx;
+        dEx_dy[m] = (ex_jp.v[m] - ex.v[m]) * ry;
+    }
+    float kx[4] = {1.f, 1.f, 1.f, 1.f}, ky = 1.f, kz = 1.f;
+    V4 pxy = zero4(), pxz = zero4(), pyz = zero4(), pyx = zero4(), pzx = zero4(), pzy = zero4();
+    const int s0 = aslab(g.L, nx, i0), s1 = aslab(g.L, ny, j), s2 = aslab(g.L, nz, k);
+    if (s0 >= 0) {
+        const long long q = apsi(g.n, g.L, 0, s0, i0, j, k);
+        const V4 o0 = ld4(f.psiH[0][0] + q), o1 = ld4(f.psiH[0][1] + q);
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            const float b = f.bH[0][i0 + m], a = f.aH[0][i0 + m];
+            kx[m] = f.ikH[0][i0 + m];
+            pxy.v[m] = o0.v[m] + (b * o0.v[m] + a * dEz_dx[m]);
+            pxz.v[m] = o1.v[m] + (b * o1.v[m] + a * dEy_dx[m]);
+        }
+        st4(f.psiH[0][0] + q, pxy);
+        st4(f.psiH[0][1] + q, pxz);
+    }
+    if (s1 >= 0) {
+        const float b = f.bH[1][j], a = f.aH[1][j];
+        ky = f.ikH[1][j];
+        const long long q = apsi(g.n, g.L, 1, s1, i0, j, k);
+        const V4 o0 = ld4(f.psiH[1][0] + q), o1 = ld4(f.psiH[1][1] + q);
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            pyz.v[m] = o0.v[m] + (b * o0.v[m] + a * dEx_dy[m]);
+            pyx.v[m] = o1.v[m] + (b * o1.v[m] + a * dEz_dy[m]);
+        }
+        st4(f.psiH[1][0] + q, pyz);
+        st4(f.psiH[1][1] + q, pyx);
+    }
+    if (s2 >= 0) {
+        const float b = f.bH[2][k], a = f.aH[2][k];
+        kz = f.ikH[2][k];
+        const long long q = apsi(g.n, g.L, 2, s2, i0, j, k);
+        const V4 o0 = ld4(f.psiH[2][0] + q), o1 = ld4(f.psiH[2][1] + q);
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            pzx.v[m] = o0.v[m] + (b * o0.v[m] + a * dEy_dz[m]);
+            pzy.v[m] = o1.v[m] + (b * o1.v[m] + a * dEx_dz[m]);
+        }
+        st4(f.psiH[2][0] + q, pzx);
+        st4(f.psiH[2][1] + q, pzy);
+    }
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+        hx.v[m] -= g.cH * (ky * dEz_dy[m] + pyx.v[m] - kz * dEy_dz[m] - pzx.v[m]);
+        hy.v[m] -= g.cH * (kz * dEx_dz[m] + pzy.v[m] - kx[m] * dEz_dx[m] - pxy.v[m]);
+        hz.v[m] -= g.cH * (kx[m] * dEy_dx[m] + pxz.v[m] - ky * dEx_dy[m] - pyz.v[m]);
+    }
+    st4(f.H[0] + e, hx);
+    st4(f.H[1] + e, hy);
+    st4(f.H[2] + e, hz);
+}
+
+// Eq. 6 on the design edges among the four, then Eq. 8, for component c of
+// cells e..e+3 at plane k; held cells (upd false) keep E, J and psi.
+__device__ __forceinline__ void fwd_ampere4(const AGrid<float> &g, const AState<float> &f, int c, long long e, int k,
+                                            long long n, const float curl[4], const float js[4], const bool upd[4]) {
+    V4 E = ld4(f.E[c] + e);
+    if (k >= g.ks0 && k < g.ks1) {
+        const int4 s4 = *reinterpret_cast<const int4 *>(f.slot[c] + e);
+        const int sl[4] = {s4.x, s4.y, s4.z, s4.w};
+        const long long ne = f.soff[3];
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            float jp = 0.f;
+            if (sl[m] >= 0 && upd[m]) {
+                const float j0 = f.J[c][e + m];
+                const long long row = n * ne + sl[m];
+                f.stE[row] = E.v[m];
+                f.stJ[row] = j0;
+                jp = j0 + (g.kJm1 * j0 + f.beta[sl[m]] * E.v[m]);
+                f.J[c][e + m] = jp;
+            }
+            if (upd[m]) E.v[m] = E.v[m] + g.cE * (curl[m] - jp - js[m]);
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < 4; m++)
+            if (upd[m]) E.v[m] = E.v[m] + g.cE * (curl[m] - js[m]);
+    }
+    st4(f.E[c] + e, E);
+}
+
+// psi update of one axis for the four cells (profiles per cell along x,
+// per row or plane along y and z); held cells keep their psi.  Returns the
+// new psi values in p and the 1/kappa factors in kap.
+__device__ __forceinline__ void psi4(float *psi, long long q, const float *bb, const float *aa, const float *ik, int x0,
+                                     bool per_cell, const float d[4], const bool upd[4], float p[4], float kap[4]) {
+    V4 o = ld4(psi + q);
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+        const int x = per_cell ? x0 + m : x0;
+        const float b = bb[x], a = aa[x];
+        kap[m] = ik[x];
+        p[m] = o.v[m] + (b * o.v[m] + a * d[m]);
+        if (upd[m]) o.v[m] = p[m];
+    }
+    st4(psi + q, o);
+}
+
+__global__ void __launch_bounds__(256) k_fwd_E4(AGrid<float> g, AState<float> f, Bunch bu, double dt) {
+    pdl_wait();
+    pdl_release();
+    const long long n = *f.n;
+    const double t_half = (n + 0.5) * dt;
+    int i0, j, k;
+    if (!group_of(g, i0, j, k)) return;
+    const int nx = g.n[0], ny = g.n[1];
+    const long long sy = nx, sz = (long long)nx * ny, e = k * sz + j * sy + i0;
+    const bool fx0 = i0 == 0, fy = j == 0, fz = k == 0;
+    const long long ojm = j > 0 ? sy : 0, okm = k > 0 ? sz : 0;
+    const V4 hx = ld4(f.H[0] + e), hy = ld4(f.H[1] + e), hz = ld4(f.H[2] + e);
+    const float hz_im = f.H[2][e - (i0 > 0 ? 1 : 0)], hy_im = f.H[1][e - (i0 > 0 ? 1 : 0)];
+    const int s0 = aslab(g.L, nx, i0), s1 = aslab(g.L, ny, j), s2 = aslab(g.L, g.n[2], k);
+    const float rx = g.r[0], ry = g.r[1], rz = g.r[2];
+    const float zero[4] = {0.f, 0.f, 0.f, 0.f};
+    // component c: curl = k1 d1 + p1 - k2 d2 - p2 over its two transverse axes
+    if (!(fy || fz)) {  // Ex: d1 = dHz/dy (psi_E[1][1]), d2 = dHy/dz (psi_E[2][0])
+        const V4 hz_jm = ld4(f.H[2] + e - ojm), hy_km = ld4(f.H[1] + e - okm);
+        const bool upd[4] = {true, true, true, true};
+        float d1[4], d2[4], k1[4] = {1.f, 1.f, 1.f, 1.f}, k2[4] = {1.f, 1.f, 1.f, 1.f}, p1[4] = {0.f, 0.f, 0.f, 0.f},
+              p2[4] = {0.f, 0.f, 0.f, 0.f}, curl[4], js[4];
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            d1[m] = (hz.v[m] - hz_jm.v[m]) * ry;
+            d2[m] = (hy.v[m] - hy_km.v[m]) * rz;
+            js[m] = (float)bunch_jx(bu, i0 + m, j, k, t_half);
+        }
+        if (s1 >= 0) psi4(f.psiE[1][1], apsi(g.n, g.L, 1, s1, i0, j, k), f.bE[1], f.aE[1], f.ikE[1], j, false, d1, upd, p1, k1);
+        if (s2 >= 0) psi4(f.psiE[2][0], apsi(g.n, g.L, 2, s2, i0, j, k), f.bE[2], f.aE[2], f.ikE[2], k, false, d2, upd, p2, k2);
+#pragma unroll
+        for (int m = 0; m < 4; m++) curl[m] = k1[m] * d1[m] + p1[m] - k2[m] * d2[m] - p2[m];
+        fwd_ampere4(g, f, 0, e, k, n, curl, js, upd);
+    }
+    if (!fz) {  // Ey: d1 = dHx/dz (psi_E[2][1]), d2 = dHz/dx (psi_E[0][0]); cell 0 held on the x face
+        const V4 hx_km = ld4(f.H[0] + e - okm);
+        const bool upd[4] = {!fx0, true, true, true};
+        float d1[4], d2[4], k1[4] = {1.f, 1.f, 1.f, 1.f}, k2[4] = {1.f, 1.f, 1.f, 1.f}, p1[4] = {0.f, 0.f, 0.f, 0.f},
+              p2[4] = {0.f, 0.f, 0.f, 0.f}, curl[4];
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            d1[m] = (hx.v[m] - hx_km.v[m]) * rz;
+            d2[m] = (hz.v[m] - (m > 0 ? hz.v[m - 1] : hz_im)) * rx;
+        }
+        if (s2 >= 0) psi4(f.psiE[2][1], apsi(g.n, g.L, 2, s2, i0, j, k), f.bE[2], f.aE[2], f.ikE[2], k, false, d1, upd, p1, k1);
+        if (s0 >= 0) psi4(f.psiE[0][0], apsi(g.n, g.L, 0, s0, i0, j, k), f.bE[0], f.aE[0], f.ikE[0], i0, true, d2, upd, p2, k2);
+#pragma unroll
+        for (int m = 0; m < 4; m++) curl[m] = k1[m] * d1[m] + p1[m] - k2[m] * d2[m] - p2[m];
+        fwd_ampere4(g, f, 1, e, k, n, curl, zero, upd);
+    }
+    if (!fy) {  // Ez: d1 = dHy/dx (psi_E[0][1]), d2 = dHx/dy (psi_E[1][0]); cell 0 held on the x face
+        const V4 hx_jm = ld4(f.H[0] + e - ojm);
+        const bool upd[4] = {!fx0, true, true, true};
+        float d1[4], d2[4], k1[4] = {1.f, 1.f, 1.f, 1.f}, k2[4] = {1.f, 1.f, 1.f, 1.f}, p1[4] = {0.f, 0.f, 0.f, 0.f},
+              p2[4] = {0.f, 0.f, 0.f, 0.f}, curl[4];
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            d1[m] = (hy.v[m] - (m > 0 ? hy.v[m - 1] : hy_im)) * rx;
+            d2[m] = (hx.v[m] - hx_jm.v[m]) * ry;
+        }
+        if (s0 >= 0) psi4(f.psiE[0][1], apsi(g.n, g.L, 0, s0, i0, j, k), f.bE[0], f.aE[0], f.ikE[0], i0, true, d1, upd, p1, k1);
+        if (s1 >= 0) psi4(f.psiE[1][0], apsi(g.n, g.L, 1, s1, i0, j, k), f.bE[1], f.aE[1], f.ikE[1], j, false, d2, upd, p2, k2);
+#pragma unroll
+        for (int m = 0; m < 4; m++) curl[m] = k1[m] * d1[m] + p1[m] - k2[m] * d2[m] - p2[m];
+        fwd_ampere4(g, f, 2, e, k, n, curl, zero, upd);
+    }
+}
+
+// Transposed Eq. 6 on the design edges among the four (stored E^n, J^n),
+// then lambda_E of component c goes back to memory.
+__device__ __forceinline__ void adj_ampere4(const AGrid<float> &g, const AState<float> &f, int c, long long e, int k,
+                                            long long n, V4 &l, const bool upd[4]) {
+    if (k >= g.ks0 && k < g.ks1) {
+        const int4 s4 = *reinterpret_cast<const int4 *>(f.slot[c] + e);
+        const int sl[4] = {s4.x, s4.y, s4.z, s4.w};
+        const long long ne = f.soff[3];
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            if (sl[m] < 0 || !upd[m]) continue;
+            const long long row = n * ne + sl[m];
+            const float LJ = f.lJ[c][e + m] - g.cE * l.v[m];  // adjoint of J^{n+1}
+            f.gb[sl[m]] += (double)LJ * (double)f.stE[row];
+            f.gk[sl[m]] += (double)LJ * (double)f.stJ[row];
+            f.lJ[c][e + m] = (1.f + g.kJm1) * LJ;
+            l.v[m] = l.v[m] + f.beta[sl[m]] * LJ;
+        }
+    }
+    st4(f.lE[c] + e, l);
+}
+
+// transposed psi recursion of one axis (adjoint side): ap = psi + s cE l,
+// A = s cE kappa^-1 l + a ap, psi <- (1 + b) ap; held cells keep psi and A = 0
+__device__ __forceinline__ void psi4_adj(float *psi, long long q, const float *bb, const float *aa, const float *ik,
+                                         int x0, bool per_cell, float s, float cE, const V4 &l, const bool upd[4],
+                                         float A[4]) {
+    V4 o = ld4(psi + q);
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+        const int x = per_cell ? x0 + m : x0;
+        const float ap = o.v[m] + s * cE * l.v[m];
+        const float Am = s * cE * ik[x] * l.v[m] + aa[x] * ap;
+        if (upd[m]) {
+            A[m] = Am;
+            o.v[m] = (1.f + bb[x]) * ap;
+        }
+    }
+    st4(psi + q, o);
+}
+
+__global__ void __launch_bounds__(256) k_adj_E4(AGrid<float> g, AState<float> f, Probe pr, const double *F) {
+    pdl_wait();
+    pdl_release();
+    const long long n = *f.n - 1;
+    int i0, j, k;
+    if (!group_of(g, i0, j, k)) return;
+    const int nx = g.n[0], ny = g.n[1];
+    const long long sy = nx, sz = (long long)nx * ny, e = k * sz + j * sy + i0;
+#pragma unroll
+    for (int m = 0; m < 4; m++) probe_source(f, pr, F, n, i0 + m, j, k, e + m);
+    const bool fx0 = i0 == 0, fy = j == 0, fz = k == 0;
+    const int s0 = aslab(g.L, nx, i0), s1 = aslab(g.L, ny, j), s2 = aslab(g.L, g.n[2], k);
+    const float cE = g.cE, rx = g.r[0], ry = g.r[1], rz = g.r[2];
+    // what the group adds to lambda_H: its own cells, and the groups at -y, -z, -x
+    float own[3][4] = {}, hz_ym[4] = {}, hy_zm[4] = {}, hx_zm[4] = {}, hx_ym[4] = {};
+    float hz_xm = 0.f, hy_xm = 0.f;
+    if (!(fy || fz)) {  // Ex: curl = ky dHz/dy + py - kz dHy/dz - pz
+        V4 l = ld4(f.lE[0] + e);
+        const bool upd[4] = {true, true, true, true};
+        float Ay[4], Az[4];
+#pragma unroll
+        for (int m = 0; m < 4; m++) { Ay[m] = cE * l.v[m]; Az[m] = -cE * l.v[m]; }
+        if (s1 >= 0) psi4_adj(f.lpsiE[1][1], apsi(g.n, g.L, 1, s1, i0, j, k), f.bE[1], f.aE[1], f.ikE[1], j, false, 1.f, cE, l, upd, Ay);
+        if (s2 >= 0) psi4_adj(f.lpsiE[2][0], apsi(g.n, g.L, 2, s2, i0, j, k), f.bE[2], f.aE[2], f.ikE[2], k, false, -1.f, cE, l, upd, Az);
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            own[2][m] += ry * Ay[m];
+            hz_ym[m] -= ry * Ay[m];
+            own[1][m] += rz * Az[m];
+            hy_zm[m] -= rz * Az[m];
+        }
+        adj_ampere4(g, f, 0, e, k, n, l, upd);
+    }
+    if (!fz) {  // Ey: curl = kz dHx/dz + pz - kx dHz/dx - px; cell 0 held on the x face
+        V4 l = ld4(f.lE[1] + e);
+        const bool upd[4] = {!fx0, true, true, true};
+        float Az[4], Ax[4];
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            Az[m] = upd[m] ? cE * l.v[m] : 0.f;
+            Ax[m] = upd[m] ? -cE * l.v[m] : 0.f;
+        }
+        if (s2 >= 0) psi4_adj(f.lpsiE[2][1], apsi(g.n, g.L, 2, s2, i0, j, k), f.bE[2], f.aE[2], f.ikE[2], k, false, 1.f, cE, l, upd, Az);
+        if (s0 >= 0) psi4_adj(f.lpsiE[0][0], apsi(g.n, g.L, 0, s0, i0, j, k), f.bE[0], f.aE[0], f.ikE[0], i0, true, -1.f, cE, l, upd, Ax);
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            own[0][m] += rz * Az[m];
+            hx_zm[m] -= rz * Az[m];
+            own[2][m] += rx * Ax[m];
+            if (m > 0) own[2][m - 1] -= rx * Ax[m];
+        }
+        hz_xm -= rx * Ax[0];
+        adj_ampere4(g, f, 1, e, k, n, l, upd);
+    }
+    if (!fy) {  // Ez: curl = kx dHy/dx + px - ky dHx/dy - py; cell 0 held on the x face
+        V4 l = ld4(f.lE[2] + e);
+        const bool upd[4] = {!fx0, true, true, true};
+        float Ax[4], Ay[4];
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            Ax[m] = upd[m] ? cE * l.v[m] : 0.f;
+            Ay[m] = upd[m] ? -cE * l.v[m] : 0.f;
+        }
+        if (s0 >= 0) psi4_adj(f.lpsiE[0][1], apsi(g.n, g.L, 0, s0, i0, j, k), f.bE[0], f.aE[0], f.ikE[0], i0, true, 1.f, cE, l, upd, Ax);
+        if (s1 >= 0) psi4_adj(f.lpsiE[1][0], apsi(g.n, g.L, 1, s1, i0, j, k), f.bE[1], f.aE[1], f.ikE[1], j, false, -1.f, cE, l, upd, Ay);
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            own[1][m] += rx * Ax[m];
+            if (m > 0) own[1][m - 1] -= rx * Ax[m];
+            own[0][m] += ry * Ay[m];
+            hx_ym[m] -= ry * Ay[m];
+        }
+        hy_xm -= rx * Ax[0];
+        adj_ampere4(g, f, 2, e, k, n, l, upd);
+    }
+    add4(f.lH[0] + e, V4{{own[0][0], own[0][1], own[0][2], own[0][3]}});
+    add4(f.lH[1] + e, V4{{own[1][0], own[1][1], own[1][2], own[1][3]}});
+    add4(f.lH[2] + e, V4{{own[2][0], own[2][1], own[2][2], own[2][3]}});
+    if (!(fy || fz)) {
+        add4(f.lH[2] + e - sy, V4{{hz_ym[0], hz_ym[1], hz_ym[2], hz_ym[3]}});
+        add4(f.lH[1] + e - sz, V4{{hy_zm[0], hy_zm[1], hy_zm[2], hy_zm[3]}});
+    }
+    if (!fz) add4(f.lH[0] + e - sz, V4{{hx_zm[0], hx_zm[1], hx_zm[2], hx_zm[3]}});
+    if (!fy) add4(f.lH[0] + e - sy, V4{{hx_ym[0], hx_ym[1], hx_ym[2], hx_ym[3]}});
+    if (i0 > 0) {
+        if (!fz) atomicAdd(f.lH[2] + e - 1, hz_xm);
+        if (!fy) atomicAdd(f.lH[1] + e - 1, hy_xm);
+    }
+}
+
+// transposed psi_H recursion of one axis: p = psi + sg cH l (l the lambda_H
+// the psi term enters), A = sg cH kappa^-1 l + a p, psi <- (1 + b) p
+__device__ __forceinline__ void psiH4_adj(float *psi, long long q, float b1, float a, float ik, float sg, float cH,
+                                          const float l[4], float A[4]) {
+    V4 o = ld4(psi + q);
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+        const float p = o.v[m] + sg * cH * l[m];
+        A[m] = sg * cH * ik * l[m] + a * p;
+        o.v[m] = b1 * p;
+    }
+    st4(psi + q, o);
+}
+
+__global__ void __launch_bounds__(256) k_adj_H4(AGrid<float> g, AState<float> f) {
+    pdl_wait();
+    pdl_release();
+    if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0) *f.n -= 1;
+    int i0, j, k;
+    if (!group_of(g, i0, j, k)) return;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const long long sy = nx, sz = (long long)nx * ny, e = k * sz + j * sy + i0;
+    const V4 LX = ld4(f.lH[0] + e), LY = ld4(f.lH[1] + e), LZ = ld4(f.lH[2] + e);
+    const float cH = g.cH, rx = g.r[0], ry = g.r[1], rz = g.r[2];
+    // adjoints of the six differences (forward differences of E)
+    float Azy[4], Ayz[4], Axz[4], Azx[4], Ayx[4], Axy[4];
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+        Azy[m] = -cH * LX.v[m]; Ayz[m] = cH * LX.v[m];
+        Axz[m] = -cH * LY.v[m]; Azx[m] = cH * LY.v[m];
+        Ayx[m] = -cH * LZ.v[m]; Axy[m] = cH * LZ.v[m];
+    }
+    const int s0 = aslab(g.L, nx, i0), s1 = aslab(g.L, ny, j), s2 = aslab(g.L, nz, k);
+    if (s0 >= 0) {  // per-cell profiles along x
+        const long long q = apsi(g.n, g.L, 0, s0, i0, j, k);
+        V4 o0 = ld4(f.lpsiH[0][0] + q), o1 = ld4(f.lpsiH[0][1] + q);
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            const float a = f.aH[0][i0 + m], kk = f.ikH[0][i0 + m], b1 = 1.f + f.bH[0][i0 + m];
+            const float pxy = o0.v[m] + cH * LY.v[m], pxz = o1.v[m] - cH * LZ.v[m];
+            Azx[m] = cH * kk * LY.v[m] + a * pxy;
+            Ayx[m] = -cH * kk * LZ.v[m] + a * pxz;
+            o0.v[m] = b1 * pxy;
+            o1.v[m] = b1 * pxz;
+        }
+        st4(f.lpsiH[0][0] + q, o0);
+        st4(f.lpsiH[0][1] + q, o1);
+    }
+    if (s1 >= 0) {
+        const long long q = apsi(g.n, g.L, 1, s1, i0, j, k);
+        const float a = f.aH[1][j], kk = f.ikH[1][j], b1 = 1.f + f.bH[1][j];
+        psiH4_adj(f.lpsiH[1][0], q, b1, a, kk, 1.f, cH, LZ.v, Axy);
+        psiH4_adj(f.lpsiH[1][1], q, b1, a, kk, -1.f, cH, LX.v, Azy);
+    }
+    if (s2 >= 0) {
+        const long long q = apsi(g.n, g.L, 2, s2, i0, j, k);
+        const float a = f.aH[2][k], kk = f.ikH[2][k], b1 = 1.f + f.bH[2][k];
+        psiH4_adj(f.lpsiH[2][0], q, b1, a, kk, 1.f, cH, LX.v, Ayz);
+        psiH4_adj(f.lpsiH[2][1], q, b1, a, kk, -1.f, cH, LY.v, Axz);
+    }
+    // d = (E[e' + e_a] - E[e']) r, E beyond the high face zero: the own cell
+    // gets -r A, the cell at +e_a gets +r A
+    float own[3][4], e2_yp[4], e0_yp[4], e1_zp[4], e0_zp[4];
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+        own[2][m] = -ry * Azy[m] - rx * Azx[m] + (m > 0 ? rx * Azx[m - 1] : 0.f);
+        own[1][m] = -rz * Ayz[m] - rx * Ayx[m] + (m > 0 ? rx * Ayx[m - 1] : 0.f);
+        own[0][m] = -rz * Axz[m] - ry * Axy[m];
+        e2_yp[m] = ry * Azy[m];
+        e0_yp[m] = ry * Axy[m];
+        e1_zp[m] = rz * Ayz[m];
+        e0_zp[m] = rz * Axz[m];
+    }
+    add4(f.lE[0] + e, V4{{own[0][0], own[0][1], own[0][2], own[0][3]}});
+    add4(f.lE[1] + e, V4{{own[1][0], own[1][1], own[1][2], own[1][3]}});
+    add4(f.lE[2] + e, V4{{own[2][0], own[2][1], own[2][2], own[2][3]}});
+    if (j + 1 < ny) {
+        add4(f.lE[2] + e + sy, V4{{e2_yp[0], e2_yp[1], e2_yp[2], e2_yp[3]}});
+        add4(f.lE[0] + e + sy, V4{{e0_yp[0], e0_yp[1], e0_yp[2], e0_yp[3]}});
+    }
+    if (k + 1 < nz) {
+        add4(f.lE[1] + e + sz, V4{{e1_zp[0], e1_zp[1], e1_zp[2], e1_zp[3]}});
+        add4(f.lE[0] + e + sz, V4{{e0_zp[0], e0_zp[1], e0_zp[2], e0_zp[3]}});
+    }
+    if (i0 + 4 < nx) {
+        atomicAdd(f.lE[2] + e + 4, rx * Azx[3]);
+        atomicAdd(f.lE[1] + e + 4, rx * Ayx[3]);
+    }
+}
+
 // ------------------------------------------------------------------ host --
 struct AdjBase {
     virtual ~AdjBase() {}
@@ -435,6 +883,7 @@ struct AdjSim : AdjBase {
     double *d_F = nullptr;
     double F[2] = {0, 0};
     cudaStream_t stream = nullptr;
+    bool use4 = false;  // FP32 with four-cell groups (nx and the CPML width multiples of 4)
     static constexpr int GRAPH_STEPS = 64;  // steps per captured graph (forward and backward)
     cudaGraphExec_t gfwd = nullptr, gbwd = nullptr;
     double wp_last = 0, gamma_last = 0;
@@ -494,6 +943,7 @@ struct AdjSim : AdjBase {
             if (k < c->design_k0 || k >= c->design_k1) return -1;
             return ((long long)(k - c->design_k0) * ny + j) * nx + i;
         };
+        use4 = std::is_same<T, float>::value && nx % 4 == 0 && g.L % 4 == 0 && !(c->flags & 1);
         g.ks0 = std::max(0, (int)c->design_k0 - 1);
         g.ks1 = std::min(nz, (int)c->design_k1 + 1);
         std::vector<int> slot_h[3];
@@ -668,6 +1118,15 @@ struct AdjSim : AdjBase {
     // 32 x 8 threads over (x, y), one plane z per grid layer
     static dim3 block3() { return dim3(32, 8, 1); }
     dim3 grid3() const { return dim3((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, g.n[2]); }
+    // four-cell groups: 32 (or 16, when that divides the row and 32 does not) groups along x
+    dim3 block4() const {
+        const int groups = g.n[0] / 4;
+        return (groups % 32 != 0 && groups % 16 == 0) ? dim3(16, 16, 1) : dim3(32, 8, 1);
+    }
+    dim3 grid4() const {
+        const dim3 b = block4();
+        return dim3((g.n[0] / 4 + b.x - 1) / b.x, (g.n[1] + b.y - 1) / b.y, g.n[2]);
+    }
 
     T kJm1_captured = T(0);
     void drop_graphs() {
@@ -677,6 +1136,16 @@ struct AdjSim : AdjBase {
     }
     void launch_forward_steps(int count) {
         const dim3 gr = grid3(), bl = block3();
+        if constexpr (std::is_same<T, float>::value) {
+            if (use4) {
+                const dim3 g4 = grid4(), b4 = block4();
+                for (int q = 0; q < count; q++) {
+                    launch_pdl(k_fwd_H4, g4, b4, 0, stream, g, f, pr, d_F);
+                    launch_pdl(k_fwd_E4, g4, b4, 0, stream, g, f, bu, cfg.dt);
+                }
+                return;
+            }
+        }
         for (int q = 0; q < count; q++) {
             launch_pdl(k_fwd_H<T>, gr, bl, 0, stream, g, f, pr, d_F);
             launch_pdl(k_fwd_E<T>, gr, bl, 0, stream, g, f, bu, cfg.dt);
@@ -684,6 +1153,16 @@ struct AdjSim : AdjBase {
     }
     void launch_backward_steps(int count) {
         const dim3 gr = grid3(), bl = block3();
+        if constexpr (std::is_same<T, float>::value) {
+            if (use4) {
+                const dim3 g4 = grid4(), b4 = block4();
+                for (int q = 0; q < count; q++) {
+                    launch_pdl(k_adj_E4, g4, b4, 0, stream, g, f, pr, (const double *)d_F);
+                    launch_pdl(k_adj_H4, g4, b4, 0, stream, g, f);
+                }
+                return;
+            }
+        }
         for (int q = 0; q < count; q++) {
             launch_pdl(k_adj_E<T>, gr, bl, 0, stream, g, f, pr, (const double *)d_F);
             launch_pdl(k_adj_H<T>, gr, bl, 0, stream, g, f);

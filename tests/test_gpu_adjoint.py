@@ -12,6 +12,9 @@
   derivative itself (wp, gamma), at a relative step of 1e-4.
 - The FP32 path's gradient against the FP64 one, and the torch.autograd
   wrapper against the direct call.
+- The FP32 kernels with four x cells per thread (nx and the CPML width
+  multiples of 4) against the one-cell FP32 kernels (flags bit 0) and the
+  FP64 path on the same study.
 """
 import numpy as np
 import pytest
@@ -113,3 +116,22 @@ def test_gradient_matches_the_oracle(A, precision, tol):
     assert np.linalg.norm(dm - dm0) <= tol * np.linalg.norm(dm0)
     assert abs(dwp / dwp0 - 1) <= tol, (dwp, dwp0)
     assert abs(dga / dga0 - 1) <= tol, (dga, dga0)
+
+
+def test_four_cell_fp32_kernels_match_one_cell_and_fp64(A):
+    from paper_1505_04007_gb300 import pic
+    res = {}
+    for name, prec, flags in (("four", pic.PIC_FP32, 0), ("one", pic.PIC_FP32, 1), ("fp64", pic.PIC_FP64, 0)):
+        cfg = A.film_config(nx=48, ny=24, nz=40, design=(10, 16), nsteps=400, sigma=4e-9, cpml=8, precision=prec)
+        cfg.flags = flags
+        st = A.Adjoint(cfg)
+        mask = np.random.default_rng(17).uniform(0.2, 0.8, st.n)
+        loss = st.forward(mask, WP, GAMMA)
+        res[name] = (loss, *st.backward())
+        st.close()
+    for ref, tol in (("one", 1e-4), ("fp64", 1e-3)):
+        L0, dm0, dw0, dg0 = res[ref]
+        L, dm, dw, dg = res["four"]
+        assert abs(L / L0 - 1) <= tol / 10, (ref, L, L0)
+        assert np.linalg.norm(dm - dm0) <= tol * np.linalg.norm(dm0), ref
+        assert abs(dw / dw0 - 1) <= tol and abs(dg / dg0 - 1) <= tol, (ref, dw, dw0, dg, dg0)
