@@ -412,13 +412,16 @@ __global__ void __launch_bounds__(256) k_adj_H(AGrid<T> g, AState<T> f) {
 }
 
 // ------------------------------------------- FP32, four cells per thread --
-// The same four kernels for FP32 state with four consecutive x cells per
-// thread (nx and the CPML width multiples of 4, so a group lies wholly
-// inside or outside the x slabs): every centre, row and plane access is one
-// 16-byte load or store, and the transposed updates add into a neighbouring
-// group with one 16-byte atomic instead of four (the contributions a group
-// makes to its own cells are summed first).  Per cell the arithmetic is that
-// of the kernels above; only the order of the atomic sums differs.
+// The forward H and E kernels and the transposed H update for FP32 state with
+// four consecutive x cells per thread (nx and the CPML width multiples of 4,
+// so a group lies wholly inside or outside the x slabs): every centre, row
+// and plane access is one 16-byte load or store, and the transposed H update
+// adds into a neighbouring group with one 16-byte atomic instead of four (the
+// contributions a group makes to its own cells are summed first).  Per cell
+// the arithmetic is that of the kernels above; only the order of the atomic
+// sums differs.  The transposed E update keeps the one-cell kernel: its
+// four-cell form measured slower (35.7 against 31.1 us per launch at
+// 192x96x96).
 struct V4 {
     float v[4];
 };
@@ -634,137 +637,6 @@ __global__ void __launch_bounds__(256) k_fwd_E4(AGrid<float> g, AState<float> f,
 #pragma unroll
         for (int m = 0; m < 4; m++) curl[m] = k1[m] * d1[m] + p1[m] - k2[m] * d2[m] - p2[m];
         fwd_ampere4(g, f, 2, e, k, n, curl, zero, upd);
-    }
-}
-
-// Transposed Eq. 6 on the design edges among the four (stored E^n, J^n),
-// then lambda_E of component c goes back to memory.
-__device__ __forceinline__ void adj_ampere4(const AGrid<float> &g, const AState<float> &f, int c, long long e, int k,
-                                            long long n, V4 &l, const bool upd[4]) {
-    if (k >= g.ks0 && k < g.ks1) {
-        const int4 s4 = *reinterpret_cast<const int4 *>(f.slot[c] + e);
-        const int sl[4] = {s4.x, s4.y, s4.z, s4.w};
-        const long long ne = f.soff[3];
-#pragma unroll
-        for (int m = 0; m < 4; m++) {
-            if (sl[m] < 0 || !upd[m]) continue;
-            const long long row = n * ne + sl[m];
-            const float LJ = f.lJ[c][e + m] - g.cE * l.v[m];  // adjoint of J^{n+1}
-            f.gb[sl[m]] += (double)LJ * (double)f.stE[row];
-            f.gk[sl[m]] += (double)LJ * (double)f.stJ[row];
-            f.lJ[c][e + m] = (1.f + g.kJm1) * LJ;
-            l.v[m] = l.v[m] + f.beta[sl[m]] * LJ;
-        }
-    }
-    st4(f.lE[c] + e, l);
-}
-
-// transposed psi recursion of one axis (adjoint side): ap = psi + s cE l,
-// A = s cE kappa^-1 l + a ap, psi <- (1 + b) ap; held cells keep psi and A = 0
-__device__ __forceinline__ void psi4_adj(float *psi, long long q, const float *bb, const float *aa, const float *ik,
-                                         int x0, bool per_cell, float s, float cE, const V4 &l, const bool upd[4],
-                                         float A[4]) {
-    V4 o = ld4(psi + q);
-#pragma unroll
-    for (int m = 0; m < 4; m++) {
-        const int x = per_cell ? x0 + m : x0;
-        const float ap = o.v[m] + s * cE * l.v[m];
-        const float Am = s * cE * ik[x] * l.v[m] + aa[x] * ap;
-        if (upd[m]) {
-            A[m] = Am;
-            o.v[m] = (1.f + bb[x]) * ap;
-        }
-    }
-    st4(psi + q, o);
-}
-
-__global__ void __launch_bounds__(256) k_adj_E4(AGrid<float> g, AState<float> f, Probe pr, const double *F) {
-    pdl_wait();
-    pdl_release();
-    const long long n = *f.n - 1;
-    int i0, j, k;
-    if (!group_of(g, i0, j, k)) return;
-    const int nx = g.n[0], ny = g.n[1];
-    const long long sy = nx, sz = (long long)nx * ny, e = k * sz + j * sy + i0;
-#pragma unroll
-    for (int m = 0; m < 4; m++) probe_source(f, pr, F, n, i0 + m, j, k, e + m);
-    const bool fx0 = i0 == 0, fy = j == 0, fz = k == 0;
-    const int s0 = aslab(g.L, nx, i0), s1 = aslab(g.L, ny, j), s2 = aslab(g.L, g.n[2], k);
-    const float cE = g.cE, rx = g.r[0], ry = g.r[1], rz = g.r[2];
-    // what the group adds to lambda_H: its own cells, and the groups at -y, -z, -x
-    float own[3][4] = {}, hz_ym[4] = {}, hy_zm[4] = {}, hx_zm[4] = {}, hx_ym[4] = {};
-    float hz_xm = 0.f, hy_xm = 0.f;
-    if (!(fy || fz)) {  // Ex: curl = ky dHz/dy + py - kz dHy/dz - pz
-        V4 l = ld4(f.lE[0] + e);
-        const bool upd[4] = {true, true, true, true};
-        float Ay[4], Az[4];
-#pragma unroll
-        for (int m = 0; m < 4; m++) { Ay[m] = cE * l.v[m]; Az[m] = -cE * l.v[m]; }
-        if (s1 >= 0) psi4_adj(f.lpsiE[1][1], apsi(g.n, g.L, 1, s1, i0, j, k), f.bE[1], f.aE[1], f.ikE[1], j, false, 1.f, cE, l, upd, Ay);
-        if (s2 >= 0) psi4_adj(f.lpsiE[2][0], apsi(g.n, g.L, 2, s2, i0, j, k), f.bE[2], f.aE[2], f.ikE[2], k, false, -1.f, cE, l, upd, Az);
-#pragma unroll
-        for (int m = 0; m < 4; m++) {
-            own[2][m] += ry * Ay[m];
-            hz_ym[m] -= ry * Ay[m];
-            own[1][m] += rz * Az[m];
-            hy_zm[m] -= rz * Az[m];
-        }
-        adj_ampere4(g, f, 0, e, k, n, l, upd);
-    }
-    if (!fz) {  // Ey: curl = kz dHx/dz + pz - kx dHz/dx - px; cell 0 held on the x face
-        V4 l = ld4(f.lE[1] + e);
-        const bool upd[4] = {!fx0, true, true, true};
-        float Az[4], Ax[4];
-#pragma unroll
-        for (int m = 0; m < 4; m++) {
-            Az[m] = upd[m] ? cE * l.v[m] : 0.f;
-            Ax[m] = upd[m] ? -cE * l.v[m] : 0.f;
-        }
-        if (s2 >= 0) psi4_adj(f.lpsiE[2][1], apsi(g.n, g.L, 2, s2, i0, j, k), f.bE[2], f.aE[2], f.ikE[2], k, false, 1.f, cE, l, upd, Az);
-        if (s0 >= 0) psi4_adj(f.lpsiE[0][0], apsi(g.n, g.L, 0, s0, i0, j, k), f.bE[0], f.aE[0], f.ikE[0], i0, true, -1.f, cE, l, upd, Ax);
-#pragma unroll
-        for (int m = 0; m < 4; m++) {
-            own[0][m] += rz * Az[m];
-            hx_zm[m] -= rz * Az[m];
-            own[2][m] += rx * Ax[m];
-            if (m > 0) own[2][m - 1] -= rx * Ax[m];
-        }
-        hz_xm -= rx * Ax[0];
-        adj_ampere4(g, f, 1, e, k, n, l, upd);
-    }
-    if (!fy) {  // Ez: curl = kx dHy/dx + px - ky dHx/dy - py; cell 0 held on the x face
-        V4 l = ld4(f.lE[2] + e);
-        const bool upd[4] = {!fx0, true, true, true};
-        float Ax[4], Ay[4];
-#pragma unroll
-        for (int m = 0; m < 4; m++) {
-            Ax[m] = upd[m] ? cE * l.v[m] : 0.f;
-            Ay[m] = upd[m] ? -cE * l.v[m] : 0.f;
-        }
-        if (s0 >= 0) psi4_adj(f.lpsiE[0][1], apsi(g.n, g.L, 0, s0, i0, j, k), f.bE[0], f.aE[0], f.ikE[0], i0, true, 1.f, cE, l, upd, Ax);
-        if (s1 >= 0) psi4_adj(f.lpsiE[1][0], apsi(g.n, g.L, 1, s1, i0, j, k), f.bE[1], f.aE[1], f.ikE[1], j, false, -1.f, cE, l, upd, Ay);
-#pragma unroll
-        for (int m = 0; m < 4; m++) {
-            own[1][m] += rx * Ax[m];
-            if (m > 0) own[1][m - 1] -= rx * Ax[m];
-            own[0][m] += ry * Ay[m];
-            hx_ym[m] -= ry * Ay[m];
-        }
-        hy_xm -= rx * Ax[0];
-        adj_ampere4(g, f, 2, e, k, n, l, upd);
-    }
-    add4(f.lH[0] + e, V4{{own[0][0], own[0][1], own[0][2], own[0][3]}});
-    add4(f.lH[1] + e, V4{{own[1][0], own[1][1], own[1][2], own[1][3]}});
-    add4(f.lH[2] + e, V4{{own[2][0], own[2][1], own[2][2], own[2][3]}});
-    if (!(fy || fz)) {
-        add4(f.lH[2] + e - sy, V4{{hz_ym[0], hz_ym[1], hz_ym[2], hz_ym[3]}});
-        add4(f.lH[1] + e - sz, V4{{hy_zm[0], hy_zm[1], hy_zm[2], hy_zm[3]}});
-    }
-    if (!fz) add4(f.lH[0] + e - sz, V4{{hx_zm[0], hx_zm[1], hx_zm[2], hx_zm[3]}});
-    if (!fy) add4(f.lH[0] + e - sy, V4{{hx_ym[0], hx_ym[1], hx_ym[2], hx_ym[3]}});
-    if (i0 > 0) {
-        if (!fz) atomicAdd(f.lH[2] + e - 1, hz_xm);
-        if (!fy) atomicAdd(f.lH[1] + e - 1, hy_xm);
     }
 }
 
@@ -1157,7 +1029,7 @@ struct AdjSim : AdjBase {
             if (use4) {
                 const dim3 g4 = grid4(), b4 = block4();
                 for (int q = 0; q < count; q++) {
-                    launch_pdl(k_adj_E4, g4, b4, 0, stream, g, f, pr, (const double *)d_F);
+                    launch_pdl(k_adj_E<T>, gr, bl, 0, stream, g, f, pr, (const double *)d_F);
                     launch_pdl(k_adj_H4, g4, b4, 0, stream, g, f);
                 }
                 return;
