@@ -8,12 +8,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <memory>
 #include <string>
+#include <thread>
 #include <type_traits>
 #include <unordered_map>
 #include <vector>
@@ -298,85 +300,141 @@ struct Sim : SimBase {
 
     int build_tables(const pic_config *c, std::vector<uint8_t> ecls[3], std::vector<T> cls[3],
                      std::vector<uint8_t> &cls_metal) {
-        // distinct multisets of the four cell ids around an edge -> class,
-        // numbered in order of first appearance (components 0, 1, 2)
-        std::unordered_map<uint32_t, int> classes;
+        // Edge classes: distinct multisets of the four cell ids around an edge,
+        // numbered in order of first appearance over components 0, 1, 2 and
+        // cells in memory order.  Host threads scan slabs of planes with
+        // classes numbered per slab; the merge then numbers them in slab
+        // order, which gives exactly the serial numbering.
         const uint8_t *mat = c->material_id;
+        const int nx = n[0], ny = n[1], nz = n[2];
+        const size_t stride[3] = {1, (size_t)nx, (size_t)nx * ny};
         auto wrapc = [&](int a, int x) {
             if (x < 0) return g.per[a] ? x + n[a] : 0;
             if (x >= n[a]) return g.per[a] ? x - n[a] : n[a] - 1;
             return x;
         };
+        const int hw = (int)std::thread::hardware_concurrency();
+        const int nthr = std::max(1, std::min({hw > 0 ? hw : 1, 16, nz}));
+        struct Part {
+            std::vector<uint32_t> keys;  // local class -> key
+            bool overflow = false;
+        };
+        std::vector<Part> part((size_t)3 * nthr);
+        for (int comp = 0; comp < 3; comp++) ecls[comp].resize((size_t)N);
+        auto scan = [&](int t) {
+            const int k0 = (int)((long long)nz * t / nthr), k1 = (int)((long long)nz * (t + 1) / nthr);
+            for (int comp = 0; comp < 3; comp++) {
+                Part &P = part[(size_t)comp * nthr + t];
+                std::unordered_map<uint32_t, int> seen;
+                uint8_t *out = ecls[comp].data();
+                const int a1 = (comp + 1) % 3, a2 = (comp + 2) % 3;
+                const size_t o1 = stride[a1], o2 = stride[a2];
+                uint32_t last_key = 0xffffffffu;
+                int last_cls = -1;
+                for (int k = k0; k < k1; k++)
+                    for (int j = 0; j < ny; j++)
+                        for (int i = 0; i < nx; i++) {
+                            const int x3[3] = {i, j, k};
+                            const size_t e = ((size_t)k * ny + j) * nx + i;
+                            int ids[4];
+                            if (x3[a1] > 0 && x3[a2] > 0) {  // no face: the four cells by their offsets
+                                ids[0] = mat[e];
+                                ids[1] = mat[e - o1];
+                                ids[2] = mat[e - o2];
+                                ids[3] = mat[e - o1 - o2];
+                            } else {
+                                int q = 0;
+                                for (int s1 = -1; s1 <= 0; s1++)
+                                    for (int s2 = -1; s2 <= 0; s2++) {
+                                        int p3[3] = {i, j, k};
+                                        p3[a1] = wrapc(a1, p3[a1] + s1);
+                                        p3[a2] = wrapc(a2, p3[a2] + s2);
+                                        ids[q++] = mat[((size_t)p3[2] * ny + p3[1]) * nx + p3[0]];
+                                    }
+                            }
+                            uint32_t key;
+                            if (ids[0] == ids[1] && ids[0] == ids[2] && ids[0] == ids[3]) {
+                                key = (uint32_t)ids[0] * 0x01010101u;  // one material (most edges)
+                            } else {
+                                std::sort(ids, ids + 4);
+                                key = (uint32_t)ids[0] | (uint32_t)ids[1] << 8 | (uint32_t)ids[2] << 16 |
+                                      (uint32_t)ids[3] << 24;
+                            }
+                            int cl = last_cls;
+                            if (key != last_key) {
+                                auto it = seen.find(key);
+                                if (it == seen.end()) {
+                                    if ((int)seen.size() >= 256) {
+                                        P.overflow = true;
+                                        return;
+                                    }
+                                    cl = (int)seen.size();
+                                    seen[key] = cl;
+                                    P.keys.push_back(key);
+                                } else {
+                                    cl = it->second;
+                                }
+                                last_key = key;
+                                last_cls = cl;
+                            }
+                            out[e] = (uint8_t)cl;
+                        }
+            }
+        };
+        auto run_all = [&](auto &&fn) {
+            std::vector<std::thread> pool;
+            for (int t = 1; t < nthr; t++) pool.emplace_back(fn, t);
+            fn(0);
+            for (auto &th : pool) th.join();
+        };
+        run_all(scan);
+        // merge: global numbers in (component, slab) order; per slab a local -> global table
         for (int q3 = 0; q3 < 3; q3++) cls[q3].assign(256, (T)0);
         cls_metal.assign(256, 0);
-        const int nx = n[0], ny = n[1], nz = n[2];
-        const size_t stride[3] = {1, (size_t)nx, (size_t)nx * ny};
-        for (int comp = 0; comp < 3; comp++) {
-            ecls[comp].resize((size_t)N);
-            uint8_t *out = ecls[comp].data();
-            const int a1 = (comp + 1) % 3, a2 = (comp + 2) % 3;
-            const size_t o1 = stride[a1], o2 = stride[a2];
-            uint32_t last_key = 0xffffffffu;
-            int last_cls = -1;
-            for (int k = 0; k < nz; k++)
-                for (int j = 0; j < ny; j++)
-                    for (int i = 0; i < nx; i++) {
-                        const int x3[3] = {i, j, k};
-                        const size_t e = ((size_t)k * ny + j) * nx + i;
-                        int ids[4];
-                        if (x3[a1] > 0 && x3[a2] > 0) {  // no face: the four cells by their offsets
-                            ids[0] = mat[e];
-                            ids[1] = mat[e - o1];
-                            ids[2] = mat[e - o2];
-                            ids[3] = mat[e - o1 - o2];
-                        } else {
-                            int t = 0;
-                            for (int s1 = -1; s1 <= 0; s1++)
-                                for (int s2 = -1; s2 <= 0; s2++) {
-                                    int p3[3] = {i, j, k};
-                                    p3[a1] = wrapc(a1, p3[a1] + s1);
-                                    p3[a2] = wrapc(a2, p3[a2] + s2);
-                                    ids[t++] = mat[((size_t)p3[2] * ny + p3[1]) * nx + p3[0]];
-                                }
-                        }
-                        uint32_t key;
-                        if (ids[0] == ids[1] && ids[0] == ids[2] && ids[0] == ids[3]) {
-                            key = (uint32_t)ids[0] * 0x01010101u;  // one material (most edges)
-                        } else {
-                            std::sort(ids, ids + 4);
-                            key = (uint32_t)ids[0] | (uint32_t)ids[1] << 8 | (uint32_t)ids[2] << 16 |
-                                  (uint32_t)ids[3] << 24;
-                        }
-                        int cl = last_cls;
-                        if (key != last_key) {
-                            auto it = classes.find(key);
-                            if (it == classes.end()) {
-                                if ((int)classes.size() >= 256)
-                                    return fail(PIC_ERR_UNSUPPORTED, "more than 256 distinct edge materials");
-                                cl = (int)classes.size();
-                                classes[key] = cl;
-                                double sw = 0, swg = 0, se = 0;
-                                for (int q4 = 0; q4 < 4; q4++) {
-                                    const pic_material &mt = c->materials[ids[q4]];
-                                    sw += mt.wp * mt.wp;
-                                    swg += mt.wp * mt.wp * mt.gamma;
-                                    se += mt.eps_inf;
-                                }
-                                const double wp2 = sw / 4.0, gam = sw > 0 ? swg / sw : 0.0, einf = se / 4.0;
-                                const double dt = c->dt;
-                                cls[0][cl] = (T)(-2.0 * gam * dt / (2.0 + gam * dt));  // kJ - 1
-                                cls[1][cl] = (T)(2.0 * dt * c->eps0 * wp2 / (2.0 + gam * dt));
-                                cls[2][cl] = (T)(dt / (c->eps0 * einf));
-                                cls_metal[cl] = wp2 > 0.0;
-                            } else {
-                                cl = it->second;
-                            }
-                            last_key = key;
-                            last_cls = cl;
-                        }
-                        out[e] = (uint8_t)cl;
+        std::unordered_map<uint32_t, int> classes;
+        std::vector<std::array<uint8_t, 256>> remap(part.size());
+        std::vector<char> identity(part.size(), 1);
+        for (size_t pi = 0; pi < part.size(); pi++) {
+            if (part[pi].overflow) return fail(PIC_ERR_UNSUPPORTED, "more than 256 distinct edge materials");
+            for (size_t q = 0; q < part[pi].keys.size(); q++) {
+                const uint32_t key = part[pi].keys[q];
+                auto it = classes.find(key);
+                int cl;
+                if (it == classes.end()) {
+                    if ((int)classes.size() >= 256)
+                        return fail(PIC_ERR_UNSUPPORTED, "more than 256 distinct edge materials");
+                    cl = (int)classes.size();
+                    classes[key] = cl;
+                    double sw = 0, swg = 0, se = 0;
+                    for (int q4 = 0; q4 < 4; q4++) {
+                        const pic_material &mt = c->materials[(key >> (8 * q4)) & 0xffu];
+                        sw += mt.wp * mt.wp;
+                        swg += mt.wp * mt.wp * mt.gamma;
+                        se += mt.eps_inf;
                     }
+                    const double wp2 = sw / 4.0, gam = sw > 0 ? swg / sw : 0.0, einf = se / 4.0;
+                    const double dt = c->dt;
+                    cls[0][cl] = (T)(-2.0 * gam * dt / (2.0 + gam * dt));  // kJ - 1
+                    cls[1][cl] = (T)(2.0 * dt * c->eps0 * wp2 / (2.0 + gam * dt));
+                    cls[2][cl] = (T)(dt / (c->eps0 * einf));
+                    cls_metal[cl] = wp2 > 0.0;
+                } else {
+                    cl = it->second;
+                }
+                remap[pi][q] = (uint8_t)cl;
+                if (cl != (int)q) identity[pi] = 0;
+            }
         }
+        run_all([&](int t) {
+            const size_t plane = (size_t)nx * ny;
+            const size_t b0 = plane * (size_t)((long long)nz * t / nthr), b1 = plane * (size_t)((long long)nz * (t + 1) / nthr);
+            for (int comp = 0; comp < 3; comp++) {
+                const size_t pi = (size_t)comp * nthr + t;
+                if (identity[pi]) continue;
+                uint8_t *out = ecls[comp].data();
+                for (size_t e = b0; e < b1; e++) out[e] = remap[pi][out[e]];
+            }
+        });
         n_classes = (int)classes.size();
         return PIC_OK;
     }
