@@ -254,7 +254,7 @@ def batched_and_sequential(ws, warm, steps, clocks=None, tune=False):
         x.sync()
         ms_seq += a0.elapsed_time(a1)
         x.close()
-    return ms_batch, ms_seq, launches, clk, (rep["best"] if rep else None), before
+    return ms_batch, ms_seq, launches, clk, ((*rep["best"], rep["best_lanes"]) if rep else None), before
 
 
 def bench_sweep(args):
@@ -267,7 +267,7 @@ def bench_sweep(args):
     torch.cuda.set_device(0)
     ws = W.sweep()
     warm = max(64, args.warmup // 64 * 64)
-    tune_steps = 0 if args.no_tune else 9 * 64  # pic_batch_tune, one round
+    tune_steps = 0 if args.no_tune else (9 + 5) * 64  # pic_batch_tune, one round (5 lane candidates for 48)
     # whole 64-step blocks within the 4000 steps
     steps = max(64, min(args.steps, ws[0].nsteps - warm - tune_steps) // 64 * 64)
     cells = sum(w.ncells for w in ws)
@@ -288,6 +288,7 @@ def bench_sweep(args):
                        "parallelism": "one batch graph (one branch per instance)",
                        "l2": "state larger than the 129 MB L2 (no flush)",
                        "launch_settings": ({"dep_smem_bytes": tuned[0], "sort_every": tuned[1],
+                                            "lanes": tuned[2] or "all",
                                             "chosen_by": f"pic_batch_tune, 1 round on steps 0..{tune_steps}"}
                                            if tuned else "library defaults (dep_smem_bytes 4096, sort_every 16)")},
             "sequential": {"value": seq, "unit": "Gcell-upd/s", "ms_per_step": ms_seq / steps,

@@ -254,13 +254,15 @@ int pic_set_tuning(pic_handle *h, const pic_tuning *t);
 /* Candidates pic_tune times: dep_smem_bytes over {0, 2048, 4096, 8192, 16384}
  * with sort_every held, then sort_every over {8, 16, 32, 64} with the best
  * box held. */
-#define PIC_TUNE_MAX_CANDIDATES 12
+#define PIC_TUNE_MAX_CANDIDATES 16
 typedef struct {
     pic_tuning best;
     int32_t n;                                    /* candidates timed */
     pic_tuning cand[PIC_TUNE_MAX_CANDIDATES];
     double us_per_step[PIC_TUNE_MAX_CANDIDATES];  /* best block of each, per step */
     int64_t steps;                                /* simulation steps taken */
+    int32_t best_lanes;                           /* pic_batch_tune: chosen lanes (else -1) */
+    int32_t lanes[PIC_TUNE_MAX_CANDIDATES];       /* pic_batch_tune: lanes of each candidate (else -1) */
 } pic_tune_report;
 
 /* Choose the tuning for this simulation by timing it: `rounds` (1..16)
@@ -300,13 +302,23 @@ int pic_batch_step(pic_batch *b, int64_t nsteps);
 /* Wait for the batch and every instance; reports device errors as pic_sync. */
 int pic_batch_sync(pic_batch *b);
 
+/* How many instances run side by side in the batch graph: the instances are
+ * dealt, largest first, to `lanes` chains (each to the chain with the fewest
+ * cells so far); the chains run side by side and the instances of a chain
+ * one after another.  0 (the default): every instance beside every other.
+ * Grids that fill the GPU alone can lose L2 locality when all run at once.
+ * Errors: PIC_ERR_ARG. */
+int pic_batch_set_lanes(pic_batch *b, int32_t lanes);
+
 /* pic_tune for the batch as a whole: each candidate is applied to every
  * instance and timed on whole batch blocks (the box candidates at the first
- * instance's sort interval); the fastest is applied to every instance.
- * Instances not at a block boundary first step to it on their own (up to 63
- * steps each); then every instance advances by report->steps = rounds x 9 x
- * 64 steps.  `report` may be NULL.  Synchronises.  Errors: PIC_ERR_ARG,
- * PIC_ERR_CUDA. */
+ * instance's sort interval), then the lanes {1, 2, 4, 8, all} (those below
+ * the instance count) with the best settings; the fastest settings are
+ * applied to every instance and the fastest lanes to the batch.  Instances
+ * not at a block boundary first step to it on their own (up to 63 steps
+ * each); then every instance advances by report->steps = rounds x (9 + lane
+ * candidates) x 64 steps.  `report` may be NULL.  Synchronises.  Errors:
+ * PIC_ERR_ARG, PIC_ERR_CUDA. */
 int pic_batch_tune(pic_batch *b, int32_t rounds, pic_tune_report *report);
 
 /* Release the batch (not its instances).  NULL is accepted. */

@@ -132,6 +132,7 @@ struct SimBase {
     virtual int step_direct(long long n) = 0;
     virtual cudaStream_t main_stream() const = 0;
     virtual int steps_to_boundary() const = 0;        // steps left in the current block (0 at a boundary)
+    virtual long long cells() const = 0;
     virtual int set_tuning(int dep_smem, int sort_every) = 0;
 };
 
@@ -617,6 +618,7 @@ struct Sim : SimBase {
     long long graph_epoch() const override { return epoch; }
     int step_direct(long long n) override { return step(n); }
     int steps_to_boundary() const override { return buffered ? DFT_BLOCK - buffered : 0; }
+    long long cells() const override { return N; }
     cudaStream_t main_stream() const override { return stream; }
 
     // DFT_BLOCK steps (a sort every sort_every, the first one included) and the DFT flush
@@ -976,7 +978,12 @@ struct Sim : SimBase {
             std::memset(rep, 0, sizeof(*rep));
             rep->best = best;
             rep->n = nc;
-            for (int c = 0; c < nc; c++) { rep->cand[c] = cand[c]; rep->us_per_step[c] = best_us[c]; }
+            rep->best_lanes = -1;
+            for (int c = 0; c < nc; c++) {
+                rep->cand[c] = cand[c];
+                rep->us_per_step[c] = best_us[c];
+                rep->lanes[c] = -1;
+            }
             rep->steps = step_host - s0;
         }
         return sync();
@@ -1519,6 +1526,7 @@ struct pic_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<long long> epochs, kernels;
+    int lanes = 0;  // instances that run side by side; 0: all of them
 
     void drop() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -1535,9 +1543,24 @@ struct pic_batch {
     int capture() {
         drop();
         CUDA_TRY(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
-        // every instance forks from the start of the capture and joins at its
-        // end, so the branches depend on nothing but that start
-        for (size_t i = 0; i < h.size(); i++) kernels[i] = h[i]->sim->launch_block_on(stream);
+        // Instances are dealt to `lanes` chains (largest first, each to the
+        // chain with the fewest cells so far); the chains fork from the start
+        // of the capture, and within a chain each instance's block starts when
+        // the one before it has finished.  One chain per instance: every
+        // instance runs beside every other.
+        const int nl = (lanes <= 0 || lanes >= (int)h.size()) ? (int)h.size() : lanes;
+        std::vector<int> order(h.size());
+        for (size_t i = 0; i < h.size(); i++) order[i] = (int)i;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return h[a]->sim->cells() > h[b]->sim->cells(); });
+        std::vector<long long> load(nl, 0);
+        std::vector<cudaStream_t> tail(nl, stream);
+        for (int i : order) {
+            const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            kernels[i] = h[i]->sim->launch_block_on(tail[l]);
+            tail[l] = h[i]->sim->main_stream();
+            load[l] += h[i]->sim->cells();
+        }
         for (size_t i = 0; i < h.size(); i++) h[i]->sim->join_to(stream);
         cudaError_t e = cudaStreamEndCapture(stream, &graph);
         if (e != cudaSuccess) { graph = nullptr; return fail(PIC_ERR_CUDA, "batch graph capture: %s", cudaGetErrorString(e)); }
@@ -1653,24 +1676,57 @@ struct pic_batch {
             return PIC_OK;
         };
         const pic_tuning start = rep_start();
-        for (int d : deps) { cand[nc] = pic_tuning{d, start.sort_every}; best_us[nc++] = 1e300; }
+        int cand_lanes[PIC_TUNE_MAX_CANDIDATES];
+        const int lanes0 = lanes;
+        for (int d : deps) { cand_lanes[nc] = lanes0; cand[nc] = pic_tuning{d, start.sort_every}; best_us[nc++] = 1e300; }
         rc = pass(0, 5);
         if (!rc) {
             const int dep_best = cand[win].dep_smem_bytes;
-            for (int e : everies) { cand[nc] = pic_tuning{dep_best, e}; best_us[nc++] = 1e300; }
+            for (int e : everies) { cand_lanes[nc] = lanes0; cand[nc] = pic_tuning{dep_best, e}; best_us[nc++] = 1e300; }
             rc = pass(5, 4);
+        }
+        // then how many instances run side by side: 1, 2, 4, 8 chains or all
+        int nlanes = 0;
+        if (!rc) {
+            const pic_tuning t = cand[win];
+            const int first = nc;
+            for (int l : {1, 2, 4, 8, 0}) {
+                if (l >= (int)h.size()) continue;
+                cand_lanes[nc] = l;
+                cand[nc] = t;
+                best_us[nc++] = 1e300;
+            }
+            nlanes = nc - first;
+            for (int r = 0; r < rounds && !rc; r++)
+                for (int c = first; c < nc && !rc; c++) {
+                    if (lanes != cand_lanes[c]) { lanes = cand_lanes[c]; drop(); }
+                    double us = 0.0;
+                    rc = time_block(e0, e1, &us);
+                    best_us[c] = std::min(best_us[c], us);
+                }
+            if (!rc) {
+                win = first;
+                for (int c = first; c < nc; c++)
+                    if (best_us[c] < best_us[win]) win = c;
+            }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         if (rc) return rc;
         rc = set_all(cand[win]);
         if (rc) return rc;
+        if (lanes != cand_lanes[win]) { lanes = cand_lanes[win]; drop(); }
         if (rep) {
             std::memset(rep, 0, sizeof(*rep));
             rep->best = cand[win];
             rep->n = nc;
-            for (int c = 0; c < nc; c++) { rep->cand[c] = cand[c]; rep->us_per_step[c] = best_us[c]; }
-            rep->steps = (long long)rounds * nc * DFT_BLOCK;
+            rep->best_lanes = cand_lanes[win];
+            for (int c = 0; c < nc; c++) {
+                rep->cand[c] = cand[c];
+                rep->us_per_step[c] = best_us[c];
+                rep->lanes[c] = cand_lanes[c];
+            }
+            rep->steps = (long long)rounds * (9 + nlanes) * DFT_BLOCK;
         }
         return PIC_OK;
     }
@@ -1723,6 +1779,17 @@ int pic_batch_step(pic_batch *b, int64_t nsteps) {
     if (!b) return fail(PIC_ERR_ARG, "NULL batch");
     if (nsteps < 0) return fail(PIC_ERR_ARG, "negative step count");
     return b->step(nsteps);
+}
+
+int pic_batch_set_lanes(pic_batch *b, int32_t lanes) {
+    g_err.clear();
+    if (!b) return fail(PIC_ERR_ARG, "NULL batch");
+    if (lanes < 0) return fail(PIC_ERR_ARG, "lanes must be >= 0");
+    if (lanes != b->lanes) {
+        b->lanes = lanes;
+        b->drop();
+    }
+    return PIC_OK;
 }
 
 int pic_batch_tune(pic_batch *b, int32_t rounds, pic_tune_report *report) {

@@ -32,7 +32,7 @@ EXPORTS = ("pic_last_error", "pic_workspace_size", "pic_create", "pic_destroy", 
            "pic_step", "pic_sync", "pic_probe_read", "pic_get_field", "pic_set_field", "pic_get_stats",
            "pic_save", "pic_load", "pic_profile_steps", "pic_dft_fold_static", "pic_batch_create",
            "pic_batch_step", "pic_batch_sync", "pic_batch_destroy", "pic_probe_kw", "pic_get_tuning",
-           "pic_set_tuning", "pic_tune", "pic_batch_tune")
+           "pic_set_tuning", "pic_tune", "pic_batch_tune", "pic_batch_set_lanes")
 
 
 class pic_material(C.Structure):
@@ -61,12 +61,13 @@ class pic_tuning(C.Structure):
     _fields_ = [("dep_smem_bytes", C.c_int32), ("sort_every", C.c_int32)]
 
 
-PIC_TUNE_MAX_CANDIDATES = 12
+PIC_TUNE_MAX_CANDIDATES = 16
 
 
 class pic_tune_report(C.Structure):
     _fields_ = [("best", pic_tuning), ("n", C.c_int32), ("cand", pic_tuning * PIC_TUNE_MAX_CANDIDATES),
-                ("us_per_step", C.c_double * PIC_TUNE_MAX_CANDIDATES), ("steps", C.c_int64)]
+                ("us_per_step", C.c_double * PIC_TUNE_MAX_CANDIDATES), ("steps", C.c_int64),
+                ("best_lanes", C.c_int32), ("lanes", C.c_int32 * PIC_TUNE_MAX_CANDIDATES)]
 
 
 class PicError(RuntimeError):
@@ -112,6 +113,7 @@ def load(path: str | None = None):
     L.pic_set_tuning.argtypes = [h, C.POINTER(pic_tuning)]
     L.pic_tune.argtypes = [h, C.c_int32, C.POINTER(pic_tune_report)]
     L.pic_batch_tune.argtypes = [h, C.c_int32, C.POINTER(pic_tune_report)]
+    L.pic_batch_set_lanes.argtypes = [h, C.c_int32]
     L.pic_save.argtypes = [h, C.c_char_p]
     L.pic_load.argtypes = [h, C.c_char_p]
     L.pic_dft_fold_static.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_uint32, C.c_void_p, C.c_int,
@@ -255,8 +257,16 @@ def pic_set_tuning(h, dep_smem_bytes: int, sort_every: int) -> None:
 
 
 def _report(r: pic_tune_report) -> dict:
-    return {"best": (r.best.dep_smem_bytes, r.best.sort_every), "steps": r.steps,
-            "candidates": [((r.cand[i].dep_smem_bytes, r.cand[i].sort_every), r.us_per_step[i]) for i in range(r.n)]}
+    out = {"best": (r.best.dep_smem_bytes, r.best.sort_every), "steps": r.steps,
+           "candidates": [((r.cand[i].dep_smem_bytes, r.cand[i].sort_every), r.us_per_step[i]) for i in range(r.n)]}
+    if r.best_lanes >= 0:
+        out["best_lanes"] = r.best_lanes
+        out["lanes"] = [r.lanes[i] for i in range(r.n)]
+    return out
+
+
+def pic_batch_set_lanes(b, lanes: int) -> None:
+    _check(load().pic_batch_set_lanes(b, int(lanes)), "pic_batch_set_lanes")
 
 
 def pic_tune(h, rounds: int = 1) -> dict:
@@ -455,6 +465,9 @@ class Batch:
     def tune(self, rounds=1):
         """pic_tune over the whole batch (every instance advances)."""
         return pic_batch_tune(self.b, rounds)
+
+    def set_lanes(self, lanes):
+        pic_batch_set_lanes(self.b, lanes)
 
     def close(self):
         if getattr(self, "b", None):

@@ -35,7 +35,7 @@ def test_struct_layout_matches_header():
     assert P.pic_config.flags.offset == C.sizeof(P.pic_config) - 8
     assert C.sizeof(P.pic_stats) == 40
     assert C.sizeof(P.pic_tuning) == 8
-    assert P.pic_tune_report.us_per_step.offset == 112 and C.sizeof(P.pic_tune_report) == 216
+    assert P.pic_tune_report.us_per_step.offset == 144 and C.sizeof(P.pic_tune_report) == 352
 
 
 def _cfg(**kw):

@@ -12,7 +12,9 @@ settings that change how fast a step runs, never what it computes.
   nine candidates on real steps, keeps the fastest, and the run it leaves
   behind still equals the oracle stepped the same number of steps.
 - pic_batch_tune applies each candidate to every instance of a batch (one
-  of them started off a block boundary) and leaves runs equal to the oracle's.
+  of them started off a block boundary), then times the lanes (instances
+  chained one after another or side by side), and the runs it leaves, stepped
+  further with either lane setting, equal the oracle's.
 - Invalid settings are rejected and leave the current ones in place.
 """
 import numpy as np
@@ -108,12 +110,17 @@ def test_batch_tune_keeps_parity(P):
     sims[1].step(10)  # off a block boundary
     b = P.Batch(sims)
     rep = b.tune(rounds=1)
-    assert rep["steps"] == 9 * 64 and len(rep["candidates"]) == 9
+    # nine launch-setting candidates, then the lanes below the instance count: one chain, or all side by side
+    assert rep["steps"] == 11 * 64 and len(rep["candidates"]) == 11
+    assert rep["lanes"][9:] == [1, 0] and rep["best_lanes"] in (1, 0)
     assert all(x.tuning == rep["best"] for x in sims)
+    b.set_lanes(1)  # the two instances one after another inside the batch graph
+    b.step(64)
+    b.set_lanes(0)
     b.step(64)
     b.sync()
     n = [x.stats().step for x in sims]
-    assert n == [9 * 64 + 64, 64 + 9 * 64 + 64]
+    assert n == [11 * 64 + 128, 64 + 11 * 64 + 128]
     for w, x, k in zip(ws, sims, n):
         o = O.from_workload(w)
         o.step(k)
