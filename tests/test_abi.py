@@ -113,3 +113,19 @@ def test_adjoint_create_rejects_invalid_config_on_host(field, value, code):
     assert A.load().pic_adj_create(C.byref(cfg), C.byref(out)) == code
     assert out.value is None
 
+
+
+def test_tuning_and_batch_entry_points_reject_null_on_host():
+    """The launch-setting and batch entry points answer PIC_ERR_ARG for a NULL
+    handle or batch without touching the device."""
+    L = P.load()
+    t = P.pic_tuning(4096, 16)
+    r = P.pic_tune_report()
+    assert L.pic_get_tuning(None, C.byref(t)) == ERR_ARG
+    assert L.pic_set_tuning(None, C.byref(t)) == ERR_ARG
+    assert L.pic_tune(None, 1, C.byref(r)) == ERR_ARG
+    assert L.pic_batch_tune(None, 1, C.byref(r)) == ERR_ARG
+    assert L.pic_batch_set_lanes(None, 2) == ERR_ARG
+    assert L.pic_batch_step(None, 64) == ERR_ARG
+    assert L.pic_batch_sync(None) == ERR_ARG
+    assert L.pic_batch_destroy(None) == 0
