@@ -53,11 +53,12 @@ struct AState {
     T *stE, *stJ;                // per step and slot: E^n, J^n
     double *gb, *gk;             // per slot: dL/dbJ, dL/dkJ contributions
     long long *n;                // device step counter (forward: next step; backward: steps left)
+    int *bx;                     // x index range [bx[0], bx[1]] of the bunch's Ex edges in the current step
 };
 
 struct Bunch {
     double qv_norm;  // q v (2 pi sigma^2)^{-3/2}
-    double inv2s2, cut2;
+    double inv2s2, cut2, cut;
     double v, x0, y0, z0, dx;
     int j0, j1, k0, k1;  // rows [j0, j1] x planes [k0, k1] hold every edge within the cut
 };
@@ -83,6 +84,20 @@ __device__ __forceinline__ void probe_term(const AState<T> &f, const Probe &p, d
     F[1] += v * sn * p.dt;
 }
 
+// Start of forward step m (one thread): the probe term of step m-1, the
+// counter from m-1 to m, and the columns of Ex edges within the bunch's cut
+// radius at t = (m + 1/2) dt, one column wider on each side.
+template <typename T>
+__device__ __forceinline__ void fwd_step_start(const AState<T> &f, const Probe &pr, double *F, const Bunch &bu,
+                                               double dt) {
+    const long long m1 = *f.n;
+    if (m1 >= 0) probe_term(f, pr, F, m1);
+    *f.n = m1 + 1;
+    const double xc = bu.x0 + bu.v * ((m1 + 1) + 0.5) * dt;
+    f.bx[0] = (int)floor((xc - bu.cut) / bu.dx - 0.5) - 1;
+    f.bx[1] = (int)ceil((xc + bu.cut) / bu.dx - 0.5) + 1;
+}
+
 __device__ __forceinline__ int aslab(int L, int n, int x) {
     if (x < L) return x;
     if (x >= n - L) return x - (n - 2 * L);
@@ -100,14 +115,10 @@ __device__ __forceinline__ long long apsi(const int n[3], int L, int a, int s, i
 // m-1 (E is E^m until the E update that follows) and advances the step
 // counter from m-1 to m (it starts at -1).
 template <typename T>
-__global__ void __launch_bounds__(256) k_fwd_H(AGrid<T> g, AState<T> f, Probe pr, double *F) {
+__global__ void __launch_bounds__(256) k_fwd_H(AGrid<T> g, AState<T> f, Probe pr, double *F, Bunch bu, double dt) {
     pdl_wait();
     pdl_release();
-    if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0) {
-        const long long m1 = *f.n;
-        if (m1 >= 0) probe_term(f, pr, F, m1);
-        *f.n = m1 + 1;
-    }
+    if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0) fwd_step_start(f, pr, F, bu, dt);
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     if (i >= nx || j >= ny) return;
@@ -148,8 +159,10 @@ __global__ void __launch_bounds__(256) k_fwd_H(AGrid<T> g, AState<T> f, Probe pr
 }
 
 // the rigid bunch current J_x at the Ex edge (i+1/2, j, k) at time t
-__device__ __forceinline__ double bunch_jx(const Bunch &b, int i, int j, int k, double t) {
-    if (j < b.j0 || j > b.j1 || k < b.k0 || k > b.k1) return 0.0;  // FP64 is slow: integer test first
+__device__ __forceinline__ double bunch_jx(const Bunch &b, const int *bx, int i, int j, int k, double t) {
+    // FP64 is slow on this part: integer tests against the rows, planes and
+    // (this step's) columns within the cut first
+    if (j < b.j0 || j > b.j1 || k < b.k0 || k > b.k1 || i < bx[0] || i > bx[1]) return 0.0;
     const double x = (i + 0.5) * b.dx - (b.x0 + b.v * t), y = j * b.dx - b.y0, z = k * b.dx - b.z0;
     const double r2 = x * x + y * y + z * z;
     return r2 > b.cut2 ? 0.0 : b.qv_norm * exp(-r2 * b.inv2s2);
@@ -205,7 +218,7 @@ __global__ void __launch_bounds__(256) k_fwd_E(AGrid<T> g, AState<T> f, Bunch bu
             const long long q = apsi(g.n, g.L, 2, s2, i, j, k);
             pz = f.psiE[2][0][q] + (f.bE[2][k] * f.psiE[2][0][q] + f.aE[2][k] * dHy_dz); f.psiE[2][0][q] = pz;
         }
-        fwd_ampere(g, f, 0, e, k, n, ky * dHz_dy + py - kz * dHy_dz - pz, (T)bunch_jx(bu, i, j, k, t_half));
+        fwd_ampere(g, f, 0, e, k, n, ky * dHz_dy + py - kz * dHy_dz - pz, (T)bunch_jx(bu, f.bx, i, j, k, t_half));
     }
     if (!(fx || fz)) {
         const T dHx_dz = (hx - f.H[0][e - okm]) * g.r[2], dHz_dx = (hz - f.H[2][e - oim]) * g.r[0];
@@ -444,14 +457,11 @@ __device__ __forceinline__ bool group_of(const AGrid<float> &g, int &i0, int &j,
     return i0 < g.n[0] && j < g.n[1];
 }
 
-__global__ void __launch_bounds__(256) k_fwd_H4(AGrid<float> g, AState<float> f, Probe pr, double *F) {
+__global__ void __launch_bounds__(256) k_fwd_H4(AGrid<float> g, AState<float> f, Probe pr, double *F, Bunch bu,
+                                                 double dt) {
     pdl_wait();
     pdl_release();
-    if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0) {
-        const long long m1 = *f.n;
-        if (m1 >= 0) probe_term(f, pr, F, m1);
-        *f.n = m1 + 1;
-    }
+    if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0) fwd_step_start(f, pr, F, bu, dt);
     int i0, j, k;
     if (!group_of(g, i0, j, k)) return;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
@@ -598,7 +608,7 @@ __global__ void __launch_bounds__(256) k_fwd_E4(AGrid<float> g, AState<float> f,
         for (int m = 0; m < 4; m++) {
             d1[m] = (hz.v[m] - hz_jm.v[m]) * ry;
             d2[m] = (hy.v[m] - hy_km.v[m]) * rz;
-            js[m] = (float)bunch_jx(bu, i0 + m, j, k, t_half);
+            js[m] = (float)bunch_jx(bu, f.bx, i0 + m, j, k, t_half);
         }
         if (s1 >= 0) psi4(f.psiE[1][1], apsi(g.n, g.L, 1, s1, i0, j, k), f.bE[1], f.aE[1], f.ikE[1], j, false, d1, upd, p1, k1);
         if (s2 >= 0) psi4(f.psiE[2][0], apsi(g.n, g.L, 2, s2, i0, j, k), f.bE[2], f.aE[2], f.ikE[2], k, false, d2, upd, p2, k2);
@@ -886,6 +896,7 @@ struct AdjSim : AdjBase {
         rc = rc ? rc : take(&f.stJ, (size_t)ne * c->nsteps + 1);
         rc = rc ? rc : take(&d_F, 2);
         rc = rc ? rc : take(&f.n, 1);
+        rc = rc ? rc : take(&f.bx, 2);
         if (rc) return rc;
         if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess)
             return set_last_error(PIC_ERR_CUDA, "adjoint: stream creation failed");
@@ -918,6 +929,7 @@ struct AdjSim : AdjBase {
         bu.qv_norm = c->bunch_q * c->bunch_v / std::pow(2.0 * M_PI * s * s, 1.5);
         bu.inv2s2 = 1.0 / (2.0 * s * s);
         bu.cut2 = 36.0 * s * s;
+        bu.cut = 6.0 * s;
         bu.v = c->bunch_v; bu.x0 = c->bunch_x0; bu.y0 = c->bunch_y0; bu.z0 = c->bunch_z0; bu.dx = c->dx;
         // rows and planes within the cut radius (6 sigma), one cell wider on each side
         const double cut = 6.0 * s / c->dx;
@@ -1012,14 +1024,14 @@ struct AdjSim : AdjBase {
             if (use4) {
                 const dim3 g4 = grid4(), b4 = block4();
                 for (int q = 0; q < count; q++) {
-                    launch_pdl(k_fwd_H4, g4, b4, 0, stream, g, f, pr, d_F);
+                    launch_pdl(k_fwd_H4, g4, b4, 0, stream, g, f, pr, d_F, bu, cfg.dt);
                     launch_pdl(k_fwd_E4, g4, b4, 0, stream, g, f, bu, cfg.dt);
                 }
                 return;
             }
         }
         for (int q = 0; q < count; q++) {
-            launch_pdl(k_fwd_H<T>, gr, bl, 0, stream, g, f, pr, d_F);
+            launch_pdl(k_fwd_H<T>, gr, bl, 0, stream, g, f, pr, d_F, bu, cfg.dt);
             launch_pdl(k_fwd_E<T>, gr, bl, 0, stream, g, f, bu, cfg.dt);
         }
     }
