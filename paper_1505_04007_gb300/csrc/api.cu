@@ -937,8 +937,14 @@ struct Sim : SimBase {
         if (buffered) rc = step(DFT_BLOCK - buffered);  // reach a block boundary
         if (rc) return rc;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
-        CUDA_TRY(cudaEventCreate(&e0));
-        CUDA_TRY(cudaEventCreate(&e1));
+        {
+            cudaError_t ce = cudaEventCreate(&e0);
+            if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+            if (ce != cudaSuccess) {
+                if (e0) cudaEventDestroy(e0);
+                return fail(PIC_ERR_CUDA, "tuning events: %s", cudaGetErrorString(ce));
+            }
+        }
         const int deps[5] = {0, 2048, 4096, 8192, 16384}, everies[4] = {8, 16, 32, 64};
         pic_tuning cand[PIC_TUNE_MAX_CANDIDATES];
         double best_us[PIC_TUNE_MAX_CANDIDATES];
@@ -1654,8 +1660,14 @@ struct pic_batch {
             }
         }
         cudaEvent_t e0 = nullptr, e1 = nullptr;
-        CUDA_TRY(cudaEventCreate(&e0));
-        CUDA_TRY(cudaEventCreate(&e1));
+        {
+            cudaError_t ce = cudaEventCreate(&e0);
+            if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+            if (ce != cudaSuccess) {
+                if (e0) cudaEventDestroy(e0);
+                return fail(PIC_ERR_CUDA, "tuning events: %s", cudaGetErrorString(ce));
+            }
+        }
         const int deps[5] = {0, 2048, 4096, 8192, 16384}, everies[4] = {8, 16, 32, 64};
         pic_tuning cand[PIC_TUNE_MAX_CANDIDATES];
         double best_us[PIC_TUNE_MAX_CANDIDATES];
