@@ -45,8 +45,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the library's default launch settings instead of choosing them with pic_tune")
-    ap.add_argument("--tuning", default=None, metavar="DEP_SMEM_BYTES,SORT_EVERY",
-                    help="use these launch settings instead of running pic_tune (e.g. 8192,32)")
+    ap.add_argument("--tuning", default=None, metavar="DEP_SMEM_BYTES,SORT_EVERY[,FIELD_BLOCK]",
+                    help="use these launch settings instead of running pic_tune (e.g. 8192,32,256)")
     ap.add_argument("--ref-seconds", type=float, default=20.0,
                     help="target CPU seconds of the oracle sample")
     return ap.parse_args()
@@ -267,7 +267,7 @@ def bench_sweep(args):
     torch.cuda.set_device(0)
     ws = W.sweep()
     warm = max(64, args.warmup // 64 * 64)
-    tune_steps = 0 if args.no_tune else (9 + 5) * 64  # pic_batch_tune, one round (5 lane candidates for 48)
+    tune_steps = 0 if args.no_tune else (12 + 5) * 64  # pic_batch_tune, one round (5 lane candidates for 48)
     # whole 64-step blocks within the 4000 steps
     steps = max(64, min(args.steps, ws[0].nsteps - warm - tune_steps) // 64 * 64)
     cells = sum(w.ncells for w in ws)
@@ -288,9 +288,9 @@ def bench_sweep(args):
                        "parallelism": "one batch graph (one branch per instance)",
                        "l2": "state larger than the 129 MB L2 (no flush)",
                        "launch_settings": ({"dep_smem_bytes": tuned[0], "sort_every": tuned[1],
-                                            "lanes": tuned[2] or "all",
+                                            "field_block": tuned[2], "lanes": tuned[3] or "all",
                                             "chosen_by": f"pic_batch_tune, 1 round on steps 0..{tune_steps}"}
-                                           if tuned else "library defaults (dep_smem_bytes 4096, sort_every 16)")},
+                                           if tuned else "library defaults (dep_smem_bytes 4096, sort_every 16, field_block 256)")},
             "sequential": {"value": seq, "unit": "Gcell-upd/s", "ms_per_step": ms_seq / steps,
                            "note": "fresh copies of the same instances over the same step range, each stepped "
                                    "alone (own 64-step graphs), one after another"},
@@ -454,12 +454,13 @@ def main():
                f"state ({state_mb:.0f} MB) fits in the 129 MB L2: an L2-resident latency figure, not an HBM rate")
     tuned = None
     if args.tuning:
-        dep, every = (int(v) for v in args.tuning.split(","))
-        sim.set_tuning(dep, every)
-        tuned = {"dep_smem_bytes": dep, "sort_every": every, "chosen_by": "--tuning"}
+        vals = [int(v) for v in args.tuning.split(",")]
+        sim.set_tuning(*vals)
+        dep, every, blk = sim.tuning
+        tuned = {"dep_smem_bytes": dep, "sort_every": every, "field_block": blk, "chosen_by": "--tuning"}
     elif not args.no_tune:  # launch settings chosen on this workload's own steps, before the warm-up
         rep = sim.tune(rounds=2)
-        tuned = {"dep_smem_bytes": rep["best"][0], "sort_every": rep["best"][1],
+        tuned = {"dep_smem_bytes": rep["best"][0], "sort_every": rep["best"][1], "field_block": rep["best"][2],
                  "chosen_by": f"pic_tune, 2 rounds on steps 0..{rep['steps']} (before the warm-up)"}
     sim.step(args.warmup)
     sim.sync()
@@ -508,7 +509,7 @@ def main():
         t0 = time.perf_counter()
         s2 = pic.Simulation(w, prec, stream=stream)
         if tuned is not None:
-            s2.set_tuning(tuned["dep_smem_bytes"], tuned["sort_every"])
+            s2.set_tuning(tuned["dep_smem_bytes"], tuned["sort_every"], tuned["field_block"])
         s2.step(args.steps)
         spec = s2.probe_read()
         t1 = time.perf_counter()
@@ -535,7 +536,8 @@ def main():
                 "config": {"workload": desc, "global_batch": world, "parallelism": f"replicas x{world}",
                            "l2": l2_note,
                            "particle_pushes_per_s": w.nparticles * args.steps * world / (ms / 1e3),
-                           "launch_settings": tuned or "library defaults (dep_smem_bytes 4096, sort_every 16)"},
+                           "launch_settings": tuned or "library defaults (dep_smem_bytes 4096, sort_every 16, "
+                                                       "field_block 256)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk}
         print(json.dumps(line), flush=True)

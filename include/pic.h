@@ -239,11 +239,17 @@ int pic_profile_steps(pic_handle *h, int64_t nsteps, double *out_us);
  *                   Default 4096.
  *   sort_every      electrons are re-sorted by 4x4x4-cell brick every this
  *                   many steps: 1, 2, 4, 8, 16, 32 or 64.  Default 16.
+ *   field_block     threads per block of the FP32 interior field kernels (four
+ *                   x cells per thread, blocks taken in turn over the boxes of
+ *                   the grid): 128, 256 or 512.  Default 256.  No effect on
+ *                   the FP64 state or on grids the four-cell kernels do not
+ *                   take.
  * The settings belong to the handle, not to the simulation state: pic_save
  * does not write them and pic_load leaves the handle's settings as they are. */
 typedef struct {
     int32_t dep_smem_bytes;
     int32_t sort_every;
+    int32_t field_block;
 } pic_tuning;
 
 int pic_get_tuning(pic_handle *h, pic_tuning *out);
@@ -252,9 +258,9 @@ int pic_get_tuning(pic_handle *h, pic_tuning *out);
 int pic_set_tuning(pic_handle *h, const pic_tuning *t);
 
 /* Candidates pic_tune times: dep_smem_bytes over {0, 2048, 4096, 8192, 16384}
- * with sort_every held, then sort_every over {8, 16, 32, 64} with the best
- * box held. */
-#define PIC_TUNE_MAX_CANDIDATES 16
+ * with the rest held, then sort_every over {8, 16, 32, 64} with the best box,
+ * then field_block over {128, 256, 512} with the best box and interval. */
+#define PIC_TUNE_MAX_CANDIDATES 20
 typedef struct {
     pic_tuning best;
     int32_t n;                                    /* candidates timed */
@@ -269,7 +275,7 @@ typedef struct {
  * passes of the candidates above, each candidate stepping one whole 64-step
  * block (CUDA events on the simulation's stream); each candidate keeps its
  * fastest block, and the fastest candidate is kept.  The blocks are real
- * steps of the simulation (it advances by report->steps = rounds x 9 x 64
+ * steps of the simulation (it advances by report->steps = rounds x 12 x 64
  * steps, plus up to 63 steps to reach a block boundary first).  `report`
  * may be NULL.  Synchronises.  Errors: PIC_ERR_ARG, PIC_ERR_CUDA. */
 int pic_tune(pic_handle *h, int32_t rounds, pic_tune_report *report);
@@ -316,8 +322,8 @@ int pic_batch_set_lanes(pic_batch *b, int32_t lanes);
  * the instance count) with the best settings; the fastest settings are
  * applied to every instance and the fastest lanes to the batch.  Instances
  * not at a block boundary first step to it on their own (up to 63 steps
- * each); then every instance advances by report->steps = rounds x (9 + lane
- * candidates) x 64 steps.  `report` may be NULL.  Synchronises.  Errors:
+ * each); then every instance advances by report->steps = rounds x (12 +
+ * lane candidates) x 64 steps.  `report` may be NULL.  Synchronises.  Errors:
  * PIC_ERR_ARG, PIC_ERR_CUDA. */
 int pic_batch_tune(pic_batch *b, int32_t rounds, pic_tune_report *report);
 

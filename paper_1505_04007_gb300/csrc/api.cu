@@ -133,7 +133,7 @@ struct SimBase {
     virtual cudaStream_t main_stream() const = 0;
     virtual int steps_to_boundary() const = 0;        // steps left in the current block (0 at a boundary)
     virtual long long cells() const = 0;
-    virtual int set_tuning(int dep_smem, int sort_every) = 0;
+    virtual int set_tuning(const pic_tuning &t) = 0;
 };
 
 template <typename T>
@@ -525,6 +525,7 @@ struct Sim : SimBase {
             std::vector<float> cE(256);
             for (int q = 0; q < 256; q++) cE[q] = (float)cls[2][q];
             use_plan = make_field_plan(g, plane_cls.data(), cE.data(), fplan);
+            fplan.block = 256;
           }
         }
         // CPML profiles: per axis (b-1, a, 1/kappa) at E positions, then at H positions
@@ -899,14 +900,19 @@ struct Sim : SimBase {
     }
 
     // ---------------------------------------------------------- tuning --
-    int set_tuning(int dep, int every) override {
+    pic_tuning tuning() const { return pic_tuning{pp.dep_smem, sort_every, fplan.block}; }
+    int set_tuning(const pic_tuning &t) override {
+        const int dep = t.dep_smem_bytes, every = t.sort_every, blk = t.field_block;
         if (dep < 0 || dep > DEP_SMEM_MAX || dep % 16 != 0)
             return fail(PIC_ERR_ARG, "dep_smem_bytes %d outside 0..%d or not a multiple of 16", dep, DEP_SMEM_MAX);
         if (every < 1 || every > DFT_BLOCK || DFT_BLOCK % every != 0)
             return fail(PIC_ERR_ARG, "sort_every %d does not divide %d", every, DFT_BLOCK);
-        if (dep != pp.dep_smem || every != sort_every) {
+        if (blk != 128 && blk != 256 && blk != 512)
+            return fail(PIC_ERR_ARG, "field_block %d is not 128, 256 or 512", blk);
+        if (dep != pp.dep_smem || every != sort_every || blk != fplan.block) {
             pp.dep_smem = dep;
             sort_every = every;
+            fplan.block = blk;
             drop_graph();  // the captured launches hold the old settings
         }
         return PIC_OK;
@@ -945,7 +951,7 @@ struct Sim : SimBase {
                 return fail(PIC_ERR_CUDA, "tuning events: %s", cudaGetErrorString(ce));
             }
         }
-        const int deps[5] = {0, 2048, 4096, 8192, 16384}, everies[4] = {8, 16, 32, 64};
+        const int deps[5] = {0, 2048, 4096, 8192, 16384}, everies[4] = {8, 16, 32, 64}, blocks[3] = {128, 256, 512};
         pic_tuning cand[PIC_TUNE_MAX_CANDIDATES];
         double best_us[PIC_TUNE_MAX_CANDIDATES];
         int nc = 0;
@@ -953,7 +959,7 @@ struct Sim : SimBase {
         auto pass = [&](int first, int count, int *win) -> int {
             for (int r = 0; r < rounds; r++)
                 for (int c = first; c < first + count; c++) {
-                    int q = set_tuning(cand[c].dep_smem_bytes, cand[c].sort_every);
+                    int q = set_tuning(cand[c]);
                     if (q) return q;
                     double us = 0.0;
                     q = time_block(e0, e1, &us);
@@ -965,20 +971,25 @@ struct Sim : SimBase {
                 if (best_us[c] < best_us[*win]) *win = c;
             return PIC_OK;
         };
-        const int every0 = sort_every;
-        for (int d : deps) { cand[nc] = pic_tuning{d, every0}; best_us[nc++] = 1e300; }
+        const pic_tuning t0 = tuning();
+        for (int d : deps) { cand[nc] = pic_tuning{d, t0.sort_every, t0.field_block}; best_us[nc++] = 1e300; }
         int win = 0;
         rc = pass(0, 5, &win);
         if (!rc) {
-            const int dep_best = cand[win].dep_smem_bytes;
-            for (int e : everies) { cand[nc] = pic_tuning{dep_best, e}; best_us[nc++] = 1e300; }
+            const pic_tuning t = cand[win];
+            for (int e : everies) { cand[nc] = pic_tuning{t.dep_smem_bytes, e, t.field_block}; best_us[nc++] = 1e300; }
             rc = pass(5, 4, &win);
+        }
+        if (!rc) {
+            const pic_tuning t = cand[win];
+            for (int b : blocks) { cand[nc] = pic_tuning{t.dep_smem_bytes, t.sort_every, b}; best_us[nc++] = 1e300; }
+            rc = pass(9, 3, &win);
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         if (rc) return rc;
         const pic_tuning best = cand[win];
-        rc = set_tuning(best.dep_smem_bytes, best.sort_every);
+        rc = set_tuning(best);
         if (rc) return rc;
         if (rep) {
             std::memset(rep, 0, sizeof(*rep));
@@ -1500,15 +1511,14 @@ int pic_profile_steps(pic_handle *h, int64_t nsteps, double *out_us) {
 int pic_get_tuning(pic_handle *h, pic_tuning *out) {
     g_err.clear();
     if (!h || !out) return fail(PIC_ERR_ARG, "NULL argument");
-    if (h->precision == PIC_FP64) *out = pic_tuning{S<double>(h)->pp.dep_smem, S<double>(h)->sort_every};
-    else *out = pic_tuning{S<float>(h)->pp.dep_smem, S<float>(h)->sort_every};
+    *out = h->precision == PIC_FP64 ? S<double>(h)->tuning() : S<float>(h)->tuning();
     return PIC_OK;
 }
 
 int pic_set_tuning(pic_handle *h, const pic_tuning *t) {
     g_err.clear();
     if (!h || !t) return fail(PIC_ERR_ARG, "NULL argument");
-    return DISPATCH(h, set_tuning(t->dep_smem_bytes, t->sort_every));
+    return DISPATCH(h, set_tuning(*t));
 }
 
 int pic_tune(pic_handle *h, int32_t rounds, pic_tune_report *report) {
@@ -1642,7 +1652,7 @@ struct pic_batch {
 
     int set_all(const pic_tuning &t) {
         for (auto *x : h) {
-            const int rc = x->sim->set_tuning(t.dep_smem_bytes, t.sort_every);
+            const int rc = x->sim->set_tuning(t);
             if (rc) return rc;
         }
         return PIC_OK;
@@ -1668,7 +1678,7 @@ struct pic_batch {
                 return fail(PIC_ERR_CUDA, "tuning events: %s", cudaGetErrorString(ce));
             }
         }
-        const int deps[5] = {0, 2048, 4096, 8192, 16384}, everies[4] = {8, 16, 32, 64};
+        const int deps[5] = {0, 2048, 4096, 8192, 16384}, everies[4] = {8, 16, 32, 64}, blocks[3] = {128, 256, 512};
         pic_tuning cand[PIC_TUNE_MAX_CANDIDATES];
         double best_us[PIC_TUNE_MAX_CANDIDATES];
         int nc = 0, rc = PIC_OK, win = 0;
@@ -1690,12 +1700,29 @@ struct pic_batch {
         const pic_tuning start = rep_start();
         int cand_lanes[PIC_TUNE_MAX_CANDIDATES];
         const int lanes0 = lanes;
-        for (int d : deps) { cand_lanes[nc] = lanes0; cand[nc] = pic_tuning{d, start.sort_every}; best_us[nc++] = 1e300; }
+        for (int d : deps) {
+            cand_lanes[nc] = lanes0;
+            cand[nc] = pic_tuning{d, start.sort_every, start.field_block};
+            best_us[nc++] = 1e300;
+        }
         rc = pass(0, 5);
         if (!rc) {
-            const int dep_best = cand[win].dep_smem_bytes;
-            for (int e : everies) { cand_lanes[nc] = lanes0; cand[nc] = pic_tuning{dep_best, e}; best_us[nc++] = 1e300; }
+            const pic_tuning t = cand[win];
+            for (int e : everies) {
+                cand_lanes[nc] = lanes0;
+                cand[nc] = pic_tuning{t.dep_smem_bytes, e, t.field_block};
+                best_us[nc++] = 1e300;
+            }
             rc = pass(5, 4);
+        }
+        if (!rc) {
+            const pic_tuning t = cand[win];
+            for (int b : blocks) {
+                cand_lanes[nc] = lanes0;
+                cand[nc] = pic_tuning{t.dep_smem_bytes, t.sort_every, b};
+                best_us[nc++] = 1e300;
+            }
+            rc = pass(9, 3);
         }
         // then how many instances run side by side: 1, 2, 4, 8 chains or all
         int nlanes = 0;
@@ -1738,7 +1765,7 @@ struct pic_batch {
                 rep->us_per_step[c] = best_us[c];
                 rep->lanes[c] = cand_lanes[c];
             }
-            rep->steps = (long long)rounds * (9 + nlanes) * DFT_BLOCK;
+            rep->steps = (long long)rounds * (12 + nlanes) * DFT_BLOCK;
         }
         return PIC_OK;
     }

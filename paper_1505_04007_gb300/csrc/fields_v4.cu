@@ -357,7 +357,7 @@ __device__ __forceinline__ bool list_cell(const BoxList &bl, long long q, int &b
     const Box &b = (bl).b[bi];                                                                         \
     (void)b;
 
-__global__ void __launch_bounds__(256) k_H4_bulk(Grid<float> g, Fields<float> f, BoxList bl) {
+__global__ void __launch_bounds__(512) k_H4_bulk(Grid<float> g, Fields<float> f, BoxList bl) {
     BOX_CELL(bl);
     h4<false>(g, f, i0, j, k, *f.step);
 }
@@ -366,12 +366,12 @@ __global__ void __launch_bounds__(256, 3) k_H4_cpml(Grid<float> g, Fields<float>
     h4<true>(g, f, i0, j, k, *f.step);
 }
 // one non-metal material, no absorbing layer
-__global__ void __launch_bounds__(256) k_E4_vac(Grid<float> g, Fields<float> f, BoxList bl) {
+__global__ void __launch_bounds__(512) k_E4_vac(Grid<float> g, Fields<float> f, BoxList bl) {
     BOX_CELL(bl);
     e4<false, false>(g, f, i0, j, k, *f.step, b.cE);
 }
 // metal or several materials, no absorbing layer
-__global__ void __launch_bounds__(256) k_E4_mat(Grid<float> g, Fields<float> f, BoxList bl) {
+__global__ void __launch_bounds__(512) k_E4_mat(Grid<float> g, Fields<float> f, BoxList bl) {
     BOX_CELL(bl);
     e4<false, true>(g, f, i0, j, k, *f.step, 0.f);
 }
@@ -391,8 +391,8 @@ long long groups(const Box &b) {
 }
 
 template <typename K>
-void launch_list(K kernel, const Grid<float> &g, const Fields<float> &f, const BoxList &bl, cudaStream_t s) {
-    const int blk = 256;
+void launch_list(K kernel, const Grid<float> &g, const Fields<float> &f, const BoxList &bl, cudaStream_t s,
+                 int blk = 256) {
     const long long total = bl.first[bl.n];
     if (total > 0) {
         launch_pdl(kernel, dim3((unsigned)((total + blk - 1) / blk)), dim3(blk), 0, s, g, f, bl);
@@ -458,15 +458,15 @@ bool make_field_plan(const Grid<float> &g, const uint8_t *plane_cls, const float
 
 void launch_v4_H(const Grid<float> &g, const Fields<float> &f, const FieldPlan &plan, cudaStream_t s, cudaStream_t s2) {
     launch_list(k_H4_cpml, g, f, plan.faces, s2);
-    launch_list(k_H4_bulk, g, f, plan.bulk, s);
+    launch_list(k_H4_bulk, g, f, plan.bulk, s, plan.block);
 }
 
 void launch_v4_E(const Grid<float> &g, const Fields<float> &f, const FieldPlan &plan, cudaStream_t s, cudaStream_t s2,
                  cudaStream_t s3, cudaStream_t s4) {
     launch_list(k_E4_cpml_vac, g, f, plan.fvac, s2);
     launch_list(k_E4_cpml_mat, g, f, plan.fmat, s4);
-    launch_list(k_E4_vac, g, f, plan.vac, s);
-    launch_list(k_E4_mat, g, f, plan.mat, s3);
+    launch_list(k_E4_vac, g, f, plan.vac, s, plan.block);
+    launch_list(k_E4_mat, g, f, plan.mat, s3, plan.block);
 }
 
 }  // namespace pic

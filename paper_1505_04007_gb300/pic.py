@@ -58,10 +58,10 @@ class pic_stats(C.Structure):
 
 
 class pic_tuning(C.Structure):
-    _fields_ = [("dep_smem_bytes", C.c_int32), ("sort_every", C.c_int32)]
+    _fields_ = [("dep_smem_bytes", C.c_int32), ("sort_every", C.c_int32), ("field_block", C.c_int32)]
 
 
-PIC_TUNE_MAX_CANDIDATES = 16
+PIC_TUNE_MAX_CANDIDATES = 20
 
 
 class pic_tune_report(C.Structure):
@@ -248,17 +248,18 @@ def pic_profile_steps(h, nsteps: int) -> dict:
 def pic_get_tuning(h) -> tuple:
     t = pic_tuning()
     _check(load().pic_get_tuning(h, C.byref(t)), "pic_get_tuning")
-    return t.dep_smem_bytes, t.sort_every
+    return t.dep_smem_bytes, t.sort_every, t.field_block
 
 
-def pic_set_tuning(h, dep_smem_bytes: int, sort_every: int) -> None:
-    t = pic_tuning(int(dep_smem_bytes), int(sort_every))
+def pic_set_tuning(h, dep_smem_bytes: int, sort_every: int, field_block: int = 256) -> None:
+    t = pic_tuning(int(dep_smem_bytes), int(sort_every), int(field_block))
     _check(load().pic_set_tuning(h, C.byref(t)), "pic_set_tuning")
 
 
 def _report(r: pic_tune_report) -> dict:
-    out = {"best": (r.best.dep_smem_bytes, r.best.sort_every), "steps": r.steps,
-           "candidates": [((r.cand[i].dep_smem_bytes, r.cand[i].sort_every), r.us_per_step[i]) for i in range(r.n)]}
+    tup = lambda t: (t.dep_smem_bytes, t.sort_every, t.field_block)  # noqa: E731
+    out = {"best": tup(r.best), "steps": r.steps,
+           "candidates": [(tup(r.cand[i]), r.us_per_step[i]) for i in range(r.n)]}
     if r.best_lanes >= 0:
         out["best_lanes"] = r.best_lanes
         out["lanes"] = [r.lanes[i] for i in range(r.n)]
@@ -416,12 +417,13 @@ class Simulation:
     def tuning(self):
         return pic_get_tuning(self.h)
 
-    def set_tuning(self, dep_smem_bytes, sort_every):
-        pic_set_tuning(self.h, dep_smem_bytes, sort_every)
+    def set_tuning(self, dep_smem_bytes, sort_every, field_block=256):
+        pic_set_tuning(self.h, dep_smem_bytes, sort_every, field_block)
 
     def tune(self, rounds=1):
-        """Time the deposit box and sort interval candidates on real steps of
-        this simulation and keep the fastest (the simulation advances)."""
+        """Time the deposit box, sort interval and field block candidates on
+        real steps of this simulation and keep the fastest (the simulation
+        advances)."""
         return pic_tune(self.h, rounds)
 
     def save(self, path):

@@ -34,8 +34,8 @@ def test_struct_layout_matches_header():
     assert C.sizeof(P.pic_material) == 24
     assert P.pic_config.flags.offset == C.sizeof(P.pic_config) - 8
     assert C.sizeof(P.pic_stats) == 40
-    assert C.sizeof(P.pic_tuning) == 8
-    assert P.pic_tune_report.us_per_step.offset == 144 and C.sizeof(P.pic_tune_report) == 352
+    assert C.sizeof(P.pic_tuning) == 12
+    assert P.pic_tune_report.us_per_step.offset == 256 and C.sizeof(P.pic_tune_report) == 512
 
 
 def _cfg(**kw):
@@ -119,7 +119,7 @@ def test_tuning_and_batch_entry_points_reject_null_on_host():
     """The launch-setting and batch entry points answer PIC_ERR_ARG for a NULL
     handle or batch without touching the device."""
     L = P.load()
-    t = P.pic_tuning(4096, 16)
+    t = P.pic_tuning(4096, 16, 256)
     r = P.pic_tune_report()
     assert L.pic_get_tuning(None, C.byref(t)) == ERR_ARG
     assert L.pic_set_tuning(None, C.byref(t)) == ERR_ARG

@@ -1,15 +1,15 @@
 """Launch tuning (pic_get_tuning / pic_set_tuning / pic_tune, include/pic.h):
 settings that change how fast a step runs, never what it computes.
 
-- Switching the deposit's shared-memory box and the sort interval in the
-  middle of a run (after a captured 64-step block, so the graph is rebuilt)
+- Switching the deposit's shared-memory box, the sort interval and the
+  interior field kernels' block size in the middle of a run (after a captured 64-step block, so the graph is rebuilt)
   keeps the FP64 path within 1e-10 of the FP64 oracle and the FP32 path
   within 2e-5, on a dense bunch (4096 electrons on a 64x24x40 grid), for box
   sizes that send every block to global atomics (0) or let the densest blocks
   accumulate in shared memory (16 KB), and for sort intervals from every step
   to once per block.
 - pic_tune started off a block boundary steps to the boundary, times its
-  nine candidates on real steps, keeps the fastest, and the run it leaves
+  twelve candidates on real steps, keeps the fastest, and the run it leaves
   behind still equals the oracle stepped the same number of steps.
 - pic_batch_tune applies each candidate to every instance of a batch (one
   of them started off a block boundary), then times the lanes (instances
@@ -58,14 +58,14 @@ def oracle200():
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
-@pytest.mark.parametrize("dep,every", [(0, 8), (16384, 1), (2048, 32), (8192, 64)])
-def test_tuning_changes_keep_parity(P, oracle200, prec, tol, dep, every):
+@pytest.mark.parametrize("dep,every,block", [(0, 8, 128), (16384, 1, 512), (2048, 32, 256), (8192, 64, 512)])
+def test_tuning_changes_keep_parity(P, oracle200, prec, tol, dep, every, block):
     w, o = oracle200
     s = P.Simulation(w, P.PIC_FP64 if prec == "fp64" else P.PIC_FP32)
-    assert s.tuning == (4096, 16)
+    assert s.tuning == (4096, 16, 256)
     s.step(64)  # one captured block under the default settings
-    s.set_tuning(dep, every)
-    assert s.tuning == (dep, every)
+    s.set_tuning(dep, every, block)
+    assert s.tuning == (dep, every, block)
     s.step(136)
     s.sync()
     assert rel(s, o) <= tol
@@ -84,16 +84,18 @@ def test_tune_off_a_block_boundary_keeps_parity(P):
     s.step(70)
     rep = s.tune(rounds=1)
     n = 70 + rep["steps"]
-    assert rep["steps"] == (64 - 70 % 64) + 9 * 64
+    assert rep["steps"] == (64 - 70 % 64) + 12 * 64
     assert s.stats().step == n
     cands = [c for c, _ in rep["candidates"]]
-    assert len(cands) == 9 and rep["best"] in cands and s.tuning == rep["best"]
+    assert len(cands) == 12 and rep["best"] in cands and s.tuning == rep["best"]
     assert [c[0] for c in cands[:5]] == [0, 2048, 4096, 8192, 16384]
-    assert [c[1] for c in cands[5:]] == [8, 16, 32, 64]
+    assert [c[1] for c in cands[5:9]] == [8, 16, 32, 64]
+    assert [c[2] for c in cands[9:]] == [128, 256, 512]
     assert all(us > 0 for _, us in rep["candidates"])
-    box_pass, sort_pass = rep["candidates"][:5], rep["candidates"][5:]
+    box_pass, sort_pass, block_pass = rep["candidates"][:5], rep["candidates"][5:9], rep["candidates"][9:]
     assert rep["best"][0] == min(box_pass, key=lambda cu: cu[1])[0][0]
-    assert rep["best"] == min(sort_pass, key=lambda cu: cu[1])[0]
+    assert rep["best"][1] == min(sort_pass, key=lambda cu: cu[1])[0][1]
+    assert rep["best"] == min(block_pass, key=lambda cu: cu[1])[0]
     s.step(30)
     s.sync()
     o = O.from_workload(dense(0))
@@ -110,9 +112,9 @@ def test_batch_tune_keeps_parity(P):
     sims[1].step(10)  # off a block boundary
     b = P.Batch(sims)
     rep = b.tune(rounds=1)
-    # nine launch-setting candidates, then the lanes below the instance count: one chain, or all side by side
-    assert rep["steps"] == 11 * 64 and len(rep["candidates"]) == 11
-    assert rep["lanes"][9:] == [1, 0] and rep["best_lanes"] in (1, 0)
+    # twelve launch-setting candidates, then the lanes below the instance count: one chain, or all side by side
+    assert rep["steps"] == 14 * 64 and len(rep["candidates"]) == 14
+    assert rep["lanes"][12:] == [1, 0] and rep["best_lanes"] in (1, 0)
     assert all(x.tuning == rep["best"] for x in sims)
     b.set_lanes(1)  # the two instances one after another inside the batch graph
     b.step(64)
@@ -120,7 +122,7 @@ def test_batch_tune_keeps_parity(P):
     b.step(64)
     b.sync()
     n = [x.stats().step for x in sims]
-    assert n == [11 * 64 + 128, 64 + 11 * 64 + 128]
+    assert n == [14 * 64 + 128, 64 + 14 * 64 + 128]
     for w, x, k in zip(ws, sims, n):
         o = O.from_workload(w)
         o.step(k)
@@ -132,11 +134,12 @@ def test_batch_tune_keeps_parity(P):
         x.close()
 
 
-@pytest.mark.parametrize("dep,every", [(1000, 16), (32768, 16), (-16, 16), (4096, 3), (4096, 128), (4096, 0)])
-def test_invalid_tuning_rejected(P, dep, every):
+@pytest.mark.parametrize("dep,every,block", [(1000, 16, 256), (32768, 16, 256), (-16, 16, 256), (4096, 3, 256),
+                                             (4096, 128, 256), (4096, 0, 256), (4096, 16, 100), (4096, 16, 1024)])
+def test_invalid_tuning_rejected(P, dep, every, block):
     s = P.Simulation(dense(0), P.PIC_FP32)
-    s.set_tuning(8192, 32)
+    s.set_tuning(8192, 32, 512)
     with pytest.raises(P.PicError):
-        s.set_tuning(dep, every)
-    assert s.tuning == (8192, 32)
+        s.set_tuning(dep, every, block)
+    assert s.tuning == (8192, 32, 512)
     s.close()
