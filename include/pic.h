@@ -239,11 +239,12 @@ int pic_profile_steps(pic_handle *h, int64_t nsteps, double *out_us);
  *                   Default 4096.
  *   sort_every      electrons are re-sorted by 4x4x4-cell brick every this
  *                   many steps: 1, 2, 4, 8, 16, 32 or 64.  Default 16.
- *   field_block     threads per block of the FP32 interior field kernels (four
- *                   x cells per thread, blocks taken in turn over the boxes of
- *                   the grid): 128, 256 or 512.  Default 256.  No effect on
- *                   the FP64 state or on grids the four-cell kernels do not
- *                   take.
+ *   field_block     threads per block of the FP32 field kernels of the cells
+ *                   away from the absorbing slabs (the H update, and the E
+ *                   update on planes without metal; four x cells per thread,
+ *                   blocks taken in turn over the boxes of the grid): 128, 256
+ *                   or 512.  Default 256.  No effect on the FP64 state or on
+ *                   grids the four-cell kernels do not take.
  * The settings belong to the handle, not to the simulation state: pic_save
  * does not write them and pic_load leaves the handle's settings as they are. */
 typedef struct {

@@ -370,8 +370,9 @@ __global__ void __launch_bounds__(512) k_E4_vac(Grid<float> g, Fields<float> f, 
     BOX_CELL(bl);
     e4<false, false>(g, f, i0, j, k, *f.step, b.cE);
 }
-// metal or several materials, no absorbing layer
-__global__ void __launch_bounds__(512) k_E4_mat(Grid<float> g, Fields<float> f, BoxList bl) {
+// metal or several materials, no absorbing layer (256-thread blocks: its
+// register count would rise above 80 under a 512-thread bound)
+__global__ void __launch_bounds__(256) k_E4_mat(Grid<float> g, Fields<float> f, BoxList bl) {
     BOX_CELL(bl);
     e4<false, true>(g, f, i0, j, k, *f.step, 0.f);
 }
@@ -466,7 +467,7 @@ void launch_v4_E(const Grid<float> &g, const Fields<float> &f, const FieldPlan &
     launch_list(k_E4_cpml_vac, g, f, plan.fvac, s2);
     launch_list(k_E4_cpml_mat, g, f, plan.fmat, s4);
     launch_list(k_E4_vac, g, f, plan.vac, s, plan.block);
-    launch_list(k_E4_mat, g, f, plan.mat, s3, plan.block);
+    launch_list(k_E4_mat, g, f, plan.mat, s3);
 }
 
 }  // namespace pic

@@ -150,7 +150,7 @@ struct BoxList {
 // metal or mixed materials (mat), inside and over the slabs (E).
 struct FieldPlan {
     BoxList bulk, faces, vac, mat, fvac, fmat;
-    int block = 256;  // threads per block of the interior kernels (bulk, vac, mat): 128, 256 or 512
+    int block = 256;  // threads per block of the interior vacuum kernels (bulk H, vac E): 128, 256 or 512
 };
 // FP32 four-cells-per-thread field kernels (nx % 4 == 0), fields_v4.cu
 // bulk/interior boxes on s, boxes over the absorbing slabs on s2 (may be s)
