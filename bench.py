@@ -91,7 +91,10 @@ def measured_peak():
 def algorithmic_bytes(w, real_bytes):
     """Bytes each field kernel must move per launch at minimum (one read of
     every input it needs, one write of every output), counted from the
-    workload geometry.  See the design doc for the per-cell figures."""
+    workload geometry: per cell 9 state values (H: read E and H, write H;
+    E: read H and E, write E) and, for E, 3 bytes of edge classes; per cell
+    and absorbing-slab axis 2 psi values read and written; per metal edge
+    J_p read and written."""
     N = w.ncells
     L = w.cpml_cells
     n = (w.nx, w.ny, w.nz)
