@@ -276,8 +276,8 @@ typedef struct {
  * passes of the candidates above, each candidate stepping one whole 64-step
  * block (CUDA events on the simulation's stream); each candidate keeps its
  * fastest block, and the fastest candidate is kept.  The blocks are real
- * steps of the simulation (it advances by report->steps = rounds x 12 x 64
- * steps, plus up to 63 steps to reach a block boundary first).  `report`
+ * steps of the simulation: it first steps to a block boundary (0 to 63
+ * steps), then rounds x 12 x 64 steps; report->steps counts both.  `report`
  * may be NULL.  Synchronises.  Errors: PIC_ERR_ARG, PIC_ERR_CUDA. */
 int pic_tune(pic_handle *h, int32_t rounds, pic_tune_report *report);
 
