@@ -396,6 +396,23 @@ def bench_adjoint(args):
                              "dmask_rel_l2": float(np.linalg.norm(r32["dm"] - r64["dm"]) / np.linalg.norm(r64["dm"])),
                              "dwp_rel": abs(r32["dwp"] / r64["dwp"] - 1), "dgamma_rel": abs(r32["dga"] / r64["dga"] - 1)},
             "fp64_forward_s": r64["fwd"], "fp64_backward_s": r64["bwd"]}
+    # checkpoint mode: field states every 64 steps, segments recomputed in the backward run
+    cfg_c = A.film_config(precision=pic.PIC_FP32)
+    cfg_c.flags = 2
+    st = A.Adjoint(cfg_c)
+    mask = np.random.default_rng(1505).uniform(0.2, 0.8, st.n)
+    st.forward(mask, wp, gamma)
+    t0 = time.perf_counter()
+    loss_c = st.forward(mask, wp, gamma)
+    t1 = time.perf_counter()
+    dm_c, _, _ = st.backward()
+    t2 = time.perf_counter()
+    st.close()
+    line["checkpoint_mode"] = {
+        "forward_s": t1 - t0, "backward_s": t2 - t1,
+        "forward_plus_backward_vs_plain": (t2 - t0) / plain_s,
+        "vs_stored_steps": {"loss_equal": loss_c == r32["loss"],
+                            "dmask_rel_l2": float(np.linalg.norm(dm_c - r32["dm"]) / np.linalg.norm(r32["dm"]))}}
     peak, src = measured_peak()
     fb, bb = adjoint_bytes(cfg, 4)
     f_gbs = fb / (r32["fwd"] / steps) / 1e9

@@ -53,7 +53,8 @@ typedef struct {
     double probe[3];        /* [m] */
     int32_t probe_comp;     /* 0..2: Ex, Ey, Ez */
     int32_t flags;          /* bit 0: keep the one-cell-per-thread kernels where the FP32
-                               four-cell ones would run (nx and cpml_cells multiples of 4) */
+                               four-cell ones would run (nx and cpml_cells multiples of 4);
+                               bit 1: checkpoint mode (below) */
     double omega0;          /* loss frequency [rad/s] */
     int64_t nsteps;
 } pic_adj_config;
@@ -78,7 +79,15 @@ int pic_adj_mask_size(const pic_adj *a, int64_t *n);
 int pic_adj_forward(pic_adj *a, const double *mask, double wp, double gamma, double *loss);
 
 /* Gradients of the L of the last forward run: dmask (host, mask size), dwp,
- * dgamma.  Errors: PIC_ERR_STATE without a forward run.  Synchronises. */
+ * dgamma.  Errors: PIC_ERR_STATE without a forward run.  Synchronises.
+ *
+ * Checkpoint mode (flags bit 1): instead of every step's E^n and J^n on the
+ * design edges, the forward run keeps the whole field state (E, H, J, CPML
+ * memory) every C = 64 ceil(sqrt(nsteps) / 64) steps, and the backward run
+ * recomputes each segment of C steps from its checkpoint before running it
+ * backward.  Memory: (ceil(nsteps / C) - 1) field states + C steps of design
+ * edges instead of nsteps steps of design edges; time: one more forward run.
+ * The results are those of the default mode (the same forward arithmetic). */
 int pic_adj_backward(pic_adj *a, double *dmask, double *dwp, double *dgamma);
 
 /* Release everything.  NULL is accepted. */

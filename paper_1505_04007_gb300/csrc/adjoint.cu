@@ -53,6 +53,7 @@ struct AState {
     T *stE, *stJ;                // per step and slot: E^n, J^n
     double *gb, *gk;             // per slot: dL/dbJ, dL/dkJ contributions
     long long *n;                // device step counter (forward: next step; backward: steps left)
+    long long seg;               // steps n with rows n % seg in the storage (all steps, or one segment)
     int *bx;                     // x index range [bx[0], bx[1]] of the bunch's Ex edges in the current step
 };
 
@@ -174,15 +175,15 @@ __device__ __forceinline__ int design_slot(const AGrid<T> &g, const AState<T> &f
 }
 
 // Eq. 6 (design edges) then Eq. 8 for component c of edge e at plane k;
-// E^n and J^n of a design edge go to storage row n on the way
+// E^n and J^n of a design edge go to storage row n % seg (nr) on the way
 template <typename T>
 __device__ __forceinline__ void fwd_ampere(const AGrid<T> &g, const AState<T> &f, int c, long long e, int k,
-                                           long long n, T curl, T js) {
+                                           long long nr, T curl, T js) {
     T E = f.E[c][e], jp = T(0);
     const int sl = design_slot(g, f, c, e, k);
     if (sl >= 0) {
         const T j0 = f.J[c][e];
-        const long long row = n * f.soff[3] + sl;
+        const long long row = nr * f.soff[3] + sl;
         f.stE[row] = E;
         f.stJ[row] = j0;
         jp = j0 + (g.kJm1 * j0 + f.beta[sl] * E);
@@ -195,7 +196,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_fwd_E(AGrid<T> g, AState<T> f, Bunch bu, double dt) {
     pdl_wait();
     pdl_release();
-    const long long n = *f.n;
+    const long long n = *f.n, nr = n % f.seg;
     const double t_half = (n + 0.5) * dt;
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(256) k_fwd_E(AGrid<T> g, AState<T> f, Bunch bu
             const long long q = apsi(g.n, g.L, 2, s2, i, j, k);
             pz = f.psiE[2][0][q] + (f.bE[2][k] * f.psiE[2][0][q] + f.aE[2][k] * dHy_dz); f.psiE[2][0][q] = pz;
         }
-        fwd_ampere(g, f, 0, e, k, n, ky * dHz_dy + py - kz * dHy_dz - pz, (T)bunch_jx(bu, f.bx, i, j, k, t_half));
+        fwd_ampere(g, f, 0, e, k, nr, ky * dHz_dy + py - kz * dHy_dz - pz, (T)bunch_jx(bu, f.bx, i, j, k, t_half));
     }
     if (!(fx || fz)) {
         const T dHx_dz = (hx - f.H[0][e - okm]) * g.r[2], dHz_dx = (hz - f.H[2][e - oim]) * g.r[0];
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(256) k_fwd_E(AGrid<T> g, AState<T> f, Bunch bu
             const long long q = apsi(g.n, g.L, 0, s0, i, j, k);
             px = f.psiE[0][0][q] + (f.bE[0][i] * f.psiE[0][0][q] + f.aE[0][i] * dHz_dx); f.psiE[0][0][q] = px;
         }
-        fwd_ampere(g, f, 1, e, k, n, kz * dHx_dz + pz - kx * dHz_dx - px, T(0));
+        fwd_ampere(g, f, 1, e, k, nr, kz * dHx_dz + pz - kx * dHz_dx - px, T(0));
     }
     if (!(fx || fy)) {
         const T dHy_dx = (hy - f.H[1][e - oim]) * g.r[0], dHx_dy = (hx - f.H[0][e - ojm]) * g.r[1];
@@ -248,8 +249,13 @@ __global__ void __launch_bounds__(256) k_fwd_E(AGrid<T> g, AState<T> f, Bunch bu
             const long long q = apsi(g.n, g.L, 1, s1, i, j, k);
             py = f.psiE[1][0][q] + (f.bE[1][j] * f.psiE[1][0][q] + f.aE[1][j] * dHx_dy); f.psiE[1][0][q] = py;
         }
-        fwd_ampere(g, f, 2, e, k, n, kx * dHy_dx + px - ky * dHx_dy - py, T(0));
+        fwd_ampere(g, f, 2, e, k, nr, kx * dHy_dx + px - ky * dHx_dy - py, T(0));
     }
+}
+
+// the step counter set on the device (kept in stream order with the steps)
+__global__ void k_set_counter(long long *n, long long v) {
+    if (threadIdx.x == 0) *n = v;
 }
 
 // the probe term of the last step, after the last E update
@@ -282,13 +288,13 @@ __device__ __forceinline__ void probe_source(const AState<T> &f, const Probe &p,
 // accumulates the bJ / kJ gradients with the stored E^n, J^n.
 template <typename T>
 __device__ __forceinline__ void adj_ampere(const AGrid<T> &g, const AState<T> &f, int c, long long e, int k, T lE,
-                                           long long n) {
+                                           long long nr) {
     const int sl = design_slot(g, f, c, e, k);
     if (sl < 0) return;  // lambda_E passes through unchanged
     const long long ne = f.soff[3];
     const T LJ = f.lJ[c][e] - g.cE * lE;  // adjoint of J^{n+1}
-    f.gb[sl] += (double)LJ * (double)f.stE[n * ne + sl];
-    f.gk[sl] += (double)LJ * (double)f.stJ[n * ne + sl];
+    f.gb[sl] += (double)LJ * (double)f.stE[nr * ne + sl];
+    f.gk[sl] += (double)LJ * (double)f.stJ[nr * ne + sl];
     f.lJ[c][e] = (T(1) + g.kJm1) * LJ;
     f.lE[c][e] = lE + f.beta[sl] * LJ;
 }
@@ -298,7 +304,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_adj_E(AGrid<T> g, AState<T> f, Probe pr, const double *F) {
     pdl_wait();
     pdl_release();
-    const long long n = *f.n - 1;
+    const long long n = *f.n - 1, nr = n % f.seg;
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     if (i >= nx || j >= ny) return;
@@ -329,7 +335,7 @@ __global__ void __launch_bounds__(256) k_adj_E(AGrid<T> g, AState<T> f, Probe pr
         }
         scat(f.lH[2], sy, j > 0, g.r[1], Ay);
         scat(f.lH[1], sz, k > 0, g.r[2], Az);
-        adj_ampere(g, f, 0, e, k, lE, n);
+        adj_ampere(g, f, 0, e, k, lE, nr);
     }
     if (!(fx || fz)) {  // Ey: curl = kz dHx/dz + pz - kx dHz/dx - px
         const T lE = f.lE[1][e];
@@ -348,7 +354,7 @@ __global__ void __launch_bounds__(256) k_adj_E(AGrid<T> g, AState<T> f, Probe pr
         }
         scat(f.lH[0], sz, k > 0, g.r[2], Az);
         scat(f.lH[2], 1, i > 0, g.r[0], Ax);
-        adj_ampere(g, f, 1, e, k, lE, n);
+        adj_ampere(g, f, 1, e, k, lE, nr);
     }
     if (!(fx || fy)) {  // Ez: curl = kx dHy/dx + px - ky dHx/dy - py
         const T lE = f.lE[2][e];
@@ -367,7 +373,7 @@ __global__ void __launch_bounds__(256) k_adj_E(AGrid<T> g, AState<T> f, Probe pr
         }
         scat(f.lH[1], 1, i > 0, g.r[0], Ax);
         scat(f.lH[0], sy, j > 0, g.r[1], Ay);
-        adj_ampere(g, f, 2, e, k, lE, n);
+        adj_ampere(g, f, 2, e, k, lE, nr);
     }
 }
 
@@ -538,7 +544,7 @@ __global__ void __launch_bounds__(256) k_fwd_H4(AGrid<float> g, AState<float> f,
 // Eq. 6 on the design edges among the four, then Eq. 8, for component c of
 // cells e..e+3 at plane k; held cells (upd false) keep E, J and psi.
 __device__ __forceinline__ void fwd_ampere4(const AGrid<float> &g, const AState<float> &f, int c, long long e, int k,
-                                            long long n, const float curl[4], const float js[4], const bool upd[4]) {
+                                            long long nr, const float curl[4], const float js[4], const bool upd[4]) {
     V4 E = ld4(f.E[c] + e);
     if (k >= g.ks0 && k < g.ks1) {
         const int4 s4 = *reinterpret_cast<const int4 *>(f.slot[c] + e);
@@ -549,7 +555,7 @@ __device__ __forceinline__ void fwd_ampere4(const AGrid<float> &g, const AState<
             float jp = 0.f;
             if (sl[m] >= 0 && upd[m]) {
                 const float j0 = f.J[c][e + m];
-                const long long row = n * ne + sl[m];
+                const long long row = nr * ne + sl[m];
                 f.stE[row] = E.v[m];
                 f.stJ[row] = j0;
                 jp = j0 + (g.kJm1 * j0 + f.beta[sl[m]] * E.v[m]);
@@ -585,7 +591,7 @@ __device__ __forceinline__ void psi4(float *psi, long long q, const float *bb, c
 __global__ void __launch_bounds__(256) k_fwd_E4(AGrid<float> g, AState<float> f, Bunch bu, double dt) {
     pdl_wait();
     pdl_release();
-    const long long n = *f.n;
+    const long long n = *f.n, nr = n % f.seg;
     const double t_half = (n + 0.5) * dt;
     int i0, j, k;
     if (!group_of(g, i0, j, k)) return;
@@ -614,7 +620,7 @@ __global__ void __launch_bounds__(256) k_fwd_E4(AGrid<float> g, AState<float> f,
         if (s2 >= 0) psi4(f.psiE[2][0], apsi(g.n, g.L, 2, s2, i0, j, k), f.bE[2], f.aE[2], f.ikE[2], k, false, d2, upd, p2, k2);
 #pragma unroll
         for (int m = 0; m < 4; m++) curl[m] = k1[m] * d1[m] + p1[m] - k2[m] * d2[m] - p2[m];
-        fwd_ampere4(g, f, 0, e, k, n, curl, js, upd);
+        fwd_ampere4(g, f, 0, e, k, nr, curl, js, upd);
     }
     if (!fz) {  // Ey: d1 = dHx/dz (psi_E[2][1]), d2 = dHz/dx (psi_E[0][0]); cell 0 held on the x face
         const V4 hx_km = ld4(f.H[0] + e - okm);
@@ -630,7 +636,7 @@ __global__ void __launch_bounds__(256) k_fwd_E4(AGrid<float> g, AState<float> f,
         if (s0 >= 0) psi4(f.psiE[0][0], apsi(g.n, g.L, 0, s0, i0, j, k), f.bE[0], f.aE[0], f.ikE[0], i0, true, d2, upd, p2, k2);
 #pragma unroll
         for (int m = 0; m < 4; m++) curl[m] = k1[m] * d1[m] + p1[m] - k2[m] * d2[m] - p2[m];
-        fwd_ampere4(g, f, 1, e, k, n, curl, zero, upd);
+        fwd_ampere4(g, f, 1, e, k, nr, curl, zero, upd);
     }
     if (!fy) {  // Ez: d1 = dHy/dx (psi_E[0][1]), d2 = dHx/dy (psi_E[1][0]); cell 0 held on the x face
         const V4 hx_jm = ld4(f.H[0] + e - ojm);
@@ -646,7 +652,7 @@ __global__ void __launch_bounds__(256) k_fwd_E4(AGrid<float> g, AState<float> f,
         if (s1 >= 0) psi4(f.psiE[1][0], apsi(g.n, g.L, 1, s1, i0, j, k), f.bE[1], f.aE[1], f.ikE[1], j, false, d2, upd, p2, k2);
 #pragma unroll
         for (int m = 0; m < 4; m++) curl[m] = k1[m] * d1[m] + p1[m] - k2[m] * d2[m] - p2[m];
-        fwd_ampere4(g, f, 2, e, k, n, curl, zero, upd);
+        fwd_ampere4(g, f, 2, e, k, nr, curl, zero, upd);
     }
 }
 
@@ -767,14 +773,23 @@ struct AdjSim : AdjBase {
     cudaStream_t stream = nullptr;
     bool use4 = false;  // FP32 with four-cell groups (nx and the CPML width multiples of 4)
     static constexpr int GRAPH_STEPS = 64;  // steps per captured graph (forward and backward)
-    cudaGraphExec_t gfwd = nullptr, gbwd = nullptr;
+    cudaGraphExec_t gfwd = nullptr, gbwd = nullptr, grec = nullptr;  // forward, backward, recompute
     double wp_last = 0, gamma_last = 0;
     bool have_forward = false;
+    // checkpoint mode (flags bit 1): the field state every C steps; each
+    // segment's E^n, J^n are recomputed from its checkpoint during the backward
+    bool ckpt = false;
+    long long C = 0, K = 1;                               // segment length, segments
+    std::vector<std::pair<T *, size_t>> state;            // the forward state arrays (E, H, J, psi)
+    size_t state_elems = 0;
+    T *ckbuf = nullptr;                                   // checkpoints 1..K-1 (0 is the zero state)
+    double *d_Fr = nullptr;                               // probe sum of the recomputed steps (discarded)
 
     ~AdjSim() override {
         if (stream) cudaStreamSynchronize(stream);
         if (gfwd) cudaGraphExecDestroy(gfwd);
         if (gbwd) cudaGraphExecDestroy(gbwd);
+        if (grec) cudaGraphExecDestroy(grec);
         for (void *p : allocs) cudaFree(p);
         if (stream) cudaStreamDestroy(stream);
     }
@@ -859,10 +874,20 @@ struct AdjSim : AdjBase {
             soff[comp + 1] = (long long)eidx_h.size();
         }
         ne = (long long)eidx_h.size();
+        ckpt = (c->flags & 2) != 0;
+        if (ckpt) {  // segments of 64 * ceil(sqrt(nsteps) / 64) steps
+            const long long r = (long long)std::ceil(std::sqrt((double)c->nsteps) / GRAPH_STEPS);
+            C = GRAPH_STEPS * std::max(1LL, r);
+            K = (c->nsteps + C - 1) / C;
+        } else {
+            C = c->nsteps;
+            K = 1;
+        }
+        f.seg = C;
         const size_t per_step = (size_t)ne * 2 * sizeof(T);
-        if (per_step && (size_t)c->nsteps > ((size_t)1 << 40) / per_step)
+        if (per_step && (size_t)C > ((size_t)1 << 40) / per_step)
             return set_last_error(PIC_ERR_OOM, "adjoint storage of %lld steps x %lld edges is too large",
-                                  (long long)c->nsteps, ne);
+                                  (long long)C, ne);
         // device arrays
         int rc = 0;
         for (int a = 0; a < 3 && !rc; a++) {
@@ -892,9 +917,25 @@ struct AdjSim : AdjBase {
         rc = rc ? rc : take(&beta_d, ne + 1);
         rc = rc ? rc : take(&f.gb, ne + 1);
         rc = rc ? rc : take(&f.gk, ne + 1);
-        rc = rc ? rc : take(&f.stE, (size_t)ne * c->nsteps + 1);
-        rc = rc ? rc : take(&f.stJ, (size_t)ne * c->nsteps + 1);
+        rc = rc ? rc : take(&f.stE, (size_t)ne * C + 1);
+        rc = rc ? rc : take(&f.stJ, (size_t)ne * C + 1);
         rc = rc ? rc : take(&d_F, 2);
+        rc = rc ? rc : take(&d_Fr, 2);
+        if (!rc) {
+            for (int a = 0; a < 3; a++) {
+                state.emplace_back(f.E[a], (size_t)N);
+                state.emplace_back(f.H[a], (size_t)N);
+                state.emplace_back(f.J[a], (size_t)N);
+                const size_t slab = (size_t)(N / g.n[a]) * 2 * g.L;
+                for (int s2 = 0; s2 < 2; s2++) {
+                    state.emplace_back(f.psiH[a][s2], slab);
+                    state.emplace_back(f.psiE[a][s2], slab);
+                }
+            }
+            state_elems = 0;
+            for (auto &st : state) state_elems += st.second;
+            if (ckpt && K > 1) rc = take(&ckbuf, state_elems * (size_t)(K - 1));
+        }
         rc = rc ? rc : take(&f.n, 1);
         rc = rc ? rc : take(&f.bx, 2);
         if (rc) return rc;
@@ -971,18 +1012,28 @@ struct AdjSim : AdjBase {
     }
 
     void clear_forward() {
-        for (int a = 0; a < 3; a++) {
-            cudaMemsetAsync(f.E[a], 0, N * sizeof(T), stream);
-            cudaMemsetAsync(f.H[a], 0, N * sizeof(T), stream);
-            cudaMemsetAsync(f.J[a], 0, N * sizeof(T), stream);
-            const size_t slab = (size_t)(N / g.n[a]) * 2 * g.L;
-            for (int s = 0; s < 2; s++) {
-                cudaMemsetAsync(f.psiH[a][s], 0, slab * sizeof(T), stream);
-                cudaMemsetAsync(f.psiE[a][s], 0, slab * sizeof(T), stream);
-            }
-        }
+        for (auto &st : state) cudaMemsetAsync(st.first, 0, st.second * sizeof(T), stream);
         cudaMemsetAsync(d_F, 0, 2 * sizeof(double), stream);
         cudaMemsetAsync(f.n, 0xff, sizeof(long long), stream);  // -1: no step taken yet
+    }
+    // the forward state to or from checkpoint k (1..K-1)
+    void save_state(long long k) {
+        T *dst = ckbuf + state_elems * (size_t)(k - 1);
+        for (auto &st : state) {
+            cudaMemcpyAsync(dst, st.first, st.second * sizeof(T), cudaMemcpyDeviceToDevice, stream);
+            dst += st.second;
+        }
+    }
+    void load_state(long long k) {
+        if (k == 0) {
+            for (auto &st : state) cudaMemsetAsync(st.first, 0, st.second * sizeof(T), stream);
+            return;
+        }
+        const T *src = ckbuf + state_elems * (size_t)(k - 1);
+        for (auto &st : state) {
+            cudaMemcpyAsync(st.first, src, st.second * sizeof(T), cudaMemcpyDeviceToDevice, stream);
+            src += st.second;
+        }
     }
     void clear_adjoint() {
         for (int a = 0; a < 3; a++) {
@@ -1016,22 +1067,25 @@ struct AdjSim : AdjBase {
     void drop_graphs() {
         if (gfwd) cudaGraphExecDestroy(gfwd);
         if (gbwd) cudaGraphExecDestroy(gbwd);
-        gfwd = gbwd = nullptr;
+        if (grec) cudaGraphExecDestroy(grec);
+        gfwd = gbwd = grec = nullptr;
     }
-    void launch_forward_steps(int count) {
+    void launch_forward_steps(int count) { launch_forward_steps(count, d_F); }
+    // forward steps that add their probe terms to Fp
+    void launch_forward_steps(int count, double *Fp) {
         const dim3 gr = grid3(), bl = block3();
         if constexpr (std::is_same<T, float>::value) {
             if (use4) {
                 const dim3 g4 = grid4(), b4 = block4();
                 for (int q = 0; q < count; q++) {
-                    launch_pdl(k_fwd_H4, g4, b4, 0, stream, g, f, pr, d_F, bu, cfg.dt);
+                    launch_pdl(k_fwd_H4, g4, b4, 0, stream, g, f, pr, Fp, bu, cfg.dt);
                     launch_pdl(k_fwd_E4, g4, b4, 0, stream, g, f, bu, cfg.dt);
                 }
                 return;
             }
         }
         for (int q = 0; q < count; q++) {
-            launch_pdl(k_fwd_H<T>, gr, bl, 0, stream, g, f, pr, d_F, bu, cfg.dt);
+            launch_pdl(k_fwd_H<T>, gr, bl, 0, stream, g, f, pr, Fp, bu, cfg.dt);
             launch_pdl(k_fwd_E<T>, gr, bl, 0, stream, g, f, bu, cfg.dt);
         }
     }
@@ -1054,12 +1108,13 @@ struct AdjSim : AdjBase {
     }
     // one block of GRAPH_STEPS steps from a graph captured on first use (the
     // step index lives in device memory, so one graph serves every block)
-    int run_block(bool fwd, cudaGraphExec_t &exec) {
+    // fwd: forward steps adding to Fp; else backward steps
+    int run_block(bool fwd, cudaGraphExec_t &exec, double *Fp = nullptr) {
         if (!exec) {
             cudaGraph_t graph = nullptr;
             if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
                 return set_last_error(PIC_ERR_CUDA, "adjoint: graph capture failed to start");
-            if (fwd) launch_forward_steps(GRAPH_STEPS);
+            if (fwd) launch_forward_steps(GRAPH_STEPS, Fp ? Fp : d_F);
             else launch_backward_steps(GRAPH_STEPS);
             cudaError_t e = cudaStreamEndCapture(stream, &graph);
             if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
@@ -1100,15 +1155,16 @@ struct AdjSim : AdjBase {
         // hold the old kJ-1, so they are rebuilt when gamma changes
         if (gfwd && kJm1_captured != g.kJm1) drop_graphs();
         clear_forward();
-        long long left = cfg.nsteps;
+        long long done = 0;
         int rc = 0;
-        while (left > 0 && !rc) {
-            if (left >= GRAPH_STEPS) {
+        while (done < cfg.nsteps && !rc) {
+            if (ckpt && done > 0 && done % C == 0) save_state(done / C);  // the state after done steps
+            if (cfg.nsteps - done >= GRAPH_STEPS) {
                 rc = run_block(true, gfwd);
-                left -= GRAPH_STEPS;
+                done += GRAPH_STEPS;
             } else {
-                launch_forward_steps((int)left);
-                left = 0;
+                launch_forward_steps((int)(cfg.nsteps - done));
+                done = cfg.nsteps;
             }
         }
         if (rc) return rc;
@@ -1128,20 +1184,37 @@ struct AdjSim : AdjBase {
         if (!have_forward) return set_last_error(PIC_ERR_STATE, "pic_adj_backward needs a forward run first");
         if (!dmask || !dwp || !dgamma) return set_last_error(PIC_ERR_ARG, "NULL argument");
         clear_adjoint();
-        {
-            const long long nst = cfg.nsteps;
-            cudaMemcpyAsync(f.n, &nst, sizeof(long long), cudaMemcpyHostToDevice, stream);
-            cudaStreamSynchronize(stream);  // nst lives on this stack frame
-        }
-        long long left = cfg.nsteps;
         int rc = 0;
-        while (left > 0 && !rc) {
-            if (left >= GRAPH_STEPS) {
-                rc = run_block(false, gbwd);
-                left -= GRAPH_STEPS;
-            } else {
-                launch_backward_steps((int)left);
-                left = 0;
+        // segments from the last to the first (one segment of all steps
+        // unless in checkpoint mode, where each is first recomputed from its
+        // checkpoint to refill the stored E^n, J^n)
+        for (long long sgm = K - 1; sgm >= 0 && !rc; sgm--) {
+            const long long start = sgm * C, len = std::min(C, (long long)cfg.nsteps - start);
+            if (ckpt) {
+                load_state(sgm);
+                k_set_counter<<<1, 32, 0, stream>>>(f.n, start - 1);
+                cudaMemsetAsync(d_Fr, 0, 2 * sizeof(double), stream);
+                long long done = 0;
+                while (done < len && !rc) {
+                    if (len - done >= GRAPH_STEPS) {
+                        rc = run_block(true, grec, d_Fr);
+                        done += GRAPH_STEPS;
+                    } else {
+                        launch_forward_steps((int)(len - done), d_Fr);
+                        done = len;
+                    }
+                }
+            }
+            k_set_counter<<<1, 32, 0, stream>>>(f.n, start + len);  // steps left at the segment's end
+            long long left = len;
+            while (left > 0 && !rc) {
+                if (left >= GRAPH_STEPS) {
+                    rc = run_block(false, gbwd);
+                    left -= GRAPH_STEPS;
+                } else {
+                    launch_backward_steps((int)left);
+                    left = 0;
+                }
             }
         }
         if (rc) return rc;

@@ -15,6 +15,9 @@
 - The FP32 kernels with four x cells per thread (nx and the CPML width
   multiples of 4) against the one-cell FP32 kernels (flags bit 0) and the
   FP64 path on the same study.
+- Checkpoint mode (flags bit 1: segments of 64 steps recomputed from field
+  checkpoints, here 6 whole segments and a partial one) against the default
+  mode: the same loss bit for bit, gradients within the atomic-order rounding.
 """
 import numpy as np
 import pytest
@@ -135,3 +138,23 @@ def test_four_cell_fp32_kernels_match_one_cell_and_fp64(A):
         assert abs(L / L0 - 1) <= tol / 10, (ref, L, L0)
         assert np.linalg.norm(dm - dm0) <= tol * np.linalg.norm(dm0), ref
         assert abs(dw / dw0 - 1) <= tol and abs(dg / dg0 - 1) <= tol, (ref, dw, dw0, dg, dg0)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-4)])
+def test_checkpoint_mode_equals_stored_steps(A, precision, tol):
+    from paper_1505_04007_gb300 import pic
+    prec = pic.PIC_FP64 if precision == "fp64" else pic.PIC_FP32
+    res = {}
+    for flags in (0, 2):
+        cfg = A.film_config(nx=48, ny=24, nz=40, design=(10, 16), nsteps=400, sigma=4e-9, cpml=8, precision=prec)
+        cfg.flags = flags
+        st = A.Adjoint(cfg)
+        mask = np.random.default_rng(19).uniform(0.2, 0.8, st.n)
+        loss = st.forward(mask, WP, GAMMA)
+        res[flags] = (loss, *st.backward())
+        st.close()
+    L0, dm0, dw0, dg0 = res[0]
+    L2, dm2, dw2, dg2 = res[2]
+    assert L2 == L0
+    assert np.linalg.norm(dm2 - dm0) <= tol * np.linalg.norm(dm0)
+    assert abs(dw2 / dw0 - 1) <= tol and abs(dg2 / dg0 - 1) <= tol
