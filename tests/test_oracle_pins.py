@@ -495,3 +495,49 @@ def test_edge_material_average_on_film():
     kJ = o.coeff(0, 0)[12, 20, 60]
     g = W.AG_GAMMA * w.dt
     assert kJ == pytest.approx((2 - g) / (2 + g), rel=1e-15)
+
+
+# ------------------------------------------------------- freeze rule (R11) --
+@pytest.mark.parametrize("target", ["metal", "face"])
+def test_freeze_rule_stops_the_step_that_would_enter(target):
+    """With the deposit off and no fields an electron moves ballistically,
+    x^{n+1} = x^n + dt u / gamma.  It must freeze on exactly the step whose
+    new position would lie in a metal cell (film below it, moving -z) or
+    within two cells of a non-periodic face (moving +x), keep the position it
+    had, and never move again."""
+    n = 24
+    mat = np.zeros((n, n, n), np.uint8)
+    mat[:8] = 1  # metal planes z < 8 cells
+    w = box_workload(n, n, n, bc=(W.BC_PEC,) * 6, material=mat, table=W.drude_table())
+    o = O.Oracle(w)
+    o.set_deposit(False)
+    d = w.dx
+    x0 = np.array([[11.3 * d, 12.5 * d, 12.7 * d]])
+    speed = 0.6 * W.C0  # |u| = gamma beta c
+    gam = math.sqrt(1.0 + (speed / W.C0) ** 2)
+    u = np.array([[0.0, 0.0, -speed]]) if target == "metal" else np.array([[speed, 0.0, 0.0]])
+    o.add_particles(x0, u, -1e-19, W.ME)
+    v = u[0] / gam
+    # the step whose new position is the first one not allowed
+    x = x0[0].copy()
+    stop = None
+    for step in range(200):
+        nxt = x + w.dt * v
+        if target == "metal":
+            bad = nxt[2] < 8 * d
+        else:
+            bad = nxt[0] >= (n - 2) * d  # the allowed region ends two cells before the face
+        if bad:
+            stop = step
+            break
+        x = nxt
+    assert stop is not None
+    o.step(stop)
+    xs, _, s = o.particles()
+    assert s[0] == 0 and np.allclose(xs[0], x, rtol=0, atol=1e-12 * d)
+    o.step(1)
+    xs, _, s = o.particles()
+    assert s[0] == 1 and np.allclose(xs[0], x, rtol=0, atol=1e-12 * d)
+    o.step(5)
+    xs2, _, s2 = o.particles()
+    assert s2[0] == 1 and np.array_equal(xs2, xs)
