@@ -541,3 +541,27 @@ def test_freeze_rule_stops_the_step_that_would_enter(target):
     o.step(5)
     xs2, _, s2 = o.particles()
     assert s2[0] == 1 and np.array_equal(xs2, xs)
+
+
+# --------------------------------------------------------- prescribed current --
+@pytest.mark.parametrize("f0", [0.0, 1.2e15])
+def test_source_current_first_step_closed_form(f0):
+    """From zero fields, one step of a prescribed current J in vacuum gives
+    E^1 = -dt/eps0 J(t_1/2) on the source edges (curl H^1/2 = 0) and leaves
+    every other edge at zero: J = amp exp(-s^2) sin(2 pi f0 (t - t0)) for
+    f0 > 0, amp (-2 s) exp(-s^2) for f0 = 0, s = (t - t0)/tau, t = dt/2."""
+    w = box_workload(12, 12, 12, bc=(W.BC_PEC,) * 6)
+    o = O.Oracle(w)
+    amp, t0, tau = 3.0e9, 2.0 * w.dt, 1.5 * w.dt
+    box = (4, 7, 5, 8, 3, 9)
+    o.add_source(1, box, amp, t0, tau, f0)
+    o.step(1)
+    t = 0.5 * w.dt
+    sarg = (t - t0) / tau
+    J = amp * math.exp(-sarg * sarg) * (math.sin(2 * math.pi * f0 * (t - t0)) if f0 > 0 else -2.0 * sarg)
+    ey = o.get_field(O.E_Y)
+    expect = np.zeros_like(ey)
+    expect[box[4]:box[5], box[2]:box[3], box[0]:box[1]] = -w.dt / W.EPS0 * J
+    assert np.allclose(ey, expect, rtol=1e-14, atol=0)
+    for c in (O.E_X, O.E_Z, O.H_X, O.H_Y, O.H_Z):
+        assert not o.get_field(c).any()
