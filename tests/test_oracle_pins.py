@@ -565,3 +565,33 @@ def test_source_current_first_step_closed_form(f0):
     assert np.allclose(ey, expect, rtol=1e-14, atol=0)
     for c in (O.E_X, O.E_Z, O.H_X, O.H_Y, O.H_Z):
         assert not o.get_field(c).any()
+
+
+# ------------------------------------------------------ edge materials (R6) --
+def test_edge_coefficients_follow_the_four_cell_rule():
+    """Random map of three materials on a grid periodic in y, absorbing in x,
+    conducting in z: every edge's (kJ, bJ, dt/(eps0 eps_inf)) equals the rule
+    written out here from the cell means -- wp^2 averaged over the four cells
+    around the edge (wrapped on the periodic axis, clamped on the others),
+    gamma weighted by wp^2, eps_inf averaged -- through the coefficients of
+    Eq. 6 and Eq. 8."""
+    rng = np.random.default_rng(23)
+    table = np.array([[0.0, 0.0, 1.0], [1.3e16, 3.0e13, 1.0], [0.9e16, 1.1e14, 2.5]])
+    mat = rng.integers(0, 3, (6, 8, 20)).astype(np.uint8)
+    w = box_workload(20, 8, 6, bc=(W.BC_CPML, W.BC_CPML, W.BC_PERIODIC, W.BC_PERIODIC, W.BC_PEC, W.BC_PEC),
+                     material=mat, table=table)
+    w.cpml_cells = 4
+    o = O.Oracle(w)
+    dt = w.dt
+    for c in range(3):
+        wp2 = edge_wp2(w, c)
+        wp2g = edge_wp2(w, c, values=table[:, 0] ** 2 * table[:, 1])
+        einf = edge_wp2(w, c, values=table[:, 2])
+        gam = np.where(wp2 > 0, wp2g / np.where(wp2 > 0, wp2, 1.0), 0.0)
+        kJ = (2 - gam * dt) / (2 + gam * dt)
+        bJ = 2 * dt * W.EPS0 * wp2 / (2 + gam * dt)
+        cE = dt / (W.EPS0 * einf)
+        metal = wp2 > 0
+        assert np.allclose(o.coeff(1, c), bJ, rtol=1e-13, atol=0)
+        assert np.allclose(o.coeff(0, c)[metal], kJ[metal], rtol=1e-13, atol=0)
+        assert np.allclose(o.coeff(2, c), cE, rtol=1e-13, atol=0)
