@@ -595,3 +595,20 @@ def test_edge_coefficients_follow_the_four_cell_rule():
         assert np.allclose(o.coeff(1, c), bJ, rtol=1e-13, atol=0)
         assert np.allclose(o.coeff(0, c)[metal], kJ[metal], rtol=1e-13, atol=0)
         assert np.allclose(o.coeff(2, c), cE, rtol=1e-13, atol=0)
+
+
+def test_oracle_result_does_not_depend_on_thread_count():
+    """The oracle's cell loops run on OpenMP threads and its particles one by
+    one in input order, so the fields and particles after some steps are the
+    same bit for bit on one thread and on several."""
+    w = W.scaled(W.c1(), 48, 24, 40, 256, 30)
+    out = []
+    for threads in (1, 4):
+        O.set_threads(threads)
+        o = O.from_workload(w)
+        o.step(30)
+        out.append(([o.get_field(c) for c in range(6)], o.particles()[0], o.probe_read()))
+    O.set_threads(len(__import__("os").sched_getaffinity(0)))
+    (f1, x1, p1), (f4, x4, p4) = out
+    assert all(np.array_equal(a, b) for a, b in zip(f1, f4))
+    assert np.array_equal(x1, x4) and np.array_equal(p1, p4)
