@@ -253,6 +253,7 @@ typedef struct {
     int32_t field_block;
 } pic_tuning;
 
+/* The handle's current launch settings into *out.  Errors: PIC_ERR_ARG (NULL). */
 int pic_get_tuning(pic_handle *h, pic_tuning *out);
 
 /* Errors: PIC_ERR_ARG (NULL or a value outside the ranges above). */

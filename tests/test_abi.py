@@ -129,3 +129,14 @@ def test_tuning_and_batch_entry_points_reject_null_on_host():
     assert L.pic_batch_step(None, 64) == ERR_ARG
     assert L.pic_batch_sync(None) == ERR_ARG
     assert L.pic_batch_destroy(None) == 0
+
+
+def test_every_entry_point_is_documented_in_its_header():
+    """Each declaration in include/*.h has its comment block right above it
+    (what it computes, the arguments and their layout, the errors)."""
+    for name in ("pic.h", "pic_adjoint.h"):
+        lines = open(os.path.join(ROOT, "include", name)).read().split("\n")
+        for i, line in enumerate(lines):
+            m = re.match(r"^\s*(?:int|const char \*)\s*(pic_\w+)\s*\(", line)
+            if m:
+                assert "*/" in "\n".join(lines[max(0, i - 3):i]), (name, m.group(1))
