@@ -17,8 +17,8 @@
  * current of a rigid Gaussian bunch (charge q, rms radius sigma) moving along
  * +x at speed v:
  *   Js_x(x, t) = q v (2 pi sigma^2)^{-3/2} exp(-|x - x0 - v t e_x|^2 / (2 sigma^2)),
- * set to zero where |x - x0 - v t e_x| > 6 sigma, evaluated on the Ex edges at
- * t = (n + 1/2) dt.
+ * evaluated on every Ex edge of the grid at t = (n + 1/2) dt (no truncation:
+ * the current is zero only where the Gaussian underflows in FP64).
  * Loss:  L = |F|^2,  F = sum_n E_c(x_p, t_{n+1}) exp(+i omega0 t_{n+1}) dt,
  * E_c interpolated trilinearly on its staggered lattice at the probe x_p
  * (the probe DFT of pic_probe_dft at one frequency).
@@ -56,7 +56,8 @@ typedef struct {
                                four-cell ones would run (nx and cpml_cells multiples of 4);
                                bit 1: checkpoint mode (below) */
     double omega0;          /* loss frequency [rad/s] */
-    int64_t nsteps;
+    int64_t nsteps;         /* steps of a forward run; nsteps x nx <= 2^28 (the bunch's
+                               per-step factors are tabulated at create) */
 } pic_adj_config;
 
 typedef struct pic_adj pic_adj;

@@ -15,7 +15,7 @@ with kJ = (2 - gamma dt)/(2 + gamma dt), bJ = 2 dt eps0 wp_e^2/(2 + gamma dt)
 the four cells around the edge (cells below a face clamped to the face; the
 mask is zero outside the design slab), eps_inf = 1.  Tangential E on the six
 faces stays zero, E beyond a high face reads as zero.  Js is the current of a
-rigid Gaussian bunch moving along +x (zero beyond six rms radii):
+rigid Gaussian bunch moving along +x, on every Ex edge (not truncated):
   Js_x = q v (2 pi s^2)^{-3/2} exp(-r^2 / (2 s^2)),  r measured from
   (x0 + v t, y0, z0) to the Ex edge, t = (n + 1/2) dt.
 Loss L = |F|^2 with F = sum_n E_c(x_p, (n+1) dt) exp(+i w0 (n+1) dt) dt, E_c
@@ -173,7 +173,7 @@ class FilmModel:
         z = k * cfg.dx - cfg.bunch_z0
         r2 = x * x + y * y + z * z
         amp = cfg.bunch_q * cfg.bunch_v / (2.0 * math.pi * s * s) ** 1.5
-        return torch.where(r2 <= 36.0 * s * s, amp * torch.exp(-r2 / (2.0 * s * s)), torch.zeros_like(r2))
+        return amp * torch.exp(-r2 / (2.0 * s * s))
 
     def step_H(self, st):
         cfg = self.cfg

@@ -54,14 +54,21 @@ struct AState {
     double *gb, *gk;             // per slot: dL/dbJ, dL/dkJ contributions
     long long *n;                // device step counter (forward: next step; backward: steps left)
     long long seg;               // steps n with rows n % seg in the storage (all steps, or one segment)
-    int *bx;                     // x index range [bx[0], bx[1]] of the bunch's Ex edges in the current step
 };
 
+// The rigid bunch's current on the Ex edges at t = (n + 1/2) dt,
+//   J_x(i+1/2, j, k) = q v (2 pi s^2)^{-3/2} exp(-r^2 / (2 s^2)),
+// on every edge of the grid (it is zero only where the Gaussian underflows).
+// The Gaussian factorises: J_x = gx[n][i] * gyz[k][j] with
+//   gx[n][i] = exp(-((i + 1/2) dx - x0 - v t)^2 / (2 s^2))
+//   gyz[k][j] = q v (2 pi s^2)^{-3/2} exp(-((j dx - y0)^2 + (k dx - z0)^2) / (2 s^2)),
+// both evaluated in FP64 on the host at create (every step of the run), so an
+// edge costs one multiply instead of an FP64 exponential.
 struct Bunch {
-    double qv_norm;  // q v (2 pi sigma^2)^{-3/2}
-    double inv2s2, cut2, cut;
-    double v, x0, y0, z0, dx;
-    int j0, j1, k0, k1;  // rows [j0, j1] x planes [k0, k1] hold every edge within the cut
+    const double *gx64, *gyz64;  // FP64 state
+    const float *gx32, *gyz32;   // FP32 state: the FP64 factors rounded to float
+    int nx, ny;
+    long long nsteps;
 };
 
 struct Probe {
@@ -85,18 +92,13 @@ __device__ __forceinline__ void probe_term(const AState<T> &f, const Probe &p, d
     F[1] += v * sn * p.dt;
 }
 
-// Start of forward step m (one thread): the probe term of step m-1, the
-// counter from m-1 to m, and the columns of Ex edges within the bunch's cut
-// radius at t = (m + 1/2) dt, one column wider on each side.
+// Start of forward step m (one thread): the probe term of step m-1 and the
+// counter from m-1 to m.
 template <typename T>
-__device__ __forceinline__ void fwd_step_start(const AState<T> &f, const Probe &pr, double *F, const Bunch &bu,
-                                               double dt) {
+__device__ __forceinline__ void fwd_step_start(const AState<T> &f, const Probe &pr, double *F) {
     const long long m1 = *f.n;
     if (m1 >= 0) probe_term(f, pr, F, m1);
     *f.n = m1 + 1;
-    const double xc = bu.x0 + bu.v * ((m1 + 1) + 0.5) * dt;
-    f.bx[0] = (int)floor((xc - bu.cut) / bu.dx - 0.5) - 1;
-    f.bx[1] = (int)ceil((xc + bu.cut) / bu.dx - 0.5) + 1;
 }
 
 __device__ __forceinline__ int aslab(int L, int n, int x) {
@@ -119,7 +121,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_fwd_H(AGrid<T> g, AState<T> f, Probe pr, double *F, Bunch bu, double dt) {
     pdl_wait();
     pdl_release();
-    if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0) fwd_step_start(f, pr, F, bu, dt);
+    if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0) fwd_step_start(f, pr, F);
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     if (i >= nx || j >= ny) return;
@@ -159,14 +161,19 @@ __global__ void __launch_bounds__(256) k_fwd_H(AGrid<T> g, AState<T> f, Probe pr
     f.H[2][e] -= g.cH * (kx * dEy_dx + pxz - ky * dEx_dy - pyz);
 }
 
-// the rigid bunch current J_x at the Ex edge (i+1/2, j, k) at time t
-__device__ __forceinline__ double bunch_jx(const Bunch &b, const int *bx, int i, int j, int k, double t) {
-    // FP64 is slow on this part: integer tests against the rows, planes and
-    // (this step's) columns within the cut first
-    if (j < b.j0 || j > b.j1 || k < b.k0 || k > b.k1 || i < bx[0] || i > bx[1]) return 0.0;
-    const double x = (i + 0.5) * b.dx - (b.x0 + b.v * t), y = j * b.dx - b.y0, z = k * b.dx - b.z0;
-    const double r2 = x * x + y * y + z * z;
-    return r2 > b.cut2 ? 0.0 : b.qv_norm * exp(-r2 * b.inv2s2);
+// the rigid bunch current J_x at the Ex edge (i+1/2, j, k) in step n
+// (t = (n + 1/2) dt), in the state precision
+template <typename T>
+__device__ __forceinline__ T bunch_jx(const Bunch &b, int i, int j, int k, long long n);
+template <>
+__device__ __forceinline__ double bunch_jx<double>(const Bunch &b, int i, int j, int k, long long n) {
+    if (n < 0 || n >= b.nsteps) return 0.0;
+    return b.gx64[n * b.nx + i] * b.gyz64[(long long)k * b.ny + j];
+}
+template <>
+__device__ __forceinline__ float bunch_jx<float>(const Bunch &b, int i, int j, int k, long long n) {
+    if (n < 0 || n >= b.nsteps) return 0.f;
+    return b.gx32[n * b.nx + i] * b.gyz32[(long long)k * b.ny + j];
 }
 
 template <typename T>
@@ -197,7 +204,7 @@ __global__ void __launch_bounds__(256) k_fwd_E(AGrid<T> g, AState<T> f, Bunch bu
     pdl_wait();
     pdl_release();
     const long long n = *f.n, nr = n % f.seg;
-    const double t_half = (n + 0.5) * dt;
+    (void)dt;
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     if (i >= nx || j >= ny) return;
@@ -219,7 +226,7 @@ __global__ void __launch_bounds__(256) k_fwd_E(AGrid<T> g, AState<T> f, Bunch bu
             const long long q = apsi(g.n, g.L, 2, s2, i, j, k);
             pz = f.psiE[2][0][q] + (f.bE[2][k] * f.psiE[2][0][q] + f.aE[2][k] * dHy_dz); f.psiE[2][0][q] = pz;
         }
-        fwd_ampere(g, f, 0, e, k, nr, ky * dHz_dy + py - kz * dHy_dz - pz, (T)bunch_jx(bu, f.bx, i, j, k, t_half));
+        fwd_ampere(g, f, 0, e, k, nr, ky * dHz_dy + py - kz * dHy_dz - pz, bunch_jx<T>(bu, i, j, k, n));
     }
     if (!(fx || fz)) {
         const T dHx_dz = (hx - f.H[0][e - okm]) * g.r[2], dHz_dx = (hz - f.H[2][e - oim]) * g.r[0];
@@ -467,7 +474,7 @@ __global__ void __launch_bounds__(256) k_fwd_H4(AGrid<float> g, AState<float> f,
                                                  double dt) {
     pdl_wait();
     pdl_release();
-    if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0) fwd_step_start(f, pr, F, bu, dt);
+    if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0) fwd_step_start(f, pr, F);
     int i0, j, k;
     if (!group_of(g, i0, j, k)) return;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
@@ -592,7 +599,7 @@ __global__ void __launch_bounds__(256) k_fwd_E4(AGrid<float> g, AState<float> f,
     pdl_wait();
     pdl_release();
     const long long n = *f.n, nr = n % f.seg;
-    const double t_half = (n + 0.5) * dt;
+    (void)dt;
     int i0, j, k;
     if (!group_of(g, i0, j, k)) return;
     const int nx = g.n[0], ny = g.n[1];
@@ -614,7 +621,7 @@ __global__ void __launch_bounds__(256) k_fwd_E4(AGrid<float> g, AState<float> f,
         for (int m = 0; m < 4; m++) {
             d1[m] = (hz.v[m] - hz_jm.v[m]) * ry;
             d2[m] = (hy.v[m] - hy_km.v[m]) * rz;
-            js[m] = (float)bunch_jx(bu, f.bx, i0 + m, j, k, t_half);
+            js[m] = bunch_jx<float>(bu, i0 + m, j, k, n);
         }
         if (s1 >= 0) psi4(f.psiE[1][1], apsi(g.n, g.L, 1, s1, i0, j, k), f.bE[1], f.aE[1], f.ikE[1], j, false, d1, upd, p1, k1);
         if (s2 >= 0) psi4(f.psiE[2][0], apsi(g.n, g.L, 2, s2, i0, j, k), f.bE[2], f.aE[2], f.ikE[2], k, false, d2, upd, p2, k2);
@@ -937,7 +944,12 @@ struct AdjSim : AdjBase {
             if (ckpt && K > 1) rc = take(&ckbuf, state_elems * (size_t)(K - 1));
         }
         rc = rc ? rc : take(&f.n, 1);
-        rc = rc ? rc : take(&f.bx, 2);
+        double *gx64 = nullptr, *gyz64 = nullptr;
+        float *gx32 = nullptr, *gyz32 = nullptr;
+        rc = rc ? rc : take(&gx64, (size_t)c->nsteps * nx);
+        rc = rc ? rc : take(&gx32, (size_t)c->nsteps * nx);
+        rc = rc ? rc : take(&gyz64, (size_t)nz * ny);
+        rc = rc ? rc : take(&gyz32, (size_t)nz * ny);
         if (rc) return rc;
         if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess)
             return set_last_error(PIC_ERR_CUDA, "adjoint: stream creation failed");
@@ -965,19 +977,32 @@ struct AdjSim : AdjBase {
         f.eidx = eidx_d;
         f.beta = beta_d;
         for (int q4 = 0; q4 < 4; q4++) f.soff[q4] = soff[q4];
-        // bunch
-        const double s = c->bunch_sigma;
-        bu.qv_norm = c->bunch_q * c->bunch_v / std::pow(2.0 * M_PI * s * s, 1.5);
-        bu.inv2s2 = 1.0 / (2.0 * s * s);
-        bu.cut2 = 36.0 * s * s;
-        bu.cut = 6.0 * s;
-        bu.v = c->bunch_v; bu.x0 = c->bunch_x0; bu.y0 = c->bunch_y0; bu.z0 = c->bunch_z0; bu.dx = c->dx;
-        // rows and planes within the cut radius (6 sigma), one cell wider on each side
-        const double cut = 6.0 * s / c->dx;
-        bu.j0 = (int)std::floor(c->bunch_y0 / c->dx - cut) - 1;
-        bu.j1 = (int)std::ceil(c->bunch_y0 / c->dx + cut) + 1;
-        bu.k0 = (int)std::floor(c->bunch_z0 / c->dx - cut) - 1;
-        bu.k1 = (int)std::ceil(c->bunch_z0 / c->dx + cut) + 1;
+        // bunch: the two factors of the Gaussian current on every Ex edge
+        {
+            const double s = c->bunch_sigma, inv2s2 = 1.0 / (2.0 * s * s);
+            const double qv_norm = c->bunch_q * c->bunch_v / std::pow(2.0 * M_PI * s * s, 1.5);
+            std::vector<double> gx((size_t)c->nsteps * nx), gyz((size_t)nz * ny);
+            for (long long n = 0; n < c->nsteps; n++) {
+                const double xc = c->bunch_x0 + c->bunch_v * ((double)n + 0.5) * c->dt;
+                for (int i = 0; i < nx; i++) {
+                    const double x = (i + 0.5) * c->dx - xc;
+                    gx[(size_t)n * nx + i] = std::exp(-x * x * inv2s2);
+                }
+            }
+            for (int k = 0; k < nz; k++)
+                for (int j = 0; j < ny; j++) {
+                    const double y = j * c->dx - c->bunch_y0, z = k * c->dx - c->bunch_z0;
+                    gyz[(size_t)k * ny + j] = qv_norm * std::exp(-(y * y + z * z) * inv2s2);
+                }
+            std::vector<float> gx_f(gx.begin(), gx.end()), gyz_f(gyz.begin(), gyz.end());
+            if (cudaMemcpy(gx64, gx.data(), gx.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(gx32, gx_f.data(), gx_f.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(gyz64, gyz.data(), gyz.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(gyz32, gyz_f.data(), gyz_f.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+                return set_last_error(PIC_ERR_CUDA, "adjoint: bunch table upload failed");
+            bu.gx64 = gx64; bu.gyz64 = gyz64; bu.gx32 = gx32; bu.gyz32 = gyz32;
+            bu.nx = nx; bu.ny = ny; bu.nsteps = c->nsteps;
+        }
         // probe stencil on the component's staggered lattice
         pr.comp = c->probe_comp;
         pr.omega = c->omega0;
@@ -1272,6 +1297,8 @@ int pic_adj_create(const pic_adj_config *c, pic_adj **out) {
         return set_last_error(PIC_ERR_ARG, "design slab [%lld, %lld) must lie inside the grid",
                               (long long)c->design_k0, (long long)c->design_k1);
     if (c->nsteps < 1) return set_last_error(PIC_ERR_ARG, "nsteps must be >= 1");
+    if (c->nsteps * c->nx > (int64_t)1 << 28)
+        return set_last_error(PIC_ERR_ARG, "nsteps x nx = %lld is above 2^28", (long long)(c->nsteps * c->nx));
     if (c->probe_comp < 0 || c->probe_comp > 2) return set_last_error(PIC_ERR_ARG, "probe_comp must be 0..2");
     for (int a = 0; a < 3; a++) {
         const double xi = c->probe[a] / c->dx;
