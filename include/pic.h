@@ -97,7 +97,12 @@ typedef struct {
     int64_t step;          /* completed time steps */
     int64_t n_particles;   /* particles added */
     int64_t n_frozen;      /* particles stopped by the boundary/metal rule */
-    int32_t device_error;  /* bit set reported by kernels (0 = none) */
+    int32_t device_error;  /* bits (0 = none): 1 an electron moved more than one cell in
+                              a step (impossible under the time-step bound pic_create
+                              checks: a guard against a corrupted state); 2 an electron's
+                              momentum became non-finite (it is frozen); 4 E or H holds
+                              a NaN or an Inf (found by the scan of pic_sync and
+                              pic_get_stats).  Bits stay set for the life of the handle. */
     int32_t n_edge_classes;
     int64_t kernel_launches; /* kernels pic_step has launched (graph replays count their kernels) */
 } pic_stats;
@@ -134,7 +139,10 @@ int pic_destroy(pic_handle *h);
  * a created stream, not 0, when sharing one. */
 int pic_set_stream(pic_handle *h, void *stream);
 
-/* Append n macro-electrons: xyz [n][3] positions [m], u [n][3] gamma*v [m/s],
+/* Append n macro-electrons of the bunch (Sec. III: an electron bunch moving
+ * parallel to the film surface excites its surface plasmons; the electrons
+ * then take part in every step as in Sec. II's particle-field coupling):
+ * xyz [n][3] positions [m], u [n][3] gamma*v [m/s],
  * charge q_macro [C] (negative for electrons) and mass m_macro [kg] of each
  * (all particles of a handle share q and m).  Every position must lie at
  * least two cells inside each non-periodic face and outside cells with
@@ -168,11 +176,24 @@ int pic_add_source(pic_handle *h, int comp, const int64_t *box, double amp, doub
 int pic_probe_dft(pic_handle *h, int np, const double *xyz, uint32_t comp_mask, int nf,
                   const double *freq_hz);
 
-/* Advance nsteps time steps (asynchronous on the handle's stream; whole
- * groups of steps are replayed from a captured CUDA graph). */
+/* Advance nsteps time steps of the method of Sec. II: per step the vacuum Yee
+ * H update, the electron push and charge-conserving current, then the Drude
+ * current of Eq. 6 before the E update of Eq. 8 (J first, then E, as the
+ * paper orders them), then the probe sample (the five stages listed at the top
+ * of this file).  Asynchronous on the handle's stream; device-side errors
+ * are reported by the next synchronising call.  Steps are grouped into
+ * blocks of 64 (one probe-DFT flush each): whole blocks replay one captured
+ * CUDA graph, a run of 8..63 steps inside a block replays a captured graph of
+ * that run (the 16 most recently used runs are kept per handle), and shorter
+ * runs are launched kernel by kernel.  The arithmetic is the same on every
+ * route.  Errors: PIC_ERR_ARG (nsteps < 0), PIC_ERR_CUDA (launch or capture
+ * failed). */
 int pic_step(pic_handle *h, int64_t nsteps);
 
-/* Wait for the handle's stream; report a kernel-side error as PIC_ERR_DEVICE. */
+/* Wait for the handle's stream, then scan E and H for NaN or Inf (one pass
+ * over the six arrays).  Returns PIC_ERR_DEVICE if a kernel set error bit 1
+ * or 2 (see pic_stats.device_error), else PIC_ERR_NONFINITE if E or H holds
+ * a non-finite value, else PIC_OK. */
 int pic_sync(pic_handle *h);
 
 /* Copy the probe spectra to out [np][3][nf][2] (re, im; components not in
@@ -199,7 +220,8 @@ int pic_get_field(pic_handle *h, int which, double *out);
  * restarts.  Synchronises. */
 int pic_set_field(pic_handle *h, int which, const double *in);
 
-/* Counters and the device error word.  Synchronises. */
+/* Counters and the device error word (after the same scan of E and H as
+ * pic_sync).  Synchronises. */
 int pic_get_stats(pic_handle *h, pic_stats *out);
 
 /* Write the complete state of the simulation to the file `path`: fields,
@@ -347,8 +369,8 @@ int pic_batch_destroy(pic_batch *b);
  * __device__ array inside the library (held on every GPU that loads the
  * library until the process exits); nf above 2048 is rejected with
  * PIC_ERR_ARG.  The first call on each device looks up that array's device
- * address with the device current; make that first call before any stream
- * capture.  Every call on a device shares the array, so calls whose work
+ * address with the device current (and again after a reset of the device
+ * gives it a new context); make that first call before any stream capture.  Every call on a device shares the array, so calls whose work
  * overlaps on the GPU (different streams, or threads) race on it; serialise
  * them on one stream.  Asynchronous on `stream` (NULL: the legacy default
  * stream); launch errors are returned, kernel faults surface at the next

@@ -134,6 +134,7 @@ struct SimBase {
     virtual int steps_to_boundary() const = 0;        // steps left in the current block (0 at a boundary)
     virtual long long cells() const = 0;
     virtual int set_tuning(const pic_tuning &t) = 0;
+    int device = -1;  // CUDA device the handle was created on
 };
 
 template <typename T>
@@ -191,6 +192,18 @@ struct Sim : SimBase {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     long long graph_kernels = 0;   // kernels in one replay of the step graph
+    // Captured runs shorter than a block: steps [pos, pos + len) of a block
+    // entered with the sort counter at `since`, with the DFT flush when they
+    // end the block.  Runs of SEG_MIN steps or more replay one of these (the
+    // SEG_CACHE most recently used are kept); shorter runs launch directly.
+    struct Segment {
+        int pos, len, since;
+        cudaGraphExec_t exec;
+        long long kernels, used;
+    };
+    std::vector<Segment> segs;
+    long long seg_clock = 0;
+    static constexpr int SEG_MIN = 8, SEG_CACHE = 16;
     long long kernels = 0;         // kernels launched by this simulation so far
 
     // all device buffers, in one pass; base == nullptr only measures
@@ -441,6 +454,7 @@ struct Sim : SimBase {
     }
 
     int create(const pic_config *c) {
+        CUDA_TRY(cudaGetDevice(&device));
         init_geometry(c);
         for (size_t e = 0; e < (size_t)N; e++)
             if (c->material_id[e] >= c->n_materials)
@@ -592,6 +606,8 @@ struct Sim : SimBase {
         if (graph) cudaGraphDestroy(graph);
         gexec = nullptr;
         graph = nullptr;
+        for (auto &sg : segs) cudaGraphExecDestroy(sg.exec);
+        segs.clear();
         epoch++;
     }
 
@@ -710,6 +726,55 @@ struct Sim : SimBase {
         return PIC_OK;
     }
 
+    // Replay (capturing it the first time) the run of len steps from the
+    // current position in the block; the host counters advance as the
+    // direct path would advance them.
+    int run_segment(int len) {
+        const int pos = buffered, since = std::min(since_sort, sort_every);
+        const bool ends = pos + len == DFT_BLOCK;
+        Segment *sg = nullptr;
+        for (auto &x : segs)
+            if (x.pos == pos && x.len == len && x.since == since) sg = &x;
+        if (!sg) {
+            if ((int)segs.size() >= SEG_CACHE) {  // drop the least recently used
+                size_t old = 0;
+                for (size_t q = 1; q < segs.size(); q++)
+                    if (segs[q].used < segs[old].used) old = q;
+                cudaGraphExecDestroy(segs[old].exec);
+                segs.erase(segs.begin() + (long)old);
+            }
+            Segment nsg{pos, len, since, nullptr, 0, 0};
+            CUDA_TRY(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+            const long long before = launch_count();
+            int ss = since;
+            for (int q = 0; q < len; q++) {
+                const bool sort = ss >= sort_every;
+                launch_step(sort);
+                ss = sort ? 1 : ss + 1;
+            }
+            if (ends) launch_dft_flush<T>(pr, d_step, DFT_BLOCK, stream);
+            nsg.kernels = launch_count() - before;
+            launch_count() = before;  // captured, not launched
+            cudaGraph_t gr = nullptr;
+            cudaError_t e = cudaStreamEndCapture(stream, &gr);
+            if (e != cudaSuccess) return fail(PIC_ERR_CUDA, "segment capture: %s", cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&nsg.exec, gr, 0);
+            cudaGraphDestroy(gr);
+            if (e != cudaSuccess) return fail(PIC_ERR_CUDA, "segment instantiate: %s", cudaGetErrorString(e));
+            segs.push_back(nsg);
+            sg = &segs.back();
+        }
+        sg->used = ++seg_clock;
+        CUDA_TRY(cudaGraphLaunch(sg->exec, stream));
+        kernels += sg->kernels;
+        int ss = since;
+        for (int q = 0; q < len; q++) ss = ss >= sort_every ? 1 : ss + 1;
+        since_sort = ss;
+        step_host += len;
+        buffered = ends ? 0 : pos + len;
+        return PIC_OK;
+    }
+
     int refresh_bold() {
         if (bold_stale) {
             launch_gather_bold<T>(g, f, p, stream);
@@ -741,6 +806,13 @@ struct Sim : SimBase {
                 since_sort = DFT_BLOCK - (DFT_BLOCK - 1) / sort_every * sort_every;  // steps since its last sort
                 continue;
             }
+            const int run = (int)std::min<long long>(nsteps, DFT_BLOCK - buffered);
+            if (run >= SEG_MIN) {  // a captured run up to the end of the block, or the last steps asked for
+                rc = run_segment(run);
+                if (rc) return rc;
+                nsteps -= run;
+                continue;
+            }
             const bool sort = since_sort >= sort_every;
             launch_step(sort);
             since_sort = sort ? 1 : since_sort + 1;
@@ -770,8 +842,19 @@ struct Sim : SimBase {
         CUDA_TRY(cudaStreamSynchronize(stream));
         int err = 0;
         CUDA_TRY(cudaMemcpy(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost));
-        if (err) return fail(PIC_ERR_DEVICE, "kernel error bits 0x%x", err);
+        if (err & (DEVERR_JUMP | DEVERR_NONFINITE))
+            return fail(PIC_ERR_DEVICE, "kernel error bits 0x%x%s", err,
+                        (err & DEVERR_NONFINITE) ? " (non-finite electron momentum: those electrons are frozen)" : "");
+        if (err & DEVERR_FIELD_NONFINITE) return fail(PIC_ERR_NONFINITE, "E or H holds a NaN or an Inf");
         return PIC_OK;
+    }
+
+    // sync() after a scan of E and H for NaN or Inf (pic_sync, pic_get_stats)
+    int check() {
+        CUDA_TRY(cudaStreamSynchronize(stream));
+        launch_nonfinite_scan<T>(f, N, d_err, stream);
+        CUDA_TRY(cudaGetLastError());
+        return sync();
     }
 
     // ------------------------------------------------------ checkpoint --
@@ -791,14 +874,45 @@ struct Sim : SimBase {
         int32_t buffered, since_sort, bold_stale, have_q, deposit, probe_np, probe_nf, nsources;
         uint32_t probe_mask, pad;
         double q, m;
+        // configuration scalars (compared on load; the configuration's arrays
+        // are compared byte by byte with the file's copy of them)
+        double d[3], dt, eps0, mu0;
+        int32_t bc[6], cpml_cells, pad2;
+        double cpml_order, cpml_sigma_fac, cpml_kappa_max, cpml_alpha_max;
     };
+
+    // Arena pieces that follow from the configuration alone (material map,
+    // edge classes and their coefficients, CPML profiles): (offset, bytes).
+    std::vector<std::pair<size_t, size_t>> config_regions() const {
+        std::vector<std::pair<size_t, size_t>> r;
+        auto add = [&](const void *ptr, size_t bytes) { r.emplace_back((size_t)((const char *)ptr - (const char *)arena), bytes); };
+        add(d_mat, (size_t)N);
+        add(d_mat_metal, 256);
+        for (int c = 0; c < 3; c++) add(d_ecls[c], (size_t)N);
+        for (int q3 = 0; q3 < 3; q3++) add(d_cls[q3], 256 * sizeof(T));
+        add(d_cls_metal, 256);
+        add(d_cls_pack, 256 * sizeof(float4));
+        for (int a = 0; a < 3; a++)
+            for (int q6 = 0; q6 < 6; q6++) add(d_prof[a * 6 + q6], (size_t)n[a] * sizeof(T));
+        return r;
+    }
 
     int save(const char *path) {
         int rc = sync();
         if (rc) return rc;
         SaveHeader hd{};
         memcpy(hd.magic, "PICSAVE1", 8);
-        hd.version = 1;
+        hd.version = 2;
+        for (int a = 0; a < 3; a++) hd.d[a] = d[a];
+        hd.dt = cfg.dt;
+        hd.eps0 = cfg.eps0;
+        hd.mu0 = cfg.mu0;
+        for (int q6 = 0; q6 < 6; q6++) hd.bc[q6] = cfg.bc[q6];
+        hd.cpml_cells = cfg.cpml_cells;
+        hd.cpml_order = cfg.cpml_order;
+        hd.cpml_sigma_fac = cfg.cpml_sigma_fac;
+        hd.cpml_kappa_max = cfg.cpml_kappa_max;
+        hd.cpml_alpha_max = cfg.cpml_alpha_max;
         hd.precision = cfg.precision;
         for (int a = 0; a < 3; a++) hd.n[a] = n[a];
         hd.arena_bytes = arena_bytes;
@@ -841,25 +955,58 @@ struct Sim : SimBase {
     int load(const char *path) {
         FILE *fp = fopen(path, "rb");
         if (!fp) return fail(PIC_ERR_ARG, "cannot open %s", path);
+        auto reject = [&](const char *why) {
+            fclose(fp);
+            return fail(PIC_ERR_ARG, "checkpoint %s: %s", path, why);
+        };
         SaveHeader hd{};
-        if (fread(&hd, sizeof hd, 1, fp) != 1 || memcmp(hd.magic, "PICSAVE1", 8) != 0 || hd.version != 1) {
-            fclose(fp);
-            return fail(PIC_ERR_ARG, "%s is not a checkpoint of this library", path);
-        }
-        if (hd.precision != cfg.precision || hd.n[0] != n[0] || hd.n[1] != n[1] || hd.n[2] != n[2] ||
-            hd.arena_bytes != arena_bytes || hd.max_particles != cfg.max_particles ||
-            hd.max_probes != cfg.max_probes || hd.max_freqs != cfg.max_freqs || hd.nsources < 0 ||
-            hd.nsources > MAX_SOURCES) {
-            fclose(fp);
-            return fail(PIC_ERR_ARG, "checkpoint %s was written by a differently configured simulation", path);
-        }
+        if (fread(&hd, sizeof hd, 1, fp) != 1 || memcmp(hd.magic, "PICSAVE1", 8) != 0 || hd.version != 2)
+            return reject("not a checkpoint of this library version");
+        bool same = hd.precision == cfg.precision && hd.arena_bytes == arena_bytes &&
+                    hd.max_particles == cfg.max_particles && hd.max_probes == cfg.max_probes &&
+                    hd.max_freqs == cfg.max_freqs && hd.dt == cfg.dt && hd.eps0 == cfg.eps0 && hd.mu0 == cfg.mu0 &&
+                    hd.cpml_cells == cfg.cpml_cells && hd.cpml_order == cfg.cpml_order &&
+                    hd.cpml_sigma_fac == cfg.cpml_sigma_fac && hd.cpml_kappa_max == cfg.cpml_kappa_max &&
+                    hd.cpml_alpha_max == cfg.cpml_alpha_max;
+        for (int a = 0; a < 3; a++) same = same && hd.n[a] == n[a] && hd.d[a] == d[a];
+        for (int q6 = 0; q6 < 6; q6++) same = same && hd.bc[q6] == cfg.bc[q6];
+        if (!same) return reject("written by a differently configured simulation");
+        // counters: everything a kernel indexes with must lie inside this handle's capacities
+        if (hd.np < 0 || hd.np > cfg.max_particles || hd.probe_np < 0 || hd.probe_np > cfg.max_probes ||
+            hd.probe_nf < 0 || hd.probe_nf > cfg.max_freqs || (hd.probe_mask & ~7u) || hd.buffered < 0 ||
+            hd.buffered >= DFT_BLOCK || hd.since_sort < 1 || hd.since_sort > DFT_BLOCK || hd.step_host < 0 ||
+            hd.nsources < 0 || hd.nsources > MAX_SOURCES || (hd.bold_stale & ~1) || (hd.have_q & ~1) ||
+            (hd.deposit & ~1) || (hd.have_q && !(std::isfinite(hd.q) && std::isfinite(hd.m) && hd.m > 0.0)))
+            return reject("counters outside this handle's capacities");
         std::vector<Source> src((size_t)hd.nsources);
-        if (hd.nsources && fread(src.data(), sizeof(Source), src.size(), fp) != src.size()) {
-            fclose(fp);
-            return fail(PIC_ERR_ARG, "truncated checkpoint %s", path);
+        if (hd.nsources && fread(src.data(), sizeof(Source), src.size(), fp) != src.size())
+            return reject("truncated");
+        for (const Source &sr : src) {
+            bool ok = sr.comp >= 0 && sr.comp < 3;
+            for (int a = 0; a < 3; a++)
+                ok = ok && sr.box[2 * a] >= 0 && sr.box[2 * a] <= sr.box[2 * a + 1] && sr.box[2 * a + 1] <= n[a];
+            if (!ok) return reject("a source outside the grid");
         }
+        // the whole arena must be there before anything is copied
+        const long body = ftell(fp);
+        if (body < 0 || fseek(fp, 0, SEEK_END) != 0) return reject("cannot be sized");
+        const long total = ftell(fp);
+        if (total < 0 || (unsigned long)total != (unsigned long)body + arena_bytes) return reject("truncated or too long");
         int rc = sync();
         if (rc) { fclose(fp); return rc; }
+        // the configuration's own arrays must match this handle's byte for byte
+        for (const auto &reg : config_regions()) {
+            std::vector<char> a(reg.second), b(reg.second);
+            if (fseek(fp, body + (long)reg.first, SEEK_SET) != 0 || fread(a.data(), 1, a.size(), fp) != a.size())
+                return reject("truncated");
+            if (cudaMemcpy(b.data(), (char *)arena + reg.first, b.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+                fclose(fp);
+                return fail(PIC_ERR_CUDA, "reading the device state failed");
+            }
+            if (memcmp(a.data(), b.data(), a.size()) != 0)
+                return reject("materials or absorbing layers differ from this handle's configuration");
+        }
+        if (fseek(fp, body, SEEK_SET) != 0) return reject("cannot be read");
         std::vector<char> buf;
         const size_t chunk = (size_t)64 << 20;
         for (size_t off = 0; off < arena_bytes; off += chunk) {
@@ -1303,6 +1450,8 @@ template <typename T>
 static int stats_t(Sim<T> *s, pic_stats *out) {
     cudaError_t e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return fail(PIC_ERR_CUDA, "%s", cudaGetErrorString(e));
+    pic::launch_nonfinite_scan<T>(s->f, s->N, s->d_err, s->stream);
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
     int err = 0;
     CUDA_TRY(cudaMemcpy(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     std::vector<uint8_t> st((size_t)s->p.n);
@@ -1456,7 +1605,7 @@ int pic_step(pic_handle *h, int64_t nsteps) {
 int pic_sync(pic_handle *h) {
     g_err.clear();
     if (!h) return fail(PIC_ERR_ARG, "NULL handle");
-    return DISPATCH(h, sync());
+    return DISPATCH(h, check());
 }
 
 int pic_probe_read(pic_handle *h, double *out) {
@@ -1798,6 +1947,9 @@ int pic_batch_create(int n, pic_handle *const *handles, void *stream, pic_batch 
         if (!handles[i]) return fail(PIC_ERR_ARG, "handle %d is NULL", i);
         for (int q = 0; q < i; q++)
             if (handles[q] == handles[i]) return fail(PIC_ERR_ARG, "handle %d appears twice", i);
+        if (handles[i]->sim->device != dev)
+            return fail(PIC_ERR_ARG, "handle %d lives on device %d, not on the current device %d", i,
+                        handles[i]->sim->device, dev);
         b->h.push_back(handles[i]);
     }
     b->epochs.assign(n, -1);

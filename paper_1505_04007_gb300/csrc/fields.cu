@@ -212,6 +212,27 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y *TILE_Z) k_jf_apply(Grid<T> g, 
     }
 }
 
+// Scan of the field state for NaN or Inf (a diverged run: too large a time
+// step for a material, or a non-finite value written by pic_set_field).
+template <typename T>
+__global__ void __launch_bounds__(256) k_nonfinite(Fields<T> f, long long n, int *err) {
+    bool bad = false;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int c = 0; c < 3; c++) bad |= !isfinite(f.E[c][i]) || !isfinite(f.H[c][i]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, DEVERR_FIELD_NONFINITE);
+}
+
+template <typename T>
+void launch_nonfinite_scan(const Fields<T> &f, long long n, int *err, cudaStream_t s) {
+    long long nblk = (n + 255) / 256;
+    if (nblk > 8 * 152) nblk = 8 * 152;
+    if (nblk < 1) nblk = 1;
+    k_nonfinite<T><<<(unsigned)nblk, 256, 0, s>>>(f, n, err);
+}
+template void launch_nonfinite_scan<float>(const Fields<float> &, long long, int *, cudaStream_t);
+template void launch_nonfinite_scan<double>(const Fields<double> &, long long, int *, cudaStream_t);
+
 static dim3 field_grid(const int n[3], dim3 blk) {
     return dim3((n[0] + blk.x - 1) / blk.x, (n[1] + blk.y - 1) / blk.y, (n[2] + blk.z - 1) / blk.z);
 }

@@ -20,8 +20,9 @@ constexpr int SCAN_TILE = 4096;  // entries per block of the prefix scan
 
 // Device error bits.
 enum : int {
-    DEVERR_JUMP = 1,       // a particle moved more than one cell in a step
-    DEVERR_NONFINITE = 2,  // non-finite momentum in the pusher
+    DEVERR_JUMP = 1,             // a particle moved more than one cell in a step
+    DEVERR_NONFINITE = 2,        // non-finite momentum in the pusher
+    DEVERR_FIELD_NONFINITE = 4,  // a NaN or Inf in E or H (scan at pic_sync / pic_get_stats)
 };
 
 // Grid geometry and scalar coefficients, passed by value to every kernel.
@@ -209,6 +210,10 @@ template <typename T>
 void launch_gather_E(const Grid<T> &g, const Fields<T> &f, const Particles<T> &p, cudaStream_t s);
 template <typename T>
 void launch_jf_apply(const Grid<T> &g, const Fields<T> &f, int max_tiles, cudaStream_t s);
+// Sets DEVERR_FIELD_NONFINITE in *err if any of the n values of E or H is a
+// NaN or an Inf.
+template <typename T>
+void launch_nonfinite_scan(const Fields<T> &f, long long n, int *err, cudaStream_t s);
 template <typename T>
 void launch_push_deposit(const Grid<T> &g, const Fields<T> &f, const Particles<T> &p,
                          const PushParams<T> &pp, cudaStream_t s);

@@ -9,6 +9,7 @@
 // holds the phase table in a fixed file-scope __device__ array that the
 // library image carries: every GPU that loads the library holds its 2 MiB
 // until the process exits, and no call here allocates anything.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -29,7 +30,37 @@ constexpr int MAX_DEVICES = 64;
 static __device__ __align__(256) double g_dft_scratch[STATIC_CHUNK * STATIC_MAX_FREQS * 2];
 
 std::mutex g_setup_mutex;
-double *g_scratch_addr[MAX_DEVICES];  // device address of g_dft_scratch per ordinal
+// Device address of g_dft_scratch per ordinal, with the id of the context it
+// was looked up in: after a device reset the primary context (and the
+// array's address) is new, so the address is looked up again.
+double *g_scratch_addr[MAX_DEVICES];
+unsigned long long g_scratch_ctx[MAX_DEVICES];
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+std::once_flag g_driver_once;
+
+// Unique id of the calling thread's current context (0 if unknown).
+unsigned long long current_ctx_id() {
+    std::call_once(g_driver_once, [] {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) == cudaSuccess &&
+            qa == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+            qb == cudaDriverEntryPointSuccess) {
+            g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(a);
+            g_ctx_id = reinterpret_cast<CtxGetIdFn>(b);
+        }
+    });
+    if (!g_ctx_current || !g_ctx_id) return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_current(&c) != CUDA_SUCCESS || !c || g_ctx_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 __global__ void k_static_phasor(const double *freq, int nf, double *ph, long long n0, int cnt, double dt) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
@@ -59,8 +90,10 @@ __global__ void k_static_fold(const double *samples, const double *ph, double *F
     out[1] += im * dt;
 }
 
-// Device address of the scratch array for the current device, looked up once
-// per device (with that device current) and cached.
+// Device address of the scratch array for the current device, looked up with
+// that device current the first time and again whenever the device's context
+// has changed (a reset); if the context id cannot be read it is looked up on
+// every call.
 int scratch_for_current_device(double **out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -73,7 +106,8 @@ int scratch_for_current_device(double **out) {
         return PIC_ERR_UNSUPPORTED;
     }
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
+    const unsigned long long ctx = current_ctx_id();
+    if (!g_scratch_addr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_dft_scratch);
         if (e != cudaSuccess || !p) {
@@ -81,6 +115,7 @@ int scratch_for_current_device(double **out) {
             return PIC_ERR_CUDA;
         }
         g_scratch_addr[dev] = static_cast<double *>(p);
+        g_scratch_ctx[dev] = current_ctx_id();  // the lookup has made the context current if it was not
     }
     *out = g_scratch_addr[dev];
     return PIC_OK;

@@ -36,14 +36,17 @@ def test_field_update_bytes_by_hand():
     assert ab["slab_cells"] == slab
     assert ab["metal_edges"] == metal
     assert ab["update_H"] == N * 36 + psi
-    assert ab["update_E"] == N * (36 + 3) + psi + metal * 8
+    # edge classes (one byte per edge, three per cell) are read on the planes
+    # holding metal edges, k0..k1, only
+    assert ab["class_bytes"] == (k1 - k0 + 1) * n * n * 3
+    assert ab["update_E"] == N * 36 + (k1 - k0 + 1) * n * n * 3 + psi + metal * 8
 
 
 def test_fp64_doubles_the_state_bytes():
     w = _film()
     a4, a8 = bench.algorithmic_bytes(w, 4), bench.algorithmic_bytes(w, 8)
     assert a8["update_H"] == 2 * a4["update_H"]
-    assert a8["update_E"] - 2 * a4["update_E"] == -3 * w.ncells  # class ids stay one byte per edge triple
+    assert a8["update_E"] - 2 * a4["update_E"] == -a4["class_bytes"]  # class ids stay one byte per edge
 
 
 def test_adjoint_step_bytes_by_hand():

@@ -1,0 +1,187 @@
+"""Edge cases of the CUDA path through the C ABI, against the FP64 oracle.
+
+- FP32 electrons that cross periodic faces (and are absorbed by a metal
+  slab) keep the FP32 parity bar of 2e-5 on the fields, with the oracle's
+  freeze decisions up to electrons that sit within FP32 rounding of a
+  freezing boundary.
+- pic_step split into runs of every kind: runs shorter than the captured
+  minimum (launched kernel by kernel), captured runs inside one 64-step
+  block, runs that end a block (with its DFT flush) and whole blocks; the
+  FP64 state equals the oracle's within 1e-10 and the spectra too.
+- Failure paths made on the host (no kernel traps or waits): a NaN written
+  into E next to live electrons makes their momentum non-finite, so they are
+  frozen and pic_sync returns PIC_ERR_DEVICE with bit 2; an FP32 field so
+  large that the Boris increment overflows does the same; a NaN away from
+  every electron is found by the scan of E and H and pic_sync returns
+  PIC_ERR_NONFINITE (bit 4 only).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1505_04007_gb300 import workloads as W
+
+from _helpers import box_workload
+
+pytestmark = pytest.mark.gpu
+
+ETA0 = (W.MU0 / W.EPS0) ** 0.5
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    from paper_1505_04007_gb300 import pic
+    pic.load()
+    return pic
+
+
+def rel_fields(s, o):
+    num = den = 0.0
+    for c in range(6):
+        sc = ETA0 if c >= 3 else 1.0
+        ref = o.get_field(c) * sc
+        num += float(np.linalg.norm(s.field(c) * sc - ref) ** 2)
+        den += float(np.linalg.norm(ref) ** 2)
+    return (num / den) ** 0.5
+
+
+def periodic_case():
+    nx, ny, nz = 32, 16, 24
+    mat = np.zeros((nz, ny, nx), np.uint8)
+    mat[4:7] = 1
+    bc = (W.BC_PERIODIC, W.BC_PERIODIC, W.BC_PERIODIC, W.BC_PERIODIC, W.BC_CPML, W.BC_CPML)
+    w = box_workload(nx, ny, nz, bc=bc, material=mat, table=W.drude_table())
+    w.cpml_cells = 6
+    rng = np.random.default_rng(3)
+    n = 300
+    w.xyz = np.stack([rng.uniform(0, nx, n), rng.uniform(0, ny, n), rng.uniform(9, 13, n)], 1) * w.dx
+    w.u = np.zeros((n, 3))
+    w.u[:, 0] = -W.electron_momentum(50.0)
+    w.u[:, 1] = 0.3 * W.electron_momentum(50.0)
+    w.u[:, 2] = -0.2 * W.electron_momentum(50.0)
+    w.q_macro = -1e-17
+    w.m_macro = W.ME * 1e-17 / W.QE
+    return w
+
+
+def test_periodic_particles_fp32(P):
+    w = periodic_case()
+    nsteps = 200
+    o = O.from_workload(w, with_probes=False)
+    s = P.Simulation(w, P.PIC_FP32, probes=False)
+    o.step(nsteps)
+    s.step(nsteps)
+    s.sync()
+    assert rel_fields(s, o) <= 2e-5
+    xo, _, so = o.particles()
+    xg, _, sg = s.particles()
+    assert so.sum() > 0
+    differ = np.flatnonzero(so != sg)
+    assert len(differ) <= 3  # freezing decided within FP32 rounding of the metal face
+    live = (so == 0) & (sg == 0)
+    d = xg[live] - xo[live]
+    L = np.array([w.nx * w.dx, w.ny * w.dy, w.nz * w.dz])
+    d -= np.round(d / L) * L * np.array([1, 1, 0])  # positions are compared modulo the periodic lengths
+    assert np.abs(d).max() <= 1e-4 * w.dx
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
+def test_step_runs_of_every_kind(P, prec, tol):
+    w = W.scaled(W.c1(), 64, 24, 40, 1024, 0)
+    o = O.from_workload(w)
+    s = P.Simulation(w, P.PIC_FP64 if prec == "fp64" else P.PIC_FP32)
+    # 5 direct; 20 captured (steps 5..24); 50 = 39 captured to the block's end + 11 captured;
+    # 7 direct; 64 = 46 captured to the end + 18 captured; 9 captured; 100 = 37 to the end + 63 captured
+    runs = [5, 20, 50, 7, 64, 9, 100]
+    for r in runs:
+        s.step(r)
+    total = sum(runs)
+    o.step(total)
+    s.sync()
+    assert s.stats().step == total
+    assert rel_fields(s, o) <= tol
+    Fo, Fg = o.probe_read(), s.probe_read()
+    assert np.linalg.norm(Fg - Fo) <= tol * np.linalg.norm(Fo)
+    # the same total again from a block boundary: whole blocks plus a captured tail
+    s.step(128 - total % 64)
+    o.step(128 - total % 64)
+    s.step(84)
+    o.step(84)
+    assert rel_fields(s, o) <= tol
+    s.close()
+
+
+def electrons_case(P, prec):
+    w = W.scaled(W.c1(), 64, 24, 40, 1024, 0)
+    s = P.Simulation(w, prec, probes=False)
+    s.step(3)
+    s.sync()
+    return w, s
+
+
+def bunch_box(w, s):
+    """Index box [k0:k1, j0:j1, i0:i1] around every electron (cells)."""
+    x = s.particles()[0]
+    c = np.floor(x / np.array([w.dx, w.dy, w.dz])).astype(int)
+    lo, hi = c.min(0) - 2, c.max(0) + 3
+    return lo, hi
+
+
+def test_nan_next_to_electrons_freezes_them(P):
+    w, s = electrons_case(P, P.PIC_FP32)
+    lo, hi = bunch_box(w, s)
+    Ex = s.field(P.PIC_EX)
+    Ex[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] = np.nan
+    s.set_field(P.PIC_EX, Ex)
+    s.step(2)
+    with pytest.raises(P.PicError) as e:
+        s.sync()
+    assert e.value.code == -8  # PIC_ERR_DEVICE
+    st = s.stats()
+    assert st.device_error & 2 and st.device_error & 4 and not st.device_error & 1
+    assert st.n_frozen == st.n_particles  # every electron saw the NaN
+    _, _, status = s.particles()
+    assert status.all()
+    s.close()
+
+
+def test_overflowing_fp32_field_freezes_electrons(P):
+    w, s = electrons_case(P, P.PIC_FP32)
+    lo, hi = bunch_box(w, s)
+    Ez = s.field(P.PIC_EZ)
+    Ez[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] = 3e37  # finite in FP32; the Boris increment is not
+    s.set_field(P.PIC_EZ, Ez)
+    s.step(1)
+    with pytest.raises(P.PicError) as e:
+        s.sync()
+    assert e.value.code == -8
+    st = s.stats()
+    assert st.device_error & 2 and not st.device_error & 1
+    assert st.n_frozen == st.n_particles
+    s.close()
+
+
+def test_nan_away_from_electrons_is_nonfinite(P):
+    w, s = electrons_case(P, P.PIC_FP32)
+    lo, hi = bunch_box(w, s)
+    Hy = s.field(P.PIC_HY)
+    Hy[30, 12, 50] = np.nan  # far from the bunch (x < 20 cells, z > 20)
+    assert not (lo[0] <= 50 < hi[0] and lo[2] <= 30 < hi[2])
+    s.set_field(P.PIC_HY, Hy)
+    s.step(1)
+    with pytest.raises(P.PicError) as e:
+        s.sync()
+    assert e.value.code == -5  # PIC_ERR_NONFINITE
+    st = s.stats()
+    assert st.device_error == 4
+    # the same steps without the NaN: a clean sync and the same frozen electrons
+    w2, s2 = electrons_case(P, P.PIC_FP32)
+    s2.step(1)
+    s2.sync()
+    st2 = s2.stats()
+    assert st2.device_error == 0 and st.n_frozen == st2.n_frozen
+    s.close()
+    s2.close()

@@ -58,7 +58,8 @@ def oracle200():
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
-@pytest.mark.parametrize("dep,every,block", [(0, 8, 128), (16384, 1, 512), (2048, 32, 256), (8192, 64, 512)])
+@pytest.mark.parametrize("dep,every,block", [(0, 8, 128), (16384, 1, 512), (2048, 32, 256), (8192, 64, 512),
+                                             (8192, 32, 128), (8192, 64, 128)])  # the last two: tuned bench settings
 def test_tuning_changes_keep_parity(P, oracle200, prec, tol, dep, every, block):
     w, o = oracle200
     s = P.Simulation(w, P.PIC_FP64 if prec == "fp64" else P.PIC_FP32)

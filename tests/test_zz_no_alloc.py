@@ -74,6 +74,12 @@ def test_static_fold_matches_probe_read_over_two_calls():
     scale = np.linalg.norm(F_ref)
     assert scale > 0
     assert np.linalg.norm(got - F_ref) <= 1e-10 * scale
+    # and the DFT definition applied in numpy to the same series:
+    # F[p][c][f] = dt sum_s x[s][p][c] exp(+i 2 pi f (s+1) dt)
+    t = (np.arange(K) + 1) * w.dt
+    ph = np.exp(1j * 2 * np.pi * np.outer(t, freqs))          # [K][nf]
+    F_def = np.einsum("spc,sf->pcf", series, ph) * w.dt
+    assert np.linalg.norm(got - F_def) <= 1e-10 * np.linalg.norm(F_def)
     assert np.all(got[:, 1] == 0)        # component outside the mask untouched
 
     # a fresh accumulator, the whole series in one call: same spectrum
