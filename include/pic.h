@@ -90,8 +90,17 @@ typedef struct {
     void *workspace;              /* optional caller-owned device memory (NULL: library allocates) */
     size_t workspace_bytes;       /* size of workspace, >= pic_workspace_size() */
     void *stream;                 /* cudaStream_t for all device work (NULL: a stream the library creates) */
-    uint64_t flags;               /* reserved, must be 0 */
+    uint64_t flags;               /* PIC_FLAG_* bits, else 0 */
 } pic_config;
+
+/* pic_config.flags: keep the FP32 field updates as two separate passes (the
+ * H update, then the E update) on a grid that would take the fused pass.
+ * The fused pass: FP32 grids with nx a multiple of 4 and no periodic axis
+ * advance E (Eq. 6 then Eq. 8) and the next step's H in one sweep over the
+ * grid (48 instead of 72 bytes per cell), holding two copies of the field
+ * state (the arena is larger by one copy of E, H, J, J_f and the CPML
+ * memory); the results are those of the split updates up to rounding order. */
+#define PIC_FLAG_SPLIT_FIELDS 1
 
 typedef struct {
     int64_t step;          /* completed time steps */
@@ -102,9 +111,13 @@ typedef struct {
                               checks: a guard against a corrupted state); 2 an electron's
                               momentum became non-finite (it is frozen); 4 E or H holds
                               a NaN or an Inf (found by the scan of pic_sync and
-                              pic_get_stats).  Bits stay set for the life of the handle. */
+                              pic_get_stats); 8 a wait of the fused field pass for its
+                              staged planes ran out of time (the pass stopped early).
+                              Bits stay set for the life of the handle. */
     int32_t n_edge_classes;
     int64_t kernel_launches; /* kernels pic_step has launched (graph replays count their kernels) */
+    int32_t field_path;    /* 1: the fused FP32 field pass (see PIC_FLAG_SPLIT_FIELDS); 0: split updates */
+    int32_t reserved;
 } pic_stats;
 
 typedef struct pic_handle pic_handle;
@@ -191,8 +204,8 @@ int pic_probe_dft(pic_handle *h, int np, const double *xyz, uint32_t comp_mask, 
 int pic_step(pic_handle *h, int64_t nsteps);
 
 /* Wait for the handle's stream, then scan E and H for NaN or Inf (one pass
- * over the six arrays).  Returns PIC_ERR_DEVICE if a kernel set error bit 1
- * or 2 (see pic_stats.device_error), else PIC_ERR_NONFINITE if E or H holds
+ * over the six arrays).  Returns PIC_ERR_DEVICE if a kernel set error bit 1,
+ * 2 or 8 (see pic_stats.device_error), else PIC_ERR_NONFINITE if E or H holds
  * a non-finite value, else PIC_OK. */
 int pic_sync(pic_handle *h);
 
@@ -246,8 +259,13 @@ int pic_load(pic_handle *h, const char *path);
  * the H update on both streams), out[1] push + deposit (its own stream),
  * out[2] E update (both streams), out[3] wait for the deposit + free-current
  * term + probe sampling, out[4] probe DFT flush per step, out[5] whole step
- * (without the brick sort that precedes every 16th step).  Runs real steps
- * (the simulation advances).  Synchronises. */
+ * (without the brick sort that precedes every 16th step).  On the fused
+ * path (pic_stats.field_path 1) the phases are: out[0] the fused field pass
+ * (E and the next step's H, both streams), out[1] J_f of two steps ago
+ * cleared + push + deposit + sources (before the pass), out[2] the
+ * free-current correction, out[3] probe sampling, out[4] and out[5] as
+ * above.  Runs real steps (the simulation advances).
+ * Synchronises. */
 int pic_profile_steps(pic_handle *h, int64_t nsteps, double *out_us);
 
 /* ---------------------------------------------------------------- tuning --

@@ -81,7 +81,7 @@ static bool has_cpml(const pic_config *c, int a) {
 
 static int validate(const pic_config *c) {
     if (!c) return fail(PIC_ERR_ARG, "config is NULL");
-    if (c->flags != 0) return fail(PIC_ERR_ARG, "flags must be 0");
+    if (c->flags & ~(uint64_t)PIC_FLAG_SPLIT_FIELDS) return fail(PIC_ERR_ARG, "unknown flags 0x%llx", (unsigned long long)c->flags);
     if (c->precision != PIC_FP32 && c->precision != PIC_FP64) return fail(PIC_ERR_ARG, "unknown precision");
     const int64_t n[3] = {c->nx, c->ny, c->nz};
     const double d[3] = {c->dx, c->dy, c->dz};
@@ -189,15 +189,33 @@ struct Sim : SimBase {
     bool bold_stale = false;
     bool have_q = false;
     double q = 0, m = 0;
+    // Fused FP32 field pass (fields_fused.cu): two copies of the field state
+    // (P[0] are the arrays of f, P[1] the second copy) and two free-current
+    // sets (J_f of even and odd steps; set 0 is f's).  While `fused_ready`,
+    // at step count n the state of step n lives in copy n & 1 with H one
+    // half step ahead (E^n, H^{n+1/2}, J_p^{n-1/2}, psi_E^n, psi_H^{n+1/2}),
+    // copy (n + 1) & 1 holds H^{n-1/2} and psi_H^{n-1/2}, and J_f of the
+    // last step is set (n - 1) & 1.  Otherwise the state is the plain one in
+    // f (E^n, H^{n-1/2}, ...), as on the split path.
+    bool fused_possible = false;  // the grid and flags take the fused pass (arena holds the second copy)
+    bool fused = false;           // ... and its plan was built
+    bool fused_ready = false;
+    FusedBuf P[2];
+    JfSet jfs[2];
+    FusedPlan fpl{};
+    int *d_tiles = nullptr;
+    float *d_plane_cE = nullptr;
+
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    cudaGraphExec_t gexec_odd = nullptr;  // fused: the block graph for blocks starting at an odd step
     long long graph_kernels = 0;   // kernels in one replay of the step graph
     // Captured runs shorter than a block: steps [pos, pos + len) of a block
     // entered with the sort counter at `since`, with the DFT flush when they
     // end the block.  Runs of SEG_MIN steps or more replay one of these (the
     // SEG_CACHE most recently used are kept); shorter runs launch directly.
     struct Segment {
-        int pos, len, since;
+        int pos, len, since, par;
         cudaGraphExec_t exec;
         long long kernels, used;
     };
@@ -209,18 +227,38 @@ struct Sim : SimBase {
     // all device buffers, in one pass; base == nullptr only measures
     void plan(Arena &a) {
         const size_t Ts = (size_t)N;
-        for (int c = 0; c < 3; c++) {
-            f.E[c] = a.take<T>(Ts);
-            f.H[c] = a.take<T>(Ts);
-            f.Jp[c] = a.take<T>(Ts);
-            f.Jf[c] = a.take<T>(Ts);
-        }
+        // the three components of each field one after another, equally
+        // spaced (the fused pass reads a field's three components with one
+        // tensor copy)
+        for (int c = 0; c < 3; c++) f.E[c] = a.take<T>(Ts);
+        for (int c = 0; c < 3; c++) f.H[c] = a.take<T>(Ts);
+        for (int c = 0; c < 3; c++) f.Jp[c] = a.take<T>(Ts);
+        for (int c = 0; c < 3; c++) f.Jf[c] = a.take<T>(Ts);
         for (int ax = 0; ax < 3; ax++) {
             size_t slab = 0;
             if (g.cpml[ax]) slab = (size_t)(N / n[ax]) * 2 * cfg.cpml_cells;
-            for (int s = 0; s < 2; s++) {
-                f.psiH[ax][s] = slab ? a.take<T>(slab) : nullptr;
-                f.psiE[ax][s] = slab ? a.take<T>(slab) : nullptr;
+            // the two components of each field's memory one after the other (one tensor copy reads both)
+            for (int s = 0; s < 2; s++) f.psiH[ax][s] = slab ? a.take<T>(slab) : nullptr;
+            for (int s = 0; s < 2; s++) f.psiE[ax][s] = slab ? a.take<T>(slab) : nullptr;
+        }
+        if constexpr (std::is_same<T, float>::value) {
+            if (fused_possible) {  // the second copy of the state and the second free-current set
+                FusedBuf &B = P[1];
+                for (int c = 0; c < 3; c++) B.E[c] = a.take<float>(Ts);
+                for (int c = 0; c < 3; c++) B.H[c] = a.take<float>(Ts);
+                for (int c = 0; c < 3; c++) B.Jp[c] = a.take<float>(Ts);
+                for (int c = 0; c < 3; c++) jfs[1].Jf[c] = a.take<float>(Ts);
+                for (int ax = 0; ax < 3; ax++) {
+                    const size_t slab = g.cpml[ax] ? (size_t)(N / n[ax]) * 2 * cfg.cpml_cells : 0;
+                    for (int s = 0; s < 2; s++) B.psiH[ax][s] = slab ? a.take<float>(slab) : nullptr;
+                    for (int s = 0; s < 2; s++) B.psiE[ax][s] = slab ? a.take<float>(slab) : nullptr;
+                }
+                jfs[1].flag = a.take<int>(n_tiles);
+                jfs[1].list = a.take<int>(n_tiles);
+                jfs[1].count = a.take<int>(1);
+                const int ntl = ((n[0] + FUSED_TX - 1) / FUSED_TX) * ((n[1] + FUSED_TY - 1) / FUSED_TY);
+                d_tiles = a.take<int>((size_t)ntl);
+                d_plane_cE = a.take<float>((size_t)n[2]);
             }
         }
         for (int ax = 0; ax < 3; ax++)
@@ -290,6 +328,11 @@ struct Sim : SimBase {
         n_tiles = (size_t)g.nt[0] * g.nt[1] * g.nt[2];
         for (int a = 0; a < 3; a++) sb.nb[a] = (n[a] + SORT_BRICK - 1) / SORT_BRICK;
         sb.nbricks = sb.nb[0] * sb.nb[1] * sb.nb[2];
+        fused_possible = std::is_same<T, float>::value && !(c->flags & PIC_FLAG_SPLIT_FIELDS) && n[0] % 4 == 0 &&
+                         !g.per[0] && !g.per[1] && !g.per[2] && (!g.cpml[0] || g.L % 4 == 0) &&
+                         ((!g.cpml[0] && !g.cpml[1]) || g.L <= FUSED_MAX_L) &&
+                         (long long)n[0] * n[1] * n[2] < (1LL << 32) && n[0] / FUSED_TX < 65536 &&
+                         (n[1] + FUSED_TY - 1) / FUSED_TY < 65536;
     }
 
     // CPML grading at position pos (cell units) along axis a: b-1, a, 1/kappa.
@@ -540,6 +583,38 @@ struct Sim : SimBase {
             for (int q = 0; q < 256; q++) cE[q] = (float)cls[2][q];
             use_plan = make_field_plan(g, plane_cls.data(), cE.data(), fplan);
             fplan.block = 256;
+            if (fused_possible) {
+                for (int c = 0; c < 3; c++) {
+                    P[0].E[c] = f.E[c];
+                    P[0].H[c] = f.H[c];
+                    P[0].Jp[c] = f.Jp[c];
+                    jfs[0].Jf[c] = f.Jf[c];
+                }
+                for (int ax = 0; ax < 3; ax++)
+                    for (int q2 = 0; q2 < 2; q2++) {
+                        P[0].psiE[ax][q2] = f.psiE[ax][q2];
+                        P[0].psiH[ax][q2] = f.psiH[ax][q2];
+                    }
+                jfs[0].flag = d_flag;
+                jfs[0].list = d_jf_list;
+                jfs[0].count = d_jf_count;
+                std::vector<int> inner, slabt;
+                fused_tiles(g, inner, slabt);
+                std::vector<int> tiles(inner);
+                tiles.insert(tiles.end(), slabt.begin(), slabt.end());
+                std::vector<float> pce(n[2]);
+                for (int k = 0; k < n[2]; k++) pce[k] = plane_cls[k] != 255 ? cE[plane_cls[k]] : -1.f;
+                CUDA_TRY(cudaMemcpy(d_tiles, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice));
+                CUDA_TRY(cudaMemcpy(d_plane_cE, pce.data(), pce.size() * sizeof(float), cudaMemcpyHostToDevice));
+                fpl.tiles = d_tiles;
+                fpl.n_inner = (int)inner.size();
+                fpl.n_slab = (int)slabt.size();
+                int sms = 0;
+                CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+                fpl.chunk = fused_chunk(n[2], (int)inner.size(), sms);
+                fpl.nchunks = (n[2] + fpl.chunk - 1) / fpl.chunk;
+                fused = fused_grid_ok(g) && fused_maps(fpl, P, n, g.L, g.cpml);
+            }
           }
         }
         // CPML profiles: per axis (b-1, a, 1/kappa) at E positions, then at H positions
@@ -603,16 +678,203 @@ struct Sim : SimBase {
 
     void drop_graph() {
         if (gexec) cudaGraphExecDestroy(gexec);
+        if (gexec_odd) cudaGraphExecDestroy(gexec_odd);
         if (graph) cudaGraphDestroy(graph);
         gexec = nullptr;
+        gexec_odd = nullptr;
         graph = nullptr;
         for (auto &sg : segs) cudaGraphExecDestroy(sg.exec);
         segs.clear();
         epoch++;
     }
 
+    // ---------------------------------------------------- fused helpers --
+    // f with E, H, J_p and the CPML memory of state copy b and free-current set j
+    Fields<T> view(int b, int j) const {
+        Fields<T> v = f;
+        if constexpr (std::is_same<T, float>::value) {
+            for (int c = 0; c < 3; c++) {
+                v.E[c] = P[b].E[c];
+                v.H[c] = P[b].H[c];
+                v.Jp[c] = P[b].Jp[c];
+                v.Jf[c] = jfs[j].Jf[c];
+            }
+            for (int ax = 0; ax < 3; ax++)
+                for (int q2 = 0; q2 < 2; q2++) {
+                    v.psiE[ax][q2] = P[b].psiE[ax][q2];
+                    v.psiH[ax][q2] = P[b].psiH[ax][q2];
+                }
+            v.jf_flag = jfs[j].flag;
+            v.jf_list = jfs[j].list;
+            v.jf_count = jfs[j].count;
+        }
+        return v;
+    }
+    // The plain state at the current step count: E^n, H^{n-1/2}, J_p^{n-1/2}
+    // and the last step's J_f (fused: from the copies that hold them).
+    Fields<T> current() const {
+        if (!fused_ready) return f;
+        const int par = (int)(step_host & 1);
+        Fields<T> v = view(par, par ^ 1);
+        const Fields<T> o = view(par ^ 1, 0);
+        for (int c = 0; c < 3; c++) v.H[c] = o.H[c];
+        for (int ax = 0; ax < 3; ax++)
+            for (int q2 = 0; q2 < 2; q2++) v.psiH[ax][q2] = o.psiH[ax][q2];
+        return v;
+    }
+
+    // Enter the fused path's state at step count n from the plain one: copy
+    // H^{n-1/2} (and psi_H) to copy 1, the rest of step n's state too when
+    // n is odd, then H^{n+1/2} in copy n & 1 (the split H update); both
+    // free-current sets start empty.
+    int enter_fused() {
+        if constexpr (std::is_same<T, float>::value) {
+            if (!fused || fused_ready) return PIC_OK;
+            const int par = (int)(step_host & 1);
+            const size_t nb = (size_t)N * sizeof(float);
+            for (int j = 0; j < 2; j++) {
+                for (int c = 0; c < 3; c++) CUDA_TRY(cudaMemsetAsync(jfs[j].Jf[c], 0, nb, stream));
+                CUDA_TRY(cudaMemsetAsync(jfs[j].flag, 0, n_tiles * sizeof(int), stream));
+                CUDA_TRY(cudaMemsetAsync(jfs[j].count, 0, sizeof(int), stream));
+            }
+            auto dd = [&](float *dst, const float *src, size_t bytes) {
+                return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, stream);
+            };
+            for (int c = 0; c < 3; c++) CUDA_TRY(dd(P[1].H[c], P[0].H[c], nb));
+            for (int ax = 0; ax < 3; ax++)
+                for (int q2 = 0; q2 < 2; q2++)
+                    if (P[0].psiH[ax][q2]) CUDA_TRY(dd(P[1].psiH[ax][q2], P[0].psiH[ax][q2], slab_bytes(ax)));
+            if (par) {
+                for (int c = 0; c < 3; c++) {
+                    CUDA_TRY(dd(P[1].E[c], P[0].E[c], nb));
+                    CUDA_TRY(dd(P[1].Jp[c], P[0].Jp[c], nb));
+                }
+                for (int ax = 0; ax < 3; ax++)
+                    for (int q2 = 0; q2 < 2; q2++)
+                        if (P[0].psiE[ax][q2]) CUDA_TRY(dd(P[1].psiE[ax][q2], P[0].psiE[ax][q2], slab_bytes(ax)));
+            }
+            launch_update_H<T>(g, view(par, 0), use_plan ? &fplan : nullptr, stream, stream);
+            CUDA_TRY(cudaGetLastError());
+            fused_ready = true;
+            drop_graph();
+        }
+        return PIC_OK;
+    }
+
+    // Back to the plain state in f (before E or H is overwritten): the last
+    // step's J_f record is dropped (both sets cleared).
+    int leave_fused() {
+        if constexpr (std::is_same<T, float>::value) {
+            if (!fused_ready) return PIC_OK;
+            const int par = (int)(step_host & 1);
+            const size_t nb = (size_t)N * sizeof(float);
+            auto dd = [&](float *dst, const float *src, size_t bytes) {
+                return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, stream);
+            };
+            if (par) {  // E^n, J_p, psi_E in copy 1 (H^{n-1/2} is in copy 0 already)
+                for (int c = 0; c < 3; c++) {
+                    CUDA_TRY(dd(P[0].E[c], P[1].E[c], nb));
+                    CUDA_TRY(dd(P[0].Jp[c], P[1].Jp[c], nb));
+                }
+                for (int ax = 0; ax < 3; ax++)
+                    for (int q2 = 0; q2 < 2; q2++)
+                        if (P[0].psiE[ax][q2]) CUDA_TRY(dd(P[0].psiE[ax][q2], P[1].psiE[ax][q2], slab_bytes(ax)));
+            } else {    // H^{n-1/2}, psi_H^{n-1/2} in copy 1
+                for (int c = 0; c < 3; c++) CUDA_TRY(dd(P[0].H[c], P[1].H[c], nb));
+                for (int ax = 0; ax < 3; ax++)
+                    for (int q2 = 0; q2 < 2; q2++)
+                        if (P[0].psiH[ax][q2]) CUDA_TRY(dd(P[0].psiH[ax][q2], P[1].psiH[ax][q2], slab_bytes(ax)));
+            }
+            for (int j = 0; j < 2; j++) {
+                for (int c = 0; c < 3; c++) CUDA_TRY(cudaMemsetAsync(jfs[j].Jf[c], 0, nb, stream));
+                CUDA_TRY(cudaMemsetAsync(jfs[j].flag, 0, n_tiles * sizeof(int), stream));
+                CUDA_TRY(cudaMemsetAsync(jfs[j].count, 0, sizeof(int), stream));
+            }
+            fused_ready = false;
+            drop_graph();
+        }
+        return PIC_OK;
+    }
+    size_t slab_bytes(int ax) const { return (size_t)(N / n[ax]) * 2 * cfg.cpml_cells * sizeof(T); }
+
+    // One step on the fused path, from the state of step n in copy `par`
+    // (= n & 1) to copy par ^ 1, on the main stream: J_f of the step before
+    // last back to zero, the electrons' E^n, push and deposit into J_f set
+    // `par`, the prescribed sources; then the fused pass (inner tiles on the
+    // main stream, the tiles over the x and y slabs beside them on aux); then
+    // the free-current correction and the probe sample.  (The push runs on
+    // its own before the pass: beside it, its blocks would wait for shared
+    // memory the pass holds.)  pe (optional) receives 7 timing events: step
+    // start, pass done, push start, push done (= pass start), correction
+    // start, correction done, tail done.
+    void launch_step_fused(bool sort, int par, cudaEvent_t *pe) {
+        if constexpr (std::is_same<T, float>::value) {
+            if (pe) cudaEventRecord(pe[0], stream);
+            if (sort) {
+                psort.n = p.n;
+                launch_sort<T>(p, psort, sb, stream);
+            }
+            const int xb = par, yb = par ^ 1;
+            const Fields<T> fx = view(xb, par);
+            if (pe) cudaEventRecord(pe[2], stream);
+            launch_jf_clear(g, jfs[par ^ 1], (int)n_tiles, stream);
+            if (p.n > 0) {
+                launch_gather_E<T>(g, fx, p, stream);
+                launch_push_deposit<T>(g, fx, p, pp, stream);
+            }
+            launch_sources<T>(g, fx, sources.data(), (int)sources.size(), cfg.dt, stream);
+            if (pe) cudaEventRecord(pe[3], stream);
+            fork_join(stream, aux, ev_hf);
+            FusedArgs a{};
+            a.g = g;
+            for (int c = 0; c < 3; c++) {
+                a.Eo[c] = P[yb].E[c];
+                a.Ho[c] = P[yb].H[c];
+                a.Jpi[c] = P[xb].Jp[c];
+                a.Jpo[c] = P[yb].Jp[c];
+            }
+            for (int ax = 0; ax < 3; ax++) {
+                for (int q2 = 0; q2 < 2; q2++) {
+                    a.psiEi[ax][q2] = P[xb].psiE[ax][q2];
+                    a.psiEo[ax][q2] = P[yb].psiE[ax][q2];
+                    a.psiHi[ax][q2] = P[xb].psiH[ax][q2];
+                    a.psiHo[ax][q2] = P[yb].psiH[ax][q2];
+                }
+                a.bE[ax] = f.bE[ax]; a.aE[ax] = f.aE[ax]; a.ikE[ax] = f.ikE[ax];
+                a.bH[ax] = f.bH[ax]; a.aH[ax] = f.aH[ax]; a.ikH[ax] = f.ikH[ax];
+                a.ecls[ax] = f.ecls[ax];
+            }
+            a.cls_pack = f.cls_pack;
+            a.plane_cE = d_plane_cE;
+            a.chunk = fpl.chunk;
+            a.err = d_err;
+            launch_fused_pass(a, fpl, xb, stream, aux);
+            fork_join(aux, stream, ev_hj);
+            if (pe) cudaEventRecord(pe[1], stream);
+            if (pe) cudaEventRecord(pe[4], stream);
+            FixArgs fa{};
+            for (int c = 0; c < 3; c++) {
+                fa.E[c] = P[yb].E[c];
+                fa.H[c] = P[yb].H[c];
+                fa.ecls[c] = f.ecls[c];
+                fa.aH[c] = f.aH[c];
+                fa.ikH[c] = f.ikH[c];
+                for (int q2 = 0; q2 < 2; q2++) fa.psiH[c][q2] = P[yb].psiH[c][q2];
+            }
+            fa.jf = jfs[par];
+            fa.cls_pack = f.cls_pack;
+            launch_jf_fix(g, fa, (int)n_tiles, stream);
+            if (pe) cudaEventRecord(pe[5], stream);
+            launch_step_tail<T>(g, view(yb, par ^ 1), pr, d_step, stream);
+            if (pe) cudaEventRecord(pe[6], stream);
+        }
+    }
+
     // ------------------------------------------------------------ batch --
-    int batch_prepare() override { return refresh_bold(); }
+    int batch_prepare() override {
+        int rc = enter_fused();
+        return rc ? rc : refresh_bold();
+    }
     bool batch_ready() const override { return buffered == 0; }
     long long launch_block_on(cudaStream_t from) override {
         const long long before = launch_count();
@@ -632,7 +894,7 @@ struct Sim : SimBase {
         step_host += DFT_BLOCK;
         since_sort = DFT_BLOCK - (DFT_BLOCK - 1) / sort_every * sort_every;  // steps since its last sort
     }
-    long long graph_epoch() const override { return epoch; }
+    long long graph_epoch() const override { return 2 * epoch + ((fused_ready && (step_host & 1)) ? 1 : 0); }
     int step_direct(long long n) override { return step(n); }
     int steps_to_boundary() const override { return buffered ? DFT_BLOCK - buffered : 0; }
     long long cells() const override { return N; }
@@ -640,7 +902,8 @@ struct Sim : SimBase {
 
     // DFT_BLOCK steps (a sort every sort_every, the first one included) and the DFT flush
     void launch_block() {
-        for (int s = 0; s < DFT_BLOCK; s++) launch_step(s % sort_every == 0);
+        const int par0 = (int)(step_host & 1);
+        for (int s = 0; s < DFT_BLOCK; s++) launch_step(s % sort_every == 0, true, nullptr, (par0 + s) & 1);
         launch_dft_flush<T>(pr, d_step, DFT_BLOCK, stream);
     }
 
@@ -658,7 +921,11 @@ struct Sim : SimBase {
     // are done.  With concurrent = false everything runs in that order on
     // the main stream.  pe (optional) receives 7 timing events: step start,
     // H done, push start, push done, E start, E done, tail done.
-    void launch_step(bool sort, bool concurrent = true, cudaEvent_t *pe = nullptr) {
+    void launch_step(bool sort, bool concurrent = true, cudaEvent_t *pe = nullptr, int par = 0) {
+        if (fused_ready) {
+            launch_step_fused(sort, par, pe);
+            return;
+        }
         if (sort) {
             psort.n = p.n;
             launch_sort<T>(p, psort, sb, stream);
@@ -712,17 +979,23 @@ struct Sim : SimBase {
         if (pe) cudaEventRecord(pe[6], stream);
     }
 
-    int ensure_graph() {
-        if (gexec) return PIC_OK;
+    // The block graph for a block starting at the current step count (on
+    // the fused path blocks starting at odd steps have their own graph).
+    int ensure_graph(cudaGraphExec_t **out = nullptr) {
+        cudaGraphExec_t &slot = (fused_ready && (step_host & 1)) ? gexec_odd : gexec;
+        if (out) *out = &slot;
+        if (slot) return PIC_OK;
         CUDA_TRY(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
         const long long before = launch_count();
         launch_block();
         graph_kernels = launch_count() - before;
         launch_count() = before;  // captured, not launched
-        cudaError_t e = cudaStreamEndCapture(stream, &graph);
-        if (e != cudaSuccess) { graph = nullptr; return fail(PIC_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e)); }
-        e = cudaGraphInstantiate(&gexec, graph, 0);
-        if (e != cudaSuccess) { gexec = nullptr; return fail(PIC_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e)); }
+        cudaGraph_t gr = nullptr;
+        cudaError_t e = cudaStreamEndCapture(stream, &gr);
+        if (e != cudaSuccess) return fail(PIC_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&slot, gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess) { slot = nullptr; return fail(PIC_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e)); }
         return PIC_OK;
     }
 
@@ -731,10 +1004,11 @@ struct Sim : SimBase {
     // direct path would advance them.
     int run_segment(int len) {
         const int pos = buffered, since = std::min(since_sort, sort_every);
+        const int par0 = fused_ready ? (int)(step_host & 1) : 0;
         const bool ends = pos + len == DFT_BLOCK;
         Segment *sg = nullptr;
         for (auto &x : segs)
-            if (x.pos == pos && x.len == len && x.since == since) sg = &x;
+            if (x.pos == pos && x.len == len && x.since == since && x.par == par0) sg = &x;
         if (!sg) {
             if ((int)segs.size() >= SEG_CACHE) {  // drop the least recently used
                 size_t old = 0;
@@ -743,13 +1017,13 @@ struct Sim : SimBase {
                 cudaGraphExecDestroy(segs[old].exec);
                 segs.erase(segs.begin() + (long)old);
             }
-            Segment nsg{pos, len, since, nullptr, 0, 0};
+            Segment nsg{pos, len, since, par0, nullptr, 0, 0};
             CUDA_TRY(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
             const long long before = launch_count();
             int ss = since;
             for (int q = 0; q < len; q++) {
                 const bool sort = ss >= sort_every;
-                launch_step(sort);
+                launch_step(sort, true, nullptr, (par0 + q) & 1);
                 ss = sort ? 1 : ss + 1;
             }
             if (ends) launch_dft_flush<T>(pr, d_step, DFT_BLOCK, stream);
@@ -777,7 +1051,7 @@ struct Sim : SimBase {
 
     int refresh_bold() {
         if (bold_stale) {
-            launch_gather_bold<T>(g, f, p, stream);
+            launch_gather_bold<T>(g, current(), p, stream);
             CUDA_TRY(cudaGetLastError());
             bold_stale = false;
         }
@@ -792,14 +1066,20 @@ struct Sim : SimBase {
         return rc;
     }
 
+    int prepare() {
+        int rc = enter_fused();
+        return rc ? rc : refresh_bold();
+    }
+
     int step_inner(long long nsteps) {
-        int rc = refresh_bold();
+        int rc = nsteps > 0 ? prepare() : refresh_bold();
         if (rc) return rc;
         while (nsteps > 0) {
             if (buffered == 0 && nsteps >= DFT_BLOCK) {
-                rc = ensure_graph();
+                cudaGraphExec_t *ex = nullptr;
+                rc = ensure_graph(&ex);
                 if (rc) return rc;
-                CUDA_TRY(cudaGraphLaunch(gexec, stream));
+                CUDA_TRY(cudaGraphLaunch(*ex, stream));
                 kernels += graph_kernels;
                 nsteps -= DFT_BLOCK;
                 step_host += DFT_BLOCK;
@@ -814,7 +1094,7 @@ struct Sim : SimBase {
                 continue;
             }
             const bool sort = since_sort >= sort_every;
-            launch_step(sort);
+            launch_step(sort, true, nullptr, (int)(step_host & 1));
             since_sort = sort ? 1 : since_sort + 1;
             CUDA_TRY(cudaGetLastError());
             buffered++;
@@ -842,9 +1122,10 @@ struct Sim : SimBase {
         CUDA_TRY(cudaStreamSynchronize(stream));
         int err = 0;
         CUDA_TRY(cudaMemcpy(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost));
-        if (err & (DEVERR_JUMP | DEVERR_NONFINITE))
-            return fail(PIC_ERR_DEVICE, "kernel error bits 0x%x%s", err,
-                        (err & DEVERR_NONFINITE) ? " (non-finite electron momentum: those electrons are frozen)" : "");
+        if (err & (DEVERR_JUMP | DEVERR_NONFINITE | DEVERR_WAIT))
+            return fail(PIC_ERR_DEVICE, "kernel error bits 0x%x%s%s", err,
+                        (err & DEVERR_NONFINITE) ? " (non-finite electron momentum: those electrons are frozen)" : "",
+                        (err & DEVERR_WAIT) ? " (a wait of the fused field pass ran out of time)" : "");
         if (err & DEVERR_FIELD_NONFINITE) return fail(PIC_ERR_NONFINITE, "E or H holds a NaN or an Inf");
         return PIC_OK;
     }
@@ -852,7 +1133,7 @@ struct Sim : SimBase {
     // sync() after a scan of E and H for NaN or Inf (pic_sync, pic_get_stats)
     int check() {
         CUDA_TRY(cudaStreamSynchronize(stream));
-        launch_nonfinite_scan<T>(f, N, d_err, stream);
+        launch_nonfinite_scan<T>(current(), N, d_err, stream);
         CUDA_TRY(cudaGetLastError());
         return sync();
     }
@@ -879,6 +1160,8 @@ struct Sim : SimBase {
         double d[3], dt, eps0, mu0;
         int32_t bc[6], cpml_cells, pad2;
         double cpml_order, cpml_sigma_fac, cpml_kappa_max, cpml_alpha_max;
+        uint64_t flags;
+        int32_t fused_ready, pad3;
     };
 
     // Arena pieces that follow from the configuration alone (material map,
@@ -913,6 +1196,8 @@ struct Sim : SimBase {
         hd.cpml_sigma_fac = cfg.cpml_sigma_fac;
         hd.cpml_kappa_max = cfg.cpml_kappa_max;
         hd.cpml_alpha_max = cfg.cpml_alpha_max;
+        hd.flags = cfg.flags;
+        hd.fused_ready = fused_ready ? 1 : 0;
         hd.precision = cfg.precision;
         for (int a = 0; a < 3; a++) hd.n[a] = n[a];
         hd.arena_bytes = arena_bytes;
@@ -967,7 +1252,8 @@ struct Sim : SimBase {
                     hd.max_freqs == cfg.max_freqs && hd.dt == cfg.dt && hd.eps0 == cfg.eps0 && hd.mu0 == cfg.mu0 &&
                     hd.cpml_cells == cfg.cpml_cells && hd.cpml_order == cfg.cpml_order &&
                     hd.cpml_sigma_fac == cfg.cpml_sigma_fac && hd.cpml_kappa_max == cfg.cpml_kappa_max &&
-                    hd.cpml_alpha_max == cfg.cpml_alpha_max;
+                    hd.cpml_alpha_max == cfg.cpml_alpha_max && hd.flags == cfg.flags &&
+                    (hd.fused_ready == 0 || (hd.fused_ready == 1 && fused));
         for (int a = 0; a < 3; a++) same = same && hd.n[a] == n[a] && hd.d[a] == d[a];
         for (int q6 = 0; q6 < 6; q6++) same = same && hd.bc[q6] == cfg.bc[q6];
         if (!same) return reject("written by a differently configured simulation");
@@ -1023,6 +1309,7 @@ struct Sim : SimBase {
         }
         fclose(fp);
         drop_graph();
+        fused_ready = hd.fused_ready != 0;
         sources = src;
         step_host = hd.step_host;
         p.n = hd.np;
@@ -1068,7 +1355,7 @@ struct Sim : SimBase {
     // one whole block under the current tuning, timed on the stream (the
     // graph is captured before the start event)
     int time_block(cudaEvent_t e0, cudaEvent_t e1, double *us) {
-        int rc = refresh_bold();
+        int rc = prepare();
         if (rc) return rc;
         rc = ensure_graph();
         if (rc) return rc;
@@ -1154,7 +1441,7 @@ struct Sim : SimBase {
     }
 
     int profile_steps(long long nsteps, double *out) {
-        int rc = refresh_bold();
+        int rc = prepare();
         if (rc) return rc;
         for (int q6 = 0; q6 < 6; q6++) out[q6] = 0.0;
         if (nsteps <= 0) return PIC_OK;
@@ -1171,7 +1458,7 @@ struct Sim : SimBase {
             for (int s = 0; s < cnt; s++) {
                 cudaEvent_t *e = &ev[(size_t)s * NE];
                 const bool sort = since_sort >= sort_every;
-                launch_step(sort, true, e);
+                launch_step(sort, true, e, (int)(step_host & 1));
                 since_sort = sort ? 1 : since_sort + 1;
                 buffered++;
                 step_host++;
@@ -1185,7 +1472,9 @@ struct Sim : SimBase {
             CUDA_TRY(cudaEventSynchronize(ev[(size_t)(cnt - 1) * NE + 7]));
             for (int s = 0; s < cnt; s++) {
                 cudaEvent_t *e = &ev[(size_t)s * NE];
-                const int from[6] = {0, 2, 4, 5, 6, 0}, to[6] = {1, 3, 5, 6, 7, 7};
+                // fused path: the pass runs from the end of the push (3) to 1
+                const int f0 = fused_ready ? 3 : 0;
+                const int from[6] = {f0, 2, 4, 5, 6, 0}, to[6] = {1, 3, 5, 6, 7, 7};
                 for (int q6 = 0; q6 < 6; q6++) {
                     float ms;
                     cudaEventElapsedTime(&ms, e[from[q6]], e[to[q6]]);
@@ -1415,11 +1704,12 @@ static int probe_kw_t(Sim<T> *s, int comp, int axis, int nk, const double *k, do
 template <typename T>
 static T *field_of(Sim<T> *s, int which) {
     const int c = which % 3;
+    const Fields<T> v = s->current();
     switch (which / 3) {
-    case 0: return s->f.E[c];
-    case 1: return s->f.H[c];
-    case 2: return s->f.Jp[c];
-    default: return s->f.Jf[c];
+    case 0: return v.E[c];
+    case 1: return v.H[c];
+    case 2: return v.Jp[c];
+    default: return v.Jf[c];
     }
 }
 
@@ -1439,6 +1729,8 @@ static int set_field_t(Sim<T> *s, int which, const double *in) {
     if (which < 0 || which > 5 || !in) return fail(PIC_ERR_ARG, "only E and H components can be set");
     int rc = s->sync();
     if (rc) return rc;
+    rc = s->leave_fused();  // back to the plain state: the next step starts the fused path again
+    if (rc) return rc;
     std::vector<T> tmp((size_t)s->N);
     for (size_t e = 0; e < (size_t)s->N; e++) tmp[e] = (T)in[e];
     CUDA_TRY(cudaMemcpy(field_of(s, which), tmp.data(), (size_t)s->N * sizeof(T), cudaMemcpyHostToDevice));
@@ -1450,7 +1742,7 @@ template <typename T>
 static int stats_t(Sim<T> *s, pic_stats *out) {
     cudaError_t e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return fail(PIC_ERR_CUDA, "%s", cudaGetErrorString(e));
-    pic::launch_nonfinite_scan<T>(s->f, s->N, s->d_err, s->stream);
+    pic::launch_nonfinite_scan<T>(s->current(), s->N, s->d_err, s->stream);
     CUDA_TRY(cudaStreamSynchronize(s->stream));
     int err = 0;
     CUDA_TRY(cudaMemcpy(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
@@ -1464,6 +1756,7 @@ static int stats_t(Sim<T> *s, pic_stats *out) {
     out->device_error = err;
     out->n_edge_classes = s->n_classes;
     out->kernel_launches = s->kernels;
+    out->field_path = s->fused ? 1 : 0;
     return PIC_OK;
 }
 

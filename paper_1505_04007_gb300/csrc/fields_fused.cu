@@ -1,0 +1,776 @@
+// fields_fused.cu -- the FP32 field updates of one step as a single pass over
+// the grid: E^{n+1} (Eq. 6 then Eq. 8, without the free current) and then
+// H^{n+3/2} (the vacuum Yee update of the next step), with their CPML terms.
+//
+// Why one pass: the two updates of a step, run one after the other, read E
+// and H twice and write each once (72 bytes per FP32 cell); the fused pass
+// reads each once and writes each once (48 bytes).  H^{n+3/2} needs E^{n+1}
+// of its own cell and of the cells at +x, +y, +z, so a block marches up a
+// column of planes: it computes E^{n+1} of plane z, then H^{n+3/2} of plane
+// z-1, keeping the planes it needs in shared memory.
+//
+// Layout of a work item: a tile of TX x TY cells (x, y) over a run of `chunk`
+// planes.  Warps 0..TY-1 own the tile's rows (one cell per lane).  H^{n+3/2}
+// at the tile's last column and row needs E^{n+1} one cell beyond the tile,
+// which belongs to the neighbouring tile: two more warps compute it again
+// here (warp TY: the row y0+TY; warp TY+1: the column x0+TX), and the
+// chunk's last E plane is likewise computed by both chunks that need it.
+// Recomputed values are used, never stored.  Because a neighbour may already
+// have written its cells of the step, the pass reads the state at step n
+// from one copy of the arrays (X) and writes step n+1 to another (Y).
+//
+// Staging: one thread streams the planes of E^n and H^{n+1/2} into a ring of
+// STAGES shared-memory slots with bulk tensor copies (cp.async.bulk.tensor,
+// one copy per field and plane, the three components at once), signalled
+// by mbarriers; every wait is bounded (on timeout the block records
+// DEVERR_WAIT, waits a bounded time for its copies in flight and returns).
+// The E^{n+1} planes go through a ring of three plain shared-memory planes.
+//
+// Free current: Eq. 8's J_f term is left out of the pass (the electrons are
+// pushed beside it and their current is not known yet).  k_jf_fix adds it
+// afterwards on the tiles the deposit wrote: dE = -dt/(eps0 eps_inf) J_f on
+// those edges, and the change of H^{n+3/2} (and of its CPML memory) that dE
+// causes through the H update, which is linear in E.
+#include <cuda.h>
+
+#include <mutex>
+
+#include "pic_internal.cuh"
+
+namespace pic {
+
+namespace {
+
+constexpr int TX = FUSED_TX, TY = FUSED_TY;
+constexpr int GX = 4, TPR = TX / GX;     // four x cells per thread, threads per tile row
+constexpr int NT = TPR * (TY + 1);       // the tile's rows and the halo row beyond it
+constexpr int STAGES = 3;
+constexpr int EW = TX + 4, EH = TY + 1;  // E^n box: x0..x0+TX+3, y0..y0+TY
+constexpr int HW = TX + 8, HH = TY + 2;  // H box: x0-4..x0+TX+3, y0-1..y0+TY
+constexpr int EBOX_B = 3 * EH * EW * 4, HBOX_B = 3 * HH * HW * 4;  // bytes a tensor copy writes
+constexpr int EBOX = (3 * EH * EW + 31) / 32 * 32;                  // floats, slots 128-byte aligned
+constexpr int HBOX = (3 * HH * HW + 31) / 32 * 32;
+constexpr int XW = TX + 4;               // E^{n+1} plane row: x0..x0+TX+3 (column TX: the halo cell)
+constexpr int NBOX = 3 * EH * XW;
+static_assert(TX % 32 == 0 && NT % 32 == 0, "whole warps");
+
+constexpr int MAX_CHUNK = 64;
+// CPML memory of the x and y slabs, staged with E and H for the tiles that
+// meet those slabs: x slabs [comp][row][2L] (both faces' slab columns), y
+// slabs [comp][slab row][x0..x0+TX+3], for 2L <= 2 FUSED_MAX_L rows/columns.
+constexpr int PX = 2 * FUSED_MAX_L;
+constexpr int PXBOX = 2 * EH * PX, PYBOX = 2 * EH * EW;  // floats (multiples of 32)
+constexpr int PY_B = PYBOX * 4;                           // bytes of a y-slab copy
+
+template <bool SLAB>
+struct __align__(128) Smem {
+    static constexpr int PS = SLAB ? STAGES : 1;
+    float e[STAGES][EBOX];
+    float h[STAGES][HBOX];
+    float pex[PS][SLAB ? PXBOX : 32], phx[PS][SLAB ? PXBOX : 32];  // psi_E, psi_H of x slabs
+    float pey[PS][SLAB ? PYBOX : 32], phy[PS][SLAB ? PYBOX : 32];  // ... of y slabs
+    float en[3][NBOX];
+    float4 cls[256];            // per edge class: kJ-1, bJ, cE, metal
+    float pcE[MAX_CHUNK + 2];   // per plane of the item
+    int pzs[MAX_CHUNK + 2];
+    unsigned long long bar[STAGES];
+    int abort_flag;
+};
+template <bool SLAB>
+constexpr size_t smem_bytes() { return sizeof(Smem<SLAB>) + 128; }  // + alignment slack
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(unsigned long long *b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned long long *b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase of parity `parity` to complete; false after ~0.2 s.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity) {
+    if (mbar_try(b, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try(b, parity))
+        if (global_ns() - t0 > 200000000ull) return false;
+    return true;
+}
+// Box of a 4-D tensor map ([3][nz][ny][nx] floats) at (x, y, z, component 0).
+__device__ __forceinline__ void tma_load(void *dst, const CUtensorMap *m, int x, int y, int z, unsigned long long *b) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"((unsigned long long)m), "r"(x), "r"(y), "r"(z), "r"(0), "r"(smem_u32(b))
+        : "memory");
+}
+
+__device__ __forceinline__ int slab_of(const Grid<float> &g, int a, int x) {
+    if (!g.cpml[a]) return -1;
+    if (x < g.L) return x;
+    if (x >= g.n[a] - g.L) return x - (g.n[a] - 2 * g.L);
+    return -1;
+}
+
+struct V4 {
+    float v[4];
+};
+__device__ __forceinline__ V4 ld4(const float *p) {
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    return V4{{q.x, q.y, q.z, q.w}};
+}
+__device__ __forceinline__ void st4(float *p, const V4 &a) {
+    *reinterpret_cast<float4 *>(p) = make_float4(a.v[0], a.v[1], a.v[2], a.v[3]);
+}
+__device__ __forceinline__ V4 zero4() { return V4{{0.f, 0.f, 0.f, 0.f}}; }
+
+// CPML curl terms of four cells: psi (p, read from X) advances as
+// psi' = psi + ((b-1) psi + a d) and the term becomes (1/kappa) d + psi';
+// cells whose E edge is held keep psi (and their term is not used).  The
+// new psi goes to Y at q when `wr`.  Profiles per cell (x slabs) or one for
+// the four (y, z slabs).
+__device__ __forceinline__ void cterm4(float t[4], const V4 &p, float *pout, unsigned q, const V4 &bm, const V4 &aa,
+                                       const V4 &ik, const float d[4], const bool up[4], bool wr) {
+    V4 o = p;
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+        const float pn = p.v[m] + (bm.v[m] * p.v[m] + aa.v[m] * d[m]);
+        if (up[m]) {
+            o.v[m] = pn;
+            t[m] = ik.v[m] * d[m] + pn;
+        }
+    }
+    if (wr) st4(pout + q, o);
+}
+__device__ __forceinline__ V4 splat(float x) { return V4{{x, x, x, x}}; }
+
+template <bool SLAB>
+__global__ void __launch_bounds__(NT, SLAB ? 2 : 3)
+    k_fused(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorMap tmH,
+            const __grid_constant__ CUtensorMap tmPEx, const __grid_constant__ CUtensorMap tmPHx,
+            const __grid_constant__ CUtensorMap tmPEy, const __grid_constant__ CUtensorMap tmPHy, const FusedArgs a) {
+    pdl_wait();
+    extern __shared__ unsigned char raw[];
+    Smem<SLAB> &S = *reinterpret_cast<Smem<SLAB> *>((reinterpret_cast<uintptr_t>(raw) + 127) & ~uintptr_t(127));
+    const Grid<float> &g = a.g;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2], L2 = 2 * g.L;
+    const int item = blockIdx.x;
+    const int packed = a.tiles[item % a.ntiles], chk = item / a.ntiles;
+    const int x0 = (packed & 0xffff) * TX, y0 = (packed >> 16) * TY;
+    const int kz0 = chk * a.chunk, kz1 = min(nz, kz0 + a.chunk);
+    const int lj = threadIdx.x / TPR, gx = threadIdx.x % TPR;  // row (TY: the halo row) and x group
+    const int li = GX * gx;
+    const bool owner = lj < TY;
+    const bool xh = owner && gx == TPR - 1;  // also E of the halo cell x0+TX of this row
+    const int gi = x0 + li, gj = y0 + lj, gih = x0 + TX;
+    const bool inside = gi < nx && gj < ny;   // nx % 4 == 0: the group is inside or outside as a whole
+    const bool inh = xh && gih < nx && gj < ny;
+    const unsigned sz = (unsigned)nx * (unsigned)ny;  // cell offsets fit 32 bits on this path
+    const unsigned cxy = (unsigned)gj * (unsigned)nx + (unsigned)gi;
+    int sx = -1, syb = -1, sxh = -1;
+    if (SLAB) {
+        if (inside) {
+            sx = slab_of(g, 0, gi);  // L % 4 == 0: the group is in an x slab as a whole
+            syb = slab_of(g, 1, gj);
+        }
+        if (inh) sxh = slab_of(g, 0, gih);
+    }
+    const float rx = g.r[0], ry = g.r[1], rz = g.r[2], cH = g.cH;
+    // held tangential E on the low faces (all axes non-periodic here): Ex at
+    // j = 0 or k = 0, Ey at i = 0 or k = 0, Ez at i = 0 or j = 0
+    const bool fy = gj == 0, fx0 = gi == 0;
+    const int p0 = kz0 - 1, np = kz1 - p0 + 1;  // planes kz0-1 .. kz1
+    // this tile's staged slab memory: x slabs (all 2L columns, rows y0..),
+    // y slabs (slab rows from ys0; index of row gj: its slab index - ys0)
+    const bool xk = SLAB && g.cpml[0] && (x0 < g.L || x0 + TX >= nx - g.L);
+    const bool yk = SLAB && g.cpml[1] && (y0 < g.L || y0 + TY >= ny - g.L);
+    const int ys0 = y0 < g.L ? 0 : y0 - (ny - L2);
+    const unsigned px_b = 2u * EH * L2 * 4u;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; s++) mbar_init(&S.bar[s], 1);
+        S.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    // per plane: the Ampere factor of its one non-metal material (-1: per-edge
+    // classes) and its z-slab index (-1: none); the class table
+    for (int q = threadIdx.x; q < np; q += NT) {
+        const int z = p0 + q;
+        S.pcE[q] = (z >= 0 && z < nz) ? a.plane_cE[z] : 0.f;
+        S.pzs[q] = (z >= 0 && z < nz) ? slab_of(g, 2, z) : -1;
+    }
+    for (int q = threadIdx.x; q < 256; q += NT) S.cls[q] = a.cls_pack[q];
+    __syncthreads();
+    const unsigned stage_bytes = EBOX_B + HBOX_B + (xk ? 2 * px_b : 0u) + (yk ? 2u * PY_B : 0u);
+    // plane p0+q into slot s: E^n and H^{n+1/2} of plane z; psi_E of plane
+    // z and psi_H of plane z-1 of the slabs this tile meets
+    auto issue = [&](int qq, int slot) {
+        const int z = p0 + qq;
+        mbar_expect(&S.bar[slot], stage_bytes);
+        tma_load(S.e[slot], &tmE, x0, y0, z, &S.bar[slot]);
+        tma_load(S.h[slot], &tmH, x0 - 4, y0 - 1, z, &S.bar[slot]);
+        if (SLAB) {
+            if (xk) {
+                tma_load(S.pex[slot], &tmPEx, 0, y0, z, &S.bar[slot]);
+                tma_load(S.phx[slot], &tmPHx, 0, y0, z - 1, &S.bar[slot]);
+            }
+            if (yk) {
+                tma_load(S.pey[slot], &tmPEy, x0, ys0, z, &S.bar[slot]);
+                tma_load(S.phy[slot], &tmPHy, x0, ys0, z - 1, &S.bar[slot]);
+            }
+        }
+    };
+    if (threadIdx.x == 0)
+        for (int q = 0; q < STAGES && q < np; q++) issue(q, q);
+
+    constexpr int HC = HH * HW, EC = EH * EW, NC = EH * XW;  // component strides in the boxes
+    const int eo = lj * EW + li;               // this group in the E box
+    const int ho = (lj + 1) * HW + (li + 4);   // ... in the H box
+    const int no = lj * XW + li;               // ... in an E^{n+1} plane
+    const int hoh = (lj + 1) * HW + (TX + 4);  // the halo cell in the H box
+    V4 hb[3] = {zero4(), zero4(), zero4()};    // H^{n+1/2} of this group, plane z-1
+    V4 ec[3] = {zero4(), zero4(), zero4()};    // E^{n+1} of this group, plane z-1
+    float hbh_x = 0.f, hbh_y = 0.f;            // Hx, Hy of the halo cell, plane z-1
+    bool ok = true;
+    int q = 0;
+    for (; q < np; q++) {
+        const int s = q % STAGES, z = p0 + q, kh = z - 1;
+        const bool doE = inside && z >= kz0 && z < nz;
+        const bool doEh = inh && z >= kz0 && z < nz;
+        const bool doH = owner && inside && kh >= kz0 && kh < kz1;
+        const float cEu = S.pcE[q];
+        const bool mat = cEu < 0.f;
+        const int szb = S.pzs[q], szh = q > 0 ? S.pzs[q - 1] : -1;
+        const unsigned cz = (unsigned)z * sz + cxy, chh = cz - sz;  // this group at planes z and z-1
+        // ---- global loads of this iteration, issued before the wait for the
+        // staged plane: CPML memory of both updates, the Drude current and
+        // the edge classes of a material plane
+        V4 pE[6], pH[6];
+        unsigned qEx = 0, qEy = 0, qEz = 0, qHx = 0, qHy = 0, qHz = 0;
+        if (doE) {
+            if (SLAB && sx >= 0) qEx = ((unsigned)z * ny + gj) * L2 + sx;
+            if (SLAB && syb >= 0) qEy = ((unsigned)z * L2 + syb) * nx + gi;
+            if (szb >= 0) {
+                qEz = (unsigned)szb * sz + cxy;
+                pE[4] = ld4(a.psiEi[2][0] + qEz);
+                pE[5] = ld4(a.psiEi[2][1] + qEz);
+            }
+        }
+        if (doH) {
+            if (SLAB && sx >= 0) qHx = ((unsigned)kh * ny + gj) * L2 + sx;
+            if (SLAB && syb >= 0) qHy = ((unsigned)kh * L2 + syb) * nx + gi;
+            if (szh >= 0) {
+                qHz = (unsigned)szh * sz + cxy;
+                pH[4] = ld4(a.psiHi[2][0] + qHz);
+                pH[5] = ld4(a.psiHi[2][1] + qHz);
+            }
+        }
+        uchar4 cl[3];
+        V4 j0[3];
+        if (doE && mat) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                cl[c] = *reinterpret_cast<const uchar4 *>(a.ecls[c] + cz);
+                j0[c] = ld4(a.Jpi[c] + cz);
+            }
+        }
+        if (!mbar_wait(&S.bar[s], (q / STAGES) & 1)) ok = false;
+        const float *e = S.e[s], *h = S.h[s];
+        float *enb = S.en[q % 3];
+        if constexpr (SLAB) {  // the staged x and y slab memory of this group
+            const int ox = lj * L2 + sx, oy = (syb - ys0) * EW + li;
+            if (doE && sx >= 0) {
+                pE[0] = ld4(S.pex[s] + ox);
+                pE[1] = ld4(S.pex[s] + EH * L2 + ox);
+            }
+            if (doE && syb >= 0) {
+                pE[2] = ld4(S.pey[s] + oy);
+                pE[3] = ld4(S.pey[s] + EH * EW + oy);
+            }
+            if (doH && sx >= 0) {
+                pH[0] = ld4(S.phx[s] + ox);
+                pH[1] = ld4(S.phx[s] + EH * L2 + ox);
+            }
+            if (doH && syb >= 0) {
+                pH[2] = ld4(S.phy[s] + oy);
+                pH[3] = ld4(S.phy[s] + EH * EW + oy);
+            }
+        }
+        V4 hc[3] = {ld4(h + ho), ld4(h + HC + ho), ld4(h + 2 * HC + ho)};
+        float hch_x = 0.f, hch_y = 0.f;
+        if (xh) {
+            hch_x = h[hoh];
+            hch_y = h[HC + hoh];
+        }
+        V4 en[3] = {zero4(), zero4(), zero4()};
+        if (doE) {
+            // ---- E^{n+1} of the group at plane z (Eq. 6, Eq. 8 without J_f)
+            const bool wr = owner && z < kz1;  // this block owns the plane's state
+            const V4 hz_jm = ld4(h + 2 * HC + ho - HW), hx_jm = ld4(h + ho - HW);
+            const float hz_im = h[2 * HC + ho - 1], hy_im = h[HC + ho - 1];
+            float t[6][4];  // curl terms: Ex (1,2), Ey (3,4), Ez (5,6)
+#pragma unroll
+            for (int m = 0; m < 4; m++) {
+                const float hzm = m ? hc[2].v[m - 1] : hz_im, hym = m ? hc[1].v[m - 1] : hy_im;
+                t[0][m] = (hc[2].v[m] - hz_jm.v[m]) * ry;  // dHz/dy
+                t[1][m] = (hc[1].v[m] - hb[1].v[m]) * rz;  // dHy/dz
+                t[2][m] = (hc[0].v[m] - hb[0].v[m]) * rz;  // dHx/dz
+                t[3][m] = (hc[2].v[m] - hzm) * rx;         // dHz/dx
+                t[4][m] = (hc[1].v[m] - hym) * rx;         // dHy/dx
+                t[5][m] = (hc[0].v[m] - hx_jm.v[m]) * ry;  // dHx/dy
+            }
+            const bool uxx = !(fy || z == 0);
+            bool ux[4], uy[4], uz[4];
+#pragma unroll
+            for (int m = 0; m < 4; m++) {
+                const bool f0 = fx0 && m == 0;
+                ux[m] = uxx;
+                uy[m] = !(f0 || z == 0);
+                uz[m] = !(f0 || fy);
+            }
+            if (SLAB && sx >= 0) {  // x slab: Ey's d/dx Hz, Ez's d/dx Hy (profiles per cell)
+                const V4 bm = ld4(a.bE[0] + gi), aa = ld4(a.aE[0] + gi), ik = ld4(a.ikE[0] + gi);
+                float d3[4], d4[4];
+#pragma unroll
+                for (int m = 0; m < 4; m++) { d3[m] = t[3][m]; d4[m] = t[4][m]; }
+                cterm4(t[3], pE[0], a.psiEo[0][0], qEx, bm, aa, ik, d3, uy, wr);
+                cterm4(t[4], pE[1], a.psiEo[0][1], qEx, bm, aa, ik, d4, uz, wr);
+            }
+            if (SLAB && syb >= 0) {  // y slab: Ez's d/dy Hx, Ex's d/dy Hz
+                const V4 bm = splat(a.bE[1][gj]), aa = splat(a.aE[1][gj]), ik = splat(a.ikE[1][gj]);
+                float d5[4], d0[4];
+#pragma unroll
+                for (int m = 0; m < 4; m++) { d5[m] = t[5][m]; d0[m] = t[0][m]; }
+                cterm4(t[5], pE[2], a.psiEo[1][0], qEy, bm, aa, ik, d5, uz, wr);
+                cterm4(t[0], pE[3], a.psiEo[1][1], qEy, bm, aa, ik, d0, ux, wr);
+            }
+            if (szb >= 0) {  // z slab: Ex's d/dz Hy, Ey's d/dz Hx
+                const V4 bm = splat(a.bE[2][z]), aa = splat(a.aE[2][z]), ik = splat(a.ikE[2][z]);
+                float d1[4], d2[4];
+#pragma unroll
+                for (int m = 0; m < 4; m++) { d1[m] = t[1][m]; d2[m] = t[2][m]; }
+                cterm4(t[1], pE[4], a.psiEo[2][0], qEz, bm, aa, ik, d1, ux, wr);
+                cterm4(t[2], pE[5], a.psiEo[2][1], qEz, bm, aa, ik, d2, uy, wr);
+            }
+            en[0] = ld4(e + eo);
+            en[1] = ld4(e + EC + eo);
+            en[2] = ld4(e + 2 * EC + eo);
+            if (!mat) {  // one non-metal material on the whole plane
+#pragma unroll
+                for (int m = 0; m < 4; m++) {
+                    if (ux[m]) en[0].v[m] += cEu * (t[0][m] - t[1][m]);
+                    if (uy[m]) en[1].v[m] += cEu * (t[2][m] - t[3][m]);
+                    if (uz[m]) en[2].v[m] += cEu * (t[4][m] - t[5][m]);
+                }
+            } else {  // per-edge classes: Eq. 6 on metal edges, then Eq. 8
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    const unsigned char k4[4] = {cl[c].x, cl[c].y, cl[c].z, cl[c].w};
+                    V4 jn = j0[c];
+                    bool metal = false;
+#pragma unroll
+                    for (int m = 0; m < 4; m++) {
+                        const float4 tc = S.cls[k4[m]];
+                        const bool up = c == 0 ? ux[m] : (c == 1 ? uy[m] : uz[m]);
+                        const float curl = t[2 * c][m] - t[2 * c + 1][m];
+                        float jp = 0.f;
+                        if (tc.w != 0.f) {
+                            metal = true;
+                            jp = up ? j0[c].v[m] + (tc.x * j0[c].v[m] + tc.y * en[c].v[m]) : j0[c].v[m];
+                            jn.v[m] = jp;
+                        }
+                        if (up) en[c].v[m] += tc.z * (curl - jp);
+                    }
+                    if (wr && metal) st4(a.Jpo[c] + cz, jn);
+                }
+            }
+        }
+        if (doEh) {
+            // ---- Ey, Ez of the halo cell x0+TX (one cell, the same updates)
+            const unsigned czh = (unsigned)z * sz + (unsigned)gj * (unsigned)nx + (unsigned)gih;
+            const float hzh = h[2 * HC + hoh], hyh = h[HC + hoh], hxh = h[hoh];
+            const float hx_jmh = h[hoh - HW];
+            float dHx_dz = (hxh - hbh_x) * rz, dHz_dx = (hzh - hc[2].v[3]) * rx;
+            float dHy_dx = (hyh - hc[1].v[3]) * rx, dHx_dy = (hxh - hx_jmh) * ry;
+            float ty1 = dHx_dz, ty2 = dHz_dx, tz1 = dHy_dx, tz2 = dHx_dy;
+            const bool uyh = z != 0, uzh = !fy;
+            if (SLAB && sxh >= 0) {
+                const int ox = lj * L2 + sxh;
+                const float bm = a.bE[0][gih], aa = a.aE[0][gih], ik = a.ikE[0][gih];
+                if (uyh) { const float p = S.pex[s][ox]; ty2 = ik * dHz_dx + (p + (bm * p + aa * dHz_dx)); }
+                if (uzh) { const float p = S.pex[s][EH * L2 + ox]; tz1 = ik * dHy_dx + (p + (bm * p + aa * dHy_dx)); }
+            }
+            if (SLAB && syb >= 0 && uzh) {
+                const float bm = a.bE[1][gj], aa = a.aE[1][gj], ik = a.ikE[1][gj];
+                const float p = S.pey[s][(syb - ys0) * EW + TX];
+                tz2 = ik * dHx_dy + (p + (bm * p + aa * dHx_dy));
+            }
+            if (szb >= 0 && uyh) {
+                const unsigned qq = (unsigned)szb * sz + (unsigned)gj * (unsigned)nx + (unsigned)gih;
+                const float bm = a.bE[2][z], aa = a.aE[2][z], ik = a.ikE[2][z];
+                const float p = a.psiEi[2][1][qq];
+                ty1 = ik * dHx_dz + (p + (bm * p + aa * dHx_dz));
+            }
+            float eyh = e[EC + lj * EW + TX], ezh = e[2 * EC + lj * EW + TX];
+            if (!mat) {
+                if (uyh) eyh += cEu * (ty1 - ty2);
+                if (uzh) ezh += cEu * (tz1 - tz2);
+            } else {
+                const float4 ty = S.cls[a.ecls[1][czh]], tz = S.cls[a.ecls[2][czh]];
+                if (uyh) {
+                    float jp = 0.f;
+                    if (ty.w != 0.f) { const float jj = a.Jpi[1][czh]; jp = jj + (ty.x * jj + ty.y * eyh); }
+                    eyh += ty.z * ((ty1 - ty2) - jp);
+                }
+                if (uzh) {
+                    float jp = 0.f;
+                    if (tz.w != 0.f) { const float jj = a.Jpi[2][czh]; jp = jj + (tz.x * jj + tz.y * ezh); }
+                    ezh += tz.z * ((tz1 - tz2) - jp);
+                }
+            }
+            enb[NC + lj * XW + TX] = eyh;
+            enb[2 * NC + lj * XW + TX] = ezh;
+        } else if (xh && z >= kz0) {
+            enb[NC + lj * XW + TX] = 0.f;  // beyond the high x face E reads as zero
+            enb[2 * NC + lj * XW + TX] = 0.f;
+        }
+        if (z >= kz0) {
+            st4(enb + no, en[0]);
+            st4(enb + NC + no, en[1]);
+            st4(enb + 2 * NC + no, en[2]);
+        }
+        if (!ok) S.abort_flag = 1;
+        __syncthreads();
+        if (S.abort_flag) break;
+        if (threadIdx.x == 0 && q + STAGES < np) {  // the slot read above is free again
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(q + STAGES, s);
+        }
+        // ---- H^{n+3/2} of the group at plane kh = z-1 from E^{n+1} of planes kh and kh+1
+        if (doH) {
+            const float *bp = S.en[(q + 2) % 3];  // plane kh
+            const float ez_ip = bp[2 * NC + no + 4], ey_ip = bp[NC + no + 4];
+            const V4 ez_jp = ld4(bp + 2 * NC + no + XW), ex_jp = ld4(bp + no + XW);
+            V4 e1[3] = {en[0], en[1], en[2]};
+            if (z >= nz) e1[0] = e1[1] = e1[2] = zero4();  // E beyond the high face reads as zero
+            float t[6][4];  // curl terms: Hx (1,2), Hy (3,4), Hz (5,6)
+#pragma unroll
+            for (int m = 0; m < 4; m++) {
+                const float ezp = m < 3 ? ec[2].v[m + 1] : ez_ip, eyp = m < 3 ? ec[1].v[m + 1] : ey_ip;
+                t[0][m] = (ez_jp.v[m] - ec[2].v[m]) * ry;   // dEz/dy
+                t[1][m] = (e1[1].v[m] - ec[1].v[m]) * rz;   // dEy/dz
+                t[2][m] = (e1[0].v[m] - ec[0].v[m]) * rz;   // dEx/dz
+                t[3][m] = (ezp - ec[2].v[m]) * rx;          // dEz/dx
+                t[4][m] = (eyp - ec[1].v[m]) * rx;          // dEy/dx
+                t[5][m] = (ex_jp.v[m] - ec[0].v[m]) * ry;   // dEx/dy
+            }
+            const bool all[4] = {true, true, true, true};
+            if (SLAB && sx >= 0) {  // x slab: Hy's d/dx Ez, Hz's d/dx Ey
+                const V4 bm = ld4(a.bH[0] + gi), aa = ld4(a.aH[0] + gi), ik = ld4(a.ikH[0] + gi);
+                float d3[4], d4[4];
+#pragma unroll
+                for (int m = 0; m < 4; m++) { d3[m] = t[3][m]; d4[m] = t[4][m]; }
+                cterm4(t[3], pH[0], a.psiHo[0][0], qHx, bm, aa, ik, d3, all, true);
+                cterm4(t[4], pH[1], a.psiHo[0][1], qHx, bm, aa, ik, d4, all, true);
+            }
+            if (SLAB && syb >= 0) {  // y slab: Hz's d/dy Ex, Hx's d/dy Ez
+                const V4 bm = splat(a.bH[1][gj]), aa = splat(a.aH[1][gj]), ik = splat(a.ikH[1][gj]);
+                float d5[4], d0[4];
+#pragma unroll
+                for (int m = 0; m < 4; m++) { d5[m] = t[5][m]; d0[m] = t[0][m]; }
+                cterm4(t[5], pH[2], a.psiHo[1][0], qHy, bm, aa, ik, d5, all, true);
+                cterm4(t[0], pH[3], a.psiHo[1][1], qHy, bm, aa, ik, d0, all, true);
+            }
+            if (szh >= 0) {  // z slab: Hx's d/dz Ey, Hy's d/dz Ex
+                const V4 bm = splat(a.bH[2][kh]), aa = splat(a.aH[2][kh]), ik = splat(a.ikH[2][kh]);
+                float d1[4], d2[4];
+#pragma unroll
+                for (int m = 0; m < 4; m++) { d1[m] = t[1][m]; d2[m] = t[2][m]; }
+                cterm4(t[1], pH[4], a.psiHo[2][0], qHz, bm, aa, ik, d1, all, true);
+                cterm4(t[2], pH[5], a.psiHo[2][1], qHz, bm, aa, ik, d2, all, true);
+            }
+            V4 hn[3];
+#pragma unroll
+            for (int m = 0; m < 4; m++) {
+                hn[0].v[m] = hb[0].v[m] - cH * (t[0][m] - t[1][m]);
+                hn[1].v[m] = hb[1].v[m] - cH * (t[2][m] - t[3][m]);
+                hn[2].v[m] = hb[2].v[m] - cH * (t[4][m] - t[5][m]);
+            }
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                st4(a.Ho[c] + chh, hn[c]);
+                st4(a.Eo[c] + chh, ec[c]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            hb[c] = hc[c];
+            ec[c] = en[c];
+        }
+        hbh_x = hch_x;
+        hbh_y = hch_y;
+    }
+    if (S.abort_flag) {
+        if (threadIdx.x == 0) {
+            atomicOr(a.err, DEVERR_WAIT);
+            // the copies issued for planes q .. q+STAGES-1 may still be in
+            // flight: wait for them (bounded) before the shared memory goes
+            const int issued = min(np, q + STAGES);
+            for (int qq = q; qq < issued; qq++)
+                if (!mbar_wait(&S.bar[qq % STAGES], (qq / STAGES) & 1)) break;
+        }
+        __syncthreads();
+    }
+}
+
+// J_f of the listed tiles back to zero (the current of two steps ago).
+__global__ void __launch_bounds__(TILE_X *TILE_Y *TILE_Z) k_jf_clear(Grid<float> g, JfSet j) {
+    pdl_wait();
+    pdl_release();
+    const int count = *j.count;
+    const int i0 = threadIdx.x % TILE_X, j0 = (threadIdx.x / TILE_X) % TILE_Y, k0 = threadIdx.x / (TILE_X * TILE_Y);
+    for (int q = blockIdx.x; q < count; q += gridDim.x) {
+        const long long t = j.list[q];
+        const int tx = (int)(t % g.nt[0]), ty = (int)((t / g.nt[0]) % g.nt[1]);
+        const int tz = (int)(t / ((long long)g.nt[0] * g.nt[1]));
+        const int i = tx * TILE_X + i0, jj = ty * TILE_Y + j0, k = tz * TILE_Z + k0;
+        if (i >= g.n[0] || jj >= g.n[1] || k >= g.n[2]) continue;
+        const long long e = ((long long)k * g.n[1] + jj) * g.n[0] + i;
+#pragma unroll
+        for (int c = 0; c < 3; c++) j.Jf[c][e] = 0.f;
+    }
+}
+
+// The free-current term of Eq. 8 on the listed tiles, after the fused pass:
+// dE = -cE J_f on every non-held edge; then its effect on the H^{n+3/2} the
+// pass computed without it.  In H_h -= cH [ (1/k_a1 d_a1 E_a2 + psi) -
+// (1/k_a2 d_a2 E_a1 + psi) ] the edge value E_c(p) enters the forward
+// differences along each axis a != c at the H cells p (with -1/d_a) and
+// p - e_a (with +1/d_a); with psi' = psi + ((b-1) psi + a dd) a change dd of
+// a difference changes H_h by -cH sgn (1/kappa + a) dd and psi by a dd
+// (profiles at the H position along a).  Cells shared with other edges or
+// tiles take atomic adds.
+__global__ void __launch_bounds__(TILE_X *TILE_Y *TILE_Z) k_jf_fix(Grid<float> g, FixArgs f) {
+    pdl_wait();
+    pdl_release();
+    const int count = *f.jf.count;
+    const int i0 = threadIdx.x % TILE_X, j0 = (threadIdx.x / TILE_X) % TILE_Y, k0 = threadIdx.x / (TILE_X * TILE_Y);
+    const int L2 = 2 * g.L;
+    for (int qt = blockIdx.x; qt < count; qt += gridDim.x) {
+        const long long t = f.jf.list[qt];
+        const int tx = (int)(t % g.nt[0]), ty = (int)((t / g.nt[0]) % g.nt[1]);
+        const int tz = (int)(t / ((long long)g.nt[0] * g.nt[1]));
+        const int p[3] = {tx * TILE_X + i0, ty * TILE_Y + j0, tz * TILE_Z + k0};
+        if (p[0] >= g.n[0] || p[1] >= g.n[1] || p[2] >= g.n[2]) continue;
+        const long long st[3] = {1, g.n[0], (long long)g.n[0] * g.n[1]};
+        const long long e = p[2] * st[2] + p[1] * st[1] + p[0];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const float jf = f.jf.Jf[c][e];
+            const int a1 = (c + 1) % 3, a2 = (c + 2) % 3;
+            if (jf == 0.f || p[a1] == 0 || p[a2] == 0) continue;  // no current, or a held edge
+            const float dE = -f.cls_pack[f.ecls[c][e]].z * jf;
+            f.E[c][e] += dE;
+#pragma unroll
+            for (int side = 0; side < 2; side++) {
+                const int ax = side ? a2 : a1;      // derivative axis
+                const int hcmp = 3 - c - ax;        // H component that takes d/d_ax E_c
+                const float sgn = ((hcmp + 1) % 3 == ax) ? 1.f : -1.f;
+                const int sidx = (hcmp - ax + 5) % 3;  // psi[ax][sidx] belongs to H_hcmp
+#pragma unroll
+                for (int lo = 0; lo < 2; lo++) {    // H cells p (lo = 0) and p - e_ax (lo = 1)
+                    if (lo && p[ax] == 0) continue;
+                    const int m = p[ax] - lo;
+                    const float dd = (lo ? g.r[ax] : -g.r[ax]) * dE;
+                    const float aa = f.aH[ax][m], ik = f.ikH[ax][m];
+                    const long long hm = e - lo * st[ax];
+                    atomicAdd(&f.H[hcmp][hm], -g.cH * sgn * (ik + aa) * dd);
+                    const int sl = slab_of(g, ax, m);
+                    if (sl >= 0) {
+                        int q3[3] = {p[0], p[1], p[2]};
+                        q3[ax] = m;
+                        long long pq;
+                        if (ax == 0) pq = ((long long)q3[2] * g.n[1] + q3[1]) * L2 + sl;
+                        else if (ax == 1) pq = ((long long)q3[2] * L2 + sl) * g.n[0] + q3[0];
+                        else pq = ((long long)sl * g.n[1] + q3[1]) * g.n[0] + q3[0];
+                        atomicAdd(&f.psiH[ax][sidx][pq], aa * dd);
+                    }
+                }
+            }
+        }
+    }
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encoder() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// Tensor map over the three components of a field ([3][nz][ny][nx] floats,
+// components `cstride` bytes apart) with a box of bw x bh cells of one plane.
+bool field_map(CUtensorMap *m, float *base, size_t cstride, const int n[3], int bw, int bh) {
+    EncodeTiledFn enc = encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)n[0], (cuuint64_t)n[1], (cuuint64_t)n[2], 3};
+    const cuuint64_t strides[3] = {(cuuint64_t)n[0] * 4, (cuuint64_t)n[0] * n[1] * 4, (cuuint64_t)cstride};
+    const cuuint32_t box[4] = {(cuuint32_t)bw, (cuuint32_t)bh, 1, 3};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Tensor map over the two components of a slab memory (components `cstride`
+// bytes apart): dims d0 x d1 x d2 floats, a box of b0 x b1 of one plane.
+bool psi_map(CUtensorMap *m, float *base, size_t cstride, int d0, int d1, int d2, int b0, int b1) {
+    EncodeTiledFn enc = encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)d0, (cuuint64_t)d1, (cuuint64_t)d2, 2};
+    const cuuint64_t strides[3] = {(cuuint64_t)d0 * 4, (cuuint64_t)d0 * d1 * 4, (cuuint64_t)cstride};
+    const cuuint32_t box[4] = {(cuuint32_t)b0, (cuuint32_t)b1, 1, 2};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool fused_grid_ok(const Grid<float> &g) {
+    if (g.n[0] % 4 != 0 || g.per[0] || g.per[1] || g.per[2]) return false;
+    if (g.cpml[0] && g.L % 4 != 0) return false;  // a four-cell group lies in an x slab as a whole or not at all
+    if ((unsigned long long)g.n[0] * g.n[1] * g.n[2] >= (1ull << 32)) return false;  // 32-bit cell offsets
+    if (g.n[0] / TX >= 65536 || (g.n[1] + TY - 1) / TY >= 65536) return false;
+    return encoder() != nullptr;
+}
+
+int fused_chunk(int nz, int inner_tiles, int sms) {
+    // about eight waves of four blocks per SM over the inner tiles, in runs
+    // of 8..MAX_CHUNK planes (each item also loads two planes beyond its run)
+    const long long slots = 4LL * (sms > 0 ? sms : 152);
+    const long long want = (8 * slots + inner_tiles - 1) / (inner_tiles > 0 ? inner_tiles : 1);
+    long long chunk = (nz + want - 1) / (want > 0 ? want : 1);
+    chunk = (chunk + 7) / 8 * 8;
+    if (chunk < 8) chunk = 8;
+    if (chunk > MAX_CHUNK) chunk = MAX_CHUNK;
+    return (int)chunk;
+}
+
+int fused_tiles(const Grid<float> &g, std::vector<int> &inner, std::vector<int> &slab) {
+    const int tx_n = (g.n[0] + TX - 1) / TX, ty_n = (g.n[1] + TY - 1) / TY;
+    inner.clear();
+    slab.clear();
+    auto touches = [&](int a, int lo, int hi) {  // cells lo..hi (inclusive) meet a slab of axis a
+        if (!g.cpml[a]) return false;
+        return lo < g.L || hi >= g.n[a] - g.L;
+    };
+    for (int ty = 0; ty < ty_n; ty++)
+        for (int tx = 0; tx < tx_n; tx++) {
+            // the tile and the halo row and column it computes E on
+            const bool s = touches(0, tx * TX, tx * TX + TX) || touches(1, ty * TY, ty * TY + TY);
+            (s ? slab : inner).push_back(tx | (ty << 16));
+        }
+    return (int)(inner.size() + slab.size());
+}
+
+bool fused_maps(FusedPlan &pl, const FusedBuf P[2], const int n[3], int L, const int cpml[3]) {
+    for (int b = 0; b < 2; b++) {
+        const size_t se = (size_t)((char *)P[b].E[1] - (char *)P[b].E[0]);
+        const size_t sh = (size_t)((char *)P[b].H[1] - (char *)P[b].H[0]);
+        if ((char *)P[b].E[2] - (char *)P[b].E[1] != (long)se || (char *)P[b].H[2] - (char *)P[b].H[1] != (long)sh)
+            return false;
+        if (se % 16 || sh % 16 || ((uintptr_t)P[b].E[0] & 15) || ((uintptr_t)P[b].H[0] & 15)) return false;
+        if (!field_map(&pl.mapE[b], P[b].E[0], se, n, EW, EH)) return false;
+        if (!field_map(&pl.mapH[b], P[b].H[0], sh, n, HW, HH)) return false;
+        // x and y slab memory (the maps of an axis without slabs stay unused)
+        pl.mapPEx[b] = pl.mapH[b];
+        pl.mapPHx[b] = pl.mapH[b];
+        pl.mapPEy[b] = pl.mapH[b];
+        pl.mapPHy[b] = pl.mapH[b];
+        if (cpml[0]) {
+            const size_t cs = (size_t)((char *)P[b].psiE[0][1] - (char *)P[b].psiE[0][0]);
+            const size_t ch = (size_t)((char *)P[b].psiH[0][1] - (char *)P[b].psiH[0][0]);
+            if (cs % 16 || ch % 16 || 2 * L > PX) return false;
+            if (!psi_map(&pl.mapPEx[b], P[b].psiE[0][0], cs, 2 * L, n[1], n[2], 2 * L, EH)) return false;
+            if (!psi_map(&pl.mapPHx[b], P[b].psiH[0][0], ch, 2 * L, n[1], n[2], 2 * L, EH)) return false;
+        }
+        if (cpml[1]) {
+            const size_t cs = (size_t)((char *)P[b].psiE[1][1] - (char *)P[b].psiE[1][0]);
+            const size_t ch = (size_t)((char *)P[b].psiH[1][1] - (char *)P[b].psiH[1][0]);
+            if (cs % 16 || ch % 16 || 2 * L > EH) return false;
+            if (!psi_map(&pl.mapPEy[b], P[b].psiE[1][0], cs, n[0], 2 * L, n[2], EW, EH)) return false;
+            if (!psi_map(&pl.mapPHy[b], P[b].psiH[1][0], ch, n[0], 2 * L, n[2], EW, EH)) return false;
+        }
+    }
+    pl.psi_maps = true;
+    static std::once_flag once;
+    static bool attr_ok = true;
+    std::call_once(once, [] {
+        attr_ok = cudaFuncSetAttribute(k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes<false>()) == cudaSuccess &&
+                  cudaFuncSetAttribute(k_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes<true>()) == cudaSuccess;
+    });
+    return attr_ok;
+}
+
+void launch_fused_pass(const FusedArgs &base, const FusedPlan &pl, int xbuf, cudaStream_t s, cudaStream_t s2) {
+    FusedArgs a = base;
+    if (pl.n_inner > 0) {
+        a.tiles = pl.tiles;
+        a.ntiles = pl.n_inner;
+        launch_pdl(k_fused<false>, dim3((unsigned)(pl.n_inner * pl.nchunks)), dim3(NT), smem_bytes<false>(), s,
+                   pl.mapE[xbuf], pl.mapH[xbuf], pl.mapPEx[xbuf], pl.mapPHx[xbuf], pl.mapPEy[xbuf], pl.mapPHy[xbuf], a);
+        launch_count() += 1;
+    }
+    if (pl.n_slab > 0) {
+        a.tiles = pl.tiles + pl.n_inner;
+        a.ntiles = pl.n_slab;
+        launch_pdl(k_fused<true>, dim3((unsigned)(pl.n_slab * pl.nchunks)), dim3(NT), smem_bytes<true>(), s2,
+                   pl.mapE[xbuf], pl.mapH[xbuf], pl.mapPEx[xbuf], pl.mapPHx[xbuf], pl.mapPEy[xbuf], pl.mapPHy[xbuf], a);
+        launch_count() += 1;
+    }
+}
+
+void launch_jf_clear(const Grid<float> &g, const JfSet &j, int max_tiles, cudaStream_t s) {
+    int nblk = max_tiles < 4 * 152 ? max_tiles : 4 * 152;
+    if (nblk < 1) nblk = 1;
+    launch_pdl(k_jf_clear, dim3(nblk), dim3(TILE_X * TILE_Y * TILE_Z), 0, s, g, j);
+    launch_count() += 1;
+}
+
+void launch_jf_fix(const Grid<float> &g, const FixArgs &f, int max_tiles, cudaStream_t s) {
+    int nblk = max_tiles < 4 * 152 ? max_tiles : 4 * 152;
+    if (nblk < 1) nblk = 1;
+    launch_pdl(k_jf_fix, dim3(nblk), dim3(TILE_X * TILE_Y * TILE_Z), 0, s, g, f);
+    launch_count() += 1;
+}
+
+}  // namespace pic

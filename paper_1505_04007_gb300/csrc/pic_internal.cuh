@@ -2,8 +2,11 @@
 // the translation units of libpic.  Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <vector>
 
 namespace pic {
 
@@ -23,6 +26,7 @@ enum : int {
     DEVERR_JUMP = 1,             // a particle moved more than one cell in a step
     DEVERR_NONFINITE = 2,        // non-finite momentum in the pusher
     DEVERR_FIELD_NONFINITE = 4,  // a NaN or Inf in E or H (scan at pic_sync / pic_get_stats)
+    DEVERR_WAIT = 8,             // a pipeline wait of the fused field pass ran out of time
 };
 
 // Grid geometry and scalar coefficients, passed by value to every kernel.
@@ -162,6 +166,69 @@ void launch_v4_E(const Grid<float> &g, const Fields<float> &f, const FieldPlan &
 // plane_cls[k]: the class all edges of plane k share if it is non-metal, else
 // 255.  Returns false when the grid does not suit these kernels.
 bool make_field_plan(const Grid<float> &g, const uint8_t *plane_cls, const float *cls_cE, FieldPlan &p);
+
+// ------------------------------------------------------- fused field pass
+// (fields_fused.cu) FP32 grids with nx % 4 == 0 and no periodic axis: one
+// pass computes E^{n+1} (without J_f) and H^{n+3/2}, reading the state at
+// step n from one copy of the arrays and writing step n+1 to the other.
+constexpr int FUSED_TX = 32, FUSED_TY = 15;  // tile of one work item (x, y)
+constexpr int FUSED_MAX_L = 8;                 // thickest x or y absorbing slab the pass stages
+
+// One copy of the state the pass reads or writes.
+struct FusedBuf {
+    float *E[3], *H[3], *Jp[3];
+    float *psiE[3][2], *psiH[3][2];
+};
+// One step's free current and its tile bookkeeping (see mark_jf_tile).
+struct JfSet {
+    float *Jf[3];
+    int *flag, *list, *count;
+};
+struct FusedArgs {
+    Grid<float> g;
+    float *Eo[3], *Ho[3];          // state at n+1 (written)
+    const float *Jpi[3];           // Drude current at n-1/2 (read)
+    float *Jpo[3];                 // ... at n+1/2 (written on metal edges)
+    const float *psiEi[3][2];
+    float *psiEo[3][2];
+    const float *psiHi[3][2];
+    float *psiHo[3][2];
+    const float *bE[3], *aE[3], *ikE[3], *bH[3], *aH[3], *ikH[3];
+    const uint8_t *ecls[3];
+    const float4 *cls_pack;
+    const float *plane_cE;         // per plane: cE of its one non-metal class, or -1 (per-edge classes)
+    const int *tiles;              // packed tile indices (tx | ty << 16)
+    int ntiles, chunk;             // tiles of this launch; planes per work item
+    int *err;
+};
+struct FixArgs {
+    float *E[3], *H[3], *psiH[3][2];  // state at n+1 (corrected in place)
+    JfSet jf;                         // this step's free current
+    const uint8_t *ecls[3];
+    const float4 *cls_pack;
+    const float *aH[3], *ikH[3];
+};
+struct FusedPlan {
+    CUtensorMap mapE[2], mapH[2];  // E and H of state copy 0 and 1
+    // CPML memory of the x and y slabs (both components of a field per map)
+    CUtensorMap mapPEx[2], mapPHx[2], mapPEy[2], mapPHy[2];
+    bool psi_maps = false;
+    const int *tiles = nullptr;    // device: inner tiles, then tiles meeting an x or y absorbing slab
+    int n_inner = 0, n_slab = 0;
+    int chunk = 32, nchunks = 1;
+};
+bool fused_grid_ok(const Grid<float> &g);
+// Planes per work item for a grid of nz planes and inner_tiles tiles on a GPU with sms SMs.
+int fused_chunk(int nz, int inner_tiles, int sms);
+// Tile lists of the pass: tiles whose cells and halo row/column stay out of
+// the x and y slabs, and the others.  Returns the tile count.
+int fused_tiles(const Grid<float> &g, std::vector<int> &inner, std::vector<int> &slab);
+// Tensor maps of both state copies (E, H components equally spaced).
+bool fused_maps(FusedPlan &pl, const FusedBuf P[2], const int n[3], int L, const int cpml[3]);
+// The pass reading copy xbuf's maps: inner tiles on s, slab tiles on s2.
+void launch_fused_pass(const FusedArgs &a, const FusedPlan &pl, int xbuf, cudaStream_t s, cudaStream_t s2);
+void launch_jf_clear(const Grid<float> &g, const JfSet &j, int max_tiles, cudaStream_t s);
+void launch_jf_fix(const Grid<float> &g, const FixArgs &f, int max_tiles, cudaStream_t s);
 
 // k-omega map of the probe line (probe.cu): out[q][f] = |sum_p F_p e^{-i k_q s_p}|^2.
 void launch_probe_kw(const double *F, const double *xyz_cells, double cell, int axis, int np, int nf, int comp,

@@ -21,6 +21,7 @@ from . import build as _build
 
 PIC_OK = 0
 PIC_FP32, PIC_FP64 = 0, 1
+PIC_FLAG_SPLIT_FIELDS = 1  # keep separate H and E updates where the fused pass would run
 PIC_EX, PIC_EY, PIC_EZ, PIC_HX, PIC_HY, PIC_HZ, PIC_JPX, PIC_JPY, PIC_JPZ, PIC_JFX, PIC_JFY, PIC_JFZ = range(12)
 
 ERRORS = {-1: "PIC_ERR_ARG", -2: "PIC_ERR_CFL", -3: "PIC_ERR_OOM", -4: "PIC_ERR_CUDA", -5: "PIC_ERR_NONFINITE",
@@ -54,7 +55,8 @@ class pic_config(C.Structure):
 
 class pic_stats(C.Structure):
     _fields_ = [("step", C.c_int64), ("n_particles", C.c_int64), ("n_frozen", C.c_int64),
-                ("device_error", C.c_int32), ("n_edge_classes", C.c_int32), ("kernel_launches", C.c_int64)]
+                ("device_error", C.c_int32), ("n_edge_classes", C.c_int32), ("kernel_launches", C.c_int64),
+                ("field_path", C.c_int32), ("reserved", C.c_int32)]
 
 
 class pic_tuning(C.Structure):
@@ -238,10 +240,15 @@ def pic_load(h, path: str) -> None:
     _check(load().pic_load(h, os.fsencode(path)), "pic_load")
 
 
-def pic_profile_steps(h, nsteps: int) -> dict:
+def pic_profile_steps(h, nsteps: int, fused: bool = False) -> dict:
+    """Per-step phase durations (us).  fused: the handle is on the fused field
+    path (pic_stats.field_path 1), whose phases are named after what they run."""
     out = np.zeros(6)
     _check(load().pic_profile_steps(h, int(nsteps), _dp(out)), "pic_profile_steps")
-    keys = ("update_H", "push_deposit", "update_E", "step_tail", "dft_flush", "step")
+    if fused:
+        keys = ("field_pass", "push_deposit", "jf_correction", "step_tail", "dft_flush", "step")
+    else:
+        keys = ("update_H", "push_deposit", "update_E", "step_tail", "dft_flush", "step")
     return dict(zip(keys, out.tolist()))
 
 
@@ -313,7 +320,7 @@ def pic_batch_destroy(b) -> None:
 
 
 def make_config(w, precision=PIC_FP32, max_particles=None, max_probes=None, max_freqs=None,
-                eps0=None, mu0=None) -> tuple[pic_config, tuple]:
+                eps0=None, mu0=None, flags=0) -> tuple[pic_config, tuple]:
     """pic_config for a Workload; returns (cfg, keepalive) where keepalive
     holds the host arrays the config points to."""
     from . import workloads as W
@@ -339,7 +346,7 @@ def make_config(w, precision=PIC_FP32, max_particles=None, max_probes=None, max_
     nfreq = 0 if w.freqs is None else len(w.freqs)
     cfg.max_probes = nprobe if max_probes is None else max_probes
     cfg.max_freqs = nfreq if max_freqs is None else max_freqs
-    cfg.flags = 0
+    cfg.flags = int(flags)
     return cfg, (mat, tab)
 
 
@@ -411,7 +418,7 @@ class Simulation:
         return pic_get_stats(self.h)
 
     def profile(self, nsteps):
-        return pic_profile_steps(self.h, nsteps)
+        return pic_profile_steps(self.h, nsteps, fused=self.stats().field_path == 1)
 
     @property
     def tuning(self):

@@ -33,7 +33,7 @@ def test_struct_layout_matches_header():
     # offsets of the trailing fields pin the ctypes mirror to the C layout
     assert C.sizeof(P.pic_material) == 24
     assert P.pic_config.flags.offset == C.sizeof(P.pic_config) - 8
-    assert C.sizeof(P.pic_stats) == 40
+    assert C.sizeof(P.pic_stats) == 48 and P.pic_stats.field_path.offset == 40
     assert C.sizeof(P.pic_tuning) == 12
     assert P.pic_tune_report.us_per_step.offset == 256 and C.sizeof(P.pic_tune_report) == 512
 
@@ -48,12 +48,17 @@ def _cfg(**kw):
 
 def test_workspace_size_is_host_only_and_scales():
     cfg, keep, w = _cfg()
+    n32f = P.pic_workspace_size(cfg)  # c1 takes the fused field pass: two copies of the state
+    cfg.flags = P.PIC_FLAG_SPLIT_FIELDS
     n32 = P.pic_workspace_size(cfg)
+    cfg.flags = 0
     cfg.precision = P.PIC_FP64
     n64 = P.pic_workspace_size(cfg)
     # 12 state arrays per cell in the state precision plus 4 bytes of tables
     assert n32 >= w.ncells * (12 * 4 + 4)
     assert n64 > n32
+    # the fused path's second copy: E, H, J_p, J_f again
+    assert n32f >= n32 + w.ncells * 12 * 4
 
 
 @pytest.mark.parametrize("mutate,code", [
@@ -61,7 +66,7 @@ def test_workspace_size_is_host_only_and_scales():
     (lambda c: c.bc.__setitem__(0, W.BC_PERIODIC), -1),                   # unpaired periodic
     (lambda c: setattr(c, "cpml_cells", 40), -1),                         # slabs do not fit
     (lambda c: setattr(c, "precision", 7), -1),
-    (lambda c: setattr(c, "flags", 1), -1),
+    (lambda c: setattr(c, "flags", 2), -1),  # an unknown flag bit
     (lambda c: setattr(c, "n_materials", 0), -1),
 ])
 def test_create_rejects_invalid_config_on_host(mutate, code):
