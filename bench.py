@@ -46,8 +46,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the library's default launch settings instead of choosing them with pic_tune")
-    ap.add_argument("--tuning", default=None, metavar="DEP_SMEM_BYTES,SORT_EVERY[,FIELD_BLOCK]",
-                    help="use these launch settings instead of running pic_tune (e.g. 8192,32,256)")
+    ap.add_argument("--tuning", default=None, metavar="DEP_SMEM_BYTES,SORT_EVERY[,FIELD_BLOCK[,FIELD_PATH]]",
+                    help="use these launch settings instead of running pic_tune (e.g. 8192,32,256,1)")
     ap.add_argument("--ref-seconds", type=float, default=20.0,
                     help="target CPU seconds of the oracle sample")
     return ap.parse_args()
@@ -311,7 +311,8 @@ def bench_sweep(args):
                        "parallelism": "one batch graph (one branch per instance)",
                        "l2": "state larger than the 129 MB L2 (no flush)",
                        "launch_settings": ({"dep_smem_bytes": tuned[0], "sort_every": tuned[1],
-                                            "field_block": tuned[2], "lanes": tuned[3] or "all",
+                                            "field_block": tuned[2], "field_path": tuned[3],
+                                            "lanes": tuned[4] or "all",
                                             "chosen_by": f"pic_batch_tune, 1 round on steps 0..{tune_steps}"}
                                            if tuned else "library defaults (dep_smem_bytes 4096, sort_every 16, field_block 256)")},
             "sequential": {"value": seq, "unit": "Gcell-upd/s", "ms_per_step": ms_seq / steps,
@@ -497,11 +498,13 @@ def main():
     if args.tuning:
         vals = [int(v) for v in args.tuning.split(",")]
         sim.set_tuning(*vals)
-        dep, every, blk = sim.tuning
-        tuned = {"dep_smem_bytes": dep, "sort_every": every, "field_block": blk, "chosen_by": "--tuning"}
+        dep, every, blk, fpath = sim.tuning
+        tuned = {"dep_smem_bytes": dep, "sort_every": every, "field_block": blk, "field_path": fpath,
+                 "chosen_by": "--tuning"}
     elif not args.no_tune:  # launch settings chosen on this workload's own steps, before the warm-up
         rep = sim.tune(rounds=2)
         tuned = {"dep_smem_bytes": rep["best"][0], "sort_every": rep["best"][1], "field_block": rep["best"][2],
+                 "field_path": rep["best"][3],
                  "chosen_by": f"pic_tune, 2 rounds on steps 0..{rep['steps']} (before the warm-up)"}
     # Warm-up: at least the W steps asked for, then on to a 64-step block
     # boundary, then the timed pattern once (any captured partial-block graph
@@ -575,7 +578,7 @@ def main():
         t0 = time.perf_counter()
         s2 = pic.Simulation(w, prec, stream=stream)
         if tuned is not None:
-            s2.set_tuning(tuned["dep_smem_bytes"], tuned["sort_every"], tuned["field_block"])
+            s2.set_tuning(tuned["dep_smem_bytes"], tuned["sort_every"], tuned["field_block"], tuned["field_path"])
         s2.step(args.steps)
         spec = s2.probe_read()
         t1 = time.perf_counter()

@@ -285,12 +285,18 @@ int pic_profile_steps(pic_handle *h, int64_t nsteps, double *out_us);
  *                   blocks taken in turn over the boxes of the grid): 128, 256
  *                   or 512.  Default 256.  No effect on the FP64 state or on
  *                   grids the four-cell kernels do not take.
+ *   field_path      1: the fused field pass (see PIC_FLAG_SPLIT_FIELDS) on a
+ *                   grid that takes it; 0: the H and E updates as two
+ *                   passes.  Default 1.  A handle whose grid does not take
+ *                   the fused pass (or created with PIC_FLAG_SPLIT_FIELDS)
+ *                   accepts 1 and reports 0.
  * The settings belong to the handle, not to the simulation state: pic_save
  * does not write them and pic_load leaves the handle's settings as they are. */
 typedef struct {
     int32_t dep_smem_bytes;
     int32_t sort_every;
     int32_t field_block;
+    int32_t field_path;
 } pic_tuning;
 
 /* The handle's current launch settings into *out.  Errors: PIC_ERR_ARG (NULL). */
@@ -301,7 +307,8 @@ int pic_set_tuning(pic_handle *h, const pic_tuning *t);
 
 /* Candidates pic_tune times: dep_smem_bytes over {0, 2048, 4096, 8192, 16384}
  * with the rest held, then sort_every over {8, 16, 32, 64} with the best box,
- * then field_block over {128, 256, 512} with the best box and interval. */
+ * then field_block over {128, 256, 512} with the best box and interval, then
+ * (on a grid that takes the fused pass) field_path {1, 0}. */
 #define PIC_TUNE_MAX_CANDIDATES 20
 typedef struct {
     pic_tuning best;
@@ -318,7 +325,8 @@ typedef struct {
  * block (CUDA events on the simulation's stream); each candidate keeps its
  * fastest block, and the fastest candidate is kept.  The blocks are real
  * steps of the simulation: it first steps to a block boundary (0 to 63
- * steps), then rounds x 12 x 64 steps; report->steps counts both.  `report`
+ * steps), then rounds x 12 x 64 steps (14 on a grid that takes the fused
+ * pass); report->steps counts both.  `report`
  * may be NULL.  Synchronises.  Errors: PIC_ERR_ARG, PIC_ERR_CUDA. */
 int pic_tune(pic_handle *h, int32_t rounds, pic_tune_report *report);
 
@@ -360,11 +368,12 @@ int pic_batch_set_lanes(pic_batch *b, int32_t lanes);
 
 /* pic_tune for the batch as a whole: each candidate is applied to every
  * instance and timed on whole batch blocks (the box candidates at the first
- * instance's sort interval), then the lanes {1, 2, 4, 8, all} (those below
- * the instance count) with the best settings; the fastest settings are
+ * instance's sort interval, with the fused pass wherever an instance's grid
+ * takes it), then field_path {1, 0}, then the lanes {1, 2, 4, 8, all} (those
+ * below the instance count) with the best settings; the fastest settings are
  * applied to every instance and the fastest lanes to the batch.  Instances
  * not at a block boundary first step to it on their own (up to 63 steps
- * each); then every instance advances by report->steps = rounds x (12 +
+ * each); then every instance advances by report->steps = rounds x (14 +
  * lane candidates) x 64 steps.  `report` may be NULL.  Synchronises.  Errors:
  * PIC_ERR_ARG, PIC_ERR_CUDA. */
 int pic_batch_tune(pic_batch *b, int32_t rounds, pic_tune_report *report);

@@ -134,6 +134,7 @@ struct SimBase {
     virtual int steps_to_boundary() const = 0;        // steps left in the current block (0 at a boundary)
     virtual long long cells() const = 0;
     virtual int set_tuning(const pic_tuning &t) = 0;
+    virtual bool fused_capable() const = 0;  // the grid takes the fused field pass
     int device = -1;  // CUDA device the handle was created on
 };
 
@@ -199,6 +200,7 @@ struct Sim : SimBase {
     // f (E^n, H^{n-1/2}, ...), as on the split path.
     bool fused_possible = false;  // the grid and flags take the fused pass (arena holds the second copy)
     bool fused = false;           // ... and its plan was built
+    bool use_fused = true;        // launch setting: take the fused pass when `fused`
     bool fused_ready = false;
     FusedBuf P[2];
     JfSet jfs[2];
@@ -729,7 +731,7 @@ struct Sim : SimBase {
     // free-current sets start empty.
     int enter_fused() {
         if constexpr (std::is_same<T, float>::value) {
-            if (!fused || fused_ready) return PIC_OK;
+            if (!fused || !use_fused || fused_ready) return PIC_OK;
             const int par = (int)(step_host & 1);
             const size_t nb = (size_t)N * sizeof(float);
             for (int j = 0; j < 2; j++) {
@@ -898,6 +900,7 @@ struct Sim : SimBase {
     int step_direct(long long n) override { return step(n); }
     int steps_to_boundary() const override { return buffered ? DFT_BLOCK - buffered : 0; }
     long long cells() const override { return N; }
+    bool fused_capable() const override { return fused; }
     cudaStream_t main_stream() const override { return stream; }
 
     // DFT_BLOCK steps (a sort every sort_every, the first one included) and the DFT flush
@@ -1334,15 +1337,25 @@ struct Sim : SimBase {
     }
 
     // ---------------------------------------------------------- tuning --
-    pic_tuning tuning() const { return pic_tuning{pp.dep_smem, sort_every, fplan.block}; }
+    pic_tuning tuning() const { return pic_tuning{pp.dep_smem, sort_every, fplan.block, (fused && use_fused) ? 1 : 0}; }
     int set_tuning(const pic_tuning &t) override {
         const int dep = t.dep_smem_bytes, every = t.sort_every, blk = t.field_block;
+        if (t.field_path != 0 && t.field_path != 1) return fail(PIC_ERR_ARG, "field_path %d is not 0 or 1", t.field_path);
         if (dep < 0 || dep > DEP_SMEM_MAX || dep % 16 != 0)
             return fail(PIC_ERR_ARG, "dep_smem_bytes %d outside 0..%d or not a multiple of 16", dep, DEP_SMEM_MAX);
         if (every < 1 || every > DFT_BLOCK || DFT_BLOCK % every != 0)
             return fail(PIC_ERR_ARG, "sort_every %d does not divide %d", every, DFT_BLOCK);
         if (blk != 128 && blk != 256 && blk != 512)
             return fail(PIC_ERR_ARG, "field_block %d is not 128, 256 or 512", blk);
+        const bool uf = t.field_path == 1;
+        if (uf != use_fused) {  // switch the field path (the state moves back to f when leaving the fused one)
+            if (!uf) {
+                int rc = leave_fused();
+                if (rc) return rc;
+            }
+            use_fused = uf;
+            drop_graph();
+        }
         if (dep != pp.dep_smem || every != sort_every || blk != fplan.block) {
             pp.dep_smem = dep;
             sort_every = every;
@@ -1406,18 +1419,23 @@ struct Sim : SimBase {
             return PIC_OK;
         };
         const pic_tuning t0 = tuning();
-        for (int d : deps) { cand[nc] = pic_tuning{d, t0.sort_every, t0.field_block}; best_us[nc++] = 1e300; }
+        for (int d : deps) { cand[nc] = pic_tuning{d, t0.sort_every, t0.field_block, t0.field_path}; best_us[nc++] = 1e300; }
         int win = 0;
         rc = pass(0, 5, &win);
         if (!rc) {
             const pic_tuning t = cand[win];
-            for (int e : everies) { cand[nc] = pic_tuning{t.dep_smem_bytes, e, t.field_block}; best_us[nc++] = 1e300; }
+            for (int e : everies) { cand[nc] = pic_tuning{t.dep_smem_bytes, e, t.field_block, t.field_path}; best_us[nc++] = 1e300; }
             rc = pass(5, 4, &win);
         }
         if (!rc) {
             const pic_tuning t = cand[win];
-            for (int b : blocks) { cand[nc] = pic_tuning{t.dep_smem_bytes, t.sort_every, b}; best_us[nc++] = 1e300; }
+            for (int b : blocks) { cand[nc] = pic_tuning{t.dep_smem_bytes, t.sort_every, b, t.field_path}; best_us[nc++] = 1e300; }
             rc = pass(9, 3, &win);
+        }
+        if (!rc && fused) {  // the fused pass against the split updates
+            const pic_tuning t = cand[win];
+            for (int fp : {1, 0}) { cand[nc] = pic_tuning{t.dep_smem_bytes, t.sort_every, t.field_block, fp}; best_us[nc++] = 1e300; }
+            rc = pass(12, 2, &win);
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -1756,7 +1774,7 @@ static int stats_t(Sim<T> *s, pic_stats *out) {
     out->device_error = err;
     out->n_edge_classes = s->n_classes;
     out->kernel_launches = s->kernels;
-    out->field_path = s->fused ? 1 : 0;
+    out->field_path = (s->fused && s->use_fused) ? 1 : 0;
     return PIC_OK;
 }
 
@@ -2144,7 +2162,7 @@ struct pic_batch {
         const int lanes0 = lanes;
         for (int d : deps) {
             cand_lanes[nc] = lanes0;
-            cand[nc] = pic_tuning{d, start.sort_every, start.field_block};
+            cand[nc] = pic_tuning{d, start.sort_every, start.field_block, start.field_path};
             best_us[nc++] = 1e300;
         }
         rc = pass(0, 5);
@@ -2152,7 +2170,7 @@ struct pic_batch {
             const pic_tuning t = cand[win];
             for (int e : everies) {
                 cand_lanes[nc] = lanes0;
-                cand[nc] = pic_tuning{t.dep_smem_bytes, e, t.field_block};
+                cand[nc] = pic_tuning{t.dep_smem_bytes, e, t.field_block, t.field_path};
                 best_us[nc++] = 1e300;
             }
             rc = pass(5, 4);
@@ -2161,10 +2179,19 @@ struct pic_batch {
             const pic_tuning t = cand[win];
             for (int b : blocks) {
                 cand_lanes[nc] = lanes0;
-                cand[nc] = pic_tuning{t.dep_smem_bytes, t.sort_every, b};
+                cand[nc] = pic_tuning{t.dep_smem_bytes, t.sort_every, b, t.field_path};
                 best_us[nc++] = 1e300;
             }
             rc = pass(9, 3);
+        }
+        if (!rc && any_fused()) {  // the fused pass (where an instance's grid takes it) against the split updates
+            const pic_tuning t = cand[win];
+            for (int fp : {1, 0}) {
+                cand_lanes[nc] = lanes0;
+                cand[nc] = pic_tuning{t.dep_smem_bytes, t.sort_every, t.field_block, fp};
+                best_us[nc++] = 1e300;
+            }
+            rc = pass(12, 2);
         }
         // then how many instances run side by side: 1, 2, 4, 8 chains or all
         int nlanes = 0;
@@ -2215,7 +2242,13 @@ struct pic_batch {
     pic_tuning rep_start() const {
         pic_tuning t{};
         pic_get_tuning(h[0], &t);
+        t.field_path = any_fused() ? 1 : 0;  // the fused pass wherever an instance's grid takes it
         return t;
+    }
+    bool any_fused() const {
+        for (auto *x : h)
+            if (x->sim->fused_capable()) return true;
+        return false;
     }
 
     ~pic_batch() {

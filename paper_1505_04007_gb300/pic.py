@@ -60,7 +60,8 @@ class pic_stats(C.Structure):
 
 
 class pic_tuning(C.Structure):
-    _fields_ = [("dep_smem_bytes", C.c_int32), ("sort_every", C.c_int32), ("field_block", C.c_int32)]
+    _fields_ = [("dep_smem_bytes", C.c_int32), ("sort_every", C.c_int32), ("field_block", C.c_int32),
+                ("field_path", C.c_int32)]
 
 
 PIC_TUNE_MAX_CANDIDATES = 20
@@ -253,18 +254,19 @@ def pic_profile_steps(h, nsteps: int, fused: bool = False) -> dict:
 
 
 def pic_get_tuning(h) -> tuple:
+    """(dep_smem_bytes, sort_every, field_block, field_path)."""
     t = pic_tuning()
     _check(load().pic_get_tuning(h, C.byref(t)), "pic_get_tuning")
-    return t.dep_smem_bytes, t.sort_every, t.field_block
+    return t.dep_smem_bytes, t.sort_every, t.field_block, t.field_path
 
 
-def pic_set_tuning(h, dep_smem_bytes: int, sort_every: int, field_block: int = 256) -> None:
-    t = pic_tuning(int(dep_smem_bytes), int(sort_every), int(field_block))
+def pic_set_tuning(h, dep_smem_bytes: int, sort_every: int, field_block: int = 256, field_path: int = 1) -> None:
+    t = pic_tuning(int(dep_smem_bytes), int(sort_every), int(field_block), int(field_path))
     _check(load().pic_set_tuning(h, C.byref(t)), "pic_set_tuning")
 
 
 def _report(r: pic_tune_report) -> dict:
-    tup = lambda t: (t.dep_smem_bytes, t.sort_every, t.field_block)  # noqa: E731
+    tup = lambda t: (t.dep_smem_bytes, t.sort_every, t.field_block, t.field_path)  # noqa: E731
     out = {"best": tup(r.best), "steps": r.steps,
            "candidates": [(tup(r.cand[i]), r.us_per_step[i]) for i in range(r.n)]}
     if r.best_lanes >= 0:
@@ -424,8 +426,8 @@ class Simulation:
     def tuning(self):
         return pic_get_tuning(self.h)
 
-    def set_tuning(self, dep_smem_bytes, sort_every, field_block=256):
-        pic_set_tuning(self.h, dep_smem_bytes, sort_every, field_block)
+    def set_tuning(self, dep_smem_bytes, sort_every, field_block=256, field_path=1):
+        pic_set_tuning(self.h, dep_smem_bytes, sort_every, field_block, field_path)
 
     def tune(self, rounds=1):
         """Time the deposit box, sort interval and field block candidates on

@@ -34,8 +34,9 @@ def test_struct_layout_matches_header():
     assert C.sizeof(P.pic_material) == 24
     assert P.pic_config.flags.offset == C.sizeof(P.pic_config) - 8
     assert C.sizeof(P.pic_stats) == 48 and P.pic_stats.field_path.offset == 40
-    assert C.sizeof(P.pic_tuning) == 12
-    assert P.pic_tune_report.us_per_step.offset == 256 and C.sizeof(P.pic_tune_report) == 512
+    assert C.sizeof(P.pic_tuning) == 16 and P.pic_tuning.field_path.offset == 12
+    # best (16) + n (4) + 20 candidates (320), then 8-byte aligned doubles
+    assert P.pic_tune_report.us_per_step.offset == 344 and C.sizeof(P.pic_tune_report) == 600
 
 
 def _cfg(**kw):
@@ -124,7 +125,7 @@ def test_tuning_and_batch_entry_points_reject_null_on_host():
     """The launch-setting and batch entry points answer PIC_ERR_ARG for a NULL
     handle or batch without touching the device."""
     L = P.load()
-    t = P.pic_tuning(4096, 16, 256)
+    t = P.pic_tuning(4096, 16, 256, 1)
     r = P.pic_tune_report()
     assert L.pic_get_tuning(None, C.byref(t)) == ERR_ARG
     assert L.pic_set_tuning(None, C.byref(t)) == ERR_ARG

@@ -58,15 +58,18 @@ def oracle200():
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
-@pytest.mark.parametrize("dep,every,block", [(0, 8, 128), (16384, 1, 512), (2048, 32, 256), (8192, 64, 512),
-                                             (8192, 32, 128), (8192, 64, 128)])  # the last two: tuned bench settings
-def test_tuning_changes_keep_parity(P, oracle200, prec, tol, dep, every, block):
+@pytest.mark.parametrize("dep,every,block,path", [(0, 8, 128, 0), (16384, 1, 512, 1), (2048, 32, 256, 0),
+                                                  (8192, 64, 512, 1), (8192, 32, 128, 1), (8192, 64, 128, 1),
+                                                  (8192, 64, 512, 0)])  # tuned bench settings among them
+def test_tuning_changes_keep_parity(P, oracle200, prec, tol, dep, every, block, path):
     w, o = oracle200
     s = P.Simulation(w, P.PIC_FP64 if prec == "fp64" else P.PIC_FP32)
-    assert s.tuning == (4096, 16, 256)
+    fused = prec == "fp32"  # the dense slice takes the fused pass in FP32
+    assert s.tuning == (4096, 16, 256, 1 if fused else 0)
     s.step(64)  # one captured block under the default settings
-    s.set_tuning(dep, every, block)
-    assert s.tuning == (dep, every, block)
+    s.set_tuning(dep, every, block, path)  # the field path switched in the middle of the run too
+    assert s.tuning == (dep, every, block, path if fused else 0)
+    assert s.stats().field_path == (path if fused else 0)
     s.step(136)
     s.sync()
     assert rel(s, o) <= tol
@@ -93,6 +96,7 @@ def test_tune_off_a_block_boundary_keeps_parity(P):
     assert [c[1] for c in cands[5:9]] == [8, 16, 32, 64]
     assert [c[2] for c in cands[9:]] == [128, 256, 512]
     assert all(us > 0 for _, us in rep["candidates"])
+    assert all(c[3] == 0 for c in cands)  # FP64: no fused pass to choose
     box_pass, sort_pass, block_pass = rep["candidates"][:5], rep["candidates"][5:9], rep["candidates"][9:]
     assert rep["best"][0] == min(box_pass, key=lambda cu: cu[1])[0][0]
     assert rep["best"][1] == min(sort_pass, key=lambda cu: cu[1])[0][1]
@@ -104,6 +108,21 @@ def test_tune_off_a_block_boundary_keeps_parity(P):
     assert rel(s, o) <= 1e-10
     Fo, Fg = o.probe_read(), s.probe_read()
     assert np.linalg.norm(Fg - Fo) <= 1e-10 * np.linalg.norm(Fo)
+    s.close()
+
+
+def test_tune_chooses_the_field_path_fp32(P):
+    s = P.Simulation(dense(0), P.PIC_FP32)
+    rep = s.tune(rounds=1)
+    cands = [c for c, _ in rep["candidates"]]
+    assert len(cands) == 14 and rep["steps"] == 14 * 64
+    assert [c[3] for c in cands[12:]] == [1, 0] and cands[12][:3] == cands[13][:3]
+    assert rep["best"] == min(rep["candidates"][12:], key=lambda cu: cu[1])[0]
+    assert s.tuning == rep["best"] and s.stats().field_path == rep["best"][3]
+    s.step(50)
+    o = O.from_workload(dense(0))
+    o.step(14 * 64 + 50)
+    assert rel(s, o) <= 2e-5
     s.close()
 
 
@@ -135,12 +154,14 @@ def test_batch_tune_keeps_parity(P):
         x.close()
 
 
-@pytest.mark.parametrize("dep,every,block", [(1000, 16, 256), (32768, 16, 256), (-16, 16, 256), (4096, 3, 256),
-                                             (4096, 128, 256), (4096, 0, 256), (4096, 16, 100), (4096, 16, 1024)])
-def test_invalid_tuning_rejected(P, dep, every, block):
+@pytest.mark.parametrize("dep,every,block,path", [(1000, 16, 256, 1), (32768, 16, 256, 1), (-16, 16, 256, 1),
+                                                  (4096, 3, 256, 1), (4096, 128, 256, 1), (4096, 0, 256, 1),
+                                                  (4096, 16, 100, 1), (4096, 16, 1024, 1), (4096, 16, 256, 2),
+                                                  (4096, 16, 256, -1)])
+def test_invalid_tuning_rejected(P, dep, every, block, path):
     s = P.Simulation(dense(0), P.PIC_FP32)
-    s.set_tuning(8192, 32, 512)
+    s.set_tuning(8192, 32, 512, 0)
     with pytest.raises(P.PicError):
-        s.set_tuning(dep, every, block)
-    assert s.tuning == (8192, 32, 512)
+        s.set_tuning(dep, every, block, path)
+    assert s.tuning == (8192, 32, 512, 0)
     s.close()
