@@ -793,6 +793,7 @@ struct Sim : SimBase {
                 CUDA_TRY(cudaMemsetAsync(jfs[j].count, 0, sizeof(int), stream));
             }
             fused_ready = false;
+            bold_stale = true;  // the fused push gathers H^{n-1/2} itself; the split one reads bold
             drop_graph();
         }
         return PIC_OK;
@@ -820,9 +821,9 @@ struct Sim : SimBase {
             const Fields<T> fx = view(xb, par);
             if (pe) cudaEventRecord(pe[2], stream);
             launch_jf_clear(g, jfs[par ^ 1], (int)n_tiles, stream);
-            if (p.n > 0) {
-                launch_gather_E<T>(g, fx, p, stream);
-                launch_push_deposit<T>(g, fx, p, pp, stream);
+            if (p.n > 0) {  // E^n, H^{n+1/2} from copy par, H^{n-1/2} from copy par ^ 1 (the pass follows)
+                const HoldPtrs<T> hold{{P[yb].H[0], P[yb].H[1], P[yb].H[2]}};
+                launch_push_deposit<T>(g, fx, p, pp, stream, &hold);
             }
             launch_sources<T>(g, fx, sources.data(), (int)sources.size(), cfg.dt, stream);
             if (pe) cudaEventRecord(pe[3], stream);

@@ -137,8 +137,13 @@ __device__ __forceinline__ void esirkepov_sites(const T (&P)[3][3], const T (&dS
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(PUSH_BLOCK) k_push_deposit(Grid<T> g, Fields<T> f, Particles<T> p, PushParams<T> pp) {
+// OLDH: the fused field path keeps H^{n-1/2} in the other copy of the
+// state until after the push, so E^n, H^{n+1/2} and H^{n-1/2} are gathered
+// here at x^n in one round (hold: that copy's H), and neither the E gather
+// beforehand nor the H^{n+1/2}(x^{n+1}) gather at the end is needed.
+template <typename T, bool OLDH>
+__global__ void __launch_bounds__(PUSH_BLOCK)
+    k_push_deposit(Grid<T> g, Fields<T> f, Particles<T> p, PushParams<T> pp, HoldPtrs<T> hold) {
     extern __shared__ __align__(16) unsigned char dep_smem[];
     T *acc = reinterpret_cast<T *>(dep_smem);
     __shared__ int bb_lo[3], bb_hi[3];
@@ -154,15 +159,26 @@ __global__ void __launch_bounds__(PUSH_BLOCK) k_push_deposit(Grid<T> g, Fields<T
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             c0[a] = p.cell[a][q]; o0[a] = p.off[a][q]; u[a] = p.u[a][q]; ul[a] = p.ulo[a][q];
-            E[a] = p.eg[a][q];
+            if (!OLDH) E[a] = p.eg[a][q];
         }
         {
             Stencil<T> st0;
             make_stencil(g, c0, o0, st0);
-            T hnew[3];
+            T hnew[3], hold3[3];
             interp_H(f, g, st0, hnew);
+            if (OLDH) {
+                E[0] = interp<1>(f.E[0], g, st0);
+                E[1] = interp<2>(f.E[1], g, st0);
+                E[2] = interp<4>(f.E[2], g, st0);
+                hold3[0] = interp<6>(hold.H[0], g, st0);
+                hold3[1] = interp<5>(hold.H[1], g, st0);
+                hold3[2] = interp<3>(hold.H[2], g, st0);
+            } else {
 #pragma unroll
-            for (int a = 0; a < 3; a++) B[a] = pp.mu0 * T(0.5) * (p.bold[a][q] + hnew[a]);
+                for (int a = 0; a < 3; a++) hold3[a] = p.bold[a][q];
+            }
+#pragma unroll
+            for (int a = 0; a < 3; a++) B[a] = pp.mu0 * T(0.5) * (hold3[a] + hnew[a]);
         }
         // relativistic Boris rotation, as an increment of u
         T um[3], t[3], s[3], up[3], du[3];
@@ -234,12 +250,14 @@ __global__ void __launch_bounds__(PUSH_BLOCK) k_push_deposit(Grid<T> g, Fields<T
                 p.u[a][q] = un[a];
                 p.ulo[a][q] = unl[a];
             }
-            Stencil<T> st1;
-            make_stencil(g, c1w, o1, st1);
-            T hb[3];
-            interp_H(f, g, st1, hb);
+            if (!OLDH) {
+                Stencil<T> st1;
+                make_stencil(g, c1w, o1, st1);
+                T hb[3];
+                interp_H(f, g, st1, hb);
 #pragma unroll
-            for (int a = 0; a < 3; a++) p.bold[a][q] = hb[a];
+                for (int a = 0; a < 3; a++) p.bold[a][q] = hb[a];
+            }
             dep = pp.deposit != 0;
         }
     }
@@ -535,9 +553,13 @@ __global__ void k_sort_copyback(Particles<T> p, Particles<T> src) {
 
 template <typename T>
 void launch_push_deposit(const Grid<T> &g, const Fields<T> &f, const Particles<T> &p, const PushParams<T> &pp,
-                         cudaStream_t s) {
+                         cudaStream_t s, const HoldPtrs<T> *hold) {
     if (p.n <= 0) return;
-    k_push_deposit<T><<<(unsigned)((p.n + PUSH_BLOCK - 1) / PUSH_BLOCK), PUSH_BLOCK, (size_t)pp.dep_smem, s>>>(g, f, p, pp);
+    const unsigned nb = (unsigned)((p.n + PUSH_BLOCK - 1) / PUSH_BLOCK);
+    if (hold)
+        k_push_deposit<T, true><<<nb, PUSH_BLOCK, (size_t)pp.dep_smem, s>>>(g, f, p, pp, *hold);
+    else
+        k_push_deposit<T, false><<<nb, PUSH_BLOCK, (size_t)pp.dep_smem, s>>>(g, f, p, pp, HoldPtrs<T>{});
     launch_count() += 1;
 }
 
@@ -579,9 +601,9 @@ void launch_sort(const Particles<T> &p, const Particles<T> &scratch, const SortB
 }
 
 template void launch_push_deposit<float>(const Grid<float> &, const Fields<float> &, const Particles<float> &,
-                                         const PushParams<float> &, cudaStream_t);
+                                         const PushParams<float> &, cudaStream_t, const HoldPtrs<float> *);
 template void launch_push_deposit<double>(const Grid<double> &, const Fields<double> &, const Particles<double> &,
-                                          const PushParams<double> &, cudaStream_t);
+                                          const PushParams<double> &, cudaStream_t, const HoldPtrs<double> *);
 template void launch_gather_E<float>(const Grid<float> &, const Fields<float> &, const Particles<float> &,
                                      cudaStream_t);
 template void launch_gather_E<double>(const Grid<double> &, const Fields<double> &, const Particles<double> &,

@@ -281,9 +281,16 @@ void launch_jf_apply(const Grid<T> &g, const Fields<T> &f, int max_tiles, cudaSt
 // NaN or an Inf.
 template <typename T>
 void launch_nonfinite_scan(const Fields<T> &f, long long n, int *err, cudaStream_t s);
+// H^{n-1/2} for a push that gathers it itself (the fused field path).
+template <typename T>
+struct HoldPtrs {
+    const T *H[3];
+};
+// hold: NULL, or the H^{n-1/2} arrays to gather at x^n (then E^n is gathered
+// in the same kernel and the particles' bold/eg arrays are not used)
 template <typename T>
 void launch_push_deposit(const Grid<T> &g, const Fields<T> &f, const Particles<T> &p,
-                         const PushParams<T> &pp, cudaStream_t s);
+                         const PushParams<T> &pp, cudaStream_t s, const HoldPtrs<T> *hold = nullptr);
 template <typename T>
 void launch_sort(const Particles<T> &p, const Particles<T> &scratch, const SortBuffers &sb, cudaStream_t s);
 template <typename T>
