@@ -507,10 +507,11 @@ def main():
                  "field_path": rep["best"][3],
                  "chosen_by": f"pic_tune, 2 rounds on steps 0..{rep['steps']} (before the warm-up)"}
     # Warm-up: at least the W steps asked for, then on to a 64-step block
-    # boundary, then the timed pattern once (any captured partial-block graph
-    # it needs is built here, not in the timed region), then on to the next
-    # boundary, so the timed steps replay exactly the graphs a user's
-    # pic_step(K) from a block boundary replays.
+    # boundary, then the timed pattern twice, each followed by the steps to
+    # the next boundary (a partial-block run is captured into a graph on its
+    # second use, here, not in the timed region), so the timed steps replay
+    # exactly the graphs a user's repeated pic_step(K) from a block boundary
+    # replays.
     s0 = sim.stats().step
 
     def to_boundary(extra=0):
@@ -518,8 +519,9 @@ def main():
         sim.step(extra + (-(done + extra)) % 64)
 
     to_boundary(args.warmup)
-    sim.step(args.steps)
-    to_boundary()
+    for _ in range(2):
+        sim.step(args.steps)
+        to_boundary()
     sim.sync()
     warm_run = sim.stats().step - s0
 
@@ -608,8 +610,8 @@ def main():
                 "config": {"workload": desc, "global_batch": world, "parallelism": f"replicas x{world}",
                            "l2": l2_note,
                            "warmup_steps": f"{warm_run} untimed steps after tuning: the {args.warmup} asked for, "
-                                           f"rounded up to a 64-step block boundary, then the {args.steps} timed "
-                                           f"steps once and on to the next boundary",
+                                           f"rounded up to a 64-step block boundary, then twice the {args.steps} "
+                                           f"timed steps and on to the next boundary",
                            "particle_pushes_per_s": w.nparticles * args.steps * world / (ms / 1e3),
                            "launch_settings": tuned or "library defaults (dep_smem_bytes 4096, sort_every 16, "
                                                        "field_block 256)"},

@@ -160,7 +160,8 @@ int pic_set_stream(pic_handle *h, void *stream);
  * (all particles of a handle share q and m).  Every position must lie at
  * least two cells inside each non-periodic face and outside cells with
  * wp > 0; otherwise nothing is added, *n_rejected (if non-NULL) receives the
- * count of offending particles and PIC_ERR_ARG is returned.  Positions on
+ * count of particles breaking the first of these two rules that some particle
+ * breaks, and PIC_ERR_ARG is returned.  Positions on
  * periodic axes are wrapped.  Exceeding max_particles is PIC_ERR_OOM. */
 int pic_add_particles(pic_handle *h, int64_t n, const double *xyz, const double *u,
                       double q_macro, double m_macro, int64_t *n_rejected);
@@ -196,9 +197,10 @@ int pic_probe_dft(pic_handle *h, int np, const double *xyz, uint32_t comp_mask, 
  * of this file).  Asynchronous on the handle's stream; device-side errors
  * are reported by the next synchronising call.  Steps are grouped into
  * blocks of 64 (one probe-DFT flush each): whole blocks replay one captured
- * CUDA graph, a run of 8..63 steps inside a block replays a captured graph of
- * that run (the 16 most recently used runs are kept per handle), and shorter
- * runs are launched kernel by kernel.  The arithmetic is the same on every
+ * CUDA graph; a run of 8..63 steps inside a block launches kernel by kernel
+ * the first time it is asked for and replays a graph captured the second
+ * time (runs are told apart by where in the block they start; the 16 most
+ * recently used are kept per handle); shorter runs launch kernel by kernel.  The arithmetic is the same on every
  * route.  Errors: PIC_ERR_ARG (nsteps < 0), PIC_ERR_CUDA (launch or capture
  * failed). */
 int pic_step(pic_handle *h, int64_t nsteps);

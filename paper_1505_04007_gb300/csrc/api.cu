@@ -167,6 +167,12 @@ struct Sim : SimBase {
     PushParams<T> pp{};
     Probes<T> pr{};
     uint8_t *d_mat = nullptr, *d_mat_metal = nullptr;
+    // building the edge classes on the device: the distinct keys found, the
+    // sorted key list, error flags, per-plane smallest / largest class
+    static constexpr int KEYSET = 1024;
+    unsigned long long *d_keyset = nullptr;
+    unsigned *d_keys = nullptr;
+    int *d_mflags = nullptr, *d_pmin = nullptr, *d_pmax = nullptr;
     uint8_t *d_ecls[3] = {nullptr, nullptr, nullptr};
     uint8_t *d_cls_metal = nullptr;
     float4 *d_cls_pack = nullptr;
@@ -214,7 +220,9 @@ struct Sim : SimBase {
     long long graph_kernels = 0;   // kernels in one replay of the step graph
     // Captured runs shorter than a block: steps [pos, pos + len) of a block
     // entered with the sort counter at `since`, with the DFT flush when they
-    // end the block.  Runs of SEG_MIN steps or more replay one of these (the
+    // end the block.  A run of SEG_MIN steps or more is captured the second
+    // time it is asked for (the first time it launches kernel by kernel:
+    // capturing costs more than one run) and replayed from then on (the
     // SEG_CACHE most recently used are kept); shorter runs launch directly.
     struct Segment {
         int pos, len, since, par;
@@ -267,6 +275,11 @@ struct Sim : SimBase {
             for (int q6 = 0; q6 < 6; q6++) d_prof[ax * 6 + q6] = a.take<T>(n[ax]);
         d_mat = a.take<uint8_t>(Ts);
         d_mat_metal = a.take<uint8_t>(256);
+        d_keyset = a.take<unsigned long long>(KEYSET);
+        d_keys = a.take<unsigned>(256);
+        d_mflags = a.take<int>(1);
+        d_pmin = a.take<int>((size_t)n[2]);
+        d_pmax = a.take<int>((size_t)n[2]);
         for (int c = 0; c < 3; c++) d_ecls[c] = a.take<uint8_t>(Ts);
         for (int q3 = 0; q3 < 3; q3++) d_cls[q3] = a.take<T>(256);
         d_cls_metal = a.take<uint8_t>(256);
@@ -357,157 +370,67 @@ struct Sim : SimBase {
         ik = 1.0 / kappa;
     }
 
-    int build_tables(const pic_config *c, std::vector<uint8_t> ecls[3], std::vector<T> cls[3],
-                     std::vector<uint8_t> &cls_metal) {
-        // Edge classes: distinct multisets of the four cell ids around an edge,
-        // numbered in order of first appearance over components 0, 1, 2 and
-        // cells in memory order.  Host threads scan slabs of planes with
-        // classes numbered per slab; the merge then numbers them in slab
-        // order, which gives exactly the serial numbering.
-        const uint8_t *mat = c->material_id;
-        const int nx = n[0], ny = n[1], nz = n[2];
-        const size_t stride[3] = {1, (size_t)nx, (size_t)nx * ny};
-        auto wrapc = [&](int a, int x) {
-            if (x < 0) return g.per[a] ? x + n[a] : 0;
-            if (x >= n[a]) return g.per[a] ? x - n[a] : n[a] - 1;
-            return x;
-        };
-        const int hw = (int)std::thread::hardware_concurrency();
-        const int nthr = std::max(1, std::min({hw > 0 ? hw : 1, 16, nz}));
-        struct Part {
-            std::vector<uint32_t> keys;  // local class -> key
-            bool overflow = false;
-        };
-        std::vector<Part> part((size_t)3 * nthr);
-        for (int comp = 0; comp < 3; comp++) ecls[comp].resize((size_t)N);
-        auto scan = [&](int t) {
-            const int k0 = (int)((long long)nz * t / nthr), k1 = (int)((long long)nz * (t + 1) / nthr);
-            for (int comp = 0; comp < 3; comp++) {
-                Part &P = part[(size_t)comp * nthr + t];
-                std::unordered_map<uint32_t, int> seen;
-                uint8_t *out = ecls[comp].data();
-                const int a1 = (comp + 1) % 3, a2 = (comp + 2) % 3;
-                const size_t o1 = stride[a1], o2 = stride[a2];
-                uint32_t last_key = 0xffffffffu;
-                int last_cls = -1;
-                for (int k = k0; k < k1; k++)
-                    for (int j = 0; j < ny; j++)
-                        for (int i = 0; i < nx; i++) {
-                            const int x3[3] = {i, j, k};
-                            const size_t e = ((size_t)k * ny + j) * nx + i;
-                            int ids[4];
-                            if (x3[a1] > 0 && x3[a2] > 0) {  // no face: the four cells by their offsets
-                                ids[0] = mat[e];
-                                ids[1] = mat[e - o1];
-                                ids[2] = mat[e - o2];
-                                ids[3] = mat[e - o1 - o2];
-                            } else {
-                                int q = 0;
-                                for (int s1 = -1; s1 <= 0; s1++)
-                                    for (int s2 = -1; s2 <= 0; s2++) {
-                                        int p3[3] = {i, j, k};
-                                        p3[a1] = wrapc(a1, p3[a1] + s1);
-                                        p3[a2] = wrapc(a2, p3[a2] + s2);
-                                        ids[q++] = mat[((size_t)p3[2] * ny + p3[1]) * nx + p3[0]];
-                                    }
-                            }
-                            uint32_t key;
-                            if (ids[0] == ids[1] && ids[0] == ids[2] && ids[0] == ids[3]) {
-                                key = (uint32_t)ids[0] * 0x01010101u;  // one material (most edges)
-                            } else {
-                                std::sort(ids, ids + 4);
-                                key = (uint32_t)ids[0] | (uint32_t)ids[1] << 8 | (uint32_t)ids[2] << 16 |
-                                      (uint32_t)ids[3] << 24;
-                            }
-                            int cl = last_cls;
-                            if (key != last_key) {
-                                auto it = seen.find(key);
-                                if (it == seen.end()) {
-                                    if ((int)seen.size() >= 256) {
-                                        P.overflow = true;
-                                        return;
-                                    }
-                                    cl = (int)seen.size();
-                                    seen[key] = cl;
-                                    P.keys.push_back(key);
-                                } else {
-                                    cl = it->second;
-                                }
-                                last_key = key;
-                                last_cls = cl;
-                            }
-                            out[e] = (uint8_t)cl;
-                        }
-            }
-        };
-        auto run_all = [&](auto &&fn) {
-            std::vector<std::thread> pool;
-            for (int t = 1; t < nthr; t++) pool.emplace_back(fn, t);
-            fn(0);
-            for (auto &th : pool) th.join();
-        };
-        run_all(scan);
-        // merge: global numbers in (component, slab) order; per slab a local -> global table
+    // Edge classes from the material map already on the device (materials.cu):
+    // the distinct sorted 4-cell keys, numbered in ascending key order; their
+    // Eq. 6 / Eq. 8 coefficients in FP64 on the host; every edge's class and
+    // per plane whether all its edges share one non-metal class (plane_cls,
+    // else 255).
+    int device_classes(const pic_config *c, std::vector<T> cls[3], std::vector<uint8_t> &cls_metal,
+                       std::vector<uint8_t> &plane_cls) {
+        CUDA_TRY(cudaMemsetAsync(d_keyset, 0xff, KEYSET * sizeof(unsigned long long), stream));
+        CUDA_TRY(cudaMemsetAsync(d_mflags, 0, sizeof(int), stream));
+        CUDA_TRY(cudaMemsetAsync(d_pmin, 0x7f, (size_t)n[2] * sizeof(int), stream));
+        CUDA_TRY(cudaMemsetAsync(d_pmax, 0x80, (size_t)n[2] * sizeof(int), stream));
+        launch_edge_keys(d_mat, n, g.per, c->n_materials, d_keyset, KEYSET, d_mflags, stream);
+        CUDA_TRY(cudaGetLastError());
+        std::vector<unsigned long long> set(KEYSET);
+        int flags = 0;
+        CUDA_TRY(cudaMemcpyAsync(set.data(), d_keyset, KEYSET * sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream));
+        CUDA_TRY(cudaMemcpyAsync(&flags, d_mflags, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        CUDA_TRY(cudaStreamSynchronize(stream));
+        if (flags & 2) return fail(PIC_ERR_ARG, "a material id is not below n_materials (%d)", c->n_materials);
+        std::vector<unsigned> keys;
+        for (unsigned long long v : set)
+            if (v != ~0ull) keys.push_back((unsigned)v);
+        if ((flags & 1) || keys.size() > 256) return fail(PIC_ERR_UNSUPPORTED, "more than 256 distinct edge materials");
+        std::sort(keys.begin(), keys.end());
         for (int q3 = 0; q3 < 3; q3++) cls[q3].assign(256, (T)0);
         cls_metal.assign(256, 0);
-        std::unordered_map<uint32_t, int> classes;
-        std::vector<std::array<uint8_t, 256>> remap(part.size());
-        std::vector<char> identity(part.size(), 1);
-        for (size_t pi = 0; pi < part.size(); pi++) {
-            if (part[pi].overflow) return fail(PIC_ERR_UNSUPPORTED, "more than 256 distinct edge materials");
-            for (size_t q = 0; q < part[pi].keys.size(); q++) {
-                const uint32_t key = part[pi].keys[q];
-                auto it = classes.find(key);
-                int cl;
-                if (it == classes.end()) {
-                    if ((int)classes.size() >= 256)
-                        return fail(PIC_ERR_UNSUPPORTED, "more than 256 distinct edge materials");
-                    cl = (int)classes.size();
-                    classes[key] = cl;
-                    double sw = 0, swg = 0, se = 0;
-                    for (int q4 = 0; q4 < 4; q4++) {
-                        const pic_material &mt = c->materials[(key >> (8 * q4)) & 0xffu];
-                        sw += mt.wp * mt.wp;
-                        swg += mt.wp * mt.wp * mt.gamma;
-                        se += mt.eps_inf;
-                    }
-                    const double wp2 = sw / 4.0, gam = sw > 0 ? swg / sw : 0.0, einf = se / 4.0;
-                    const double dt = c->dt;
-                    cls[0][cl] = (T)(-2.0 * gam * dt / (2.0 + gam * dt));  // kJ - 1
-                    cls[1][cl] = (T)(2.0 * dt * c->eps0 * wp2 / (2.0 + gam * dt));
-                    cls[2][cl] = (T)(dt / (c->eps0 * einf));
-                    cls_metal[cl] = wp2 > 0.0;
-                } else {
-                    cl = it->second;
-                }
-                remap[pi][q] = (uint8_t)cl;
-                if (cl != (int)q) identity[pi] = 0;
+        for (size_t cl = 0; cl < keys.size(); cl++) {
+            double sw = 0, swg = 0, se = 0;
+            for (int q4 = 0; q4 < 4; q4++) {
+                const pic_material &mt = c->materials[(keys[cl] >> (8 * q4)) & 0xffu];
+                sw += mt.wp * mt.wp;
+                swg += mt.wp * mt.wp * mt.gamma;
+                se += mt.eps_inf;
             }
+            const double wp2 = sw / 4.0, gam = sw > 0 ? swg / sw : 0.0, einf = se / 4.0;
+            const double dt = c->dt;
+            cls[0][cl] = (T)(-2.0 * gam * dt / (2.0 + gam * dt));  // kJ - 1
+            cls[1][cl] = (T)(2.0 * dt * c->eps0 * wp2 / (2.0 + gam * dt));
+            cls[2][cl] = (T)(dt / (c->eps0 * einf));
+            cls_metal[cl] = wp2 > 0.0;
         }
-        run_all([&](int t) {
-            const size_t plane = (size_t)nx * ny;
-            const size_t b0 = plane * (size_t)((long long)nz * t / nthr), b1 = plane * (size_t)((long long)nz * (t + 1) / nthr);
-            for (int comp = 0; comp < 3; comp++) {
-                const size_t pi = (size_t)comp * nthr + t;
-                if (identity[pi]) continue;
-                uint8_t *out = ecls[comp].data();
-                for (size_t e = b0; e < b1; e++) out[e] = remap[pi][out[e]];
-            }
-        });
-        n_classes = (int)classes.size();
+        n_classes = (int)keys.size();
+        CUDA_TRY(cudaMemcpyAsync(d_keys, keys.data(), keys.size() * sizeof(unsigned), cudaMemcpyHostToDevice, stream));
+        launch_edge_classes(d_mat, n, g.per, d_keys, (int)keys.size(), d_ecls, d_pmin, d_pmax, stream);
+        CUDA_TRY(cudaGetLastError());
+        std::vector<int> pmin(n[2]), pmax(n[2]);
+        CUDA_TRY(cudaMemcpyAsync(pmin.data(), d_pmin, n[2] * sizeof(int), cudaMemcpyDeviceToHost, stream));
+        CUDA_TRY(cudaMemcpyAsync(pmax.data(), d_pmax, n[2] * sizeof(int), cudaMemcpyDeviceToHost, stream));
+        CUDA_TRY(cudaStreamSynchronize(stream));
+        plane_cls.assign(n[2], 255);
+        for (int k = 0; k < n[2]; k++)
+            if (pmin[k] == pmax[k] && pmin[k] >= 0 && pmin[k] < 256 && !cls_metal[pmin[k]]) plane_cls[k] = (uint8_t)pmin[k];
         return PIC_OK;
     }
 
     int create(const pic_config *c) {
         CUDA_TRY(cudaGetDevice(&device));
         init_geometry(c);
-        for (size_t e = 0; e < (size_t)N; e++)
-            if (c->material_id[e] >= c->n_materials)
-                return fail(PIC_ERR_ARG, "material id %d at cell %zu out of range", c->material_id[e], e);
-        std::vector<uint8_t> ecls[3], cls_metal;
+        std::vector<uint8_t> cls_metal, plane_cls;
         std::vector<T> cls[3];
-        int rc = build_tables(c, ecls, cls, cls_metal);
-        if (rc) return rc;
+        int rc = PIC_OK;
 
         Arena sizing;
         plan(sizing);
@@ -549,13 +472,13 @@ struct Sim : SimBase {
                 CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
         }
 
-        // material map and per-material metal flag (particle absorption)
+        // material map and per-material metal flag (particle absorption), then the edge classes
         std::vector<uint8_t> metal(256, 0);
         for (int m2 = 0; m2 < c->n_materials; m2++) metal[m2] = c->materials[m2].wp > 0.0;
         CUDA_TRY(cudaMemcpyAsync(d_mat, c->material_id, (size_t)N, cudaMemcpyHostToDevice, stream));
         CUDA_TRY(cudaMemcpyAsync(d_mat_metal, metal.data(), 256, cudaMemcpyHostToDevice, stream));
-        for (int comp = 0; comp < 3; comp++)
-            CUDA_TRY(cudaMemcpyAsync(d_ecls[comp], ecls[comp].data(), (size_t)N, cudaMemcpyHostToDevice, stream));
+        rc = device_classes(c, cls, cls_metal, plane_cls);
+        if (rc) return rc;
         for (int q3 = 0; q3 < 3; q3++)
             CUDA_TRY(cudaMemcpyAsync(d_cls[q3], cls[q3].data(), 256 * sizeof(T), cudaMemcpyHostToDevice, stream));
         std::vector<float4> pack(256);
@@ -568,19 +491,6 @@ struct Sim : SimBase {
         // take the kernel without per-edge material reads)
         if constexpr (std::is_same<T, float>::value) {
           if (n[0] % 4 == 0) {
-            std::vector<uint8_t> plane_cls(n[2], 255);
-            for (int k = 0; k < n[2]; k++) {
-                int first = -1;
-                bool mixed = false;
-                for (int comp = 0; comp < 3 && !mixed; comp++) {
-                    const uint8_t *row = ecls[comp].data() + (size_t)k * n[1] * n[0];
-                    for (size_t q = 0; q < (size_t)n[1] * n[0]; q++) {
-                        if (first < 0) first = row[q];
-                        else if (row[q] != first) { mixed = true; break; }
-                    }
-                }
-                if (!mixed && first >= 0 && !cls_metal[first]) plane_cls[k] = (uint8_t)first;
-            }
             std::vector<float> cE(256);
             for (int q = 0; q < 256; q++) cE[q] = (float)cls[2][q];
             use_plan = make_field_plan(g, plane_cls.data(), cE.data(), fplan);
@@ -685,7 +595,8 @@ struct Sim : SimBase {
         gexec = nullptr;
         gexec_odd = nullptr;
         graph = nullptr;
-        for (auto &sg : segs) cudaGraphExecDestroy(sg.exec);
+        for (auto &sg : segs)
+            if (sg.exec) cudaGraphExecDestroy(sg.exec);
         segs.clear();
         epoch++;
     }
@@ -1013,14 +924,18 @@ struct Sim : SimBase {
         Segment *sg = nullptr;
         for (auto &x : segs)
             if (x.pos == pos && x.len == len && x.since == since && x.par == par0) sg = &x;
-        if (!sg) {
-            if ((int)segs.size() >= SEG_CACHE) {  // drop the least recently used
+        if (!sg) {  // first use: remember it and launch directly
+            if ((int)segs.size() >= SEG_CACHE) {
                 size_t old = 0;
                 for (size_t q = 1; q < segs.size(); q++)
                     if (segs[q].used < segs[old].used) old = q;
-                cudaGraphExecDestroy(segs[old].exec);
+                if (segs[old].exec) cudaGraphExecDestroy(segs[old].exec);
                 segs.erase(segs.begin() + (long)old);
             }
+            segs.push_back(Segment{pos, len, since, par0, nullptr, 0, ++seg_clock});
+            return run_direct(len);
+        }
+        if (!sg->exec) {
             Segment nsg{pos, len, since, par0, nullptr, 0, 0};
             CUDA_TRY(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
             const long long before = launch_count();
@@ -1039,8 +954,8 @@ struct Sim : SimBase {
             e = cudaGraphInstantiate(&nsg.exec, gr, 0);
             cudaGraphDestroy(gr);
             if (e != cudaSuccess) return fail(PIC_ERR_CUDA, "segment instantiate: %s", cudaGetErrorString(e));
-            segs.push_back(nsg);
-            sg = &segs.back();
+            sg->exec = nsg.exec;
+            sg->kernels = nsg.kernels;
         }
         sg->used = ++seg_clock;
         CUDA_TRY(cudaGraphLaunch(sg->exec, stream));
@@ -1097,19 +1012,28 @@ struct Sim : SimBase {
                 nsteps -= run;
                 continue;
             }
+            rc = run_direct(1);
+            if (rc) return rc;
+            nsteps--;
+        }
+        CUDA_TRY(cudaGetLastError());
+        return PIC_OK;
+    }
+
+    // len steps launched kernel by kernel (within the current block)
+    int run_direct(int len) {
+        for (int q = 0; q < len; q++) {
             const bool sort = since_sort >= sort_every;
             launch_step(sort, true, nullptr, (int)(step_host & 1));
             since_sort = sort ? 1 : since_sort + 1;
             CUDA_TRY(cudaGetLastError());
             buffered++;
             step_host++;
-            nsteps--;
             if (buffered == DFT_BLOCK) {
                 launch_dft_flush<T>(pr, d_step, DFT_BLOCK, stream);
                 buffered = 0;
             }
         }
-        CUDA_TRY(cudaGetLastError());
         return PIC_OK;
     }
 
@@ -1535,18 +1459,16 @@ static int add_particles_t(Sim<T> *s, int64_t n, const double *xyz, const double
     std::vector<int> cell[3];
     std::vector<T> off[3], uu[3], ulo[3];
     for (int a = 0; a < 3; a++) { cell[a].resize(n); off[a].resize(n); uu[a].resize(n); ulo[a].resize(n); }
-    std::vector<uint8_t> mat((size_t)s->N);
-    int64_t bad = 0;
-    // the material map lives on the device; copy it once for the check
-    if (n > 0) {
-        CUDA_TRY(cudaMemcpyAsync(mat.data(), s->d_mat, (size_t)s->N, cudaMemcpyDeviceToHost, s->stream));
-        CUDA_TRY(cudaStreamSynchronize(s->stream));
-    }
-    std::vector<uint8_t> metal(256);
-    CUDA_TRY(cudaMemcpy(metal.data(), s->d_mat_metal, 256, cudaMemcpyDeviceToHost));
-    for (int64_t q2 = 0; q2 < n; q2++) {
+    // host threads over slices of the input: cell, offset and momentum split
+    // in the state precision, and the boundary-margin rule
+    const int hw = (int)std::thread::hardware_concurrency();
+    const int nthr = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)(hw > 0 ? hw : 1), 16, n / 65536 + 1}));
+    std::vector<int64_t> bad_t(nthr, 0);
+    auto convert = [&](int t) {
+    const int64_t lo = n * t / nthr, hi = n * (t + 1) / nthr;
+    int64_t &bad = bad_t[t];
+    for (int64_t q2 = lo; q2 < hi; q2++) {
         bool ok = true;
-        int c3[3];
         for (int a = 0; a < 3; a++) {
             double xi = xyz[3 * q2 + a] / s->d[a];
             if (!std::isfinite(xi) || !std::isfinite(u[3 * q2 + a])) { ok = false; xi = 0; }
@@ -1557,7 +1479,6 @@ static int add_particles_t(Sim<T> *s, int64_t n, const double *xyz, const double
             if (s->g.per[a] && ci >= s->n[a]) { ci -= s->n[a]; }
             if (!s->g.per[a] && (xi < 2.0 || xi >= s->n[a] - 2.0)) ok = false;
             ci = std::min(std::max(ci, 0), s->n[a] - 1);
-            c3[a] = ci;
             cell[a][q2] = ci;
             T ot = (T)o;
             if (ot >= T(1)) ot = std::nextafter(T(1), T(0));
@@ -1565,11 +1486,21 @@ static int add_particles_t(Sim<T> *s, int64_t n, const double *xyz, const double
             uu[a][q2] = (T)u[3 * q2 + a];
             ulo[a][q2] = (T)(u[3 * q2 + a] - (double)uu[a][q2]);
         }
-        if (ok && metal[mat[((size_t)c3[2] * s->n[1] + c3[1]) * s->n[0] + c3[0]]]) ok = false;
         if (!ok) bad++;
     }
+    };
+    {
+        std::vector<std::thread> pool;
+        for (int t = 1; t < nthr; t++) pool.emplace_back(convert, t);
+        convert(0);
+        for (auto &th : pool) th.join();
+    }
+    int64_t bad = 0;
+    for (int64_t b : bad_t) bad += b;
     if (n_rejected) *n_rejected = bad;
     if (bad) return fail(PIC_ERR_ARG, "%lld particles outside the allowed region", (long long)bad);
+    // the arrays go beyond the live count first; cells inside a metal (the
+    // material map lives on the device) are counted there before they count
     const long long base = s->p.n;
     std::vector<long long> ids(n);
     for (int64_t q2 = 0; q2 < n; q2++) ids[q2] = base + q2;
@@ -1581,6 +1512,19 @@ static int add_particles_t(Sim<T> *s, int64_t n, const double *xyz, const double
     }
     CUDA_TRY(cudaMemcpyAsync(s->p.id + base, ids.data(), n * sizeof(long long), cudaMemcpyHostToDevice, s->stream));
     CUDA_TRY(cudaMemsetAsync(s->p.status + base, 0, (size_t)n, s->stream));
+    if (n > 0) {
+        unsigned long long *d_cnt = reinterpret_cast<unsigned long long *>(s->d_keyset);  // scratch after create
+        unsigned long long in_metal = 0;
+        CUDA_TRY(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), s->stream));
+        launch_count_in_metal(s->p.cell, base, n, s->n, s->d_mat, s->d_mat_metal, d_cnt, s->stream);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaMemcpyAsync(&in_metal, d_cnt, sizeof(in_metal), cudaMemcpyDeviceToHost, s->stream));
+        CUDA_TRY(cudaStreamSynchronize(s->stream));
+        if (in_metal) {
+            if (n_rejected) *n_rejected = (int64_t)in_metal;
+            return fail(PIC_ERR_ARG, "%lld particles inside a metal cell", (long long)in_metal);
+        }
+    }
     CUDA_TRY(cudaStreamSynchronize(s->stream));
     s->p.n = base + n;
     s->have_q = true;

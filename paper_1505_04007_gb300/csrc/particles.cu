@@ -551,6 +551,26 @@ __global__ void k_sort_copyback(Particles<T> p, Particles<T> src) {
     p.id[q] = src.id[q];
 }
 
+// Electrons [base, base + n) whose cell holds a metal (wp > 0): counted into *count.
+__global__ void k_count_in_metal(const int *c0, const int *c1, const int *c2, long long base, long long n, int nx, int ny,
+                                 const uint8_t *mat, const uint8_t *mat_metal, unsigned long long *count) {
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    bool bad = false;
+    if (q < n) {
+        const long long e = ((long long)c2[base + q] * ny + c1[base + q]) * nx + c0[base + q];
+        bad = mat_metal[mat[e]] != 0;
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(count, (unsigned long long)__popc(b));
+}
+
+void launch_count_in_metal(int *const cell[3], long long base, long long n, const int nn[3], const uint8_t *mat,
+                           const uint8_t *mat_metal, unsigned long long *count, cudaStream_t s) {
+    if (n <= 0) return;
+    k_count_in_metal<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(cell[0], cell[1], cell[2], base, n, nn[0], nn[1], mat,
+                                                                 mat_metal, count);
+}
+
 template <typename T>
 void launch_push_deposit(const Grid<T> &g, const Fields<T> &f, const Particles<T> &p, const PushParams<T> &pp,
                          cudaStream_t s, const HoldPtrs<T> *hold) {

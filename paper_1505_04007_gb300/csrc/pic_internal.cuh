@@ -230,6 +230,17 @@ void launch_fused_pass(const FusedArgs &a, const FusedPlan &pl, int xbuf, cudaSt
 void launch_jf_clear(const Grid<float> &g, const JfSet &j, int max_tiles, cudaStream_t s);
 void launch_jf_fix(const Grid<float> &g, const FixArgs &f, int max_tiles, cudaStream_t s);
 
+// Edge classes on the device (materials.cu).  launch_edge_keys adds every
+// distinct sorted 4-cell key of the grid to gset (gcap slots of ~0: empty)
+// and sets flags bit 0 when a set overflows, bit 1 when a material id is not
+// below n_materials.  launch_edge_classes writes each edge's class (the
+// position of its key in the ascending list keys) and per plane the smallest
+// and largest class (pmin, pmax preset to INT_MAX-like / negative values).
+void launch_edge_keys(const uint8_t *mat, const int n[3], const int per[3], int n_materials, unsigned long long *gset,
+                      int gcap, int *flags, cudaStream_t s);
+void launch_edge_classes(const uint8_t *mat, const int n[3], const int per[3], const unsigned *keys, int nkeys,
+                         uint8_t *const ecls[3], int *pmin, int *pmax, cudaStream_t s);
+
 // k-omega map of the probe line (probe.cu): out[q][f] = |sum_p F_p e^{-i k_q s_p}|^2.
 void launch_probe_kw(const double *F, const double *xyz_cells, double cell, int axis, int np, int nf, int comp,
                      const double *k, int nk, double *out, cudaStream_t s);
@@ -281,6 +292,10 @@ void launch_jf_apply(const Grid<T> &g, const Fields<T> &f, int max_tiles, cudaSt
 // NaN or an Inf.
 template <typename T>
 void launch_nonfinite_scan(const Fields<T> &f, long long n, int *err, cudaStream_t s);
+// Electrons [base, base + n) whose cell is metal, counted into *count (added to).
+void launch_count_in_metal(int *const cell[3], long long base, long long n, const int nn[3], const uint8_t *mat,
+                           const uint8_t *mat_metal, unsigned long long *count, cudaStream_t s);
+
 // H^{n-1/2} for a push that gathers it itself (the fused field path).
 template <typename T>
 struct HoldPtrs {

@@ -93,19 +93,26 @@ def test_step_runs_of_every_kind(P, prec, tol):
     w = W.scaled(W.c1(), 64, 24, 40, 1024, 0)
     o = O.from_workload(w)
     s = P.Simulation(w, P.PIC_FP64 if prec == "fp64" else P.PIC_FP32)
-    # 5 direct; 20 captured (steps 5..24); 50 = 39 captured to the block's end + 11 captured;
-    # 7 direct; 64 = 46 captured to the end + 18 captured; 9 captured; 100 = 37 to the end + 63 captured
+    # 5 direct; 20 (steps 5..24); 50 = 39 to the block's end + 11; 7 direct;
+    # 64 = 46 to the end + 18; 9; 100 = 37 to the end + 63.  Runs of 8 or more
+    # launch directly the first time and replay a captured graph from the
+    # second time: the pattern runs three times, from block boundaries.
     runs = [5, 20, 50, 7, 64, 9, 100]
-    for r in runs:
-        s.step(r)
-    total = sum(runs)
+    total = 0
+    for rep in range(3):
+        for r in runs:
+            s.step(r)
+            total += r
+        pad = -total % 64
+        s.step(pad)
+        total += pad
     o.step(total)
     s.sync()
     assert s.stats().step == total
     assert rel_fields(s, o) <= tol
     Fo, Fg = o.probe_read(), s.probe_read()
     assert np.linalg.norm(Fg - Fo) <= tol * np.linalg.norm(Fo)
-    # the same total again from a block boundary: whole blocks plus a captured tail
+    # from a block boundary: whole blocks plus a tail
     s.step(128 - total % 64)
     o.step(128 - total % 64)
     s.step(84)
@@ -185,3 +192,30 @@ def test_nan_away_from_electrons_is_nonfinite(P):
     assert st2.device_error == 0 and st.n_frozen == st2.n_frozen
     s.close()
     s2.close()
+
+
+def test_create_builds_edge_classes_on_the_device(P):
+    """The material map is checked and the per-edge classes are built on the
+    device: a film in vacuum has exactly three classes (vacuum, metal, the
+    half-metal edges on the film faces); an id not below n_materials is an
+    argument error; more than 256 distinct four-cell combinations are
+    unsupported."""
+    mat = np.zeros((24, 20, 32), np.uint8)
+    mat[8:12] = 1
+    w = box_workload(32, 20, 24, bc=(W.BC_CPML,) * 6, material=mat, table=W.drude_table())
+    s = P.Simulation(w, P.PIC_FP32, particles=False, probes=False)
+    assert s.stats().n_edge_classes == 3
+    s.close()
+    bad = mat.copy()
+    bad[15, 10, 7] = 2  # the table has materials 0 and 1
+    wb = box_workload(32, 20, 24, bc=(W.BC_CPML,) * 6, material=bad, table=W.drude_table())
+    with pytest.raises(P.PicError) as e:
+        P.Simulation(wb, P.PIC_FP32, particles=False, probes=False)
+    assert e.value.code == -1
+    rng = np.random.default_rng(11)
+    many = rng.integers(0, 40, size=mat.shape).astype(np.uint8)
+    table = np.array([[1e14 * (m + 1), 1e13, 1.0] for m in range(40)])
+    wm = box_workload(32, 20, 24, bc=(W.BC_CPML,) * 6, material=many, table=table)
+    with pytest.raises(P.PicError) as e:
+        P.Simulation(wm, P.PIC_FP32, particles=False, probes=False)
+    assert e.value.code == -7
