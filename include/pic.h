@@ -95,7 +95,9 @@ typedef struct {
 
 /* pic_config.flags: keep the FP32 field updates as two separate passes (the
  * H update, then the E update) on a grid that would take the fused pass.
- * The fused pass: FP32 grids with nx a multiple of 4 and no periodic axis
+ * The fused pass: FP32 grids with nx a multiple of 4, no periodic axis and,
+ * where an axis has absorbing layers, cpml_cells <= 8 (a multiple of 4 along
+ * x) and more than 32 + cpml_cells cells along x, 15 + cpml_cells along y,
  * advance E (Eq. 6 then Eq. 8) and the next step's H in one sweep over the
  * grid (48 instead of 72 bytes per cell), holding two copies of the field
  * state (the arena is larger by one copy of E, H, J, J_f and the CPML

@@ -346,6 +346,7 @@ struct Sim : SimBase {
         fused_possible = std::is_same<T, float>::value && !(c->flags & PIC_FLAG_SPLIT_FIELDS) && n[0] % 4 == 0 &&
                          !g.per[0] && !g.per[1] && !g.per[2] && (!g.cpml[0] || g.L % 4 == 0) &&
                          ((!g.cpml[0] && !g.cpml[1]) || g.L <= FUSED_MAX_L) &&
+                         (!g.cpml[0] || n[0] > FUSED_TX + g.L) && (!g.cpml[1] || n[1] > FUSED_TY + g.L) &&
                          (long long)n[0] * n[1] * n[2] < (1LL << 32) && n[0] / FUSED_TX < 65536 &&
                          (n[1] + FUSED_TY - 1) / FUSED_TY < 65536;
     }
@@ -510,20 +511,21 @@ struct Sim : SimBase {
                 jfs[0].flag = d_flag;
                 jfs[0].list = d_jf_list;
                 jfs[0].count = d_jf_count;
-                std::vector<int> inner, slabt;
-                fused_tiles(g, inner, slabt);
-                std::vector<int> tiles(inner);
-                tiles.insert(tiles.end(), slabt.begin(), slabt.end());
+                std::vector<int> kinds[4];
+                fused_tiles(g, kinds);
+                std::vector<int> tiles;
+                for (int k = 0; k < 4; k++) {
+                    tiles.insert(tiles.end(), kinds[k].begin(), kinds[k].end());
+                    fpl.n_kind[k] = (int)kinds[k].size();
+                }
                 std::vector<float> pce(n[2]);
                 for (int k = 0; k < n[2]; k++) pce[k] = plane_cls[k] != 255 ? cE[plane_cls[k]] : -1.f;
                 CUDA_TRY(cudaMemcpy(d_tiles, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice));
                 CUDA_TRY(cudaMemcpy(d_plane_cE, pce.data(), pce.size() * sizeof(float), cudaMemcpyHostToDevice));
                 fpl.tiles = d_tiles;
-                fpl.n_inner = (int)inner.size();
-                fpl.n_slab = (int)slabt.size();
                 int sms = 0;
                 CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
-                fpl.chunk = fused_chunk(n[2], (int)inner.size(), sms);
+                fpl.chunk = fused_chunk(n[2], fpl.n_kind[0], sms);
                 fpl.nchunks = (n[2] + fpl.chunk - 1) / fpl.chunk;
                 fused = fused_grid_ok(g) && fused_maps(fpl, P, n, g.L, g.cpml);
             }
@@ -715,7 +717,8 @@ struct Sim : SimBase {
     // (= n & 1) to copy par ^ 1, on the main stream: J_f of the step before
     // last back to zero, the electrons' E^n, push and deposit into J_f set
     // `par`, the prescribed sources; then the fused pass (inner tiles on the
-    // main stream, the tiles over the x and y slabs beside them on aux); then
+    // main stream, the three kinds of tiles over the x and y slabs beside
+    // them on aux, aux2, aux3); then
     // the free-current correction and the probe sample.  (The push runs on
     // its own before the pass: beside it, its blocks would wait for shared
     // memory the pass holds.)  pe (optional) receives 7 timing events: step
@@ -738,7 +741,8 @@ struct Sim : SimBase {
             }
             launch_sources<T>(g, fx, sources.data(), (int)sources.size(), cfg.dt, stream);
             if (pe) cudaEventRecord(pe[3], stream);
-            fork_join(stream, aux, ev_hf);
+            cudaEventRecord(ev_ef, stream);
+            for (cudaStream_t x : {aux, aux2, aux3}) cudaStreamWaitEvent(x, ev_ef, 0);
             FusedArgs a{};
             a.g = g;
             for (int c = 0; c < 3; c++) {
@@ -762,8 +766,11 @@ struct Sim : SimBase {
             a.plane_cE = d_plane_cE;
             a.chunk = fpl.chunk;
             a.err = d_err;
-            launch_fused_pass(a, fpl, xb, stream, aux);
-            fork_join(aux, stream, ev_hj);
+            const cudaStream_t sk[3] = {aux, aux2, aux3};
+            launch_fused_pass(a, fpl, xb, stream, sk);
+            fork_join(aux, stream, ev_ej);
+            fork_join(aux2, stream, ev_ej2);
+            fork_join(aux3, stream, ev_ej3);
             if (pe) cudaEventRecord(pe[1], stream);
             if (pe) cudaEventRecord(pe[4], stream);
             FixArgs fa{};

@@ -10,14 +10,23 @@
 // z-1, keeping the planes it needs in shared memory.
 //
 // Layout of a work item: a tile of TX x TY cells (x, y) over a run of `chunk`
-// planes.  Warps 0..TY-1 own the tile's rows (one cell per lane).  H^{n+3/2}
-// at the tile's last column and row needs E^{n+1} one cell beyond the tile,
-// which belongs to the neighbouring tile: two more warps compute it again
-// here (warp TY: the row y0+TY; warp TY+1: the column x0+TX), and the
-// chunk's last E plane is likewise computed by both chunks that need it.
-// Recomputed values are used, never stored.  Because a neighbour may already
-// have written its cells of the step, the pass reads the state at step n
-// from one copy of the arrays (X) and writes step n+1 to another (Y).
+// planes.  A thread owns four consecutive x cells of one row (TX/4 threads
+// per row).  H^{n+3/2} at the tile's last column and row needs E^{n+1} one
+// cell beyond the tile, which belongs to the neighbouring tile: the last
+// thread of each row also computes that row's cell at x0+TX, and one more
+// row of threads computes the row y0+TY; the chunk's last E plane is
+// likewise computed by both chunks that need it.  Recomputed values are
+// used, never stored.  Because a neighbour may already have written its
+// cells of the step, the pass reads the state at step n from one copy of
+// the arrays (X) and writes step n+1 to another (Y).
+//
+// Tiles come in four kinds, each a kernel of its own (template K): tiles
+// whose cells, halo row and halo column stay out of the x and y absorbing
+// slabs (K = 0; z slabs are handled per plane), tiles that meet a y slab
+// only (K = 1), an x slab only (K = 2), or both (K = 3).  The slab kinds
+// stage the slab's CPML memory with E and H; they trade the third E^{n+1}
+// plane and the shared class table for that staging, so that the x-only and
+// y-only kinds still fit three blocks on an SM.
 //
 // Staging: one thread streams the planes of E^n and H^{n+1/2} into a ring of
 // STAGES shared-memory slots with bulk tensor copies (cp.async.bulk.tensor,
@@ -56,28 +65,34 @@ static_assert(TX % 32 == 0 && NT % 32 == 0, "whole warps");
 
 constexpr int MAX_CHUNK = 64;
 // CPML memory of the x and y slabs, staged with E and H for the tiles that
-// meet those slabs: x slabs [comp][row][2L] (both faces' slab columns), y
-// slabs [comp][slab row][x0..x0+TX+3], for 2L <= 2 FUSED_MAX_L rows/columns.
-constexpr int PX = 2 * FUSED_MAX_L;
-constexpr int PXBOX = 2 * EH * PX, PYBOX = 2 * EH * EW;  // floats (multiples of 32)
-constexpr int PY_B = PYBOX * 4;                           // bytes of a y-slab copy
+// meet those slabs.  A tile meets the slab of one face only (the grid checks
+// guarantee it), so a copy takes that face's L slab columns or rows: x slabs
+// [comp][row y0..y0+TY][L columns], y slabs [comp][up to FUSED_MAX_L slab
+// rows][x0..x0+TX+3].
+constexpr int PXW = FUSED_MAX_L, PYH = FUSED_MAX_L;
+constexpr int PXBOX = 2 * EH * PXW, PYBOX = 2 * PYH * EW;  // floats (multiples of 32)
+static_assert(PXBOX % 32 == 0 && PYBOX % 32 == 0, "128-byte aligned slots");
 
-template <bool SLAB>
+template <int K>
 struct __align__(128) Smem {
-    static constexpr int PS = SLAB ? STAGES : 1;
+    static constexpr bool XS = (K & 2) != 0, YS = (K & 1) != 0;
+    static constexpr int NEN = K ? 2 : 3;  // E^{n+1} planes in the ring
     float e[STAGES][EBOX];
     float h[STAGES][HBOX];
-    float pex[PS][SLAB ? PXBOX : 32], phx[PS][SLAB ? PXBOX : 32];  // psi_E, psi_H of x slabs
-    float pey[PS][SLAB ? PYBOX : 32], phy[PS][SLAB ? PYBOX : 32];  // ... of y slabs
-    float en[3][NBOX];
-    float4 cls[256];            // per edge class: kJ-1, bJ, cE, metal
+    float pex[XS ? STAGES : 1][XS ? PXBOX : 32], phx[XS ? STAGES : 1][XS ? PXBOX : 32];  // psi_E, psi_H, x slab
+    float pey[YS ? STAGES : 1][YS ? PYBOX : 32], phy[YS ? STAGES : 1][YS ? PYBOX : 32];  // ... y slab
+    float en[NEN][NBOX];
+    float4 cls[K ? 1 : 256];    // per edge class: kJ-1, bJ, cE, metal (the slab kinds read it from global)
     float pcE[MAX_CHUNK + 2];   // per plane of the item
     int pzs[MAX_CHUNK + 2];
     unsigned long long bar[STAGES];
     int abort_flag;
 };
-template <bool SLAB>
-constexpr size_t smem_bytes() { return sizeof(Smem<SLAB>) + 128; }  // + alignment slack
+template <int K>
+constexpr size_t smem_bytes() { return sizeof(Smem<K>) + 128; }  // + alignment slack
+static_assert(3 * (smem_bytes<0>() + 1024) <= 233472 && 3 * (smem_bytes<1>() + 1024) <= 233472 &&
+                  3 * (smem_bytes<2>() + 1024) <= 233472,
+              "three blocks of the inner, y-slab and x-slab kinds on one SM");
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -157,16 +172,18 @@ __device__ __forceinline__ void cterm4(float t[4], const V4 &p, float *pout, uns
 }
 __device__ __forceinline__ V4 splat(float x) { return V4{{x, x, x, x}}; }
 
-template <bool SLAB>
-__global__ void __launch_bounds__(NT, SLAB ? 2 : 3)
+template <int K>
+__global__ void __launch_bounds__(NT, K == 3 ? 2 : 3)
     k_fused(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorMap tmH,
             const __grid_constant__ CUtensorMap tmPEx, const __grid_constant__ CUtensorMap tmPHx,
             const __grid_constant__ CUtensorMap tmPEy, const __grid_constant__ CUtensorMap tmPHy, const FusedArgs a) {
+    constexpr bool XS = Smem<K>::XS, YS = Smem<K>::YS, SLAB = K != 0;
+    constexpr int NEN = Smem<K>::NEN;
     pdl_wait();
     extern __shared__ unsigned char raw[];
-    Smem<SLAB> &S = *reinterpret_cast<Smem<SLAB> *>((reinterpret_cast<uintptr_t>(raw) + 127) & ~uintptr_t(127));
+    Smem<K> &S = *reinterpret_cast<Smem<K> *>((reinterpret_cast<uintptr_t>(raw) + 127) & ~uintptr_t(127));
     const Grid<float> &g = a.g;
-    const int nx = g.n[0], ny = g.n[1], nz = g.n[2], L2 = 2 * g.L;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2], L = g.L, L2 = 2 * g.L;
     const int item = blockIdx.x;
     const int packed = a.tiles[item % a.ntiles], chk = item / a.ntiles;
     const int x0 = (packed & 0xffff) * TX, y0 = (packed >> 16) * TY;
@@ -180,25 +197,23 @@ __global__ void __launch_bounds__(NT, SLAB ? 2 : 3)
     const bool inh = xh && gih < nx && gj < ny;
     const unsigned sz = (unsigned)nx * (unsigned)ny;  // cell offsets fit 32 bits on this path
     const unsigned cxy = (unsigned)gj * (unsigned)nx + (unsigned)gi;
+    // slab index of the group along x and y, and of the halo cell along x (-1: none)
     int sx = -1, syb = -1, sxh = -1;
-    if (SLAB) {
-        if (inside) {
-            sx = slab_of(g, 0, gi);  // L % 4 == 0: the group is in an x slab as a whole
-            syb = slab_of(g, 1, gj);
-        }
-        if (inh) sxh = slab_of(g, 0, gih);
-    }
+    if (XS && inside) sx = slab_of(g, 0, gi);  // L % 4 == 0: the group is in an x slab as a whole
+    if (YS && inside) syb = slab_of(g, 1, gj);
+    if (XS && inh) sxh = slab_of(g, 0, gih);
     const float rx = g.r[0], ry = g.r[1], rz = g.r[2], cH = g.cH;
     // held tangential E on the low faces (all axes non-periodic here): Ex at
     // j = 0 or k = 0, Ey at i = 0 or k = 0, Ez at i = 0 or j = 0
     const bool fy = gj == 0, fx0 = gi == 0;
     const int p0 = kz0 - 1, np = kz1 - p0 + 1;  // planes kz0-1 .. kz1
-    // this tile's staged slab memory: x slabs (all 2L columns, rows y0..),
-    // y slabs (slab rows from ys0; index of row gj: its slab index - ys0)
-    const bool xk = SLAB && g.cpml[0] && (x0 < g.L || x0 + TX >= nx - g.L);
-    const bool yk = SLAB && g.cpml[1] && (y0 < g.L || y0 + TY >= ny - g.L);
-    const int ys0 = y0 < g.L ? 0 : y0 - (ny - L2);
-    const unsigned px_b = 2u * EH * L2 * 4u;
+    // the staged slab memory of the one face this tile meets: x slab columns
+    // from compact column xs0, y slab rows from compact row ys0
+    const int xs0 = x0 < L ? 0 : L;
+    const int ys0 = y0 < L ? y0 : max(y0, ny - L) - (ny - L2);
+    const int pyh = min(PYH, L2);                             // rows of a y-slab copy
+    const int pxc = EH * L, pyc = pyh * EW;                   // component strides of the copies
+    const int pxo = lj * L + (sx - xs0), pyo = (syb - ys0) * EW + li;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; s++) mbar_init(&S.bar[s], 1);
@@ -213,25 +228,31 @@ __global__ void __launch_bounds__(NT, SLAB ? 2 : 3)
         S.pcE[q] = (z >= 0 && z < nz) ? a.plane_cE[z] : 0.f;
         S.pzs[q] = (z >= 0 && z < nz) ? slab_of(g, 2, z) : -1;
     }
-    for (int q = threadIdx.x; q < 256; q += NT) S.cls[q] = a.cls_pack[q];
+    if constexpr (K == 0)
+        for (int q = threadIdx.x; q < 256; q += NT) S.cls[q] = a.cls_pack[q];
     __syncthreads();
-    const unsigned stage_bytes = EBOX_B + HBOX_B + (xk ? 2 * px_b : 0u) + (yk ? 2u * PY_B : 0u);
+    auto cls_at = [&](unsigned k) -> float4 {
+        if constexpr (K == 0) return S.cls[k];
+        else return __ldg(a.cls_pack + k);
+    };
+    // bytes one stage receives: the E and H boxes, and per staged slab two
+    // copies (psi_E, psi_H) of two components each
+    const unsigned xbox = 2u * EH * (unsigned)L * 4u, ybox = 2u * (unsigned)pyh * EW * 4u;
+    const unsigned stage_bytes = EBOX_B + HBOX_B + (XS ? 2u * xbox : 0u) + (YS ? 2u * ybox : 0u);
     // plane p0+q into slot s: E^n and H^{n+1/2} of plane z; psi_E of plane
-    // z and psi_H of plane z-1 of the slabs this tile meets
+    // z and psi_H of plane z-1 of the slab this tile meets
     auto issue = [&](int qq, int slot) {
         const int z = p0 + qq;
         mbar_expect(&S.bar[slot], stage_bytes);
         tma_load(S.e[slot], &tmE, x0, y0, z, &S.bar[slot]);
         tma_load(S.h[slot], &tmH, x0 - 4, y0 - 1, z, &S.bar[slot]);
-        if (SLAB) {
-            if (xk) {
-                tma_load(S.pex[slot], &tmPEx, 0, y0, z, &S.bar[slot]);
-                tma_load(S.phx[slot], &tmPHx, 0, y0, z - 1, &S.bar[slot]);
-            }
-            if (yk) {
-                tma_load(S.pey[slot], &tmPEy, x0, ys0, z, &S.bar[slot]);
-                tma_load(S.phy[slot], &tmPHy, x0, ys0, z - 1, &S.bar[slot]);
-            }
+        if constexpr (XS) {
+            tma_load(S.pex[slot], &tmPEx, xs0, y0, z, &S.bar[slot]);
+            tma_load(S.phx[slot], &tmPHx, xs0, y0, z - 1, &S.bar[slot]);
+        }
+        if constexpr (YS) {
+            tma_load(S.pey[slot], &tmPEy, x0, ys0, z, &S.bar[slot]);
+            tma_load(S.phy[slot], &tmPHy, x0, ys0, z - 1, &S.bar[slot]);
         }
     };
     if (threadIdx.x == 0)
@@ -244,7 +265,7 @@ __global__ void __launch_bounds__(NT, SLAB ? 2 : 3)
     const int hoh = (lj + 1) * HW + (TX + 4);  // the halo cell in the H box
     V4 hb[3] = {zero4(), zero4(), zero4()};    // H^{n+1/2} of this group, plane z-1
     V4 ec[3] = {zero4(), zero4(), zero4()};    // E^{n+1} of this group, plane z-1
-    float hbh_x = 0.f, hbh_y = 0.f;            // Hx, Hy of the halo cell, plane z-1
+    float hbh_x = 0.f;                         // Hx of the halo cell, plane z-1
     bool ok = true;
     int q = 0;
     for (; q < np; q++) {
@@ -257,26 +278,26 @@ __global__ void __launch_bounds__(NT, SLAB ? 2 : 3)
         const int szb = S.pzs[q], szh = q > 0 ? S.pzs[q - 1] : -1;
         const unsigned cz = (unsigned)z * sz + cxy, chh = cz - sz;  // this group at planes z and z-1
         // ---- global loads of this iteration, issued before the wait for the
-        // staged plane: CPML memory of both updates, the Drude current and
-        // the edge classes of a material plane
-        V4 pE[6], pH[6];
+        // staged plane: z-slab CPML memory of both updates, the Drude current
+        // and the edge classes of a material plane
+        V4 pEz[2], pHz[2];
         unsigned qEx = 0, qEy = 0, qEz = 0, qHx = 0, qHy = 0, qHz = 0;
         if (doE) {
-            if (SLAB && sx >= 0) qEx = ((unsigned)z * ny + gj) * L2 + sx;
-            if (SLAB && syb >= 0) qEy = ((unsigned)z * L2 + syb) * nx + gi;
+            if (XS && sx >= 0) qEx = ((unsigned)z * ny + gj) * L2 + sx;
+            if (YS && syb >= 0) qEy = ((unsigned)z * L2 + syb) * nx + gi;
             if (szb >= 0) {
                 qEz = (unsigned)szb * sz + cxy;
-                pE[4] = ld4(a.psiEi[2][0] + qEz);
-                pE[5] = ld4(a.psiEi[2][1] + qEz);
+                pEz[0] = ld4(a.psiEi[2][0] + qEz);
+                pEz[1] = ld4(a.psiEi[2][1] + qEz);
             }
         }
         if (doH) {
-            if (SLAB && sx >= 0) qHx = ((unsigned)kh * ny + gj) * L2 + sx;
-            if (SLAB && syb >= 0) qHy = ((unsigned)kh * L2 + syb) * nx + gi;
+            if (XS && sx >= 0) qHx = ((unsigned)kh * ny + gj) * L2 + sx;
+            if (YS && syb >= 0) qHy = ((unsigned)kh * L2 + syb) * nx + gi;
             if (szh >= 0) {
                 qHz = (unsigned)szh * sz + cxy;
-                pH[4] = ld4(a.psiHi[2][0] + qHz);
-                pH[5] = ld4(a.psiHi[2][1] + qHz);
+                pHz[0] = ld4(a.psiHi[2][0] + qHz);
+                pHz[1] = ld4(a.psiHi[2][1] + qHz);
             }
         }
         uchar4 cl[3];
@@ -289,33 +310,19 @@ __global__ void __launch_bounds__(NT, SLAB ? 2 : 3)
             }
         }
         if (!mbar_wait(&S.bar[s], (q / STAGES) & 1)) ok = false;
+        if constexpr (SLAB) {
+            // every thread is done with iteration q-1: its E^{n+1} plane and
+            // its staging slot are free again
+            __syncthreads();
+            if (threadIdx.x == 0 && q >= 1 && q - 1 + STAGES < np) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(q - 1 + STAGES, (q - 1) % STAGES);
+            }
+        }
         const float *e = S.e[s], *h = S.h[s];
-        float *enb = S.en[q % 3];
-        if constexpr (SLAB) {  // the staged x and y slab memory of this group
-            const int ox = lj * L2 + sx, oy = (syb - ys0) * EW + li;
-            if (doE && sx >= 0) {
-                pE[0] = ld4(S.pex[s] + ox);
-                pE[1] = ld4(S.pex[s] + EH * L2 + ox);
-            }
-            if (doE && syb >= 0) {
-                pE[2] = ld4(S.pey[s] + oy);
-                pE[3] = ld4(S.pey[s] + EH * EW + oy);
-            }
-            if (doH && sx >= 0) {
-                pH[0] = ld4(S.phx[s] + ox);
-                pH[1] = ld4(S.phx[s] + EH * L2 + ox);
-            }
-            if (doH && syb >= 0) {
-                pH[2] = ld4(S.phy[s] + oy);
-                pH[3] = ld4(S.phy[s] + EH * EW + oy);
-            }
-        }
+        float *enb = S.en[q % NEN];
         V4 hc[3] = {ld4(h + ho), ld4(h + HC + ho), ld4(h + 2 * HC + ho)};
-        float hch_x = 0.f, hch_y = 0.f;
-        if (xh) {
-            hch_x = h[hoh];
-            hch_y = h[HC + hoh];
-        }
+        const float hch_x = xh ? h[hoh] : 0.f;
         V4 en[3] = {zero4(), zero4(), zero4()};
         if (doE) {
             // ---- E^{n+1} of the group at plane z (Eq. 6, Eq. 8 without J_f)
@@ -342,29 +349,29 @@ __global__ void __launch_bounds__(NT, SLAB ? 2 : 3)
                 uy[m] = !(f0 || z == 0);
                 uz[m] = !(f0 || fy);
             }
-            if (SLAB && sx >= 0) {  // x slab: Ey's d/dx Hz, Ez's d/dx Hy (profiles per cell)
+            if (XS && sx >= 0) {  // x slab: Ey's d/dx Hz, Ez's d/dx Hy (profiles per cell)
                 const V4 bm = ld4(a.bE[0] + gi), aa = ld4(a.aE[0] + gi), ik = ld4(a.ikE[0] + gi);
                 float d3[4], d4[4];
 #pragma unroll
                 for (int m = 0; m < 4; m++) { d3[m] = t[3][m]; d4[m] = t[4][m]; }
-                cterm4(t[3], pE[0], a.psiEo[0][0], qEx, bm, aa, ik, d3, uy, wr);
-                cterm4(t[4], pE[1], a.psiEo[0][1], qEx, bm, aa, ik, d4, uz, wr);
+                cterm4(t[3], ld4(S.pex[s] + pxo), a.psiEo[0][0], qEx, bm, aa, ik, d3, uy, wr);
+                cterm4(t[4], ld4(S.pex[s] + pxc + pxo), a.psiEo[0][1], qEx, bm, aa, ik, d4, uz, wr);
             }
-            if (SLAB && syb >= 0) {  // y slab: Ez's d/dy Hx, Ex's d/dy Hz
+            if (YS && syb >= 0) {  // y slab: Ez's d/dy Hx, Ex's d/dy Hz
                 const V4 bm = splat(a.bE[1][gj]), aa = splat(a.aE[1][gj]), ik = splat(a.ikE[1][gj]);
                 float d5[4], d0[4];
 #pragma unroll
                 for (int m = 0; m < 4; m++) { d5[m] = t[5][m]; d0[m] = t[0][m]; }
-                cterm4(t[5], pE[2], a.psiEo[1][0], qEy, bm, aa, ik, d5, uz, wr);
-                cterm4(t[0], pE[3], a.psiEo[1][1], qEy, bm, aa, ik, d0, ux, wr);
+                cterm4(t[5], ld4(S.pey[s] + pyo), a.psiEo[1][0], qEy, bm, aa, ik, d5, uz, wr);
+                cterm4(t[0], ld4(S.pey[s] + pyc + pyo), a.psiEo[1][1], qEy, bm, aa, ik, d0, ux, wr);
             }
             if (szb >= 0) {  // z slab: Ex's d/dz Hy, Ey's d/dz Hx
                 const V4 bm = splat(a.bE[2][z]), aa = splat(a.aE[2][z]), ik = splat(a.ikE[2][z]);
                 float d1[4], d2[4];
 #pragma unroll
                 for (int m = 0; m < 4; m++) { d1[m] = t[1][m]; d2[m] = t[2][m]; }
-                cterm4(t[1], pE[4], a.psiEo[2][0], qEz, bm, aa, ik, d1, ux, wr);
-                cterm4(t[2], pE[5], a.psiEo[2][1], qEz, bm, aa, ik, d2, uy, wr);
+                cterm4(t[1], pEz[0], a.psiEo[2][0], qEz, bm, aa, ik, d1, ux, wr);
+                cterm4(t[2], pEz[1], a.psiEo[2][1], qEz, bm, aa, ik, d2, uy, wr);
             }
             en[0] = ld4(e + eo);
             en[1] = ld4(e + EC + eo);
@@ -384,7 +391,7 @@ __global__ void __launch_bounds__(NT, SLAB ? 2 : 3)
                     bool metal = false;
 #pragma unroll
                     for (int m = 0; m < 4; m++) {
-                        const float4 tc = S.cls[k4[m]];
+                        const float4 tc = cls_at(k4[m]);
                         const bool up = c == 0 ? ux[m] : (c == 1 ? uy[m] : uz[m]);
                         const float curl = t[2 * c][m] - t[2 * c + 1][m];
                         float jp = 0.f;
@@ -408,15 +415,15 @@ __global__ void __launch_bounds__(NT, SLAB ? 2 : 3)
             float dHy_dx = (hyh - hc[1].v[3]) * rx, dHx_dy = (hxh - hx_jmh) * ry;
             float ty1 = dHx_dz, ty2 = dHz_dx, tz1 = dHy_dx, tz2 = dHx_dy;
             const bool uyh = z != 0, uzh = !fy;
-            if (SLAB && sxh >= 0) {
-                const int ox = lj * L2 + sxh;
+            if (XS && sxh >= 0) {
+                const int ox = lj * L + (sxh - xs0);
                 const float bm = a.bE[0][gih], aa = a.aE[0][gih], ik = a.ikE[0][gih];
                 if (uyh) { const float p = S.pex[s][ox]; ty2 = ik * dHz_dx + (p + (bm * p + aa * dHz_dx)); }
-                if (uzh) { const float p = S.pex[s][EH * L2 + ox]; tz1 = ik * dHy_dx + (p + (bm * p + aa * dHy_dx)); }
+                if (uzh) { const float p = S.pex[s][pxc + ox]; tz1 = ik * dHy_dx + (p + (bm * p + aa * dHy_dx)); }
             }
-            if (SLAB && syb >= 0 && uzh) {
+            if (YS && syb >= 0 && uzh) {
                 const float bm = a.bE[1][gj], aa = a.aE[1][gj], ik = a.ikE[1][gj];
-                const float p = S.pey[s][(syb - ys0) * EW + TX];
+                const float p = S.pey[s][pyo - li + TX];
                 tz2 = ik * dHx_dy + (p + (bm * p + aa * dHx_dy));
             }
             if (szb >= 0 && uyh) {
@@ -430,7 +437,7 @@ __global__ void __launch_bounds__(NT, SLAB ? 2 : 3)
                 if (uyh) eyh += cEu * (ty1 - ty2);
                 if (uzh) ezh += cEu * (tz1 - tz2);
             } else {
-                const float4 ty = S.cls[a.ecls[1][czh]], tz = S.cls[a.ecls[2][czh]];
+                const float4 ty = cls_at(a.ecls[1][czh]), tz = cls_at(a.ecls[2][czh]);
                 if (uyh) {
                     float jp = 0.f;
                     if (ty.w != 0.f) { const float jj = a.Jpi[1][czh]; jp = jj + (ty.x * jj + ty.y * eyh); }
@@ -456,13 +463,15 @@ __global__ void __launch_bounds__(NT, SLAB ? 2 : 3)
         if (!ok) S.abort_flag = 1;
         __syncthreads();
         if (S.abort_flag) break;
-        if (threadIdx.x == 0 && q + STAGES < np) {  // the slot read above is free again
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(q + STAGES, s);
+        if constexpr (!SLAB) {
+            if (threadIdx.x == 0 && q + STAGES < np) {  // the slot read above is free again
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(q + STAGES, s);
+            }
         }
         // ---- H^{n+3/2} of the group at plane kh = z-1 from E^{n+1} of planes kh and kh+1
         if (doH) {
-            const float *bp = S.en[(q + 2) % 3];  // plane kh
+            const float *bp = S.en[(q + NEN - 1) % NEN];  // plane kh
             const float ez_ip = bp[2 * NC + no + 4], ey_ip = bp[NC + no + 4];
             const V4 ez_jp = ld4(bp + 2 * NC + no + XW), ex_jp = ld4(bp + no + XW);
             V4 e1[3] = {en[0], en[1], en[2]};
@@ -479,29 +488,29 @@ __global__ void __launch_bounds__(NT, SLAB ? 2 : 3)
                 t[5][m] = (ex_jp.v[m] - ec[0].v[m]) * ry;   // dEx/dy
             }
             const bool all[4] = {true, true, true, true};
-            if (SLAB && sx >= 0) {  // x slab: Hy's d/dx Ez, Hz's d/dx Ey
+            if (XS && sx >= 0) {  // x slab: Hy's d/dx Ez, Hz's d/dx Ey
                 const V4 bm = ld4(a.bH[0] + gi), aa = ld4(a.aH[0] + gi), ik = ld4(a.ikH[0] + gi);
                 float d3[4], d4[4];
 #pragma unroll
                 for (int m = 0; m < 4; m++) { d3[m] = t[3][m]; d4[m] = t[4][m]; }
-                cterm4(t[3], pH[0], a.psiHo[0][0], qHx, bm, aa, ik, d3, all, true);
-                cterm4(t[4], pH[1], a.psiHo[0][1], qHx, bm, aa, ik, d4, all, true);
+                cterm4(t[3], ld4(S.phx[s] + pxo), a.psiHo[0][0], qHx, bm, aa, ik, d3, all, true);
+                cterm4(t[4], ld4(S.phx[s] + pxc + pxo), a.psiHo[0][1], qHx, bm, aa, ik, d4, all, true);
             }
-            if (SLAB && syb >= 0) {  // y slab: Hz's d/dy Ex, Hx's d/dy Ez
+            if (YS && syb >= 0) {  // y slab: Hz's d/dy Ex, Hx's d/dy Ez
                 const V4 bm = splat(a.bH[1][gj]), aa = splat(a.aH[1][gj]), ik = splat(a.ikH[1][gj]);
                 float d5[4], d0[4];
 #pragma unroll
                 for (int m = 0; m < 4; m++) { d5[m] = t[5][m]; d0[m] = t[0][m]; }
-                cterm4(t[5], pH[2], a.psiHo[1][0], qHy, bm, aa, ik, d5, all, true);
-                cterm4(t[0], pH[3], a.psiHo[1][1], qHy, bm, aa, ik, d0, all, true);
+                cterm4(t[5], ld4(S.phy[s] + pyo), a.psiHo[1][0], qHy, bm, aa, ik, d5, all, true);
+                cterm4(t[0], ld4(S.phy[s] + pyc + pyo), a.psiHo[1][1], qHy, bm, aa, ik, d0, all, true);
             }
             if (szh >= 0) {  // z slab: Hx's d/dz Ey, Hy's d/dz Ex
                 const V4 bm = splat(a.bH[2][kh]), aa = splat(a.aH[2][kh]), ik = splat(a.ikH[2][kh]);
                 float d1[4], d2[4];
 #pragma unroll
                 for (int m = 0; m < 4; m++) { d1[m] = t[1][m]; d2[m] = t[2][m]; }
-                cterm4(t[1], pH[4], a.psiHo[2][0], qHz, bm, aa, ik, d1, all, true);
-                cterm4(t[2], pH[5], a.psiHo[2][1], qHz, bm, aa, ik, d2, all, true);
+                cterm4(t[1], pHz[0], a.psiHo[2][0], qHz, bm, aa, ik, d1, all, true);
+                cterm4(t[2], pHz[1], a.psiHo[2][1], qHz, bm, aa, ik, d2, all, true);
             }
             V4 hn[3];
 #pragma unroll
@@ -522,7 +531,6 @@ __global__ void __launch_bounds__(NT, SLAB ? 2 : 3)
             ec[c] = en[c];
         }
         hbh_x = hch_x;
-        hbh_y = hch_y;
     }
     if (S.abort_flag) {
         if (threadIdx.x == 0) {
@@ -666,6 +674,10 @@ bool psi_map(CUtensorMap *m, float *base, size_t cstride, int d0, int d1, int d2
 bool fused_grid_ok(const Grid<float> &g) {
     if (g.n[0] % 4 != 0 || g.per[0] || g.per[1] || g.per[2]) return false;
     if (g.cpml[0] && g.L % 4 != 0) return false;  // a four-cell group lies in an x slab as a whole or not at all
+    // a tile (with its halo column and row) meets the x or y slab of one face at most
+    if ((g.cpml[0] || g.cpml[1]) && g.L > FUSED_MAX_L) return false;
+    if (g.cpml[0] && g.n[0] <= TX + g.L) return false;
+    if (g.cpml[1] && g.n[1] <= TY + g.L) return false;
     if ((unsigned long long)g.n[0] * g.n[1] * g.n[2] >= (1ull << 32)) return false;  // 32-bit cell offsets
     if (g.n[0] / TX >= 65536 || (g.n[1] + TY - 1) / TY >= 65536) return false;
     return encoder() != nullptr;
@@ -683,10 +695,9 @@ int fused_chunk(int nz, int inner_tiles, int sms) {
     return (int)chunk;
 }
 
-int fused_tiles(const Grid<float> &g, std::vector<int> &inner, std::vector<int> &slab) {
+int fused_tiles(const Grid<float> &g, std::vector<int> kinds[4]) {
     const int tx_n = (g.n[0] + TX - 1) / TX, ty_n = (g.n[1] + TY - 1) / TY;
-    inner.clear();
-    slab.clear();
+    for (int k = 0; k < 4; k++) kinds[k].clear();
     auto touches = [&](int a, int lo, int hi) {  // cells lo..hi (inclusive) meet a slab of axis a
         if (!g.cpml[a]) return false;
         return lo < g.L || hi >= g.n[a] - g.L;
@@ -694,10 +705,10 @@ int fused_tiles(const Grid<float> &g, std::vector<int> &inner, std::vector<int> 
     for (int ty = 0; ty < ty_n; ty++)
         for (int tx = 0; tx < tx_n; tx++) {
             // the tile and the halo row and column it computes E on
-            const bool s = touches(0, tx * TX, tx * TX + TX) || touches(1, ty * TY, ty * TY + TY);
-            (s ? slab : inner).push_back(tx | (ty << 16));
+            const int k = (touches(0, tx * TX, tx * TX + TX) ? 2 : 0) | (touches(1, ty * TY, ty * TY + TY) ? 1 : 0);
+            kinds[k].push_back(tx | (ty << 16));
         }
-    return (int)(inner.size() + slab.size());
+    return tx_n * ty_n;
 }
 
 bool fused_maps(FusedPlan &pl, const FusedBuf P[2], const int n[3], int L, const int cpml[3]) {
@@ -717,45 +728,64 @@ bool fused_maps(FusedPlan &pl, const FusedBuf P[2], const int n[3], int L, const
         if (cpml[0]) {
             const size_t cs = (size_t)((char *)P[b].psiE[0][1] - (char *)P[b].psiE[0][0]);
             const size_t ch = (size_t)((char *)P[b].psiH[0][1] - (char *)P[b].psiH[0][0]);
-            if (cs % 16 || ch % 16 || 2 * L > PX) return false;
-            if (!psi_map(&pl.mapPEx[b], P[b].psiE[0][0], cs, 2 * L, n[1], n[2], 2 * L, EH)) return false;
-            if (!psi_map(&pl.mapPHx[b], P[b].psiH[0][0], ch, 2 * L, n[1], n[2], 2 * L, EH)) return false;
+            if (cs % 16 || ch % 16 || L > PXW || L % 4) return false;
+            if (!psi_map(&pl.mapPEx[b], P[b].psiE[0][0], cs, 2 * L, n[1], n[2], L, EH)) return false;
+            if (!psi_map(&pl.mapPHx[b], P[b].psiH[0][0], ch, 2 * L, n[1], n[2], L, EH)) return false;
         }
         if (cpml[1]) {
             const size_t cs = (size_t)((char *)P[b].psiE[1][1] - (char *)P[b].psiE[1][0]);
             const size_t ch = (size_t)((char *)P[b].psiH[1][1] - (char *)P[b].psiH[1][0]);
-            if (cs % 16 || ch % 16 || 2 * L > EH) return false;
-            if (!psi_map(&pl.mapPEy[b], P[b].psiE[1][0], cs, n[0], 2 * L, n[2], EW, EH)) return false;
-            if (!psi_map(&pl.mapPHy[b], P[b].psiH[1][0], ch, n[0], 2 * L, n[2], EW, EH)) return false;
+            const int rows = 2 * L < PYH ? 2 * L : PYH;
+            if (cs % 16 || ch % 16 || L > PYH) return false;
+            if (!psi_map(&pl.mapPEy[b], P[b].psiE[1][0], cs, n[0], 2 * L, n[2], EW, rows)) return false;
+            if (!psi_map(&pl.mapPHy[b], P[b].psiH[1][0], ch, n[0], 2 * L, n[2], EW, rows)) return false;
         }
     }
     pl.psi_maps = true;
     static std::once_flag once;
     static bool attr_ok = true;
     std::call_once(once, [] {
-        attr_ok = cudaFuncSetAttribute(k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_bytes<false>()) == cudaSuccess &&
-                  cudaFuncSetAttribute(k_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_bytes<true>()) == cudaSuccess;
+        attr_ok = cudaFuncSetAttribute(k_fused<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes<0>()) == cudaSuccess &&
+                  cudaFuncSetAttribute(k_fused<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes<1>()) == cudaSuccess &&
+                  cudaFuncSetAttribute(k_fused<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes<2>()) == cudaSuccess &&
+                  cudaFuncSetAttribute(k_fused<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes<3>()) == cudaSuccess;
     });
     return attr_ok;
 }
 
-void launch_fused_pass(const FusedArgs &base, const FusedPlan &pl, int xbuf, cudaStream_t s, cudaStream_t s2) {
+template <int K>
+static void launch_kind(const FusedArgs &a, const FusedPlan &pl, int xbuf, int items, cudaStream_t s) {
+    launch_pdl(k_fused<K>, dim3((unsigned)items), dim3(NT), smem_bytes<K>(), s, pl.mapE[xbuf], pl.mapH[xbuf],
+               pl.mapPEx[xbuf], pl.mapPHx[xbuf], pl.mapPEy[xbuf], pl.mapPHy[xbuf], a);
+    launch_count() += 1;
+}
+
+void launch_fused_pass(const FusedArgs &base, const FusedPlan &pl, int xbuf, cudaStream_t s,
+                       const cudaStream_t sk[3]) {
+    int first[5] = {0};
+    for (int k = 0; k < 4; k++) first[k + 1] = first[k] + pl.n_kind[k];
     FusedArgs a = base;
-    if (pl.n_inner > 0) {
-        a.tiles = pl.tiles;
-        a.ntiles = pl.n_inner;
-        launch_pdl(k_fused<false>, dim3((unsigned)(pl.n_inner * pl.nchunks)), dim3(NT), smem_bytes<false>(), s,
-                   pl.mapE[xbuf], pl.mapH[xbuf], pl.mapPEx[xbuf], pl.mapPHx[xbuf], pl.mapPEy[xbuf], pl.mapPHy[xbuf], a);
-        launch_count() += 1;
+    // the slab kinds first, each on its own stream (their items take longer,
+    // so their blocks are dispatched before the inner ones), the corner tiles
+    // (two blocks per SM) before the x-slab and y-slab tiles; then the inner
+    // tiles on s
+    for (int k = 3; k >= 1; k--) {
+        if (pl.n_kind[k] == 0) continue;
+        a.tiles = pl.tiles + first[k];
+        a.ntiles = pl.n_kind[k];
+        const int items = pl.n_kind[k] * pl.nchunks;
+        if (k == 1) launch_kind<1>(a, pl, xbuf, items, sk[0]);
+        else if (k == 2) launch_kind<2>(a, pl, xbuf, items, sk[1]);
+        else launch_kind<3>(a, pl, xbuf, items, sk[2]);
     }
-    if (pl.n_slab > 0) {
-        a.tiles = pl.tiles + pl.n_inner;
-        a.ntiles = pl.n_slab;
-        launch_pdl(k_fused<true>, dim3((unsigned)(pl.n_slab * pl.nchunks)), dim3(NT), smem_bytes<true>(), s2,
-                   pl.mapE[xbuf], pl.mapH[xbuf], pl.mapPEx[xbuf], pl.mapPHx[xbuf], pl.mapPEy[xbuf], pl.mapPHy[xbuf], a);
-        launch_count() += 1;
+    if (pl.n_kind[0] > 0) {
+        a.tiles = pl.tiles;
+        a.ntiles = pl.n_kind[0];
+        launch_kind<0>(a, pl, xbuf, pl.n_kind[0] * pl.nchunks, s);
     }
 }
 

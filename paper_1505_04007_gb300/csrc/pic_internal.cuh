@@ -213,20 +213,24 @@ struct FusedPlan {
     // CPML memory of the x and y slabs (both components of a field per map)
     CUtensorMap mapPEx[2], mapPHx[2], mapPEy[2], mapPHy[2];
     bool psi_maps = false;
-    const int *tiles = nullptr;    // device: inner tiles, then tiles meeting an x or y absorbing slab
-    int n_inner = 0, n_slab = 0;
+    // device: the tiles of the four kinds one after another (inner, y slab
+    // only, x slab only, both), n_kind[k] of kind k
+    const int *tiles = nullptr;
+    int n_kind[4] = {0, 0, 0, 0};
     int chunk = 32, nchunks = 1;
 };
 bool fused_grid_ok(const Grid<float> &g);
 // Planes per work item for a grid of nz planes and inner_tiles tiles on a GPU with sms SMs.
 int fused_chunk(int nz, int inner_tiles, int sms);
-// Tile lists of the pass: tiles whose cells and halo row/column stay out of
-// the x and y slabs, and the others.  Returns the tile count.
-int fused_tiles(const Grid<float> &g, std::vector<int> &inner, std::vector<int> &slab);
+// Tile lists of the pass by kind: bit 0 set when the tile (with its halo
+// row) meets a y slab, bit 1 when it (with its halo column) meets an x slab.
+// Returns the tile count.
+int fused_tiles(const Grid<float> &g, std::vector<int> kinds[4]);
 // Tensor maps of both state copies (E, H components equally spaced).
 bool fused_maps(FusedPlan &pl, const FusedBuf P[2], const int n[3], int L, const int cpml[3]);
-// The pass reading copy xbuf's maps: inner tiles on s, slab tiles on s2.
-void launch_fused_pass(const FusedArgs &a, const FusedPlan &pl, int xbuf, cudaStream_t s, cudaStream_t s2);
+// The pass reading copy xbuf's maps: inner tiles on s, the y-slab, x-slab
+// and corner kinds on sk[0], sk[1], sk[2] (launched first).
+void launch_fused_pass(const FusedArgs &a, const FusedPlan &pl, int xbuf, cudaStream_t s, const cudaStream_t sk[3]);
 void launch_jf_clear(const Grid<float> &g, const JfSet &j, int max_tiles, cudaStream_t s);
 void launch_jf_fix(const Grid<float> &g, const FixArgs &f, int max_tiles, cudaStream_t s);
 

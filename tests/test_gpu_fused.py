@@ -3,10 +3,14 @@ over the grid, two copies of the state, the free current added afterwards)
 against the FP64 oracle and against the split FP32 updates.
 
 - Grids of every shape the pass tiles unevenly (x not a multiple of the
-  32-cell tile, y not a multiple of the 8-row tile, z not a multiple of the
-  32-plane chunk), CPML on all six faces or PEC on some, metal planes, two
-  prescribed sources: fields and J_p within 2e-5 of the oracle; the split
-  updates (PIC_FLAG_SPLIT_FIELDS) agree with the fused pass to 1e-5.
+  32-cell tile, y not a multiple of the 15-row tile, z not a multiple of the
+  plane chunk), CPML on all six faces or PEC on some, metal planes, three
+  prescribed sources (two inside the x and y slabs): fields and J_p within
+  2e-5 of the oracle; the split updates (PIC_FLAG_SPLIT_FIELDS) agree with
+  the fused pass to 1e-5.  All four tile kinds run (inner, y slab, x slab,
+  corner).
+- A grid too narrow for the pass's tiles (a tile would meet the slabs of
+  both faces) takes the split updates and keeps parity.
 - Electrons (dense C1 slice): fields, spectra within 2e-5 of the oracle.
 - Reading the state at odd and even step counts (the pass keeps H half a
   step ahead) gives the oracle's E^n, H^{n-1/2}, J_p and the last step's
@@ -63,7 +67,7 @@ def sources_for(w):
             (1, (3, 7, 2, 5, 18, 19), 4e17, 36 * w.dt, 9 * w.dt, 1.2e15)]  # inside the x and y slabs
 
 
-SHAPES = [(64, 24, 40), (36, 21, 45), (100, 25, 70)]
+SHAPES = [(64, 24, 40), (44, 24, 45), (100, 25, 70)]
 BCS = [(W.BC_CPML,) * 6, (W.BC_PEC, W.BC_CPML, W.BC_CPML, W.BC_PEC, W.BC_CPML, W.BC_CPML)]
 
 
@@ -93,6 +97,20 @@ def test_fused_pass_against_oracle_and_split(P, shape, bc):
         jo, jg = o.get_field(6 + c), s.field(P.PIC_JPX + c)
         assert np.linalg.norm(jg - jo) <= 2e-5 * max(np.linalg.norm(jo), 1e-300)
     assert s.stats().device_error == 0
+
+
+@pytest.mark.parametrize("shape", [(36, 30, 40), (64, 21, 40)])
+def test_narrow_grid_takes_the_split_updates(P, shape):
+    w = film_box(*shape)
+    o = O.from_workload(w, with_particles=False, with_probes=False)
+    s = P.Simulation(w, P.PIC_FP32, particles=False, probes=False)
+    assert s.stats().field_path == 0 and s.tuning[3] == 0
+    src = sources_for(w)[0]
+    o.add_source(*src)
+    P.pic_add_source(s.h, *src)
+    o.step(90)
+    s.step(90)
+    assert rel(fields(s.field), fields(o.get_field)) <= 2e-5
 
 
 def test_fused_pass_with_electrons(P):
