@@ -180,8 +180,10 @@ __global__ void __launch_bounds__(NT, K == 3 ? 2 : 3)
     constexpr bool XS = Smem<K>::XS, YS = Smem<K>::YS, SLAB = K != 0;
     constexpr int NEN = Smem<K>::NEN;
     pdl_wait();
-    extern __shared__ unsigned char raw[];
-    Smem<K> &S = *reinterpret_cast<Smem<K> *>((reinterpret_cast<uintptr_t>(raw) + 127) & ~uintptr_t(127));
+    extern __shared__ __align__(128) unsigned char raw[];
+    // 128-byte aligned by pointer arithmetic on raw, so that the accesses
+    // through S stay shared-memory accesses
+    Smem<K> &S = *reinterpret_cast<Smem<K> *>(raw + ((128u - (smem_u32(raw) & 127u)) & 127u));
     const Grid<float> &g = a.g;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], L = g.L, L2 = 2 * g.L;
     const int item = blockIdx.x;
