@@ -260,6 +260,24 @@ def batched_and_sequential(ws, warm, steps, clocks=None, tune=False):
     ms_batch = e0.elapsed_time(e1)
     clk = clocks.stop() if clocks is not None else None
     launches = sum(x.stats().kernel_launches for x in sims) - k0
+    # the fused passes as one joint pass per step against a branch per
+    # instance: the next `steps` steps both ways, joint last
+    joint = None
+    if sum(x.stats().field_path for x in sims) >= 2:
+        ms = {}
+        for j in (0, 1):
+            b.set_joint(j)
+            b.step(64)  # capture under the setting, outside the timed steps
+            b.sync()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(b.stream)
+            b.step(steps)
+            a1.record(b.stream)
+            b.sync()
+            ms[j] = a0.elapsed_time(a1) / steps
+        joint = {"joint_ms_per_step": ms[1], "branches_ms_per_step": ms[0],
+                 "steps": f"branches {before + steps + 64}..{before + 2 * steps + 64}, joint "
+                          f"{before + 2 * steps + 128}..{before + 3 * steps + 128} (64 untimed steps before each)"}
     b.close()
     for x in sims:
         x.close()
@@ -277,7 +295,7 @@ def batched_and_sequential(ws, warm, steps, clocks=None, tune=False):
         x.sync()
         ms_seq += a0.elapsed_time(a1)
         x.close()
-    return ms_batch, ms_seq, launches, clk, ((*rep["best"], rep["best_lanes"]) if rep else None), before
+    return ms_batch, ms_seq, launches, clk, ((*rep["best"], rep["best_lanes"]) if rep else None), before, joint
 
 
 def bench_sweep(args):
@@ -294,21 +312,23 @@ def bench_sweep(args):
     # whole 64-step blocks within the 4000 steps
     steps = max(64, min(args.steps, ws[0].nsteps - warm - tune_steps) // 64 * 64)
     cells = sum(w.ncells for w in ws)
-    ms_batch, ms_seq, launches, clk, tuned, before = batched_and_sequential(ws, warm, steps, ClockSampler(0),
-                                                                            tune=not args.no_tune)
+    ms_batch, ms_seq, launches, clk, tuned, before, joint = batched_and_sequential(ws, warm, steps, ClockSampler(0),
+                                                                                   tune=not args.no_tune)
     value = cells * steps / (ms_batch / 1e3) / 1e9
     seq = cells * steps / (ms_seq / 1e3) / 1e9
     t1 = W.table1(65536)
     t1_steps = 1024
     t1_cells = sum(w.ncells for w in t1)
-    tb, ts, _, _, t1_tuned, t1_before = batched_and_sequential(t1, 128, t1_steps, tune=not args.no_tune)
+    tb, ts, _, _, t1_tuned, t1_before, _ = batched_and_sequential(t1, 128, t1_steps, tune=not args.no_tune)
     line = {"metric": "Gcell-upd/s", "value": value, "unit": "Gcell-upd/s", "n_gpus": 1, "steps": steps,
             "warmup": warm, "ms_per_step": ms_batch / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"sweep: {len(ws)} instances, {cells / 1e6:.1f}M cells in all "
                                    f"(128..320 x 64..128 x 64..96, films 10-60 nm, 10-100 keV, gaps 5-20 nm, "
                                    f"2e4 e- each), steps {before}..{before + steps} of the 4000-step sweep timed",
-                       "parallelism": "one batch graph (one branch per instance)",
+                       "parallelism": ("one batch graph: per step the instances' own work on their own streams "
+                                       "around one joint fused field pass over all of them (four launches)"
+                                       if joint else "one batch graph (one branch per instance)"),
                        "l2": "state larger than the 129 MB L2 (no flush)",
                        "launch_settings": ({"dep_smem_bytes": tuned[0], "sort_every": tuned[1],
                                             "field_block": tuned[2], "field_path": tuned[3],
@@ -319,6 +339,7 @@ def bench_sweep(args):
                            "note": "fresh copies of the same instances over the same step range, each stepped "
                                    "alone (own 64-step graphs), one after another"},
             "batched_vs_sequential": value / seq,
+            "joint_pass": joint,
             "small_grids": {"workload": f"Table 1 series: {len(t1)} quasi-2D films, 2048 x 2 x 82..147 cells "
                                         f"({t1_cells / 1e6:.2f}M in all), 1024 e- each, "
                                         f"steps {t1_before}..{t1_before + t1_steps}",

@@ -339,9 +339,15 @@ int pic_tune(pic_handle *h, int32_t rounds, pic_tune_report *report);
  * stepped together.  The paper has no counterpart; it serves parameter sweeps
  * (films of different thicknesses, bunches of different energies): every
  * whole block of 64 steps of every instance is captured into one CUDA graph,
- * one branch per instance on that instance's own streams, so instances too
- * small to fill the GPU run side by side instead of one after another.  The
- * arithmetic of each instance is exactly that of pic_step. */
+ * so instances too small to fill the GPU share it instead of running one
+ * after another.  Instances whose grids take the fused field pass (two or
+ * more of them, pic_stats.field_path 1) step together: per step, each one's
+ * push, deposit and sources on its own stream, then ONE joint field pass
+ * whose work items (tiles x plane chunks) are those of all of them, launched
+ * once per tile kind, then each one's free-current correction and probe
+ * sample.  The other instances run their blocks as branches of their own on
+ * their own streams.  The arithmetic of each instance is that of pic_step
+ * (see pic_batch_set_joint for the rounding of the joint pass). */
 typedef struct pic_batch pic_batch;
 
 /* Group n handles (not owned; each must outlive the batch and appear once).
@@ -369,6 +375,16 @@ int pic_batch_sync(pic_batch *b);
  * Grids that fill the GPU alone can lose L2 locality when all run at once.
  * Errors: PIC_ERR_ARG. */
 int pic_batch_set_lanes(pic_batch *b, int32_t lanes);
+
+/* joint = 1 (the default): the fused passes of the instances that take one
+ * run as one joint pass per step (above; its work items are runs of 32
+ * planes of a tile column, longer than an instance alone uses, since the
+ * joint pass has items enough to fill the GPU); 0: every instance runs its
+ * blocks as a branch of its own.  The results agree to FP32 rounding (the
+ * joint kernels are compiled separately, and the compiler may contract
+ * products and sums into FMAs differently).  Errors: PIC_ERR_ARG (joint not
+ * 0 or 1). */
+int pic_batch_set_joint(pic_batch *b, int32_t joint);
 
 /* pic_tune for the batch as a whole: each candidate is applied to every
  * instance and timed on whole batch blocks (the box candidates at the first

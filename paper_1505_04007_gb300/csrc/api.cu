@@ -135,6 +135,13 @@ struct SimBase {
     virtual long long cells() const = 0;
     virtual int set_tuning(const pic_tuning &t) = 0;
     virtual bool fused_capable() const = 0;  // the grid takes the fused field pass
+    // joint fused pass of a batch (see Sim::joint_*)
+    virtual bool joint_capable() const = 0;
+    virtual void joint_entry(FusedInst &e, int chunk) const = 0;
+    virtual void joint_items(int inst, int chunk, std::vector<int4> items[4]) const = 0;
+    virtual int fused_chunk_planes() const = 0;
+    virtual long long joint_pre(int s, cudaStream_t from) = 0;
+    virtual long long joint_post(int s, cudaStream_t from) = 0;
     int device = -1;  // CUDA device the handle was created on
 };
 
@@ -212,6 +219,7 @@ struct Sim : SimBase {
     JfSet jfs[2];
     FusedPlan fpl{};
     int *d_tiles = nullptr;
+    std::vector<int> h_tiles;     // host copy of d_tiles
     float *d_plane_cE = nullptr;
 
     cudaGraph_t graph = nullptr;
@@ -521,6 +529,7 @@ struct Sim : SimBase {
                 std::vector<float> pce(n[2]);
                 for (int k = 0; k < n[2]; k++) pce[k] = plane_cls[k] != 255 ? cE[plane_cls[k]] : -1.f;
                 CUDA_TRY(cudaMemcpy(d_tiles, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice));
+                h_tiles = tiles;
                 CUDA_TRY(cudaMemcpy(d_plane_cE, pce.data(), pce.size() * sizeof(float), cudaMemcpyHostToDevice));
                 fpl.tiles = d_tiles;
                 int sms = 0;
@@ -716,15 +725,29 @@ struct Sim : SimBase {
     // One step on the fused path, from the state of step n in copy `par`
     // (= n & 1) to copy par ^ 1, on the main stream: J_f of the step before
     // last back to zero, the electrons' E^n, push and deposit into J_f set
-    // `par`, the prescribed sources; then the fused pass (inner tiles on the
-    // main stream, the three kinds of tiles over the x and y slabs beside
-    // them on aux, aux2, aux3); then
-    // the free-current correction and the probe sample.  (The push runs on
-    // its own before the pass: beside it, its blocks would wait for shared
+    // `par`, the prescribed sources (fused_pre); then the fused pass (inner
+    // tiles on the main stream, the three kinds of tiles over the x and y
+    // slabs beside them on aux, aux2, aux3); then the free-current
+    // correction and the probe sample (fused_post).  (The push runs on its
+    // own before the pass: beside it, its blocks would wait for shared
     // memory the pass holds.)  pe (optional) receives 7 timing events: step
     // start, pass done, push start, push done (= pass start), correction
     // start, correction done, tail done.
     void launch_step_fused(bool sort, int par, cudaEvent_t *pe) {
+        if constexpr (std::is_same<T, float>::value) {
+            fused_pre(sort, par, pe);
+            cudaEventRecord(ev_ef, stream);
+            for (cudaStream_t x : {aux, aux2, aux3}) cudaStreamWaitEvent(x, ev_ef, 0);
+            const cudaStream_t sk[3] = {aux, aux2, aux3};
+            launch_fused_pass(fused_args(par), fpl, par, stream, sk);
+            fork_join(aux, stream, ev_ej);
+            fork_join(aux2, stream, ev_ej2);
+            fork_join(aux3, stream, ev_ej3);
+            if (pe) cudaEventRecord(pe[1], stream);
+            fused_post(par, pe);
+        }
+    }
+    void fused_pre(bool sort, int par, cudaEvent_t *pe) {
         if constexpr (std::is_same<T, float>::value) {
             if (pe) cudaEventRecord(pe[0], stream);
             if (sort) {
@@ -741,9 +764,13 @@ struct Sim : SimBase {
             }
             launch_sources<T>(g, fx, sources.data(), (int)sources.size(), cfg.dt, stream);
             if (pe) cudaEventRecord(pe[3], stream);
-            cudaEventRecord(ev_ef, stream);
-            for (cudaStream_t x : {aux, aux2, aux3}) cudaStreamWaitEvent(x, ev_ef, 0);
-            FusedArgs a{};
+        }
+    }
+    // the arguments of a fused pass reading copy xb and writing copy xb ^ 1
+    FusedArgs fused_args(int xb) const {
+        FusedArgs a{};
+        if constexpr (std::is_same<T, float>::value) {
+            const int yb = xb ^ 1;
             a.g = g;
             for (int c = 0; c < 3; c++) {
                 a.Eo[c] = P[yb].E[c];
@@ -766,12 +793,12 @@ struct Sim : SimBase {
             a.plane_cE = d_plane_cE;
             a.chunk = fpl.chunk;
             a.err = d_err;
-            const cudaStream_t sk[3] = {aux, aux2, aux3};
-            launch_fused_pass(a, fpl, xb, stream, sk);
-            fork_join(aux, stream, ev_ej);
-            fork_join(aux2, stream, ev_ej2);
-            fork_join(aux3, stream, ev_ej3);
-            if (pe) cudaEventRecord(pe[1], stream);
+        }
+        return a;
+    }
+    void fused_post(int par, cudaEvent_t *pe) {
+        if constexpr (std::is_same<T, float>::value) {
+            const int yb = par ^ 1;
             if (pe) cudaEventRecord(pe[4], stream);
             FixArgs fa{};
             for (int c = 0; c < 3; c++) {
@@ -789,6 +816,47 @@ struct Sim : SimBase {
             launch_step_tail<T>(g, view(yb, par ^ 1), pr, d_step, stream);
             if (pe) cudaEventRecord(pe[6], stream);
         }
+    }
+
+    // ---------------------------------------------------- joint fused pass --
+    // In a batch, the fused passes of every instance that takes one run as a
+    // single joint pass per step; each instance contributes its steps' work
+    // before and after the pass, its table entry and its work items.
+    bool joint_capable() const override { return fused && use_fused && fused_ready; }
+    // (the joint pass has enough items to cut columns into fewer, longer
+    // runs of planes than the instance alone: `chunk` planes per item)
+    void joint_entry(FusedInst &e, int chunk) const override {
+        for (int xb = 0; xb < 2; xb++) {
+            e.maps[xb] = fpl.maps[xb];
+            e.a[xb] = fused_args(xb);
+            e.a[xb].chunk = chunk;
+        }
+        e.par0 = (int)(step_host & 1);
+    }
+    void joint_items(int inst, int chunk, std::vector<int4> items[4]) const override {
+        const int nch = (n[2] + chunk - 1) / chunk;
+        for (int k = 0, first = 0; k < 4; first += fpl.n_kind[k], k++)
+            for (int c = 0; c < nch; c++)  // tile-major within each chunk, as a single pass orders them
+                for (int t = 0; t < fpl.n_kind[k]; t++) items[k].push_back(make_int4(inst, h_tiles[first + t], c, 0));
+    }
+    int fused_chunk_planes() const override { return fpl.chunk; }
+    // step s of a joint block: the work before the pass, forked from `from`
+    long long joint_pre(int s, cudaStream_t from) override {
+        const long long before = launch_count();
+        cudaEventRecord(ev_bfork, from);
+        cudaStreamWaitEvent(stream, ev_bfork, 0);
+        const int par = (int)((step_host + s) & 1);
+        fused_pre(s % sort_every == 0, par, nullptr);
+        return launch_count() - before;
+    }
+    // ... and after it (the DFT flush after the block's last step)
+    long long joint_post(int s, cudaStream_t from) override {
+        const long long before = launch_count();
+        cudaEventRecord(ev_bfork, from);
+        cudaStreamWaitEvent(stream, ev_bfork, 0);
+        fused_post((int)((step_host + s) & 1), nullptr);
+        if (s == DFT_BLOCK - 1) launch_dft_flush<T>(pr, d_step, DFT_BLOCK, stream);
+        return launch_count() - before;
     }
 
     // ------------------------------------------------------------ batch --
@@ -1955,6 +2023,12 @@ struct pic_batch {
     cudaGraphExec_t exec = nullptr;
     std::vector<long long> epochs, kernels;
     int lanes = 0;  // instances that run side by side; 0: all of them
+    bool joint = true;  // the fused passes of the instances that take one run as one joint pass per step
+    int joint_chunk = 32;  // planes per work item of the joint pass (0: each instance's own)
+    cudaStream_t jaux[3] = {nullptr, nullptr, nullptr};  // slab kinds of the joint pass
+    FusedInst *d_tab = nullptr;
+    int4 *d_items = nullptr;
+    size_t tab_cap = 0, items_cap = 0;
 
     void drop() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -1968,17 +2042,71 @@ struct pic_batch {
             if (h[i]->sim->graph_epoch() != epochs[i]) return true;
         return false;
     }
+    // The joint pass's tables for the instances J (before the capture; the
+    // previous batch graph may still read the old ones).
+    int joint_tables(const std::vector<int> &J, FusedJoint &jt) {
+        std::vector<FusedInst> tab(J.size());
+        std::vector<int4> items[4];
+        for (size_t q = 0; q < J.size(); q++) {
+            const int chunk = joint_chunk > 0 ? joint_chunk : h[J[q]]->sim->fused_chunk_planes();
+            h[J[q]]->sim->joint_entry(tab[q], chunk);
+            h[J[q]]->sim->joint_items((int)q, chunk, items);
+        }
+        size_t nitems = 0;
+        for (auto &v : items) nitems += v.size();
+        CUDA_TRY(cudaStreamSynchronize(stream));
+        if (tab.size() > tab_cap) {
+            if (d_tab) cudaFree(d_tab);
+            d_tab = nullptr;
+            tab_cap = 0;
+            CUDA_TRY(cudaMalloc(&d_tab, tab.size() * sizeof(FusedInst)));
+            tab_cap = tab.size();
+        }
+        if (nitems > items_cap) {
+            if (d_items) cudaFree(d_items);
+            d_items = nullptr;
+            items_cap = 0;
+            CUDA_TRY(cudaMalloc(&d_items, nitems * sizeof(int4)));
+            items_cap = nitems;
+        }
+        CUDA_TRY(cudaMemcpy(d_tab, tab.data(), tab.size() * sizeof(FusedInst), cudaMemcpyHostToDevice));
+        size_t off = 0;
+        jt = FusedJoint{};
+        jt.tab = d_tab;
+        for (int k = 0; k < 4; k++) {
+            if (!items[k].empty())
+                CUDA_TRY(cudaMemcpy(d_items + off, items[k].data(), items[k].size() * sizeof(int4),
+                                    cudaMemcpyHostToDevice));
+            jt.items[k] = d_items + off;
+            jt.nitems[k] = (int)items[k].size();
+            off += items[k].size();
+        }
+        return PIC_OK;
+    }
     int capture() {
         drop();
+        // Instances whose fused pass joins the joint pass (J, two or more)
+        // and the others (R), which run whole blocks of their own.
+        std::vector<int> J, R;
+        for (size_t i = 0; i < h.size(); i++) (joint && h[i]->sim->joint_capable() ? J : R).push_back((int)i);
+        if (J.size() < 2) {
+            R.insert(R.end(), J.begin(), J.end());
+            J.clear();
+        }
+        FusedJoint jt{};
+        if (!J.empty()) {
+            const int rc = joint_tables(J, jt);
+            if (rc) return rc;
+        }
+        const long long count0 = launch_count();
         CUDA_TRY(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
-        // Instances are dealt to `lanes` chains (largest first, each to the
-        // chain with the fewest cells so far); the chains fork from the start
-        // of the capture, and within a chain each instance's block starts when
-        // the one before it has finished.  One chain per instance: every
+        // The instances of R are dealt to `lanes` chains (largest first, each
+        // to the chain with the fewest cells so far); the chains fork from the
+        // start of the capture, and within a chain each instance's block starts
+        // when the one before it has finished.  One chain per instance: every
         // instance runs beside every other.
-        const int nl = (lanes <= 0 || lanes >= (int)h.size()) ? (int)h.size() : lanes;
-        std::vector<int> order(h.size());
-        for (size_t i = 0; i < h.size(); i++) order[i] = (int)i;
+        const int nl = (lanes <= 0 || lanes >= (int)R.size()) ? (int)R.size() : lanes;
+        std::vector<int> order(R);
         std::stable_sort(order.begin(), order.end(),
                          [&](int a, int b) { return h[a]->sim->cells() > h[b]->sim->cells(); });
         std::vector<long long> load(nl, 0);
@@ -1989,7 +2117,28 @@ struct pic_batch {
             tail[l] = h[i]->sim->main_stream();
             load[l] += h[i]->sim->cells();
         }
-        for (size_t i = 0; i < h.size(); i++) h[i]->sim->join_to(stream);
+        // The instances of J step together: per step, each one's work before
+        // the pass on its own stream, then one joint pass over all of them,
+        // then each one's work after it.
+        for (int i : J) kernels[i] = 0;
+        for (int st = 0; st < DFT_BLOCK && !J.empty(); st++) {
+            for (int i : J) kernels[i] += h[i]->sim->joint_pre(st, stream);
+            for (int i : J) h[i]->sim->join_to(stream);
+            jt.phase = st & 1;
+            cudaEventRecord(ev, stream);
+            for (cudaStream_t x : jaux) cudaStreamWaitEvent(x, ev, 0);
+            const long long k0 = launch_count();
+            launch_fused_joint(jt, stream, jaux);
+            kernels[J[0]] += launch_count() - k0;  // the joint pass is counted on the first instance
+            for (cudaStream_t x : jaux) {
+                cudaEventRecord(ev, x);
+                cudaStreamWaitEvent(stream, ev, 0);
+            }
+            for (int i : J) kernels[i] += h[i]->sim->joint_post(st, stream);
+            for (int i : J) h[i]->sim->join_to(stream);
+        }
+        for (int i : R) h[i]->sim->join_to(stream);
+        launch_count() = count0;  // captured, not launched
         cudaError_t e = cudaStreamEndCapture(stream, &graph);
         if (e != cudaSuccess) { graph = nullptr; return fail(PIC_ERR_CUDA, "batch graph capture: %s", cudaGetErrorString(e)); }
         e = cudaGraphInstantiate(&exec, graph, 0);
@@ -2207,6 +2356,10 @@ struct pic_batch {
         if (stream) cudaStreamSynchronize(stream);
         drop();
         if (ev) cudaEventDestroy(ev);
+        for (cudaStream_t x : jaux)
+            if (x) cudaStreamDestroy(x);
+        if (d_tab) cudaFree(d_tab);
+        if (d_items) cudaFree(d_items);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -2239,6 +2392,7 @@ int pic_batch_create(int n, pic_handle *const *handles, void *stream, pic_batch 
         b->own_stream = true;
     }
     CUDA_TRY(cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming));
+    for (cudaStream_t &x : b->jaux) CUDA_TRY(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
     *out = b.release();
     return PIC_OK;
 }
@@ -2256,6 +2410,17 @@ int pic_batch_set_lanes(pic_batch *b, int32_t lanes) {
     if (lanes < 0) return fail(PIC_ERR_ARG, "lanes must be >= 0");
     if (lanes != b->lanes) {
         b->lanes = lanes;
+        b->drop();
+    }
+    return PIC_OK;
+}
+
+int pic_batch_set_joint(pic_batch *b, int32_t joint) {
+    g_err.clear();
+    if (!b) return fail(PIC_ERR_ARG, "NULL batch");
+    if (joint != 0 && joint != 1) return fail(PIC_ERR_ARG, "joint must be 0 or 1");
+    if ((joint != 0) != b->joint) {
+        b->joint = joint != 0;
         b->drop();
     }
     return PIC_OK;

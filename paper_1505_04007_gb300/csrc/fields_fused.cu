@@ -43,6 +43,7 @@
 #include <cuda.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "pic_internal.cuh"
 
@@ -73,7 +74,7 @@ constexpr int PXW = FUSED_MAX_L, PYH = FUSED_MAX_L;
 constexpr int PXBOX = 2 * EH * PXW, PYBOX = 2 * PYH * EW;  // floats (multiples of 32)
 static_assert(PXBOX % 32 == 0 && PYBOX % 32 == 0, "128-byte aligned slots");
 
-template <int K>
+template <int K, bool J>
 struct __align__(128) Smem {
     static constexpr bool XS = (K & 2) != 0, YS = (K & 1) != 0;
     static constexpr int NEN = K ? 2 : 3;  // E^{n+1} planes in the ring
@@ -87,14 +88,24 @@ struct __align__(128) Smem {
     int pzs[MAX_CHUNK + 2];
     unsigned long long bar[STAGES];
     int abort_flag;
+    typename std::conditional<J, FusedArgs, int>::type args;  // a joint pass: the item's instance
 };
-template <int K>
-constexpr size_t smem_bytes() { return sizeof(Smem<K>) + 128; }  // + alignment slack
-static_assert(3 * (smem_bytes<0>() + 1024) <= 233472 && 3 * (smem_bytes<1>() + 1024) <= 233472 &&
-                  3 * (smem_bytes<2>() + 1024) <= 233472,
+template <int K, bool J>
+constexpr size_t smem_bytes() { return sizeof(Smem<K, J>) + 128; }  // + alignment slack
+static_assert(3 * (smem_bytes<0, true>() + 1024) <= 233472 && 3 * (smem_bytes<1, true>() + 1024) <= 233472 &&
+                  3 * (smem_bytes<2, true>() + 1024) <= 233472,
               "three blocks of the inner, y-slab and x-slab kinds on one SM");
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// The block's shared memory as Smem<K, J>, 128-byte aligned by pointer
+// arithmetic on the dynamic array, so that accesses through it stay
+// shared-memory accesses.
+template <int K, bool J>
+__device__ __forceinline__ Smem<K, J> &smem_of() {
+    extern __shared__ __align__(128) unsigned char raw[];
+    return *reinterpret_cast<Smem<K, J> *>(raw + ((128u - (smem_u32(raw) & 127u)) & 127u));
+}
 
 __device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
@@ -172,22 +183,16 @@ __device__ __forceinline__ void cterm4(float t[4], const V4 &p, float *pout, uns
 }
 __device__ __forceinline__ V4 splat(float x) { return V4{{x, x, x, x}}; }
 
-template <int K>
-__global__ void __launch_bounds__(NT, K == 3 ? 2 : 3)
-    k_fused(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorMap tmH,
-            const __grid_constant__ CUtensorMap tmPEx, const __grid_constant__ CUtensorMap tmPHx,
-            const __grid_constant__ CUtensorMap tmPEy, const __grid_constant__ CUtensorMap tmPHy, const FusedArgs a) {
-    constexpr bool XS = Smem<K>::XS, YS = Smem<K>::YS, SLAB = K != 0;
-    constexpr int NEN = Smem<K>::NEN;
-    pdl_wait();
-    extern __shared__ __align__(128) unsigned char raw[];
-    // 128-byte aligned by pointer arithmetic on raw, so that the accesses
-    // through S stay shared-memory accesses
-    Smem<K> &S = *reinterpret_cast<Smem<K> *>(raw + ((128u - (smem_u32(raw) & 127u)) & 127u));
+// One work item of kind K: the tile `packed` over plane chunk `chk` of the
+// instance with arguments a and tensor maps tm (E, H, psi_E x, psi_H x,
+// psi_E y, psi_H y).  J: a joint pass (a lives in shared memory).
+template <int K, bool J>
+__device__ __forceinline__ void fused_item(const FusedArgs &a, const CUtensorMap *tm, int packed, int chk) {
+    constexpr bool XS = Smem<K, J>::XS, YS = Smem<K, J>::YS, SLAB = K != 0;
+    constexpr int NEN = Smem<K, J>::NEN;
+    Smem<K, J> &S = smem_of<K, J>();
     const Grid<float> &g = a.g;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], L = g.L, L2 = 2 * g.L;
-    const int item = blockIdx.x;
-    const int packed = a.tiles[item % a.ntiles], chk = item / a.ntiles;
     const int x0 = (packed & 0xffff) * TX, y0 = (packed >> 16) * TY;
     const int kz0 = chk * a.chunk, kz1 = min(nz, kz0 + a.chunk);
     const int lj = threadIdx.x / TPR, gx = threadIdx.x % TPR;  // row (TY: the halo row) and x group
@@ -246,15 +251,15 @@ __global__ void __launch_bounds__(NT, K == 3 ? 2 : 3)
     auto issue = [&](int qq, int slot) {
         const int z = p0 + qq;
         mbar_expect(&S.bar[slot], stage_bytes);
-        tma_load(S.e[slot], &tmE, x0, y0, z, &S.bar[slot]);
-        tma_load(S.h[slot], &tmH, x0 - 4, y0 - 1, z, &S.bar[slot]);
+        tma_load(S.e[slot], &tm[0], x0, y0, z, &S.bar[slot]);
+        tma_load(S.h[slot], &tm[1], x0 - 4, y0 - 1, z, &S.bar[slot]);
         if constexpr (XS) {
-            tma_load(S.pex[slot], &tmPEx, xs0, y0, z, &S.bar[slot]);
-            tma_load(S.phx[slot], &tmPHx, xs0, y0, z - 1, &S.bar[slot]);
+            tma_load(S.pex[slot], &tm[2], xs0, y0, z, &S.bar[slot]);
+            tma_load(S.phx[slot], &tm[3], xs0, y0, z - 1, &S.bar[slot]);
         }
         if constexpr (YS) {
-            tma_load(S.pey[slot], &tmPEy, x0, ys0, z, &S.bar[slot]);
-            tma_load(S.phy[slot], &tmPHy, x0, ys0, z - 1, &S.bar[slot]);
+            tma_load(S.pey[slot], &tm[4], x0, ys0, z, &S.bar[slot]);
+            tma_load(S.phy[slot], &tm[5], x0, ys0, z - 1, &S.bar[slot]);
         }
     };
     if (threadIdx.x == 0)
@@ -547,6 +552,35 @@ __global__ void __launch_bounds__(NT, K == 3 ? 2 : 3)
     }
 }
 
+template <int K>
+__global__ void __launch_bounds__(NT, K == 3 ? 2 : 3)
+    k_fused(const __grid_constant__ FusedMaps maps, const __grid_constant__ FusedArgs a) {
+    pdl_wait();
+    fused_item<K, false>(a, maps.m, a.tiles[blockIdx.x % a.ntiles], (int)blockIdx.x / a.ntiles);
+}
+
+// A joint pass: item blockIdx.x of kind K of any instance; the instance's
+// arguments are copied into shared memory, its maps read from the table
+// (the host wrote them before the launch).
+template <int K>
+__global__ void __launch_bounds__(NT, K == 3 ? 2 : 3) k_fused_joint(const __grid_constant__ FusedJoint jt) {
+    pdl_wait();
+    Smem<K, true> &S = smem_of<K, true>();
+    const int4 e = jt.items[K][blockIdx.x];
+    const FusedInst &in = jt.tab[e.x];
+    const int xb = in.par0 ^ jt.phase;
+    const int4 *src = reinterpret_cast<const int4 *>(&in.a[xb]);
+    int4 *dst = reinterpret_cast<int4 *>(&S.args);
+    static_assert(sizeof(FusedArgs) % 16 == 0, "arguments copied in 16-byte pieces");
+    for (int w = threadIdx.x; w < (int)(sizeof(FusedArgs) / 16); w += NT) dst[w] = src[w];
+    const CUtensorMap *tm = in.maps[xb].m;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 6; q++)
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&tm[q]) : "memory");
+    __syncthreads();
+    fused_item<K, true>(S.args, tm, e.y, e.z);
+}
+
 // J_f of the listed tiles back to zero (the current of two steps ago).
 __global__ void __launch_bounds__(TILE_X *TILE_Y *TILE_Z) k_jf_clear(Grid<float> g, JfSet j) {
     pdl_wait();
@@ -715,54 +749,53 @@ int fused_tiles(const Grid<float> &g, std::vector<int> kinds[4]) {
 
 bool fused_maps(FusedPlan &pl, const FusedBuf P[2], const int n[3], int L, const int cpml[3]) {
     for (int b = 0; b < 2; b++) {
+        CUtensorMap *m = pl.maps[b].m;
         const size_t se = (size_t)((char *)P[b].E[1] - (char *)P[b].E[0]);
         const size_t sh = (size_t)((char *)P[b].H[1] - (char *)P[b].H[0]);
         if ((char *)P[b].E[2] - (char *)P[b].E[1] != (long)se || (char *)P[b].H[2] - (char *)P[b].H[1] != (long)sh)
             return false;
         if (se % 16 || sh % 16 || ((uintptr_t)P[b].E[0] & 15) || ((uintptr_t)P[b].H[0] & 15)) return false;
-        if (!field_map(&pl.mapE[b], P[b].E[0], se, n, EW, EH)) return false;
-        if (!field_map(&pl.mapH[b], P[b].H[0], sh, n, HW, HH)) return false;
+        if (!field_map(&m[0], P[b].E[0], se, n, EW, EH)) return false;
+        if (!field_map(&m[1], P[b].H[0], sh, n, HW, HH)) return false;
         // x and y slab memory (the maps of an axis without slabs stay unused)
-        pl.mapPEx[b] = pl.mapH[b];
-        pl.mapPHx[b] = pl.mapH[b];
-        pl.mapPEy[b] = pl.mapH[b];
-        pl.mapPHy[b] = pl.mapH[b];
+        for (int q = 2; q < 6; q++) m[q] = m[1];
         if (cpml[0]) {
             const size_t cs = (size_t)((char *)P[b].psiE[0][1] - (char *)P[b].psiE[0][0]);
             const size_t ch = (size_t)((char *)P[b].psiH[0][1] - (char *)P[b].psiH[0][0]);
             if (cs % 16 || ch % 16 || L > PXW || L % 4) return false;
-            if (!psi_map(&pl.mapPEx[b], P[b].psiE[0][0], cs, 2 * L, n[1], n[2], L, EH)) return false;
-            if (!psi_map(&pl.mapPHx[b], P[b].psiH[0][0], ch, 2 * L, n[1], n[2], L, EH)) return false;
+            if (!psi_map(&m[2], P[b].psiE[0][0], cs, 2 * L, n[1], n[2], L, EH)) return false;
+            if (!psi_map(&m[3], P[b].psiH[0][0], ch, 2 * L, n[1], n[2], L, EH)) return false;
         }
         if (cpml[1]) {
             const size_t cs = (size_t)((char *)P[b].psiE[1][1] - (char *)P[b].psiE[1][0]);
             const size_t ch = (size_t)((char *)P[b].psiH[1][1] - (char *)P[b].psiH[1][0]);
             const int rows = 2 * L < PYH ? 2 * L : PYH;
             if (cs % 16 || ch % 16 || L > PYH) return false;
-            if (!psi_map(&pl.mapPEy[b], P[b].psiE[1][0], cs, n[0], 2 * L, n[2], EW, rows)) return false;
-            if (!psi_map(&pl.mapPHy[b], P[b].psiH[1][0], ch, n[0], 2 * L, n[2], EW, rows)) return false;
+            if (!psi_map(&m[4], P[b].psiE[1][0], cs, n[0], 2 * L, n[2], EW, rows)) return false;
+            if (!psi_map(&m[5], P[b].psiH[1][0], ch, n[0], 2 * L, n[2], EW, rows)) return false;
         }
     }
-    pl.psi_maps = true;
     static std::once_flag once;
     static bool attr_ok = true;
     std::call_once(once, [] {
-        attr_ok = cudaFuncSetAttribute(k_fused<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_bytes<0>()) == cudaSuccess &&
-                  cudaFuncSetAttribute(k_fused<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_bytes<1>()) == cudaSuccess &&
-                  cudaFuncSetAttribute(k_fused<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_bytes<2>()) == cudaSuccess &&
-                  cudaFuncSetAttribute(k_fused<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_bytes<3>()) == cudaSuccess;
+        auto set = [](const void *k, size_t bytes) {
+            return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
+        };
+        attr_ok = set((const void *)k_fused<0>, smem_bytes<0, false>()) &&
+                  set((const void *)k_fused<1>, smem_bytes<1, false>()) &&
+                  set((const void *)k_fused<2>, smem_bytes<2, false>()) &&
+                  set((const void *)k_fused<3>, smem_bytes<3, false>()) &&
+                  set((const void *)k_fused_joint<0>, smem_bytes<0, true>()) &&
+                  set((const void *)k_fused_joint<1>, smem_bytes<1, true>()) &&
+                  set((const void *)k_fused_joint<2>, smem_bytes<2, true>()) &&
+                  set((const void *)k_fused_joint<3>, smem_bytes<3, true>());
     });
     return attr_ok;
 }
 
 template <int K>
 static void launch_kind(const FusedArgs &a, const FusedPlan &pl, int xbuf, int items, cudaStream_t s) {
-    launch_pdl(k_fused<K>, dim3((unsigned)items), dim3(NT), smem_bytes<K>(), s, pl.mapE[xbuf], pl.mapH[xbuf],
-               pl.mapPEx[xbuf], pl.mapPHx[xbuf], pl.mapPEy[xbuf], pl.mapPHy[xbuf], a);
+    launch_pdl(k_fused<K>, dim3((unsigned)items), dim3(NT), smem_bytes<K, false>(), s, pl.maps[xbuf], a);
     launch_count() += 1;
 }
 
@@ -789,6 +822,20 @@ void launch_fused_pass(const FusedArgs &base, const FusedPlan &pl, int xbuf, cud
         a.ntiles = pl.n_kind[0];
         launch_kind<0>(a, pl, xbuf, pl.n_kind[0] * pl.nchunks, s);
     }
+}
+
+template <int K>
+static void launch_joint_kind(const FusedJoint &jt, cudaStream_t s) {
+    if (jt.nitems[K] == 0) return;
+    launch_pdl(k_fused_joint<K>, dim3((unsigned)jt.nitems[K]), dim3(NT), smem_bytes<K, true>(), s, jt);
+    launch_count() += 1;
+}
+
+void launch_fused_joint(const FusedJoint &jt, cudaStream_t s, const cudaStream_t sk[3]) {
+    launch_joint_kind<3>(jt, sk[2]);  // the slab kinds first, as for a single instance
+    launch_joint_kind<2>(jt, sk[1]);
+    launch_joint_kind<1>(jt, sk[0]);
+    launch_joint_kind<0>(jt, s);
 }
 
 void launch_jf_clear(const Grid<float> &g, const JfSet &j, int max_tiles, cudaStream_t s) {

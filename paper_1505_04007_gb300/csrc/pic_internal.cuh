@@ -201,6 +201,27 @@ struct FusedArgs {
     int ntiles, chunk;             // tiles of this launch; planes per work item
     int *err;
 };
+// The six tensor maps of one input copy: E, H, and the x and y slab CPML
+// memory (psi_E x, psi_H x, psi_E y, psi_H y).
+struct FusedMaps {
+    CUtensorMap m[6];
+};
+// One instance of a joint pass over several simulations (a device table
+// entry): maps and arguments for reading copy 0 and copy 1; at phase p the
+// pass reads copy par0 ^ p.
+struct FusedInst {
+    FusedMaps maps[2];
+    FusedArgs a[2];
+    int par0;
+};
+// A joint pass: the instance table and, per tile kind, the work items
+// {instance, packed tile, chunk, 0} of every instance.
+struct FusedJoint {
+    const FusedInst *tab;
+    const int4 *items[4];
+    int nitems[4];
+    int phase;
+};
 struct FixArgs {
     float *E[3], *H[3], *psiH[3][2];  // state at n+1 (corrected in place)
     JfSet jf;                         // this step's free current
@@ -209,10 +230,7 @@ struct FixArgs {
     const float *aH[3], *ikH[3];
 };
 struct FusedPlan {
-    CUtensorMap mapE[2], mapH[2];  // E and H of state copy 0 and 1
-    // CPML memory of the x and y slabs (both components of a field per map)
-    CUtensorMap mapPEx[2], mapPHx[2], mapPEy[2], mapPHy[2];
-    bool psi_maps = false;
+    FusedMaps maps[2];             // reading state copy 0 and 1
     // device: the tiles of the four kinds one after another (inner, y slab
     // only, x slab only, both), n_kind[k] of kind k
     const int *tiles = nullptr;
@@ -231,6 +249,9 @@ bool fused_maps(FusedPlan &pl, const FusedBuf P[2], const int n[3], int L, const
 // The pass reading copy xbuf's maps: inner tiles on s, the y-slab, x-slab
 // and corner kinds on sk[0], sk[1], sk[2] (launched first).
 void launch_fused_pass(const FusedArgs &a, const FusedPlan &pl, int xbuf, cudaStream_t s, const cudaStream_t sk[3]);
+// A joint pass (phase jt.phase) over the instances of jt: inner items on s,
+// the y-slab, x-slab and corner kinds on sk[0], sk[1], sk[2] (launched first).
+void launch_fused_joint(const FusedJoint &jt, cudaStream_t s, const cudaStream_t sk[3]);
 void launch_jf_clear(const Grid<float> &g, const JfSet &j, int max_tiles, cudaStream_t s);
 void launch_jf_fix(const Grid<float> &g, const FixArgs &f, int max_tiles, cudaStream_t s);
 

@@ -33,7 +33,7 @@ EXPORTS = ("pic_last_error", "pic_workspace_size", "pic_create", "pic_destroy", 
            "pic_step", "pic_sync", "pic_probe_read", "pic_get_field", "pic_set_field", "pic_get_stats",
            "pic_save", "pic_load", "pic_profile_steps", "pic_dft_fold_static", "pic_batch_create",
            "pic_batch_step", "pic_batch_sync", "pic_batch_destroy", "pic_probe_kw", "pic_get_tuning",
-           "pic_set_tuning", "pic_tune", "pic_batch_tune", "pic_batch_set_lanes")
+           "pic_set_tuning", "pic_tune", "pic_batch_tune", "pic_batch_set_lanes", "pic_batch_set_joint")
 
 
 class pic_material(C.Structure):
@@ -117,6 +117,7 @@ def load(path: str | None = None):
     L.pic_tune.argtypes = [h, C.c_int32, C.POINTER(pic_tune_report)]
     L.pic_batch_tune.argtypes = [h, C.c_int32, C.POINTER(pic_tune_report)]
     L.pic_batch_set_lanes.argtypes = [h, C.c_int32]
+    L.pic_batch_set_joint.argtypes = [h, C.c_int32]
     L.pic_save.argtypes = [h, C.c_char_p]
     L.pic_load.argtypes = [h, C.c_char_p]
     L.pic_dft_fold_static.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_uint32, C.c_void_p, C.c_int,
@@ -277,6 +278,10 @@ def _report(r: pic_tune_report) -> dict:
 
 def pic_batch_set_lanes(b, lanes: int) -> None:
     _check(load().pic_batch_set_lanes(b, int(lanes)), "pic_batch_set_lanes")
+
+
+def pic_batch_set_joint(b, joint: int) -> None:
+    _check(load().pic_batch_set_joint(b, int(joint)), "pic_batch_set_joint")
 
 
 def pic_tune(h, rounds: int = 1) -> dict:
@@ -479,6 +484,11 @@ class Batch:
 
     def set_lanes(self, lanes):
         pic_batch_set_lanes(self.b, lanes)
+
+    def set_joint(self, joint):
+        """1: one joint fused field pass per step over the instances that take
+        the fused pass; 0: every instance on a branch of its own."""
+        pic_batch_set_joint(self.b, int(joint))
 
     def close(self):
         if getattr(self, "b", None):

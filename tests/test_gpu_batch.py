@@ -87,3 +87,64 @@ def test_batch_recaptures_after_change(P):
         o.step(128)
         check(o, s, 2e-5)
     b.close()
+
+
+def sources_for(w):
+    c = (w.nx // 2, w.ny // 2, w.nz // 2)
+    return [(2, (c[0], c[0] + 1, c[1], c[1] + 1, c[2], c[2] + 1), 1e18, 30 * w.dt, 8 * w.dt, 0.0),
+            (1, (4, 9, 3, 6, c[2] - 2, c[2] - 1), 4e17, 36 * w.dt, 9 * w.dt, 1.2e15)]  # inside the x and y slabs
+
+
+def test_joint_pass_equals_separate_branches(P):
+    """FP32 instances that take the fused pass step through ONE joint field
+    pass per step (pic_batch_set_joint 1, the default); the same instances as
+    separate branches (0) give the same fields up to FP32 rounding (the joint
+    kernels are compiled separately, and the compiler may contract a product
+    and a sum into one FMA differently: rel-L2 <= 1e-6 between the two), and
+    both match the oracle."""
+    ws = W.sweep(n=3, seed=11, nsteps=128, **SMALL)
+    runs = []
+    for joint in (1, 0):
+        sims = [P.Simulation(w, P.PIC_FP32, particles=False) for w in ws]
+        for w, s in zip(ws, sims):
+            assert s.stats().field_path == 1
+            for src in sources_for(w):
+                P.pic_add_source(s.h, *src)
+        b = P.Batch(sims)
+        b.set_joint(joint)
+        b.step(128)
+        b.sync()
+        runs.append(sims)
+        b.close()
+    for w, sj, sb in zip(ws, *runs):
+        d = rel_l2(fields_of(sj.field), fields_of(sb.field))
+        dj = rel_l2([sj.field(P.PIC_JPX + c) for c in range(3)], [sb.field(P.PIC_JPX + c) for c in range(3)])
+        o = O.from_workload(w, with_particles=False)
+        for src in sources_for(w):
+            o.add_source(*src)
+        o.step(128)
+        fj, _ = check(o, sj, 2e-5)
+        fb, _ = check(o, sb, 2e-5)
+        assert d <= 1e-6 and dj <= 1e-6, (w.name, d, dj, fj, fb)
+        assert sj.stats().step == 128 and sj.stats().device_error == 0
+
+
+def test_joint_pass_beside_other_instances(P):
+    """Two FP32 instances in the joint pass beside an FP64 instance and an FP32
+    instance held to the split updates (their own branches), with electrons;
+    then a tuning change that moves one instance out of the joint pass."""
+    ws = W.sweep(n=4, seed=13, nsteps=192, **SMALL)
+    sims = [P.Simulation(ws[0], P.PIC_FP32), P.Simulation(ws[1], P.PIC_FP32),
+            P.Simulation(ws[2], P.PIC_FP64), P.Simulation(ws[3], P.PIC_FP32, flags=P.PIC_FLAG_SPLIT_FIELDS)]
+    assert [s.stats().field_path for s in sims] == [1, 1, 0, 0]
+    b = P.Batch(sims)
+    b.step(128)
+    t = sims[1].tuning
+    sims[1].set_tuning(t[0], t[1], t[2], 0)  # instance 1 leaves the joint pass: one instance left there
+    b.step(64)
+    b.sync()
+    for w, s, tol in zip(ws, sims, (2e-5, 2e-5, 1e-10, 2e-5)):
+        o = O.from_workload(w)
+        o.step(192)
+        check(o, s, tol)
+    b.close()
