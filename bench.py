@@ -189,14 +189,14 @@ def traffic_for(kernel, workload):
     if not os.path.exists(p):
         return None
     try:
-        d = json.load(open(p))
         import hashlib
-        src = os.path.join(ROOT, "paper_1505_04007_gb300", "csrc", d["source"])
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        k = d["kernels"].get(kernel)
-        if k is None or d.get("source_sha") != sha or d.get("workload_key") != workload:
-            return None
-        return float(k["dram_bytes_per_launch_full"])
+        for d in json.load(open(p))["entries"]:
+            src = os.path.join(ROOT, "paper_1505_04007_gb300", "csrc", d["source"])
+            sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+            k = d["kernels"].get(kernel)
+            if k is not None and d.get("source_sha") == sha and d.get("workload_key") == workload:
+                return float(k["dram_bytes_per_launch_full"])
+        return None
     except Exception:
         return None
 
@@ -281,20 +281,29 @@ def batched_and_sequential(ws, warm, steps, clocks=None, tune=False):
     b.close()
     for x in sims:
         x.close()
-    ms_seq = 0.0
-    for w in ws:
-        x = pic.Simulation(w, pic.PIC_FP32)
-        if rep:
-            x.set_tuning(*rep["best"])
-        x.step(before)
-        x.sync()
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(x.stream)
-        x.step(steps)
-        a1.record(x.stream)
-        x.sync()
-        ms_seq += a0.elapsed_time(a1)
-        x.close()
+    def sequential(path=None):
+        ms_seq = 0.0
+        for w in ws:
+            x = pic.Simulation(w, pic.PIC_FP32)
+            if rep:
+                x.set_tuning(*rep["best"])
+            if path is not None:
+                t = x.tuning
+                x.set_tuning(t[0], t[1], t[2], path)
+            x.step(before)
+            x.sync()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(x.stream)
+            x.step(steps)
+            a1.record(x.stream)
+            x.sync()
+            ms_seq += a0.elapsed_time(a1)
+            x.close()
+        return ms_seq
+
+    ms_seq = sequential()
+    if joint is not None:  # alone, a small grid steps faster on the split updates
+        joint["sequential_split_ms_per_step"] = sequential(0) / steps
     return ms_batch, ms_seq, launches, clk, ((*rep["best"], rep["best_lanes"]) if rep else None), before, joint
 
 
