@@ -265,10 +265,9 @@ int pic_load(pic_handle *h, const char *path);
  * term + probe sampling, out[4] probe DFT flush per step, out[5] whole step
  * (without the brick sort that precedes every 16th step).  On the fused
  * path (pic_stats.field_path 1) the phases are: out[0] the fused field pass
- * (E and the next step's H, both streams), out[1] J_f of two steps ago
- * cleared + push + deposit + sources (before the pass), out[2] the
- * free-current correction, out[3] probe sampling, out[4] and out[5] as
- * above.  Runs real steps (the simulation advances).
+ * (E and the next step's H, all four tile kinds), out[1] push + deposit +
+ * sources (before the pass), out[2] the free-current correction, out[3]
+ * probe sampling, out[4] and out[5] as above.  Runs real steps (the simulation advances).
  * Synchronises. */
 int pic_profile_steps(pic_handle *h, int64_t nsteps, double *out_us);
 
@@ -341,11 +340,11 @@ int pic_tune(pic_handle *h, int32_t rounds, pic_tune_report *report);
  * whole block of 64 steps of every instance is captured into one CUDA graph,
  * so instances too small to fill the GPU share it instead of running one
  * after another.  Instances whose grids take the fused field pass (two or
- * more of them, pic_stats.field_path 1) step together: per step, each one's
- * push, deposit and sources on its own stream, then ONE joint field pass
- * whose work items (tiles x plane chunks) are those of all of them, launched
- * once per tile kind, then each one's free-current correction and probe
- * sample.  The other instances run their blocks as branches of their own on
+ * more of them, pic_stats.field_path 1) step together: per step ONE joint
+ * field pass whose work items (tiles x plane chunks) are those of all of
+ * them, launched once per tile kind, beside each one's push, deposit and
+ * sources on its own streams, then each one's free-current correction and
+ * probe sample.  The other instances run their blocks as branches of their own on
  * their own streams.  The arithmetic of each instance is that of pic_step
  * (see pic_batch_set_joint for the rounding of the joint pass). */
 typedef struct pic_batch pic_batch;

@@ -715,7 +715,7 @@ struct Sim : SimBase {
                 CUDA_TRY(cudaMemsetAsync(jfs[j].count, 0, sizeof(int), stream));
             }
             fused_ready = false;
-            bold_stale = true;  // the fused push gathers H^{n-1/2} itself; the split one reads bold
+
             drop_graph();
         }
         return PIC_OK;
@@ -725,17 +725,25 @@ struct Sim : SimBase {
     // One step on the fused path, from the state of step n in copy `par`
     // (= n & 1) to copy par ^ 1, on the main stream: J_f of the step before
     // last back to zero, the electrons' E^n, push and deposit into J_f set
-    // `par`, the prescribed sources (fused_pre); then the fused pass (inner
-    // tiles on the main stream, the three kinds of tiles over the x and y
-    // slabs beside them on aux, aux2, aux3); then the free-current
-    // correction and the probe sample (fused_post).  (The push runs on its
-    // own before the pass: beside it, its blocks would wait for shared
-    // memory the pass holds.)  pe (optional) receives 7 timing events: step
-    // start, pass done, push start, push done (= pass start), correction
-    // start, correction done, tail done.
+    // `par` and the prescribed sources; then the fused pass (inner tiles on
+    // the main stream, the three kinds of tiles over the x and y slabs on
+    // aux, aux2, aux3); then the free-current correction and the probe
+    // sample (fused_post).  pe (optional) receives timing events: 0 step
+    // start, 2 and 3 push start and done, 8 pass start, 1 pass done, 4 and 5
+    // correction start and done, 6 tail done.
     void launch_step_fused(bool sort, int par, cudaEvent_t *pe) {
         if constexpr (std::is_same<T, float>::value) {
-            fused_pre(sort, par, pe);
+            if (pe) cudaEventRecord(pe[0], stream);
+            fused_pre(sort, par);
+            // The push and the sources read E^n and H^{n+1/2} from copy par,
+            // which the pass only reads, so they could run beside it; they run
+            // before it: beside it the two share the SMs, and the step took as
+            // long (616 against 621 us on c3) with the pass stretched by the
+            // push's share.
+            if (pe) cudaEventRecord(pe[2], stream);
+            fused_push(par, stream);
+            if (pe) cudaEventRecord(pe[3], stream);
+            if (pe) cudaEventRecord(pe[8], stream);
             cudaEventRecord(ev_ef, stream);
             for (cudaStream_t x : {aux, aux2, aux3}) cudaStreamWaitEvent(x, ev_ef, 0);
             const cudaStream_t sk[3] = {aux, aux2, aux3};
@@ -747,23 +755,23 @@ struct Sim : SimBase {
             fused_post(par, pe);
         }
     }
-    void fused_pre(bool sort, int par, cudaEvent_t *pe) {
+    // the brick sort and J_f of the step before last back to zero
+    void fused_pre(bool sort, int par) {
         if constexpr (std::is_same<T, float>::value) {
-            if (pe) cudaEventRecord(pe[0], stream);
             if (sort) {
                 psort.n = p.n;
                 launch_sort<T>(p, psort, sb, stream);
             }
-            const int xb = par, yb = par ^ 1;
-            const Fields<T> fx = view(xb, par);
-            if (pe) cudaEventRecord(pe[2], stream);
             launch_jf_clear(g, jfs[par ^ 1], (int)n_tiles, stream);
-            if (p.n > 0) {  // E^n, H^{n+1/2} from copy par, H^{n-1/2} from copy par ^ 1 (the pass follows)
-                const HoldPtrs<T> hold{{P[yb].H[0], P[yb].H[1], P[yb].H[2]}};
-                launch_push_deposit<T>(g, fx, p, pp, stream, &hold);
-            }
-            launch_sources<T>(g, fx, sources.data(), (int)sources.size(), cfg.dt, stream);
-            if (pe) cudaEventRecord(pe[3], stream);
+        }
+    }
+    // the electrons' push and deposit into J_f set `par` (E^n, H^{n+1/2} from
+    // copy par, H^{n-1/2} at x^n kept per electron) and the prescribed sources
+    void fused_push(int par, cudaStream_t s) {
+        if constexpr (std::is_same<T, float>::value) {
+            const Fields<T> fx = view(par, par);
+            if (p.n > 0) launch_push_deposit<T>(g, fx, p, pp, s, true);
+            launch_sources<T>(g, fx, sources.data(), (int)sources.size(), cfg.dt, s);
         }
     }
     // the arguments of a fused pass reading copy xb and writing copy xb ^ 1
@@ -840,13 +848,19 @@ struct Sim : SimBase {
                 for (int t = 0; t < fpl.n_kind[k]; t++) items[k].push_back(make_int4(inst, h_tiles[first + t], c, 0));
     }
     int fused_chunk_planes() const override { return fpl.chunk; }
-    // step s of a joint block: the work before the pass, forked from `from`
+    // step s of a joint block: the work beside the pass, forked from `from`
+    // (the sort and the J_f clear on the main stream, the push and the
+    // sources on the high-priority side stream; joint_post orders the
+    // correction after them)
     long long joint_pre(int s, cudaStream_t from) override {
         const long long before = launch_count();
         cudaEventRecord(ev_bfork, from);
         cudaStreamWaitEvent(stream, ev_bfork, 0);
         const int par = (int)((step_host + s) & 1);
-        fused_pre(s % sort_every == 0, par, nullptr);
+        fused_pre(s % sort_every == 0, par);
+        fork_join(stream, side, ev_fork);
+        fused_push(par, side);
+        fork_join(side, stream, ev_join);
         return launch_count() - before;
     }
     // ... and after it (the DFT flush after the block's last step)
@@ -1465,7 +1479,7 @@ struct Sim : SimBase {
         if (nsteps <= 0) return PIC_OK;
         // The steps run exactly as pic_step runs them (same streams and
         // overlap), with timing events at the phase boundaries.
-        constexpr int NE = 8;
+        constexpr int NE = 9;
         const int B = DFT_BLOCK;
         std::vector<cudaEvent_t> ev((size_t)B * NE);
         for (auto &e : ev) CUDA_TRY(cudaEventCreate(&e));
@@ -1490,8 +1504,8 @@ struct Sim : SimBase {
             CUDA_TRY(cudaEventSynchronize(ev[(size_t)(cnt - 1) * NE + 7]));
             for (int s = 0; s < cnt; s++) {
                 cudaEvent_t *e = &ev[(size_t)s * NE];
-                // fused path: the pass runs from the end of the push (3) to 1
-                const int f0 = fused_ready ? 3 : 0;
+                // fused path: the pass runs from its start (8) to 1, beside the push (2 to 3)
+                const int f0 = fused_ready ? 8 : 0;
                 const int from[6] = {f0, 2, 4, 5, 6, 0}, to[6] = {1, 3, 5, 6, 7, 7};
                 for (int q6 = 0; q6 < 6; q6++) {
                     float ms;
@@ -1611,6 +1625,7 @@ static int add_particles_t(Sim<T> *s, int64_t n, const double *xyz, const double
         s->pp.jscale[c] = (T)(-q / (s->cfg.dt * s->d[a1] * s->d[a2]));
     }
     s->bold_stale = true;
+    s->since_sort = DFT_BLOCK;  // the new electrons are in input order: sort before the next push
     s->drop_graph();
     return PIC_OK;
 }
@@ -2117,13 +2132,13 @@ struct pic_batch {
             tail[l] = h[i]->sim->main_stream();
             load[l] += h[i]->sim->cells();
         }
-        // The instances of J step together: per step, each one's work before
-        // the pass on its own stream, then one joint pass over all of them,
-        // then each one's work after it.
+        // The instances of J step together: per step, each one's sort, push
+        // and sources on its own streams beside one joint pass over all of
+        // them (the pass reads only what those leave alone), then each one's
+        // correction and probe sample after both.
         for (int i : J) kernels[i] = 0;
         for (int st = 0; st < DFT_BLOCK && !J.empty(); st++) {
             for (int i : J) kernels[i] += h[i]->sim->joint_pre(st, stream);
-            for (int i : J) h[i]->sim->join_to(stream);
             jt.phase = st & 1;
             cudaEventRecord(ev, stream);
             for (cudaStream_t x : jaux) cudaStreamWaitEvent(x, ev, 0);

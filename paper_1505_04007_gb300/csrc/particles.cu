@@ -137,13 +137,13 @@ __device__ __forceinline__ void esirkepov_sites(const T (&P)[3][3], const T (&dS
     }
 }
 
-// OLDH: the fused field path keeps H^{n-1/2} in the other copy of the
-// state until after the push, so E^n, H^{n+1/2} and H^{n-1/2} are gathered
-// here at x^n in one round (hold: that copy's H), and neither the E gather
-// beforehand nor the H^{n+1/2}(x^{n+1}) gather at the end is needed.
-template <typename T, bool OLDH>
+// GE: E^n is gathered here at x^n (the fused field path, where the push
+// runs beside a pass that reads E^n and H^{n+1/2} and writes the other copy
+// of the state) rather than read from eg (gathered beside the H update on
+// the split path).
+template <typename T, bool GE>
 __global__ void __launch_bounds__(PUSH_BLOCK)
-    k_push_deposit(Grid<T> g, Fields<T> f, Particles<T> p, PushParams<T> pp, HoldPtrs<T> hold) {
+    k_push_deposit(Grid<T> g, Fields<T> f, Particles<T> p, PushParams<T> pp) {
     extern __shared__ __align__(16) unsigned char dep_smem[];
     T *acc = reinterpret_cast<T *>(dep_smem);
     __shared__ int bb_lo[3], bb_hi[3];
@@ -159,24 +159,20 @@ __global__ void __launch_bounds__(PUSH_BLOCK)
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             c0[a] = p.cell[a][q]; o0[a] = p.off[a][q]; u[a] = p.u[a][q]; ul[a] = p.ulo[a][q];
-            if (!OLDH) E[a] = p.eg[a][q];
+            if (!GE) E[a] = p.eg[a][q];
         }
         {
             Stencil<T> st0;
             make_stencil(g, c0, o0, st0);
             T hnew[3], hold3[3];
             interp_H(f, g, st0, hnew);
-            if (OLDH) {
+            if (GE) {
                 E[0] = interp<1>(f.E[0], g, st0);
                 E[1] = interp<2>(f.E[1], g, st0);
                 E[2] = interp<4>(f.E[2], g, st0);
-                hold3[0] = interp<6>(hold.H[0], g, st0);
-                hold3[1] = interp<5>(hold.H[1], g, st0);
-                hold3[2] = interp<3>(hold.H[2], g, st0);
-            } else {
-#pragma unroll
-                for (int a = 0; a < 3; a++) hold3[a] = p.bold[a][q];
             }
+#pragma unroll
+            for (int a = 0; a < 3; a++) hold3[a] = p.bold[a][q];
 #pragma unroll
             for (int a = 0; a < 3; a++) B[a] = pp.mu0 * T(0.5) * (hold3[a] + hnew[a]);
         }
@@ -250,7 +246,7 @@ __global__ void __launch_bounds__(PUSH_BLOCK)
                 p.u[a][q] = un[a];
                 p.ulo[a][q] = unl[a];
             }
-            if (!OLDH) {
+            {
                 Stencil<T> st1;
                 make_stencil(g, c1w, o1, st1);
                 T hb[3];
@@ -573,13 +569,13 @@ void launch_count_in_metal(int *const cell[3], long long base, long long n, cons
 
 template <typename T>
 void launch_push_deposit(const Grid<T> &g, const Fields<T> &f, const Particles<T> &p, const PushParams<T> &pp,
-                         cudaStream_t s, const HoldPtrs<T> *hold) {
+                         cudaStream_t s, bool gather_E) {
     if (p.n <= 0) return;
     const unsigned nb = (unsigned)((p.n + PUSH_BLOCK - 1) / PUSH_BLOCK);
-    if (hold)
-        k_push_deposit<T, true><<<nb, PUSH_BLOCK, (size_t)pp.dep_smem, s>>>(g, f, p, pp, *hold);
+    if (gather_E)
+        k_push_deposit<T, true><<<nb, PUSH_BLOCK, (size_t)pp.dep_smem, s>>>(g, f, p, pp);
     else
-        k_push_deposit<T, false><<<nb, PUSH_BLOCK, (size_t)pp.dep_smem, s>>>(g, f, p, pp, HoldPtrs<T>{});
+        k_push_deposit<T, false><<<nb, PUSH_BLOCK, (size_t)pp.dep_smem, s>>>(g, f, p, pp);
     launch_count() += 1;
 }
 
@@ -621,9 +617,9 @@ void launch_sort(const Particles<T> &p, const Particles<T> &scratch, const SortB
 }
 
 template void launch_push_deposit<float>(const Grid<float> &, const Fields<float> &, const Particles<float> &,
-                                         const PushParams<float> &, cudaStream_t, const HoldPtrs<float> *);
+                                         const PushParams<float> &, cudaStream_t, bool);
 template void launch_push_deposit<double>(const Grid<double> &, const Fields<double> &, const Particles<double> &,
-                                          const PushParams<double> &, cudaStream_t, const HoldPtrs<double> *);
+                                          const PushParams<double> &, cudaStream_t, bool);
 template void launch_gather_E<float>(const Grid<float> &, const Fields<float> &, const Particles<float> &,
                                      cudaStream_t);
 template void launch_gather_E<double>(const Grid<double> &, const Fields<double> &, const Particles<double> &,

@@ -321,16 +321,12 @@ void launch_nonfinite_scan(const Fields<T> &f, long long n, int *err, cudaStream
 void launch_count_in_metal(int *const cell[3], long long base, long long n, const int nn[3], const uint8_t *mat,
                            const uint8_t *mat_metal, unsigned long long *count, cudaStream_t s);
 
-// H^{n-1/2} for a push that gathers it itself (the fused field path).
-template <typename T>
-struct HoldPtrs {
-    const T *H[3];
-};
-// hold: NULL, or the H^{n-1/2} arrays to gather at x^n (then E^n is gathered
-// in the same kernel and the particles' bold/eg arrays are not used)
+// gather_E: E^n is gathered at x^n in the same kernel (the fused field
+// path) instead of read from the particles' eg array; H^{n-1/2}(x^n) comes
+// from bold, and bold <- H^{n+1/2}(x^{n+1}) at the end, on both paths.
 template <typename T>
 void launch_push_deposit(const Grid<T> &g, const Fields<T> &f, const Particles<T> &p,
-                         const PushParams<T> &pp, cudaStream_t s, const HoldPtrs<T> *hold = nullptr);
+                         const PushParams<T> &pp, cudaStream_t s, bool gather_E = false);
 template <typename T>
 void launch_sort(const Particles<T> &p, const Particles<T> &scratch, const SortBuffers &sb, cudaStream_t s);
 template <typename T>
