@@ -536,6 +536,8 @@ struct Sim : SimBase {
                 CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
                 fpl.chunk = fused_chunk(n[2], fpl.n_kind[0], sms);
                 fpl.nchunks = (n[2] + fpl.chunk - 1) / fpl.chunk;
+                fpl.slab_chunk = fused_slab_chunk(fpl.chunk);
+                fpl.slab_nchunks = (n[2] + fpl.slab_chunk - 1) / fpl.slab_chunk;
                 fused = fused_grid_ok(g) && fused_maps(fpl, P, n, g.L, g.cpml);
             }
           }

@@ -235,11 +235,14 @@ struct FusedPlan {
     // only, x slab only, both), n_kind[k] of kind k
     const int *tiles = nullptr;
     int n_kind[4] = {0, 0, 0, 0};
-    int chunk = 32, nchunks = 1;
+    int chunk = 32, nchunks = 1;   // planes per item of the inner tiles, and items per tile column
+    int slab_chunk = 8, slab_nchunks = 1;  // ... of the slab kinds (shorter runs: more of their items at once)
 };
 bool fused_grid_ok(const Grid<float> &g);
 // Planes per work item for a grid of nz planes and inner_tiles tiles on a GPU with sms SMs.
 int fused_chunk(int nz, int inner_tiles, int sms);
+// Planes per work item of the slab kinds, given the inner tiles' run.
+int fused_slab_chunk(int chunk);
 // Tile lists of the pass by kind: bit 0 set when the tile (with its halo
 // row) meets a y slab, bit 1 when it (with its halo column) meets an x slab.
 // Returns the tile count.
