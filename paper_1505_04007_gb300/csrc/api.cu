@@ -15,7 +15,6 @@
 #include <cstring>
 #include <memory>
 #include <string>
-#include <thread>
 #include <type_traits>
 #include <unordered_map>
 #include <vector>
@@ -1547,76 +1546,42 @@ static int add_particles_t(Sim<T> *s, int64_t n, const double *xyz, const double
     if (s->p.n + n > s->cfg.max_particles)
         return fail(PIC_ERR_OOM, "%lld particles exceed max_particles=%lld", (long long)(s->p.n + n),
                     (long long)s->cfg.max_particles);
-    std::vector<int> cell[3];
-    std::vector<T> off[3], uu[3], ulo[3];
-    for (int a = 0; a < 3; a++) { cell[a].resize(n); off[a].resize(n); uu[a].resize(n); ulo[a].resize(n); }
-    // host threads over slices of the input: cell, offset and momentum split
-    // in the state precision, and the boundary-margin rule
-    const int hw = (int)std::thread::hardware_concurrency();
-    const int nthr = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)(hw > 0 ? hw : 1), 16, n / 65536 + 1}));
-    std::vector<int64_t> bad_t(nthr, 0);
-    auto convert = [&](int t) {
-    const int64_t lo = n * t / nthr, hi = n * (t + 1) / nthr;
-    int64_t &bad = bad_t[t];
-    for (int64_t q2 = lo; q2 < hi; q2++) {
-        bool ok = true;
-        for (int a = 0; a < 3; a++) {
-            double xi = xyz[3 * q2 + a] / s->d[a];
-            if (!std::isfinite(xi) || !std::isfinite(u[3 * q2 + a])) { ok = false; xi = 0; }
-            if (s->g.per[a]) xi -= std::floor(xi / s->n[a]) * s->n[a];
-            double fl = std::floor(xi);
-            int ci = (int)fl;
-            double o = xi - fl;
-            if (s->g.per[a] && ci >= s->n[a]) { ci -= s->n[a]; }
-            if (!s->g.per[a] && (xi < 2.0 || xi >= s->n[a] - 2.0)) ok = false;
-            ci = std::min(std::max(ci, 0), s->n[a] - 1);
-            cell[a][q2] = ci;
-            T ot = (T)o;
-            if (ot >= T(1)) ot = std::nextafter(T(1), T(0));
-            off[a][q2] = ot;
-            uu[a][q2] = (T)u[3 * q2 + a];
-            ulo[a][q2] = (T)(u[3 * q2 + a] - (double)uu[a][q2]);
-        }
-        if (!ok) bad++;
-    }
-    };
-    {
-        std::vector<std::thread> pool;
-        for (int t = 1; t < nthr; t++) pool.emplace_back(convert, t);
-        convert(0);
-        for (auto &th : pool) th.join();
-    }
-    int64_t bad = 0;
-    for (int64_t b : bad_t) bad += b;
-    if (n_rejected) *n_rejected = bad;
-    if (bad) return fail(PIC_ERR_ARG, "%lld particles outside the allowed region", (long long)bad);
-    // the arrays go beyond the live count first; cells inside a metal (the
-    // material map lives on the device) are counted there before they count
+    // The caller's arrays go to the device as they are (into the sort's
+    // scratch arrays, free between steps), where one kernel converts them
+    // into the particle arrays beyond the live count and counts the
+    // electrons outside the allowed region and those inside a metal.
     const long long base = s->p.n;
-    std::vector<long long> ids(n);
-    for (int64_t q2 = 0; q2 < n; q2++) ids[q2] = base + q2;
-    for (int a = 0; a < 3; a++) {
-        CUDA_TRY(cudaMemcpyAsync(s->p.cell[a] + base, cell[a].data(), n * sizeof(int), cudaMemcpyHostToDevice, s->stream));
-        CUDA_TRY(cudaMemcpyAsync(s->p.off[a] + base, off[a].data(), n * sizeof(T), cudaMemcpyHostToDevice, s->stream));
-        CUDA_TRY(cudaMemcpyAsync(s->p.u[a] + base, uu[a].data(), n * sizeof(T), cudaMemcpyHostToDevice, s->stream));
-        CUDA_TRY(cudaMemcpyAsync(s->p.ulo[a] + base, ulo[a].data(), n * sizeof(T), cudaMemcpyHostToDevice, s->stream));
-    }
-    CUDA_TRY(cudaMemcpyAsync(s->p.id + base, ids.data(), n * sizeof(long long), cudaMemcpyHostToDevice, s->stream));
-    CUDA_TRY(cudaMemsetAsync(s->p.status + base, 0, (size_t)n, s->stream));
     if (n > 0) {
+        const size_t bytes = (size_t)n * 3 * sizeof(double);
+        char *stage = reinterpret_cast<char *>(s->psort.cell[0]);
+        const size_t room = (size_t)(reinterpret_cast<char *>(s->psort.id + s->cfg.max_particles) - stage);
+        if (2 * bytes + 16 > room) return fail(PIC_ERR_OOM, "particle staging area too small");
+        double *d_xyz = reinterpret_cast<double *>(stage);
+        double *d_u = reinterpret_cast<double *>(stage + (bytes + 15) / 16 * 16);
         unsigned long long *d_cnt = reinterpret_cast<unsigned long long *>(s->d_keyset);  // scratch after create
-        unsigned long long in_metal = 0;
-        CUDA_TRY(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), s->stream));
-        launch_count_in_metal(s->p.cell, base, n, s->n, s->d_mat, s->d_mat_metal, d_cnt, s->stream);
+        CUDA_TRY(cudaMemsetAsync(d_cnt, 0, 2 * sizeof(unsigned long long), s->stream));
+        CUDA_TRY(cudaMemcpyAsync(d_xyz, xyz, bytes, cudaMemcpyHostToDevice, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(d_u, u, bytes, cudaMemcpyHostToDevice, s->stream));
+        ParticleIn in{};
+        for (int a = 0; a < 3; a++) {
+            in.d[a] = s->d[a];
+            in.n[a] = s->n[a];
+            in.per[a] = s->g.per[a];
+        }
+        launch_particles_in<T>(d_xyz, d_u, n, base, in, s->p, s->d_mat, s->d_mat_metal, d_cnt, s->stream);
         CUDA_TRY(cudaGetLastError());
-        CUDA_TRY(cudaMemcpyAsync(&in_metal, d_cnt, sizeof(in_metal), cudaMemcpyDeviceToHost, s->stream));
+        unsigned long long cnt[2] = {0, 0};
+        CUDA_TRY(cudaMemcpyAsync(cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, s->stream));
         CUDA_TRY(cudaStreamSynchronize(s->stream));
-        if (in_metal) {
-            if (n_rejected) *n_rejected = (int64_t)in_metal;
-            return fail(PIC_ERR_ARG, "%lld particles inside a metal cell", (long long)in_metal);
+        if (cnt[0]) {
+            if (n_rejected) *n_rejected = (int64_t)cnt[0];
+            return fail(PIC_ERR_ARG, "%lld particles outside the allowed region", (long long)cnt[0]);
+        }
+        if (cnt[1]) {
+            if (n_rejected) *n_rejected = (int64_t)cnt[1];
+            return fail(PIC_ERR_ARG, "%lld particles inside a metal cell", (long long)cnt[1]);
         }
     }
-    CUDA_TRY(cudaStreamSynchronize(s->stream));
     s->p.n = base + n;
     s->have_q = true;
     s->q = q;

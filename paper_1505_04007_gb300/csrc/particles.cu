@@ -142,7 +142,7 @@ __device__ __forceinline__ void esirkepov_sites(const T (&P)[3][3], const T (&dS
 // of the state) rather than read from eg (gathered beside the H update on
 // the split path).
 template <typename T, bool GE>
-__global__ void __launch_bounds__(PUSH_BLOCK)
+__global__ void __launch_bounds__(PUSH_BLOCK, sizeof(T) == 4 ? 4 : 1)
     k_push_deposit(Grid<T> g, Fields<T> f, Particles<T> p, PushParams<T> pp) {
     extern __shared__ __align__(16) unsigned char dep_smem[];
     T *acc = reinterpret_cast<T *>(dep_smem);
@@ -547,24 +547,59 @@ __global__ void k_sort_copyback(Particles<T> p, Particles<T> src) {
     p.id[q] = src.id[q];
 }
 
-// Electrons [base, base + n) whose cell holds a metal (wp > 0): counted into *count.
-__global__ void k_count_in_metal(const int *c0, const int *c1, const int *c2, long long base, long long n, int nx, int ny,
-                                 const uint8_t *mat, const uint8_t *mat_metal, unsigned long long *count) {
+// New electrons [base, base + n) from SI positions and momenta (xyz, u: n x 3
+// doubles, copied to the device as given): the (cell, offset) position and
+// the compensated momentum in the state precision, input ids, status 0.
+// counts[0]: electrons with a non-finite value or outside the allowed
+// region (within two cells of a non-periodic face); counts[1]: the others
+// whose cell holds a metal (wp > 0).
+template <typename T>
+__global__ void k_particles_in(const double *xyz, const double *u, long long n, long long base, ParticleIn in,
+                               Particles<T> p, const uint8_t *mat, const uint8_t *mat_metal,
+                               unsigned long long *counts) {
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    bool bad = false;
+    bool bad = false, metal = false;
     if (q < n) {
-        const long long e = ((long long)c2[base + q] * ny + c1[base + q]) * nx + c0[base + q];
-        bad = mat_metal[mat[e]] != 0;
+        const long long k = base + q;
+        int ci[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            double xi = xyz[3 * q + a] / in.d[a];
+            const double ua = u[3 * q + a];
+            if (!isfinite(xi) || !isfinite(ua)) { bad = true; xi = 0.0; }
+            if (in.per[a]) xi -= floor(xi / in.n[a]) * in.n[a];
+            const double fl = floor(xi);
+            int c = (int)fl;
+            const double o = xi - fl;
+            if (in.per[a] && c >= in.n[a]) c -= in.n[a];
+            if (!in.per[a] && (xi < 2.0 || xi >= in.n[a] - 2.0)) bad = true;
+            c = min(max(c, 0), in.n[a] - 1);
+            ci[a] = c;
+            T ot = (T)o;
+            if (ot >= T(1)) ot = nextafter(T(1), T(0));
+            const T ut = (T)ua;
+            p.cell[a][k] = c;
+            p.off[a][k] = ot;
+            p.u[a][k] = ut;
+            p.ulo[a][k] = (T)(ua - (double)ut);
+        }
+        p.id[k] = k;
+        p.status[k] = 0;
+        if (!bad) metal = mat_metal[mat[((long long)ci[2] * in.n[1] + ci[1]) * in.n[0] + ci[0]]] != 0;
     }
-    const unsigned b = __ballot_sync(0xffffffffu, bad);
-    if ((threadIdx.x & 31) == 0 && b) atomicAdd(count, (unsigned long long)__popc(b));
+    const unsigned bb = __ballot_sync(0xffffffffu, bad), bm = __ballot_sync(0xffffffffu, metal);
+    if ((threadIdx.x & 31) == 0) {
+        if (bb) atomicAdd(&counts[0], (unsigned long long)__popc(bb));
+        if (bm) atomicAdd(&counts[1], (unsigned long long)__popc(bm));
+    }
 }
 
-void launch_count_in_metal(int *const cell[3], long long base, long long n, const int nn[3], const uint8_t *mat,
-                           const uint8_t *mat_metal, unsigned long long *count, cudaStream_t s) {
+template <typename T>
+void launch_particles_in(const double *xyz, const double *u, long long n, long long base, const ParticleIn &in,
+                         const Particles<T> &p, const uint8_t *mat, const uint8_t *mat_metal,
+                         unsigned long long *counts, cudaStream_t s) {
     if (n <= 0) return;
-    k_count_in_metal<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(cell[0], cell[1], cell[2], base, n, nn[0], nn[1], mat,
-                                                                 mat_metal, count);
+    k_particles_in<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(xyz, u, n, base, in, p, mat, mat_metal, counts);
 }
 
 template <typename T>
@@ -616,6 +651,12 @@ void launch_sort(const Particles<T> &p, const Particles<T> &scratch, const SortB
     launch_count() += 1;
 }
 
+template void launch_particles_in<float>(const double *, const double *, long long, long long, const ParticleIn &,
+                                        const Particles<float> &, const uint8_t *, const uint8_t *,
+                                        unsigned long long *, cudaStream_t);
+template void launch_particles_in<double>(const double *, const double *, long long, long long, const ParticleIn &,
+                                         const Particles<double> &, const uint8_t *, const uint8_t *,
+                                         unsigned long long *, cudaStream_t);
 template void launch_push_deposit<float>(const Grid<float> &, const Fields<float> &, const Particles<float> &,
                                          const PushParams<float> &, cudaStream_t, bool);
 template void launch_push_deposit<double>(const Grid<double> &, const Fields<double> &, const Particles<double> &,

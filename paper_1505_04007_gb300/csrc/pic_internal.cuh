@@ -321,8 +321,18 @@ void launch_jf_apply(const Grid<T> &g, const Fields<T> &f, int max_tiles, cudaSt
 template <typename T>
 void launch_nonfinite_scan(const Fields<T> &f, long long n, int *err, cudaStream_t s);
 // Electrons [base, base + n) whose cell is metal, counted into *count (added to).
-void launch_count_in_metal(int *const cell[3], long long base, long long n, const int nn[3], const uint8_t *mat,
-                           const uint8_t *mat_metal, unsigned long long *count, cudaStream_t s);
+// The grid as the conversion of new electrons needs it.
+struct ParticleIn {
+    double d[3];
+    int n[3], per[3];
+};
+// New electrons [base, base + n) from device copies of the caller's xyz and
+// u (n x 3 doubles each, SI); counts[0] the rejected (non-finite or within
+// two cells of a non-periodic face), counts[1] the others inside a metal.
+template <typename T>
+void launch_particles_in(const double *xyz, const double *u, long long n, long long base, const ParticleIn &in,
+                         const Particles<T> &p, const uint8_t *mat, const uint8_t *mat_metal,
+                         unsigned long long *counts, cudaStream_t s);
 
 // gather_E: E^n is gathered at x^n in the same kernel (the fused field
 // path) instead of read from the particles' eg array; H^{n-1/2}(x^n) comes
