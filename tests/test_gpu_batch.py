@@ -148,3 +148,26 @@ def test_joint_pass_beside_other_instances(P):
         o.step(192)
         check(o, s, tol)
     b.close()
+
+
+def test_joint_pass_instances_at_odd_and_even_steps(P):
+    """A block of an instance starts where its probes were last set up: one
+    instance enters the batch at step 37 (its probes set up then), the other
+    at 0, so the joint pass reads state copy 1 of the first and copy 0 of the
+    second in the same launch; both keep oracle parity on the fields."""
+    ws = W.sweep(n=2, seed=17, nsteps=165, **SMALL)
+    sims = [P.Simulation(w, P.PIC_FP32, probes=False) for w in ws]
+    sims[0].step(37)
+    for w, s in zip(ws, sims):
+        s.probe_dft(w.probes, w.freqs, w.comp_mask)  # the block position restarts here
+    b = P.Batch(sims)
+    b.step(128)
+    b.sync()
+    assert [s.stats().step for s in sims] == [165, 128]
+    for w, s, n in zip(ws, sims, (165, 128)):
+        o = O.from_workload(w, with_probes=False)
+        o.step(n)
+        f = rel_l2(fields_of(s.field), fields_of(o.get_field))
+        assert f <= 2e-5, (w.name, f)
+        assert s.stats().device_error == 0
+    b.close()
