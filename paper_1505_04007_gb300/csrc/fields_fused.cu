@@ -88,7 +88,7 @@ struct __align__(128) Smem {
     int pzs[MAX_CHUNK + 2];
     unsigned long long bar[STAGES];
     int abort_flag;
-    typename std::conditional<J, FusedArgs, int>::type args;  // a joint pass: the item's instance
+    alignas(16) typename std::conditional<J, FusedArgs, int>::type args;  // a joint pass: the item's instance (copied in 16-byte pieces)
 };
 template <int K, bool J>
 constexpr size_t smem_bytes() { return sizeof(Smem<K, J>) + 128; }  // + alignment slack
