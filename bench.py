@@ -424,7 +424,10 @@ def bench_adjoint(args):
     w.xyz, w.u = np.zeros((0, 3)), np.zeros((0, 3))
     w.probes = np.array([list(cfg.probe)])
     w.freqs = np.array([cfg.omega0 / (2 * np.pi)])
+    # (its launch settings chosen by pic_tune, as the plain bench does: on a
+    # grid this small the split field updates beat the fused pass)
     sim = pic.Simulation(w, pic.PIC_FP32, particles=False)
+    plain_tuning = sim.tune(rounds=1)["best"]
     sim.step(256)
     sim.sync()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -443,6 +446,7 @@ def bench_adjoint(args):
                                    f"{steps} steps, loss |F(wp/sqrt2)|^2 of Ez",
                        "note": "value counts one forward + one backward step as one cell-update; host wall clock"},
             "forward_s": r32["fwd"], "backward_s": r32["bwd"], "plain_step_s": plain_s,
+            "plain_step_launch_settings": list(plain_tuning),
             "forward_plus_backward_vs_plain": (r32["fwd"] + r32["bwd"]) / plain_s,
             "fp32_vs_fp64": {"loss_rel": abs(r32["loss"] / r64["loss"] - 1),
                              "dmask_rel_l2": float(np.linalg.norm(r32["dm"] - r64["dm"]) / np.linalg.norm(r64["dm"])),
