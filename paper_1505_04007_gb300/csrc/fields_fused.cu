@@ -33,10 +33,13 @@
 // one copy per field and plane, the three components at once), signalled
 // by mbarriers; every wait is bounded (on timeout the block records
 // DEVERR_WAIT, waits a bounded time for its copies in flight and returns).
-// The E^{n+1} planes go through a ring of three plain shared-memory planes.
+// The E^{n+1} planes go through a ring of plain shared-memory planes (three
+// in the inner kind; two, with a second barrier per plane, in the slab kinds).
+// A joint pass (k_fused_joint) runs the items of several simulations in one
+// launch per kind, with each instance's arguments and maps from a table.
 //
-// Free current: Eq. 8's J_f term is left out of the pass (the electrons are
-// pushed beside it and their current is not known yet).  k_jf_fix adds it
+// Free current: Eq. 8's J_f term is left out of the pass (the pass does not
+// wait for the push, and in a batch runs beside it).  k_jf_fix adds it
 // afterwards on the tiles the deposit wrote: dE = -dt/(eps0 eps_inf) J_f on
 // those edges, and the change of H^{n+3/2} (and of its CPML memory) that dE
 // causes through the H update, which is linear in E.
