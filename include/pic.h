@@ -141,7 +141,8 @@ int pic_workspace_size(const pic_config *cfg, size_t *bytes);
  * caller keeps it alive until pic_destroy), else from cudaMalloc.
  * *out receives an opaque handle owned by the library until pic_destroy.
  * Errors: PIC_ERR_ARG, PIC_ERR_CFL, PIC_ERR_OOM, PIC_ERR_UNSUPPORTED (more
- * than 256 distinct edge materials), PIC_ERR_CUDA. */
+ * than 256 distinct edge materials, 2^32 cells or more, ny above 262140 or
+ * nz above 131070), PIC_ERR_CUDA. */
 int pic_create(const pic_config *cfg, pic_handle **out);
 
 /* Release the handle and any memory the library allocated.  Waits for the

@@ -96,6 +96,8 @@ static int validate(const pic_config *c) {
                         c->cpml_cells);
     }
     if (c->ny > 4 * 65535LL || c->nz > 2 * 65535LL) return fail(PIC_ERR_UNSUPPORTED, "grid too tall for the launch shape");
+    // cell offsets in 32 bits (the gathers); such a grid would not fit a GPU's memory anyway
+    if ((unsigned long long)n[0] * n[1] * n[2] >= (1ull << 32)) return fail(PIC_ERR_UNSUPPORTED, "2^32 cells or more");
     if (c->cpml_cells < 1 && (has_cpml(c, 0) || has_cpml(c, 1) || has_cpml(c, 2)))
         return fail(PIC_ERR_ARG, "cpml_cells must be >= 1");
     if (!(c->dt > 0.0) || !(c->eps0 > 0.0) || !(c->mu0 > 0.0)) return fail(PIC_ERR_ARG, "dt, eps0, mu0 must be > 0");

@@ -69,10 +69,12 @@ __device__ __forceinline__ void make_stencil(const Grid<T> &g, const int c[3], c
 template <int STAG, typename T>
 __device__ __forceinline__ T interp(const T *__restrict__ F, const Grid<T> &g, const Stencil<T> &s) {
     constexpr int sx = STAG & 1, sy = (STAG >> 1) & 1, sz = (STAG >> 2) & 1;
-    const long long nx = g.n[0], nxy = (long long)g.n[0] * g.n[1];
-    const int x0 = s.i0[0][sx], x1 = s.i1[0][sx];
-    const long long r00 = s.i0[2][sz] * nxy + s.i0[1][sy] * nx, r01 = s.i0[2][sz] * nxy + s.i1[1][sy] * nx;
-    const long long r10 = s.i1[2][sz] * nxy + s.i0[1][sy] * nx, r11 = s.i1[2][sz] * nxy + s.i1[1][sy] * nx;
+    // 32-bit cell offsets: pic_create takes grids of fewer than 2^32 cells
+    const unsigned nx = (unsigned)g.n[0], nxy = (unsigned)g.n[0] * (unsigned)g.n[1];
+    const unsigned x0 = (unsigned)s.i0[0][sx], x1 = (unsigned)s.i1[0][sx];
+    const unsigned z0 = (unsigned)s.i0[2][sz] * nxy, z1 = (unsigned)s.i1[2][sz] * nxy;
+    const unsigned y0 = (unsigned)s.i0[1][sy] * nx, y1 = (unsigned)s.i1[1][sy] * nx;
+    const unsigned r00 = z0 + y0, r01 = z0 + y1, r10 = z1 + y0, r11 = z1 + y1;
     const T wx = s.w[0][sx], wy = s.w[1][sy], wz = s.w[2][sz];
     const T ux = T(1) - wx, uy = T(1) - wy, uz = T(1) - wz;
     const T v00 = ux * F[r00 + x0] + wx * F[r00 + x1];

@@ -47,6 +47,16 @@ def _cfg(**kw):
     return cfg, keep, w
 
 
+def test_grids_of_2_to_the_32_cells_are_unsupported():
+    cfg, keep, w = _cfg()
+    cfg.nx, cfg.ny, cfg.nz = 2048, 2048, 1023  # just below 2^32 cells: sized (host only)
+    assert P.pic_workspace_size(cfg) > 2048 * 2048 * 1023 * 12 * 4
+    cfg.nz = 1024
+    with pytest.raises(P.PicError) as e:
+        P.pic_workspace_size(cfg)
+    assert e.value.code == -7  # PIC_ERR_UNSUPPORTED: cell offsets are 32-bit
+
+
 def test_workspace_size_is_host_only_and_scales():
     cfg, keep, w = _cfg()
     n32f = P.pic_workspace_size(cfg)  # c1 takes the fused field pass: two copies of the state
