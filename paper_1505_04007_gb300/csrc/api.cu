@@ -213,6 +213,9 @@ struct Sim : SimBase {
     // last step is set (n - 1) & 1.  Otherwise the state is the plain one in
     // f (E^n, H^{n-1/2}, ...), as on the split path.
     bool fused_possible = false;  // the grid and flags take the fused pass (arena holds the second copy)
+    // the device reads pageable host memory coherently (a Grace system): the
+    // caller's host arrays are read by kernels directly instead of copied
+    bool host_direct = false;
     bool fused = false;           // ... and its plan was built
     bool use_fused = true;        // launch setting: take the fused pass when `fused`
     bool fused_ready = false;
@@ -485,7 +488,18 @@ struct Sim : SimBase {
         // material map and per-material metal flag (particle absorption), then the edge classes
         std::vector<uint8_t> metal(256, 0);
         for (int m2 = 0; m2 < c->n_materials; m2++) metal[m2] = c->materials[m2].wp > 0.0;
-        CUDA_TRY(cudaMemcpyAsync(d_mat, c->material_id, (size_t)N, cudaMemcpyHostToDevice, stream));
+        {
+            int pma = 0;
+            CUDA_TRY(cudaDeviceGetAttribute(&pma, cudaDevAttrPageableMemoryAccess, device));
+            host_direct = pma == 1;
+        }
+        if (host_direct) {  // read where it is; done before any later return
+            launch_copy_bytes(c->material_id, d_mat, N, stream);
+            CUDA_TRY(cudaGetLastError());
+            CUDA_TRY(cudaStreamSynchronize(stream));
+        } else {
+            CUDA_TRY(cudaMemcpyAsync(d_mat, c->material_id, (size_t)N, cudaMemcpyHostToDevice, stream));
+        }
         CUDA_TRY(cudaMemcpyAsync(d_mat_metal, metal.data(), 256, cudaMemcpyHostToDevice, stream));
         rc = device_classes(c, cls, cls_metal, plane_cls);
         if (rc) return rc;
@@ -1548,22 +1562,28 @@ static int add_particles_t(Sim<T> *s, int64_t n, const double *xyz, const double
     if (s->p.n + n > s->cfg.max_particles)
         return fail(PIC_ERR_OOM, "%lld particles exceed max_particles=%lld", (long long)(s->p.n + n),
                     (long long)s->cfg.max_particles);
-    // The caller's arrays go to the device as they are (into the sort's
-    // scratch arrays, free between steps), where one kernel converts them
-    // into the particle arrays beyond the live count and counts the
-    // electrons outside the allowed region and those inside a metal.
+    // One kernel converts the caller's arrays into the particle arrays beyond
+    // the live count and counts the electrons outside the allowed region and
+    // those inside a metal.  It reads the arrays where they are on a device
+    // with coherent access to pageable host memory, else from copies in the
+    // sort's scratch arrays (free between steps).
     const long long base = s->p.n;
     if (n > 0) {
         const size_t bytes = (size_t)n * 3 * sizeof(double);
         char *stage = reinterpret_cast<char *>(s->psort.cell[0]);
         const size_t room = (size_t)(reinterpret_cast<char *>(s->psort.id + s->cfg.max_particles) - stage);
         if (2 * bytes + 16 > room) return fail(PIC_ERR_OOM, "particle staging area too small");
-        double *d_xyz = reinterpret_cast<double *>(stage);
-        double *d_u = reinterpret_cast<double *>(stage + (bytes + 15) / 16 * 16);
+        const double *d_xyz = reinterpret_cast<double *>(stage);
+        const double *d_u = reinterpret_cast<double *>(stage + (bytes + 15) / 16 * 16);
         unsigned long long *d_cnt = reinterpret_cast<unsigned long long *>(s->d_keyset);  // scratch after create
         CUDA_TRY(cudaMemsetAsync(d_cnt, 0, 2 * sizeof(unsigned long long), s->stream));
-        CUDA_TRY(cudaMemcpyAsync(d_xyz, xyz, bytes, cudaMemcpyHostToDevice, s->stream));
-        CUDA_TRY(cudaMemcpyAsync(d_u, u, bytes, cudaMemcpyHostToDevice, s->stream));
+        if (s->host_direct) {  // the kernel reads the caller's arrays where they are (synchronised below)
+            d_xyz = xyz;
+            d_u = u;
+        } else {
+            CUDA_TRY(cudaMemcpyAsync(const_cast<double *>(d_xyz), xyz, bytes, cudaMemcpyHostToDevice, s->stream));
+            CUDA_TRY(cudaMemcpyAsync(const_cast<double *>(d_u), u, bytes, cudaMemcpyHostToDevice, s->stream));
+        }
         ParticleIn in{};
         for (int a = 0; a < 3; a++) {
             in.d[a] = s->d[a];

@@ -130,7 +130,31 @@ __global__ void __launch_bounds__(256) k_edge_classes(const uint8_t *mat, int nx
     }
 }
 
+// n bytes from src (any memory the device can read: on a device with
+// coherent access to pageable host memory, the caller's host array) to dst.
+__global__ void __launch_bounds__(256) k_copy_bytes(const unsigned char *src, unsigned char *dst, long long n) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if ((((uintptr_t)src | (uintptr_t)dst) & 15) == 0) {
+        const long long n16 = n / 16;
+        for (long long q = t; q < n16; q += stride)
+            reinterpret_cast<uint4 *>(dst)[q] = reinterpret_cast<const uint4 *>(src)[q];
+        for (long long q = n16 * 16 + t; q < n; q += stride) dst[q] = src[q];
+    } else {
+        for (long long q = t; q < n; q += stride) dst[q] = src[q];
+    }
+}
+
 }  // namespace
+
+void launch_copy_bytes(const void *src, void *dst, long long n, cudaStream_t s) {
+    if (n <= 0) return;
+    long long nblk = (n / 16 + 255) / 256;
+    if (nblk > 8 * 152) nblk = 8 * 152;
+    if (nblk < 1) nblk = 1;
+    k_copy_bytes<<<(unsigned)nblk, 256, 0, s>>>(static_cast<const unsigned char *>(src),
+                                                static_cast<unsigned char *>(dst), n);
+}
 
 void launch_edge_keys(const uint8_t *mat, const int n[3], const int per[3], int n_materials, unsigned long long *gset,
                       int gcap, int *flags, cudaStream_t s) {

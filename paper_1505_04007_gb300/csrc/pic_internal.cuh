@@ -258,6 +258,9 @@ void launch_fused_joint(const FusedJoint &jt, cudaStream_t s, const cudaStream_t
 void launch_jf_clear(const Grid<float> &g, const JfSet &j, int max_tiles, cudaStream_t s);
 void launch_jf_fix(const Grid<float> &g, const FixArgs &f, int max_tiles, cudaStream_t s);
 
+// Copy n bytes on the device from src (device memory, or host memory on a
+// device that reads pageable host memory coherently) to dst (materials.cu).
+void launch_copy_bytes(const void *src, void *dst, long long n, cudaStream_t s);
 // Edge classes on the device (materials.cu).  launch_edge_keys adds every
 // distinct sorted 4-cell key of the grid to gset (gcap slots of ~0: empty)
 // and sets flags bit 0 when a set overflows, bit 1 when a material id is not
