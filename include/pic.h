@@ -104,6 +104,14 @@ typedef struct {
  * memory); the results are those of the split updates up to rounding order. */
 #define PIC_FLAG_SPLIT_FIELDS 1
 
+/* pic_config.flags: copy the caller's host arrays (the material map here,
+ * positions and momenta in pic_add_particles) through the CUDA runtime.
+ * Without it, on a device that reads pageable host memory coherently
+ * (cudaDevAttrPageableMemoryAccess, e.g. a Grace system) kernels read them
+ * where they are, before the call returns; elsewhere they are copied either
+ * way.  The results are the same. */
+#define PIC_FLAG_STAGED_UPLOAD 2
+
 typedef struct {
     int64_t step;          /* completed time steps */
     int64_t n_particles;   /* particles added */

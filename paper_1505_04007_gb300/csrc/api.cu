@@ -80,7 +80,8 @@ static bool has_cpml(const pic_config *c, int a) {
 
 static int validate(const pic_config *c) {
     if (!c) return fail(PIC_ERR_ARG, "config is NULL");
-    if (c->flags & ~(uint64_t)PIC_FLAG_SPLIT_FIELDS) return fail(PIC_ERR_ARG, "unknown flags 0x%llx", (unsigned long long)c->flags);
+    if (c->flags & ~(uint64_t)(PIC_FLAG_SPLIT_FIELDS | PIC_FLAG_STAGED_UPLOAD))
+        return fail(PIC_ERR_ARG, "unknown flags 0x%llx", (unsigned long long)c->flags);
     if (c->precision != PIC_FP32 && c->precision != PIC_FP64) return fail(PIC_ERR_ARG, "unknown precision");
     const int64_t n[3] = {c->nx, c->ny, c->nz};
     const double d[3] = {c->dx, c->dy, c->dz};
@@ -491,7 +492,7 @@ struct Sim : SimBase {
         {
             int pma = 0;
             CUDA_TRY(cudaDeviceGetAttribute(&pma, cudaDevAttrPageableMemoryAccess, device));
-            host_direct = pma == 1;
+            host_direct = pma == 1 && !(c->flags & PIC_FLAG_STAGED_UPLOAD);
         }
         if (host_direct) {  // read where it is; done before any later return
             launch_copy_bytes(c->material_id, d_mat, N, stream);

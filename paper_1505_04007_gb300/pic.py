@@ -22,6 +22,7 @@ from . import build as _build
 PIC_OK = 0
 PIC_FP32, PIC_FP64 = 0, 1
 PIC_FLAG_SPLIT_FIELDS = 1  # keep separate H and E updates where the fused pass would run
+PIC_FLAG_STAGED_UPLOAD = 2  # copy host arrays through the runtime rather than read them with kernels
 PIC_EX, PIC_EY, PIC_EZ, PIC_HX, PIC_HY, PIC_HZ, PIC_JPX, PIC_JPY, PIC_JPZ, PIC_JFX, PIC_JFY, PIC_JFZ = range(12)
 
 ERRORS = {-1: "PIC_ERR_ARG", -2: "PIC_ERR_CFL", -3: "PIC_ERR_OOM", -4: "PIC_ERR_CUDA", -5: "PIC_ERR_NONFINITE",

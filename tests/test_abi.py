@@ -77,7 +77,7 @@ def test_workspace_size_is_host_only_and_scales():
     (lambda c: c.bc.__setitem__(0, W.BC_PERIODIC), -1),                   # unpaired periodic
     (lambda c: setattr(c, "cpml_cells", 40), -1),                         # slabs do not fit
     (lambda c: setattr(c, "precision", 7), -1),
-    (lambda c: setattr(c, "flags", 2), -1),  # an unknown flag bit
+    (lambda c: setattr(c, "flags", 4), -1),  # an unknown flag bit
     (lambda c: setattr(c, "n_materials", 0), -1),
 ])
 def test_create_rejects_invalid_config_on_host(mutate, code):

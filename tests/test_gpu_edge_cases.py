@@ -219,3 +219,30 @@ def test_create_builds_edge_classes_on_the_device(P):
     with pytest.raises(P.PicError) as e:
         P.Simulation(wm, P.PIC_FP32, particles=False, probes=False)
     assert e.value.code == -7
+
+
+def test_staged_upload_matches_direct_reads(P):
+    """The material map and the particle arrays are read by kernels where
+    they are (a device with coherent access to pageable host memory) or
+    copied through the runtime (PIC_FLAG_STAGED_UPLOAD): the same state."""
+    w = W.scaled(W.c1(), 64, 24, 40, 1024, 0)
+    a = P.Simulation(w, P.PIC_FP32, probes=False)
+    b = P.Simulation(w, P.PIC_FP32, probes=False, flags=P.PIC_FLAG_STAGED_UPLOAD)
+    for x, y in zip(a.particles(), b.particles()):
+        assert np.array_equal(x, y)
+    assert a.stats().n_edge_classes == b.stats().n_edge_classes
+    a.close()
+    b.close()
+    # fields only, a film and a prescribed source: no atomic sums, bit for bit
+    mat = np.zeros((30, 24, 40), np.uint8)
+    mat[8:13] = 1
+    wf = box_workload(40, 24, 30, bc=(W.BC_CPML,) * 6, material=mat, table=W.drude_table())
+    sims = [P.Simulation(wf, P.PIC_FP32, particles=False, probes=False, flags=fl)
+            for fl in (0, P.PIC_FLAG_STAGED_UPLOAD)]
+    for s in sims:
+        P.pic_add_source(s.h, 2, (20, 21, 12, 13, 16, 17), 1e18, 30 * wf.dt, 8 * wf.dt, 0.0)
+        s.step(64)
+    for c in range(9):
+        assert np.array_equal(sims[0].field(c), sims[1].field(c)), c
+    for s in sims:
+        s.close()
