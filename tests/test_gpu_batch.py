@@ -171,3 +171,23 @@ def test_joint_pass_instances_at_odd_and_even_steps(P):
         assert f <= 2e-5, (w.name, f)
         assert s.stats().device_error == 0
     b.close()
+
+
+def test_joint_pass_mixed_slabs_and_faces(P):
+    """Instances with 8-cell and 4-cell absorbing layers and one with
+    conducting x faces share the joint pass (each item reads its own
+    instance's layer thickness and tile kinds); each matches the oracle."""
+    ws = W.sweep(n=3, seed=19, nsteps=128, **SMALL)
+    ws[1].cpml_cells = 4
+    ws[2].bc = (W.BC_PEC, W.BC_PEC) + tuple(ws[2].bc[2:])
+    sims = [P.Simulation(w, P.PIC_FP32) for w in ws]
+    assert [s.stats().field_path for s in sims] == [1, 1, 1]
+    b = P.Batch(sims)
+    b.step(128)
+    b.sync()
+    for w, s in zip(ws, sims):
+        o = O.from_workload(w)
+        o.step(128)
+        check(o, s, 2e-5)
+        assert s.stats().device_error == 0
+    b.close()
