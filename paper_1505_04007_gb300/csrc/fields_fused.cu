@@ -38,6 +38,14 @@
 // A joint pass (k_fused_joint) runs the items of several simulations in one
 // launch per kind, with each instance's arguments and maps from a table.
 //
+// What is not staged by tensor copies: per-plane and per-column/row tables
+// (material factor, z-slab index and profiles, x- and y-slab profiles, the
+// class table) go to shared memory once per item; the per-cell operands of
+// material planes (edge classes, Drude current) and of z-slab planes (CPML
+// memory) are loaded from global memory at the top of the plane's iteration,
+// the halo cell's too (a load chained behind a class lookup stalled whole
+// warps), and are brought into L2 two planes ahead (prefetch.global.L2).
+//
 // Free current: Eq. 8's J_f term is left out of the pass (the pass does not
 // wait for the push, and in a batch runs beside it).  k_jf_fix adds it
 // afterwards on the tiles the deposit wrote: dE = -dt/(eps0 eps_inf) J_f on
@@ -89,6 +97,9 @@ struct __align__(128) Smem {
     float4 cls[K ? 1 : 256];    // per edge class: kJ-1, bJ, cE, metal (the slab kinds read it from global)
     float pcE[MAX_CHUNK + 2];   // per plane of the item
     int pzs[MAX_CHUNK + 2];
+    float pzp[6][MAX_CHUNK + 2];  // ... its z-slab profiles (b-1, a, 1/kappa of E, then of H; 0 outside)
+    alignas(16) float prx[XS ? 6 : 1][XS ? XW : 4];  // x-slab profiles of columns x0..x0+TX+3 (same order)
+    float pry[YS ? 6 : 1][YS ? EH : 1];              // y-slab profiles of rows y0..y0+TY
     unsigned long long bar[STAGES];
     int abort_flag;
     alignas(16) typename std::conditional<J, FusedArgs, int>::type args;  // a joint pass: the item's instance (copied in 16-byte pieces)
@@ -145,6 +156,11 @@ __device__ __forceinline__ void tma_load(void *dst, const CUtensorMap *m, int x,
         " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
         "l"((unsigned long long)m), "r"(x), "r"(y), "r"(z), "r"(0), "r"(smem_u32(b))
         : "memory");
+}
+
+// Bring the line holding p into L2 (no register is held for it).
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"((unsigned long long)__cvta_generic_to_global(p)));
 }
 
 __device__ __forceinline__ int slab_of(const Grid<float> &g, int a, int x) {
@@ -225,26 +241,6 @@ __device__ __forceinline__ void fused_item(const FusedArgs &a, const CUtensorMap
     const int pxc = EH * L, pyc = pyh * EW;                   // component strides of the copies
     const int pxo = lj * L + (sx - xs0), pyo = (syb - ys0) * EW + li;
 
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; s++) mbar_init(&S.bar[s], 1);
-        S.abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    // per plane: the Ampere factor of its one non-metal material (-1: per-edge
-    // classes) and its z-slab index (-1: none); the class table
-    for (int q = threadIdx.x; q < np; q += NT) {
-        const int z = p0 + q;
-        S.pcE[q] = (z >= 0 && z < nz) ? a.plane_cE[z] : 0.f;
-        S.pzs[q] = (z >= 0 && z < nz) ? slab_of(g, 2, z) : -1;
-    }
-    if constexpr (K == 0)
-        for (int q = threadIdx.x; q < 256; q += NT) S.cls[q] = a.cls_pack[q];
-    __syncthreads();
-    auto cls_at = [&](unsigned k) -> float4 {
-        if constexpr (K == 0) return S.cls[k];
-        else return __ldg(a.cls_pack + k);
-    };
     // bytes one stage receives: the E and H boxes, and per staged slab two
     // copies (psi_E, psi_H) of two components each
     const unsigned xbox = 2u * EH * (unsigned)L * 4u, ybox = 2u * (unsigned)pyh * EW * 4u;
@@ -265,8 +261,81 @@ __device__ __forceinline__ void fused_item(const FusedArgs &a, const CUtensorMap
             tma_load(S.phy[slot], &tm[5], x0, ys0, z - 1, &S.bar[slot]);
         }
     };
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; s++) mbar_init(&S.bar[s], 1);
+        S.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        // the first planes are on their way while the tables below load
         for (int q = 0; q < STAGES && q < np; q++) issue(q, q);
+    }
+    // Tables of the item in shared memory: per plane the Ampere factor of its
+    // one non-metal material (-1: per-edge classes), its z-slab index (-1:
+    // none) and z-slab profiles; the class table; the x- and y-slab profiles
+    // of the tile.  Every value is loaded before any is stored (a store to
+    // shared memory could otherwise order the loads of a joint pass's
+    // arguments, which live there too, one after another).
+    static_assert(MAX_CHUNK + 2 <= NT && 6 * XW <= 2 * NT && 6 * EH <= NT, "one or two table entries per thread");
+    {
+        const int t = threadIdx.x;
+        const int z = p0 + t;
+        const bool pl = t < np && z >= 0 && z < nz;
+        const int sz2 = pl ? slab_of(g, 2, z) : -1;
+        const bool zs = sz2 >= 0;
+        const float cE = pl ? a.plane_cE[z] : 0.f;
+        float pz[6];
+        pz[0] = zs ? a.bE[2][z] : 0.f;
+        pz[1] = zs ? a.aE[2][z] : 0.f;
+        pz[2] = zs ? a.ikE[2][z] : 0.f;
+        pz[3] = zs ? a.bH[2][z] : 0.f;
+        pz[4] = zs ? a.aH[2][z] : 0.f;
+        pz[5] = zs ? a.ikH[2][z] : 0.f;
+        float4 c0 = {}, c1 = {};
+        if constexpr (K == 0) {
+            c0 = a.cls_pack[t];
+            c1 = a.cls_pack[t + NT];
+        }
+        // profile r of axis ax at i: b-1, a, 1/kappa of E, then of H
+        auto prof = [&](int ax, int r, int i) -> float {
+            switch (r) {
+                case 0: return a.bE[ax][i];
+                case 1: return a.aE[ax][i];
+                case 2: return a.ikE[ax][i];
+                case 3: return a.bH[ax][i];
+                case 4: return a.aH[ax][i];
+                default: return a.ikH[ax][i];
+            }
+        };
+        float px0 = 0.f, px1 = 0.f, py = 0.f;
+        const int u1 = t + NT;
+        if constexpr (XS) {
+            if (x0 + t % XW < nx) px0 = prof(0, t / XW, x0 + t % XW);
+            if (u1 < 6 * XW && x0 + u1 % XW < nx) px1 = prof(0, u1 / XW, x0 + u1 % XW);
+        }
+        if constexpr (YS)
+            if (t < 6 * EH && y0 + t % EH < ny) py = prof(1, t / EH, y0 + t % EH);
+        if (t < np) {
+            S.pcE[t] = cE;
+            S.pzs[t] = sz2;
+#pragma unroll
+            for (int r = 0; r < 6; r++) S.pzp[r][t] = pz[r];
+        }
+        if constexpr (K == 0) {
+            S.cls[t] = c0;
+            S.cls[t + NT] = c1;
+        }
+        if constexpr (XS) {
+            S.prx[t / XW][t % XW] = px0;
+            if (u1 < 6 * XW) S.prx[u1 / XW][u1 % XW] = px1;
+        }
+        if constexpr (YS)
+            if (t < 6 * EH) S.pry[t / EH][t % EH] = py;
+    }
+    __syncthreads();
+    auto cls_at = [&](unsigned k) -> float4 {
+        if constexpr (K == 0) return S.cls[k];
+        else return __ldg(a.cls_pack + k);
+    };
 
     constexpr int HC = HH * HW, EC = EH * EW, NC = EH * XW;  // component strides in the boxes
     const int eo = lj * EW + li;               // this group in the E box
@@ -319,6 +388,49 @@ __device__ __forceinline__ void fused_item(const FusedArgs &a, const CUtensorMap
                 j0[c] = ld4(a.Jpi[c] + cz);
             }
         }
+        // the halo cell's classes and Drude current (Ey, Ez) and z-slab memory
+        // (Ey's d/dz Hx)
+        unsigned char clh[2] = {0, 0};
+        float jh[2] = {0.f, 0.f}, pzh = 0.f;
+        if (doEh && mat) {
+            const unsigned czh = cz + (unsigned)(gih - gi);
+            clh[0] = a.ecls[1][czh];
+            clh[1] = a.ecls[2][czh];
+            jh[0] = a.Jpi[1][czh];
+            jh[1] = a.Jpi[2][czh];
+        }
+        if (doEh && szb >= 0) pzh = a.psiEi[2][1][(unsigned)szb * sz + cxy + (unsigned)(gih - gi)];
+        // ---- the same global operands of plane z+2 (E) and z+1 (H) into L2, so
+        // that their loads two iterations on do not wait on DRAM: a material or
+        // z-slab plane is otherwise several times slower than a vacuum one
+        if (q + 2 < np && z + 2 < nz) {
+            const unsigned c2 = cz + 2 * sz;
+            if (S.pcE[q + 2] < 0.f) {
+                if (inside) {
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        prefetch_l2(a.Jpi[c] + c2);
+                        prefetch_l2(a.ecls[c] + c2);
+                    }
+                }
+                if (inh) {
+                    const unsigned c2h = c2 + (unsigned)(gih - gi);
+                    prefetch_l2(a.Jpi[1] + c2h);
+                    prefetch_l2(a.Jpi[2] + c2h);
+                    prefetch_l2(a.ecls[1] + c2h);
+                    prefetch_l2(a.ecls[2] + c2h);
+                }
+            }
+            const int s2 = S.pzs[q + 2], s2h = S.pzs[q + 1];
+            if (inside && s2 >= 0) {
+                prefetch_l2(a.psiEi[2][0] + (unsigned)s2 * sz + cxy);
+                prefetch_l2(a.psiEi[2][1] + (unsigned)s2 * sz + cxy);
+            }
+            if (owner && inside && s2h >= 0) {
+                prefetch_l2(a.psiHi[2][0] + (unsigned)s2h * sz + cxy);
+                prefetch_l2(a.psiHi[2][1] + (unsigned)s2h * sz + cxy);
+            }
+        }
         if (!mbar_wait(&S.bar[s], (q / STAGES) & 1)) ok = false;
         if constexpr (SLAB) {
             // every thread is done with iteration q-1: its E^{n+1} plane and
@@ -360,7 +472,7 @@ __device__ __forceinline__ void fused_item(const FusedArgs &a, const CUtensorMap
                 uz[m] = !(f0 || fy);
             }
             if (XS && sx >= 0) {  // x slab: Ey's d/dx Hz, Ez's d/dx Hy (profiles per cell)
-                const V4 bm = ld4(a.bE[0] + gi), aa = ld4(a.aE[0] + gi), ik = ld4(a.ikE[0] + gi);
+                const V4 bm = ld4(&S.prx[0][li]), aa = ld4(&S.prx[1][li]), ik = ld4(&S.prx[2][li]);
                 float d3[4], d4[4];
 #pragma unroll
                 for (int m = 0; m < 4; m++) { d3[m] = t[3][m]; d4[m] = t[4][m]; }
@@ -368,7 +480,7 @@ __device__ __forceinline__ void fused_item(const FusedArgs &a, const CUtensorMap
                 cterm4(t[4], ld4(S.pex[s] + pxc + pxo), a.psiEo[0][1], qEx, bm, aa, ik, d4, uz, wr);
             }
             if (YS && syb >= 0) {  // y slab: Ez's d/dy Hx, Ex's d/dy Hz
-                const V4 bm = splat(a.bE[1][gj]), aa = splat(a.aE[1][gj]), ik = splat(a.ikE[1][gj]);
+                const V4 bm = splat(S.pry[0][lj]), aa = splat(S.pry[1][lj]), ik = splat(S.pry[2][lj]);
                 float d5[4], d0[4];
 #pragma unroll
                 for (int m = 0; m < 4; m++) { d5[m] = t[5][m]; d0[m] = t[0][m]; }
@@ -376,7 +488,7 @@ __device__ __forceinline__ void fused_item(const FusedArgs &a, const CUtensorMap
                 cterm4(t[0], ld4(S.pey[s] + pyc + pyo), a.psiEo[1][1], qEy, bm, aa, ik, d0, ux, wr);
             }
             if (szb >= 0) {  // z slab: Ex's d/dz Hy, Ey's d/dz Hx
-                const V4 bm = splat(a.bE[2][z]), aa = splat(a.aE[2][z]), ik = splat(a.ikE[2][z]);
+                const V4 bm = splat(S.pzp[0][q]), aa = splat(S.pzp[1][q]), ik = splat(S.pzp[2][q]);
                 float d1[4], d2[4];
 #pragma unroll
                 for (int m = 0; m < 4; m++) { d1[m] = t[1][m]; d2[m] = t[2][m]; }
@@ -418,7 +530,6 @@ __device__ __forceinline__ void fused_item(const FusedArgs &a, const CUtensorMap
         }
         if (doEh) {
             // ---- Ey, Ez of the halo cell x0+TX (one cell, the same updates)
-            const unsigned czh = (unsigned)z * sz + (unsigned)gj * (unsigned)nx + (unsigned)gih;
             const float hzh = h[2 * HC + hoh], hyh = h[HC + hoh], hxh = h[hoh];
             const float hx_jmh = h[hoh - HW];
             float dHx_dz = (hxh - hbh_x) * rz, dHz_dx = (hzh - hc[2].v[3]) * rx;
@@ -427,35 +538,33 @@ __device__ __forceinline__ void fused_item(const FusedArgs &a, const CUtensorMap
             const bool uyh = z != 0, uzh = !fy;
             if (XS && sxh >= 0) {
                 const int ox = lj * L + (sxh - xs0);
-                const float bm = a.bE[0][gih], aa = a.aE[0][gih], ik = a.ikE[0][gih];
+                const float bm = S.prx[0][TX], aa = S.prx[1][TX], ik = S.prx[2][TX];
                 if (uyh) { const float p = S.pex[s][ox]; ty2 = ik * dHz_dx + (p + (bm * p + aa * dHz_dx)); }
                 if (uzh) { const float p = S.pex[s][pxc + ox]; tz1 = ik * dHy_dx + (p + (bm * p + aa * dHy_dx)); }
             }
             if (YS && syb >= 0 && uzh) {
-                const float bm = a.bE[1][gj], aa = a.aE[1][gj], ik = a.ikE[1][gj];
+                const float bm = S.pry[0][lj], aa = S.pry[1][lj], ik = S.pry[2][lj];
                 const float p = S.pey[s][pyo - li + TX];
                 tz2 = ik * dHx_dy + (p + (bm * p + aa * dHx_dy));
             }
             if (szb >= 0 && uyh) {
-                const unsigned qq = (unsigned)szb * sz + (unsigned)gj * (unsigned)nx + (unsigned)gih;
-                const float bm = a.bE[2][z], aa = a.aE[2][z], ik = a.ikE[2][z];
-                const float p = a.psiEi[2][1][qq];
-                ty1 = ik * dHx_dz + (p + (bm * p + aa * dHx_dz));
+                const float bm = S.pzp[0][q], aa = S.pzp[1][q], ik = S.pzp[2][q];
+                ty1 = ik * dHx_dz + (pzh + (bm * pzh + aa * dHx_dz));
             }
             float eyh = e[EC + lj * EW + TX], ezh = e[2 * EC + lj * EW + TX];
             if (!mat) {
                 if (uyh) eyh += cEu * (ty1 - ty2);
                 if (uzh) ezh += cEu * (tz1 - tz2);
             } else {
-                const float4 ty = cls_at(a.ecls[1][czh]), tz = cls_at(a.ecls[2][czh]);
+                const float4 ty = cls_at(clh[0]), tz = cls_at(clh[1]);
                 if (uyh) {
                     float jp = 0.f;
-                    if (ty.w != 0.f) { const float jj = a.Jpi[1][czh]; jp = jj + (ty.x * jj + ty.y * eyh); }
+                    if (ty.w != 0.f) jp = jh[0] + (ty.x * jh[0] + ty.y * eyh);
                     eyh += ty.z * ((ty1 - ty2) - jp);
                 }
                 if (uzh) {
                     float jp = 0.f;
-                    if (tz.w != 0.f) { const float jj = a.Jpi[2][czh]; jp = jj + (tz.x * jj + tz.y * ezh); }
+                    if (tz.w != 0.f) jp = jh[1] + (tz.x * jh[1] + tz.y * ezh);
                     ezh += tz.z * ((tz1 - tz2) - jp);
                 }
             }
@@ -499,7 +608,7 @@ __device__ __forceinline__ void fused_item(const FusedArgs &a, const CUtensorMap
             }
             const bool all[4] = {true, true, true, true};
             if (XS && sx >= 0) {  // x slab: Hy's d/dx Ez, Hz's d/dx Ey
-                const V4 bm = ld4(a.bH[0] + gi), aa = ld4(a.aH[0] + gi), ik = ld4(a.ikH[0] + gi);
+                const V4 bm = ld4(&S.prx[3][li]), aa = ld4(&S.prx[4][li]), ik = ld4(&S.prx[5][li]);
                 float d3[4], d4[4];
 #pragma unroll
                 for (int m = 0; m < 4; m++) { d3[m] = t[3][m]; d4[m] = t[4][m]; }
@@ -507,7 +616,7 @@ __device__ __forceinline__ void fused_item(const FusedArgs &a, const CUtensorMap
                 cterm4(t[4], ld4(S.phx[s] + pxc + pxo), a.psiHo[0][1], qHx, bm, aa, ik, d4, all, true);
             }
             if (YS && syb >= 0) {  // y slab: Hz's d/dy Ex, Hx's d/dy Ez
-                const V4 bm = splat(a.bH[1][gj]), aa = splat(a.aH[1][gj]), ik = splat(a.ikH[1][gj]);
+                const V4 bm = splat(S.pry[3][lj]), aa = splat(S.pry[4][lj]), ik = splat(S.pry[5][lj]);
                 float d5[4], d0[4];
 #pragma unroll
                 for (int m = 0; m < 4; m++) { d5[m] = t[5][m]; d0[m] = t[0][m]; }
@@ -515,7 +624,7 @@ __device__ __forceinline__ void fused_item(const FusedArgs &a, const CUtensorMap
                 cterm4(t[0], ld4(S.phy[s] + pyc + pyo), a.psiHo[1][1], qHy, bm, aa, ik, d0, all, true);
             }
             if (szh >= 0) {  // z slab: Hx's d/dz Ey, Hy's d/dz Ex
-                const V4 bm = splat(a.bH[2][kh]), aa = splat(a.aH[2][kh]), ik = splat(a.ikH[2][kh]);
+                const V4 bm = splat(S.pzp[3][q - 1]), aa = splat(S.pzp[4][q - 1]), ik = splat(S.pzp[5][q - 1]);
                 float d1[4], d2[4];
 #pragma unroll
                 for (int m = 0; m < 4; m++) { d1[m] = t[1][m]; d2[m] = t[2][m]; }
