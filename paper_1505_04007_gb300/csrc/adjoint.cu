@@ -1278,6 +1278,7 @@ struct pic_adj {
 extern "C" {
 
 int pic_adj_create(const pic_adj_config *c, pic_adj **out) {
+    pic::NvtxRange nvtx_range("pic_adj_create");
     using namespace pic;
     set_last_error(PIC_OK, "%s", "");
     if (!out) return set_last_error(PIC_ERR_ARG, "out is NULL");
@@ -1333,18 +1334,21 @@ int pic_adj_mask_size(const pic_adj *a, int64_t *n) {
 }
 
 int pic_adj_forward(pic_adj *a, const double *mask, double wp, double gamma, double *loss) {
+    pic::NvtxRange nvtx_range("pic_adj_forward");
     pic::set_last_error(PIC_OK, "%s", "");
     if (!a) return pic::set_last_error(PIC_ERR_ARG, "NULL handle");
     return a->sim->forward(mask, wp, gamma, loss);
 }
 
 int pic_adj_backward(pic_adj *a, double *dmask, double *dwp, double *dgamma) {
+    pic::NvtxRange nvtx_range("pic_adj_backward");
     pic::set_last_error(PIC_OK, "%s", "");
     if (!a) return pic::set_last_error(PIC_ERR_ARG, "NULL handle");
     return a->sim->backward(dmask, dwp, dgamma);
 }
 
 int pic_adj_destroy(pic_adj *a) {
+    pic::NvtxRange nvtx_range("pic_adj_destroy");
     pic::set_last_error(PIC_OK, "%s", "");
     if (!a) return PIC_OK;
     delete a->sim;

@@ -2,9 +2,11 @@
 //
 // A handle owns one simulation instance on one device: a single arena of
 // device memory (caller workspace or one cudaMalloc), the per-edge material
-// classes and CPML profiles built on the host at create time, the particle
-// and probe buffers, and a captured CUDA graph that replays DFT_BLOCK steps
-// plus one probe-DFT flush.
+// classes (built on the device from the material map at create time) and
+// CPML profiles, the particle and probe buffers, and a captured CUDA graph
+// that replays DFT_BLOCK steps plus one probe-DFT flush.  Every entry point
+// opens an NVTX range named after it, so that a timeline profiler shows the
+// host side of each call beside the kernels it launched.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -1827,6 +1829,7 @@ int pic_workspace_size(const pic_config *cfg, size_t *bytes) {
 }
 
 int pic_create(const pic_config *cfg, pic_handle **out) {
+    NvtxRange nvtx_range("pic_create");
     g_err.clear();
     if (!out) return fail(PIC_ERR_ARG, "out is NULL");
     *out = nullptr;
@@ -1855,6 +1858,7 @@ int pic_create(const pic_config *cfg, pic_handle **out) {
 }
 
 int pic_destroy(pic_handle *h) {
+    NvtxRange nvtx_range("pic_destroy");
     g_err.clear();
     if (!h) return PIC_OK;
     delete h->sim;
@@ -1882,6 +1886,7 @@ int pic_set_stream(pic_handle *h, void *stream) {
 
 int pic_add_particles(pic_handle *h, int64_t n, const double *xyz, const double *u, double q_macro,
                       double m_macro, int64_t *n_rejected) {
+    NvtxRange nvtx_range("pic_add_particles");
     g_err.clear();
     if (!h) return fail(PIC_ERR_ARG, "NULL handle");
     return h->precision == PIC_FP64 ? add_particles_t(S<double>(h), n, xyz, u, q_macro, m_macro, n_rejected)
@@ -1889,6 +1894,7 @@ int pic_add_particles(pic_handle *h, int64_t n, const double *xyz, const double 
 }
 
 int pic_get_particles(pic_handle *h, double *xyz, double *u, uint8_t *status) {
+    NvtxRange nvtx_range("pic_get_particles");
     g_err.clear();
     if (!h) return fail(PIC_ERR_ARG, "NULL handle");
     return h->precision == PIC_FP64 ? get_particles_t(S<double>(h), xyz, u, status)
@@ -1926,6 +1932,7 @@ int pic_add_source(pic_handle *h, int comp, const int64_t *box, double amp, doub
 }
 
 int pic_probe_dft(pic_handle *h, int np, const double *xyz, uint32_t comp_mask, int nf, const double *freq_hz) {
+    NvtxRange nvtx_range("pic_probe_dft");
     g_err.clear();
     if (!h) return fail(PIC_ERR_ARG, "NULL handle");
     return h->precision == PIC_FP64 ? probe_dft_t(S<double>(h), np, xyz, comp_mask, nf, freq_hz)
@@ -1933,24 +1940,28 @@ int pic_probe_dft(pic_handle *h, int np, const double *xyz, uint32_t comp_mask, 
 }
 
 int pic_step(pic_handle *h, int64_t nsteps) {
+    NvtxRange nvtx_range("pic_step");
     g_err.clear();
     if (!h) return fail(PIC_ERR_ARG, "NULL handle");
     return DISPATCH(h, step(nsteps));
 }
 
 int pic_sync(pic_handle *h) {
+    NvtxRange nvtx_range("pic_sync");
     g_err.clear();
     if (!h) return fail(PIC_ERR_ARG, "NULL handle");
     return DISPATCH(h, check());
 }
 
 int pic_probe_read(pic_handle *h, double *out) {
+    NvtxRange nvtx_range("pic_probe_read");
     g_err.clear();
     if (!h || !out) return fail(PIC_ERR_ARG, "NULL argument");
     return h->precision == PIC_FP64 ? probe_read_t(S<double>(h), out) : probe_read_t(S<float>(h), out);
 }
 
 int pic_probe_kw(pic_handle *h, int comp, int axis, int nk, const double *k, double *out) {
+    NvtxRange nvtx_range("pic_probe_kw");
     g_err.clear();
     if (!h) return fail(PIC_ERR_ARG, "NULL handle");
     return h->precision == PIC_FP64 ? probe_kw_t(S<double>(h), comp, axis, nk, k, out)
@@ -1958,12 +1969,14 @@ int pic_probe_kw(pic_handle *h, int comp, int axis, int nk, const double *k, dou
 }
 
 int pic_get_field(pic_handle *h, int which, double *out) {
+    NvtxRange nvtx_range("pic_get_field");
     g_err.clear();
     if (!h) return fail(PIC_ERR_ARG, "NULL handle");
     return h->precision == PIC_FP64 ? get_field_t(S<double>(h), which, out) : get_field_t(S<float>(h), which, out);
 }
 
 int pic_set_field(pic_handle *h, int which, const double *in) {
+    NvtxRange nvtx_range("pic_set_field");
     g_err.clear();
     if (!h) return fail(PIC_ERR_ARG, "NULL handle");
     return h->precision == PIC_FP64 ? set_field_t(S<double>(h), which, in) : set_field_t(S<float>(h), which, in);
@@ -1976,18 +1989,21 @@ int pic_get_stats(pic_handle *h, pic_stats *out) {
 }
 
 int pic_save(pic_handle *h, const char *path) {
+    NvtxRange nvtx_range("pic_save");
     g_err.clear();
     if (!h || !path) return fail(PIC_ERR_ARG, "NULL argument");
     return DISPATCH(h, save(path));
 }
 
 int pic_load(pic_handle *h, const char *path) {
+    NvtxRange nvtx_range("pic_load");
     g_err.clear();
     if (!h || !path) return fail(PIC_ERR_ARG, "NULL argument");
     return DISPATCH(h, load(path));
 }
 
 int pic_profile_steps(pic_handle *h, int64_t nsteps, double *out_us) {
+    NvtxRange nvtx_range("pic_profile_steps");
     g_err.clear();
     if (!h || !out_us) return fail(PIC_ERR_ARG, "NULL argument");
     return DISPATCH(h, profile_steps(nsteps, out_us));
@@ -2007,6 +2023,7 @@ int pic_set_tuning(pic_handle *h, const pic_tuning *t) {
 }
 
 int pic_tune(pic_handle *h, int32_t rounds, pic_tune_report *report) {
+    NvtxRange nvtx_range("pic_tune");
     g_err.clear();
     if (!h) return fail(PIC_ERR_ARG, "NULL handle");
     return DISPATCH(h, tune(rounds, report));
@@ -2372,6 +2389,7 @@ struct pic_batch {
 extern "C" {
 
 int pic_batch_create(int n, pic_handle *const *handles, void *stream, pic_batch **out) {
+    NvtxRange nvtx_range("pic_batch_create");
     g_err.clear();
     if (!out) return fail(PIC_ERR_ARG, "out is NULL");
     *out = nullptr;
@@ -2403,6 +2421,7 @@ int pic_batch_create(int n, pic_handle *const *handles, void *stream, pic_batch 
 }
 
 int pic_batch_step(pic_batch *b, int64_t nsteps) {
+    NvtxRange nvtx_range("pic_batch_step");
     g_err.clear();
     if (!b) return fail(PIC_ERR_ARG, "NULL batch");
     if (nsteps < 0) return fail(PIC_ERR_ARG, "negative step count");
@@ -2432,6 +2451,7 @@ int pic_batch_set_joint(pic_batch *b, int32_t joint) {
 }
 
 int pic_batch_tune(pic_batch *b, int32_t rounds, pic_tune_report *report) {
+    NvtxRange nvtx_range("pic_batch_tune");
     g_err.clear();
     if (!b) return fail(PIC_ERR_ARG, "NULL batch");
     const int rc = b->tune(rounds, report);
@@ -2440,6 +2460,7 @@ int pic_batch_tune(pic_batch *b, int32_t rounds, pic_tune_report *report) {
 }
 
 int pic_batch_sync(pic_batch *b) {
+    NvtxRange nvtx_range("pic_batch_sync");
     g_err.clear();
     if (!b) return fail(PIC_ERR_ARG, "NULL batch");
     CUDA_TRY(cudaStreamSynchronize(b->stream));
@@ -2451,6 +2472,7 @@ int pic_batch_sync(pic_batch *b) {
 }
 
 int pic_batch_destroy(pic_batch *b) {
+    NvtxRange nvtx_range("pic_batch_destroy");
     g_err.clear();
     delete b;
     return PIC_OK;

@@ -4,11 +4,21 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <vector>
 
 namespace pic {
+
+// An NVTX range over the rest of the enclosing scope, opened by every entry
+// point of the C ABI (a no-op unless a timeline profiler is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Tiles that carry the "free current was deposited here this step" flag.
 constexpr int TILE_X = 32, TILE_Y = 4, TILE_Z = 4;
