@@ -99,6 +99,37 @@ def test_fused_pass_against_oracle_and_split(P, shape, bc):
     assert s.stats().device_error == 0
 
 
+@pytest.mark.parametrize("shape", [(64, 24, 40), (100, 25, 70)])
+def test_fused_pass_metal_inside_z_slabs(P, shape):
+    """Metal planes inside both z absorbing slabs: planes that hold per-edge
+    classes (Eq. 6) and z-slab CPML memory at once, for the group and its halo
+    cell, against the oracle and the split updates."""
+    nx, ny, nz = shape
+    mat = np.zeros((nz, ny, nx), np.uint8)
+    mat[4:11] = 1
+    mat[nz - 6:nz - 2] = 1
+    w = box_workload(nx, ny, nz, bc=(W.BC_CPML,) * 6, material=mat, table=W.drude_table())
+    o = O.from_workload(w, with_particles=False, with_probes=False)
+    s = P.Simulation(w, P.PIC_FP32, particles=False, probes=False)
+    t = P.Simulation(w, P.PIC_FP32, particles=False, probes=False, flags=P.PIC_FLAG_SPLIT_FIELDS)
+    assert s.stats().field_path == 1
+    for src in sources_for(w):
+        o.add_source(*src)
+        P.pic_add_source(s.h, *src)
+        P.pic_add_source(t.h, *src)
+    o.step(120)
+    s.step(120)
+    t.step(120)
+    ref = fields(o.get_field)
+    got = fields(s.field)
+    assert rel(got, ref) <= 2e-5
+    assert rel(got, fields(t.field)) <= 1e-5
+    for c in range(3):
+        jo, jg = o.get_field(6 + c), s.field(P.PIC_JPX + c)
+        assert np.linalg.norm(jg - jo) <= 2e-5 * max(np.linalg.norm(jo), 1e-300)
+    assert s.stats().device_error == 0
+
+
 @pytest.mark.parametrize("shape", [(36, 30, 40), (64, 21, 40)])
 def test_narrow_grid_takes_the_split_updates(P, shape):
     w = film_box(*shape)
